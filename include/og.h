@@ -1,0 +1,173 @@
+/*
+ * og.h -- C-ABI of the GB300 short-range TreePM tree-force library.
+ *
+ * The library computes the short-range part of the TreePM gravitational
+ * acceleration of the OpenGadget3 paper (arxiv 2609.17658):
+ *   - Sect. 4.1   "Oct-Tree": recursive subdivision of the box into eight
+ *                 sub-cubes, monopole moments (mass, centre of mass);
+ *   - Sect. 4.1.1 "Tree construction": nodes, nextnode/sibling threading,
+ *                 particles inserted in space-filling-curve order (here a
+ *                 63-bit Morton key sorted by an LSD radix sort);
+ *   - Sect. 4.1.2 "Tree walk": Barnes-Hut or relative opening criterion,
+ *                 a boundary check, accepted nodes act as a point mass at
+ *                 their centre of mass;
+ *   - Sect. 4.1.3 "Force evaluation": Newtonian M/r^3 beyond h, the spline
+ *                 softened kernel inside h, h = 2.8 eps (eps Plummer
+ *                 equivalent);
+ *   - Sect. 4.2   "Particle Mesh": the short-range potential
+ *                 phi_s = -G m erfc(r / 2 r_s) / r of the force split;
+ *   - Sect. 3.4 / 19.2: one walk per group of spatially close particles.
+ *
+ * Conventions for every entry point:
+ *   - All calls return og_status.  Errors are negative, never abort the
+ *     process, and leave a thread-local message for og_last_error().
+ *   - The caller owns every input and output buffer.  The library copies what
+ *     it needs; og_ctx and og_tree are opaque handles owned by the library.
+ *   - Pointers are host pointers unless the OG_DEVICE_PTRS flag is set in
+ *     og_params.flags, in which case the position, mass, previous
+ *     acceleration and output pointers are device pointers on the context's
+ *     device.  Host-pointer calls are synchronous; device-pointer calls are
+ *     ordered on the context's stream and return before the work finishes.
+ *   - Positions are AoS double[N][3] in box units; they are reduced to the
+ *     periodic cube [0, box)^3 and stored as 32-bit fixed point per axis.
+ *     Accelerations are float[N][3] in units of G M / L^2 (M mass unit,
+ *     L length unit of the inputs), in the caller's particle order.
+ *   - A context is not thread safe, except og_serve_* which lock internally.
+ */
+#ifndef OG_H
+#define OG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OG_OK = 0,
+    OG_PENDING = 1,          /* og_serve_poll: not finished yet */
+    OG_ERR_ARG = -1,         /* invalid argument (NaN position, N out of range, ...) */
+    OG_ERR_OOM = -2,         /* device or host allocation failed */
+    OG_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    OG_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out */
+    OG_ERR_BUDGET = -5,      /* the request does not fit the HBM budget */
+    OG_ERR_OVERFLOW = -6,    /* a fixed-capacity device buffer overflowed */
+    OG_ERR_STATE = -7        /* call not valid in the handle's state */
+} og_status;
+
+typedef enum {
+    OG_OPEN_BH = 0,          /* Barnes-Hut: open iff l^2 > theta^2 d^2 (Sect. 4.1.2) */
+    OG_OPEN_REL = 1          /* relative: open iff G M l^2 > alpha |a_old|_min d^4 (Sect. 4.1.2) */
+} og_open;
+
+enum {
+    OG_DEVICE_PTRS = 1,      /* input/output pointers are device pointers */
+    OG_DEBUG_DUMP_LISTS = 2  /* keep the interaction lists of the last force call */
+};
+
+typedef struct {
+    double box;              /* L > 0: periodic cube [0, L)^3 */
+    double G;                /* gravitational constant (default 1) */
+    double eps;              /* Plummer-equivalent softening; h = 2.8 eps (Sect. 4.1.3) */
+    double r_s;              /* split scale A_smth (Sect. 4.2); <= 0: no split, no cutoff */
+    double rcut_over_rs;     /* cutoff radius / r_s (default 4.5); r_cut must be < L/2 */
+    double theta;            /* Barnes-Hut opening angle (default 0.5) */
+    double alpha;            /* relative-criterion tolerance (default 0.005) */
+    double theta_first_pass; /* OG_OPEN_REL without a_old: BH angle of the first pass */
+    int32_t opening;         /* og_open */
+    int32_t leaf_max;        /* particles per leaf cell; 1 = one particle per leaf (Sect. 4.1) */
+    int32_t group_max;       /* targets per group, 1..32 (0 = 32) */
+    int32_t flags;           /* OG_DEVICE_PTRS | OG_DEBUG_DUMP_LISTS */
+} og_params;
+
+typedef struct og_ctx og_ctx;
+typedef struct og_tree og_tree;
+
+/* Sizes of a built tree (for og_tree_export). */
+typedef struct {
+    int64_t n;               /* particles */
+    int64_t nodes;           /* octree nodes, root included */
+    int64_t children;        /* entries of the child array */
+    int64_t groups;          /* walk groups */
+    int64_t list_entries;    /* entries kept by the last OG_DEBUG_DUMP_LISTS force call */
+    int64_t interactions;    /* PP + PN entries evaluated by the last force call, all passes */
+    int64_t interactions_last_pass;
+    double  ms_build;        /* device time of the last build (ms) */
+    double  ms_force;        /* device time of the last force call, all passes (ms) */
+    double  ms_walk;         /* device time of the walk kernels of the last force call (ms) */
+} og_tree_info;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device
+ * memory the serving loop may admit (0 = no bound).  Owns a CUDA stream. */
+og_status og_create(og_ctx **ctx, int device, size_t hbm_budget_bytes);
+og_status og_destroy(og_ctx *ctx);
+/* Order all further work of the context on `stream` (a cudaStream_t of the
+ * context's device; NULL restores the context's own stream). */
+og_status og_set_stream(og_ctx *ctx, void *stream);
+/* Fill p with the defaults listed in og_params. */
+og_status og_params_default(og_params *p);
+
+/* ---- one system -------------------------------------------------------- */
+
+/* Build the tree of N particles (Sect. 4.1.1): fixed point, Morton keys,
+ * radix sort, octree topology and threading, moments, groups.
+ * pos: double[N][3], mass: double[N] (finite, >= 0).  1 <= N < 2^26.
+ * Returns OG_ERR_ARG for NaN/inf inputs, bad parameters or r_cut >= L/2. */
+og_status og_tree_build(og_ctx *ctx, const double *pos, const double *mass, int64_t n,
+                        const og_params *p, og_tree **out);
+
+/* Recompute moments for drifted positions of the same N particles with the
+ * topology kept; node extents grow to cover the drifted members. */
+og_status og_tree_refit(og_tree *t, const double *pos);
+
+/* Short-range accelerations (Sect. 4.1.2, 4.1.3, 4.2).
+ * a_old: float[N][3] previous accelerations for OG_OPEN_REL, or NULL (then a
+ *        first Barnes-Hut pass with theta_first_pass supplies them);
+ * acc:   float[N][3] out;  n_pp, n_pn: uint32[N] out or NULL.
+ * n_pp(i) = PP entries of i's group list minus itself, n_pn(i) = PN entries. */
+og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_pp,
+                        uint32_t *n_pn);
+
+og_status og_tree_info_get(const og_tree *t, og_tree_info *info);
+
+/* Copy one internal array of the tree to host memory (test and debug use).
+ * field: one of og_field; bytes must equal the field's size:
+ *   OG_F_SKEY     uint64[n]      sorted Morton keys
+ *   OG_F_PERM     uint32[n]      sorted index -> caller index
+ *   OG_F_SPOS     uint32[3][n]   sorted fixed-point positions (x row, y, z)
+ *   OG_F_LEVEL    uint8[nodes]   node level (0 root .. 21)
+ *   OG_F_NBEG     uint32[nodes]  first sorted particle of the node
+ *   OG_F_NEND     uint32[nodes]  one past the last
+ *   OG_F_PARENT   int32[nodes]   parent node (-1 root)
+ *   OG_F_CBEG     uint32[nodes]  first entry of the node in the child array
+ *   OG_F_CCNT     uint32[nodes]  number of children
+ *   OG_F_CHILD    uint32[children] unified refs: particle < n, node id + n
+ *   OG_F_MASS     double[nodes]  node mass
+ *   OG_F_COM      uint32[nodes][3] centre of mass, fixed point
+ *   OG_F_NEXTNODE int32[nodes]   first child (unified ref)
+ *   OG_F_SIBLING  int32[nodes]   item after the node's subtree (-1 end)
+ *   OG_F_PNEXT    int32[n]       item after a particle (-1 end)
+ *   OG_F_GBEG     uint32[groups] first sorted particle of a group
+ *   OG_F_GEND     uint32[groups] one past the last
+ *   OG_F_GBOX     uint32[groups][6] integer bounding box lo xyz, hi xyz
+ *   OG_F_LISTS    uint32[list_entries][2] (group, unified ref) pairs of the
+ *                 last OG_DEBUG_DUMP_LISTS force call, in no particular order */
+enum {
+    OG_F_SKEY = 0, OG_F_PERM, OG_F_SPOS, OG_F_LEVEL, OG_F_NBEG, OG_F_NEND, OG_F_PARENT,
+    OG_F_CBEG, OG_F_CCNT, OG_F_CHILD, OG_F_MASS, OG_F_COM, OG_F_NEXTNODE, OG_F_SIBLING,
+    OG_F_PNEXT, OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS
+};
+og_status og_tree_export(const og_tree *t, int field, void *host_dst, size_t bytes);
+
+og_status og_tree_free(og_tree *t);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *og_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OG_H */

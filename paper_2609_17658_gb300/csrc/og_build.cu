@@ -1,0 +1,672 @@
+// og_build.cu -- tree construction on the GPU (Sect. 4.1.1 "Tree construction").
+//
+// The paper builds the tree by inserting particles one at a time in
+// space-filling-curve order and then computing moments bottom-up.  Here the
+// same tree is built fully in parallel from the sorted keys:
+//
+//   a1/a2  k_quantize_keys   f64 positions -> u32 fixed point -> 63-bit Morton key
+//   a3     radix sort (og_sort.cu), k_permute gathers sorted SoA positions/masses
+//   a4     k_split_levels   level of every adjacent-key split (shared 3-bit digits)
+//          k_split_nodes    the node a split belongs to: its key range (galloping
+//                           search on key prefixes) and whether it is the node's
+//                           first split; first splits are numbered by a scan
+//          k_split_node_id  node id of every split
+//          k_link           parent of every node, owner node of every particle,
+//                           octant-occupancy bits of every node
+//          k_place          child array in key order, grouped by parent
+//          k_threading      nextnode / sibling threading (unified index space)
+//   a5     k_moments        bottom-up FP64 mass and sum m x; 8 lanes per node hold
+//                           the 8 octant slots and combine them with warp
+//                           shuffles in the fixed order ((0+1)+(2+3))+((4+5)+(6+7));
+//                           the last child to finish climbs to the parent
+//   a6     k_frontier .. k_group_fin   walk groups and their integer boxes
+//          k_records        32-byte child records read by the walk
+//
+// Every decision is integer or IEEE FP64 with a fixed operation order, so the
+// result is identical to the oracle's recursive construction.
+#include <cstdio>
+
+#include "og_internal.h"
+
+namespace og {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ uint64_t spread21(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ int lcp_levels(uint64_t a, uint64_t b) {
+    uint64_t x = a ^ b;
+    return x == 0 ? kLevels : (__clzll((long long)x) - 1) / 3;
+}
+
+__device__ __forceinline__ int digit_at(uint64_t key, int lev) {
+    return (int)((key >> (3 * (kLevels - lev))) & 7u);
+}
+
+__device__ __forceinline__ uint32_t quantize(double v, double box, uint32_t *status) {
+    if (!isfinite(v)) {
+        atomicOr(status, ST_BAD_INPUT);
+        return 0;
+    }
+    double t = __ddiv_rn(v, box);
+    t = __dsub_rn(t, floor(t));
+    double q = floor(__dmul_rn(t, 4294967296.0));
+    if (q >= 4294967296.0) q = 0.0;
+    return (uint32_t)q;
+}
+
+__global__ void k_quantize_keys(const double *__restrict__ pos, const double *__restrict__ mass,
+                                int64_t n, double box, uint32_t *qx, uint32_t *qy, uint32_t *qz,
+                                uint64_t *key, uint32_t *idx, uint32_t *status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t x = quantize(pos[3 * i + 0], box, status);
+    uint32_t y = quantize(pos[3 * i + 1], box, status);
+    uint32_t z = quantize(pos[3 * i + 2], box, status);
+    double m = mass[i];
+    if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
+    qx[i] = x;
+    qy[i] = y;
+    qz[i] = z;
+    key[i] = (spread21(x >> 11) << 2) | (spread21(y >> 11) << 1) | spread21(z >> 11);
+    idx[i] = (uint32_t)i;
+}
+
+__global__ void k_permute(int64_t n, const uint32_t *__restrict__ perm,
+                          const uint32_t *__restrict__ qx, const uint32_t *__restrict__ qy,
+                          const uint32_t *__restrict__ qz, const double *__restrict__ mass,
+                          uint32_t *px, uint32_t *py, uint32_t *pz, float *pm32, double *pm64) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = perm[i];
+    px[i] = qx[j];
+    py[i] = qy[j];
+    pz[i] = qz[j];
+    double m = mass[j];
+    pm64[i] = m;
+    pm32[i] = __double2float_rn(m);
+}
+
+__global__ void k_split_levels(const uint64_t *__restrict__ skey, int64_t n, uint8_t *lv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    lv[i] = (uint8_t)lcp_levels(skey[i], skey[i + 1]);
+}
+
+// Node of split i: the maximal key range around i whose keys share lv[i]
+// leading digits.  It is the node's first split iff no split of the same
+// level lies between the range start and i.
+__global__ void k_split_nodes(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ lv,
+                              int64_t n, uint32_t *sb, uint32_t *se, uint32_t *first) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int L = lv[i];
+    const uint64_t ki = skey[i];
+    // smallest b <= i with lcp(skey[b], ki) >= L: gallop left, then bisect
+    int64_t ok = i, step = 1, bad = -1;
+    while (true) {
+        int64_t j = i - step;
+        if (j < 0) { bad = -1; break; }
+        if (lcp_levels(skey[j], ki) >= L) { ok = j; step <<= 1; }
+        else { bad = j; break; }
+    }
+    while (ok - bad > 1) {
+        int64_t mid = bad + (ok - bad) / 2;
+        if (lcp_levels(skey[mid], ki) >= L) ok = mid; else bad = mid;
+    }
+    const int64_t b = ok;
+    // largest e-1 >= i+1 with lcp(ki, skey[e-1]) >= L
+    ok = i + 1;
+    step = 1;
+    int64_t badr = n;
+    while (true) {
+        int64_t j = i + 1 + step;
+        if (j >= n) { badr = n; break; }
+        if (lcp_levels(ki, skey[j]) >= L) { ok = j; step <<= 1; }
+        else { badr = j; break; }
+    }
+    while (badr - ok > 1) {
+        int64_t mid = ok + (badr - ok) / 2;
+        if (lcp_levels(ki, skey[mid]) >= L) ok = mid; else badr = mid;
+    }
+    sb[i] = (uint32_t)b;
+    se[i] = (uint32_t)(ok + 1);
+    first[i] = (L >= 1 && (b == i || lcp_levels(skey[b], ki) > L)) ? 1u : 0u;
+}
+
+__global__ void k_node_init(int64_t n, const uint32_t *__restrict__ first,
+                            const uint32_t *__restrict__ nid, const uint8_t *__restrict__ lv,
+                            const uint32_t *__restrict__ sb, const uint32_t *__restrict__ se,
+                            uint8_t *nlev, uint32_t *nbeg, uint32_t *nend) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        nlev[0] = 0;
+        nbeg[0] = 0;
+        nend[0] = (uint32_t)n;
+    }
+    if (i >= n - 1 || !first[i]) return;
+    uint32_t id = 1 + nid[i];
+    nlev[id] = lv[i];
+    nbeg[id] = sb[i];
+    nend[id] = se[i];
+}
+
+__global__ void k_split_node_id(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ lv,
+                                const uint32_t *__restrict__ sb, const uint32_t *__restrict__ first,
+                                const uint32_t *__restrict__ nid, int64_t n, uint32_t *sid) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int L = lv[i];
+    if (L == 0) { sid[i] = 0; return; }
+    if (first[i]) { sid[i] = 1 + nid[i]; return; }
+    // first split f in [b, i]: smallest j with lcp(skey[b], skey[j+1]) == L
+    const int64_t b = sb[i];
+    const uint64_t kb = skey[b];
+    int64_t lo = b, hi = i;  // answer in [lo, hi]; hi satisfies the predicate
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (lcp_levels(kb, skey[mid + 1]) <= L) hi = mid; else lo = mid + 1;
+    }
+    sid[i] = 1 + nid[lo];
+}
+
+__global__ void k_link(int64_t n, int64_t m, const uint64_t *__restrict__ skey,
+                       const uint8_t *__restrict__ lv, const uint32_t *__restrict__ sid,
+                       const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ nbeg,
+                       const uint32_t *__restrict__ nend, int32_t *npar, uint32_t *owner,
+                       uint32_t *occ, uint32_t *nnc, uint32_t *status) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        const int64_t p = t;
+        int dl = p > 0 ? lv[p - 1] : -1;
+        int dr = p < n - 1 ? lv[p] : -1;
+        uint32_t own;
+        if (dl < 0 && dr < 0) own = 0;
+        else own = sid[dl >= dr ? p - 1 : p];
+        if (own >= (uint32_t)m) {
+            atomicOr(status, ST_INTERNAL);
+            own = 0;
+        }
+        owner[p] = own;
+        int lo = nlev[own];
+        if (lo < kLevels) atomicOr(&occ[own], 1u << digit_at(skey[p], lo + 1));
+    } else if (t < n + m - 1) {
+        const int64_t id = t - n + 1;
+        const int64_t b = nbeg[id], e = nend[id];
+        int dl = b > 0 ? lv[b - 1] : -1;
+        int dr = e < n ? lv[e - 1] : -1;
+        uint32_t par;
+        if (dl < 0 && dr < 0) par = 0;
+        else par = sid[dl >= dr ? b - 1 : e - 1];
+        npar[id] = (int32_t)par;
+        if (par >= (uint32_t)m || nlev[par] >= nlev[id] || nlev[par] >= kLevels) {
+            atomicOr(status, ST_INTERNAL);
+            return;
+        }
+        atomicOr(&occ[par], 1u << digit_at(skey[b], nlev[par] + 1));
+        atomicAdd(&nnc[par], 1u);
+    } else if (t == n + m - 1) {
+        npar[0] = -1;
+    }
+}
+
+__global__ void k_ccnt(int64_t m, const uint8_t *__restrict__ nlev,
+                       const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
+                       const uint32_t *__restrict__ occ, uint32_t *nccnt) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= m) return;
+    nccnt[id] = nlev[id] == kLevels ? nend[id] - nbeg[id] : (uint32_t)__popc(occ[id]);
+}
+
+__global__ void k_place(int64_t n, int64_t m, const uint64_t *__restrict__ skey,
+                        const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ nbeg,
+                        const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
+                        const int32_t *__restrict__ npar, const uint32_t *__restrict__ owner,
+                        uint32_t *child, uint32_t *npos, int64_t nchild, uint32_t *status) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        const int64_t p = t;
+        uint32_t own = owner[p];
+        int lo = nlev[own];
+        uint32_t slot;
+        if (lo == kLevels) {
+            slot = ncbeg[own] + (uint32_t)(p - nbeg[own]);
+        } else {
+            int d = digit_at(skey[p], lo + 1);
+            slot = ncbeg[own] + __popc(occ[own] & ((1u << d) - 1u));
+        }
+        if (slot >= (uint64_t)nchild) { atomicOr(status, ST_INTERNAL); return; }
+        child[slot] = (uint32_t)p;
+    } else if (t < n + m - 1) {
+        const int64_t id = t - n + 1;
+        uint32_t par = (uint32_t)npar[id];
+        int d = digit_at(skey[nbeg[id]], nlev[par] + 1);
+        uint32_t slot = ncbeg[par] + __popc(occ[par] & ((1u << d) - 1u));
+        if (slot >= (uint64_t)nchild) { atomicOr(status, ST_INTERNAL); return; }
+        child[slot] = (uint32_t)(n + id);
+        npos[id] = slot;
+    }
+}
+
+__global__ void k_threading(int64_t n, int64_t m, int64_t nchild, const uint32_t *__restrict__ child,
+                            const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ nccnt,
+                            const int32_t *__restrict__ npar, const uint32_t *__restrict__ npos,
+                            const uint32_t *__restrict__ owner, int32_t *nnext, int32_t *nsib,
+                            int32_t *pnext, uint32_t *status) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < m) {
+        nnext[c] = (int32_t)child[ncbeg[c]];
+        if (c == 0) nsib[0] = -1;
+    }
+    if (c >= nchild) return;
+    const uint32_t item = child[c];
+    int64_t par = item < n ? (int64_t)owner[item] : (int64_t)npar[item - n];
+    int64_t cc = c;
+    int32_t after = -1;
+    for (int guard = 0;; ++guard) {
+        if (guard > 2 * kLevels + 2 || par < 0 || par >= m) { atomicOr(status, ST_INTERNAL); break; }
+        if (cc + 1 < (int64_t)ncbeg[par] + nccnt[par]) { after = (int32_t)child[cc + 1]; break; }
+        if (par == 0) { after = -1; break; }
+        cc = npos[par];
+        par = npar[par];
+    }
+    if (item < n) pnext[item] = after;
+    else nsib[item - n] = after;
+}
+
+// a5: moments.  One team of 8 lanes per node; lane s holds octant slot s.
+__global__ void __launch_bounds__(kT) k_moments(
+    int64_t n, int64_t m, const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ nbeg,
+    const uint32_t *__restrict__ nend, const uint32_t *__restrict__ ncbeg,
+    const uint32_t *__restrict__ occ, const uint32_t *__restrict__ child,
+    const int32_t *__restrict__ npar, const uint32_t *__restrict__ nnc, uint32_t *arrive,
+    const uint32_t *__restrict__ px, const uint32_t *__restrict__ py,
+    const uint32_t *__restrict__ pz, const double *__restrict__ pm64, double *nM, double *nS,
+    uint32_t *ncom, int64_t nchild, uint32_t *status) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & 7;
+    const unsigned tmask = 0xffu << (lane & 24);
+    int64_t node = gt >> 3;
+    if (node >= m) return;  // whole team leaves together
+    if (nnc[node] != 0) return;
+    for (int guard = 0;; ++guard) {
+        if (guard > kLevels + 2) {
+            if (sub == 0) atomicOr(status, ST_INTERNAL);
+            break;
+        }
+        const int L = nlev[node];
+        double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+        if (L == kLevels) {
+            if (sub == 0) {
+                for (uint32_t q = nbeg[node]; q < nend[node]; ++q) {
+                    double mq = pm64[q];
+                    M = __dadd_rn(M, mq);
+                    Sx = __dadd_rn(Sx, __dmul_rn(mq, (double)px[q]));
+                    Sy = __dadd_rn(Sy, __dmul_rn(mq, (double)py[q]));
+                    Sz = __dadd_rn(Sz, __dmul_rn(mq, (double)pz[q]));
+                }
+            }
+        } else {
+            const uint32_t o = occ[node];
+            const uint32_t slot = ncbeg[node] + __popc(o & ((1u << sub) - 1u));
+            if (((o >> sub) & 1u) && slot < (uint64_t)nchild) {
+                uint32_t item = child[slot];
+                if (item < n) {
+                    double mq = pm64[item];
+                    M = mq;
+                    Sx = __dmul_rn(mq, (double)px[item]);
+                    Sy = __dmul_rn(mq, (double)py[item]);
+                    Sz = __dmul_rn(mq, (double)pz[item]);
+                } else {
+                    int64_t j = item - n;
+                    M = __ldcg(&nM[j]);
+                    Sx = __ldcg(&nS[3 * j + 0]);
+                    Sy = __ldcg(&nS[3 * j + 1]);
+                    Sz = __ldcg(&nS[3 * j + 2]);
+                }
+            }
+#pragma unroll
+            for (int d = 1; d < 8; d <<= 1) {
+                M = __dadd_rn(M, __shfl_xor_sync(tmask, M, d));
+                Sx = __dadd_rn(Sx, __shfl_xor_sync(tmask, Sx, d));
+                Sy = __dadd_rn(Sy, __shfl_xor_sync(tmask, Sy, d));
+                Sz = __dadd_rn(Sz, __shfl_xor_sync(tmask, Sz, d));
+            }
+        }
+        int go = 0;
+        if (sub == 0) {
+            nM[node] = M;
+            nS[3 * node + 0] = Sx;
+            nS[3 * node + 1] = Sy;
+            nS[3 * node + 2] = Sz;
+            uint32_t c[3];
+            if (M > 0.0) {
+                c[0] = (uint32_t)rint(__ddiv_rn(Sx, M));
+                c[1] = (uint32_t)rint(__ddiv_rn(Sy, M));
+                c[2] = (uint32_t)rint(__ddiv_rn(Sz, M));
+            } else {
+                // massless node: the cell centre
+                const uint32_t q = nbeg[node];
+                const uint32_t pc[3] = {px[q], py[q], pz[q]};
+                for (int a = 0; a < 3; ++a) {
+                    uint64_t mask = L == 0 ? 0ull : ~((1ull << (32 - L)) - 1ull);
+                    c[a] = (uint32_t)(((uint64_t)pc[a] & mask) + (1ull << (31 - L)));
+                }
+            }
+            ncom[3 * node + 0] = c[0];
+            ncom[3 * node + 1] = c[1];
+            ncom[3 * node + 2] = c[2];
+            __threadfence();
+            if (node != 0) {
+                int32_t par = npar[node];
+                uint32_t old = atomicAdd(&arrive[par], 1u);
+                go = (old + 1 == nnc[par]) ? 1 : 0;
+            }
+        }
+        go = __shfl_sync(tmask, go, lane & 24);
+        if (!go) break;
+        __threadfence();
+        node = npar[node];
+    }
+}
+
+__global__ void k_frontier(int64_t n, int G, const uint32_t *__restrict__ owner,
+                           const int32_t *__restrict__ npar, const uint32_t *__restrict__ nbeg,
+                           const uint32_t *__restrict__ nend, uint32_t *fp) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t node = owner[p];
+    for (int guard = 0; node != 0 && nend[node] - nbeg[node] <= (uint32_t)G && guard <= kLevels + 2;
+         ++guard)
+        node = (uint32_t)npar[node];
+    fp[p] = node;
+}
+
+__global__ void k_runmark(int64_t n, const uint32_t *__restrict__ fp, uint32_t *rs) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    rs[p] = (p == 0 || fp[p] != fp[p - 1]) ? (uint32_t)p : 0u;
+}
+
+__global__ void k_groupmark(int64_t n, int G, const uint32_t *__restrict__ runstart, uint32_t *gs) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    gs[p] = ((p - runstart[p]) % G == 0) ? 1u : 0u;
+}
+
+__global__ void k_group_init(int64_t n, const uint32_t *__restrict__ gs,
+                             const uint32_t *__restrict__ gid, uint32_t *gbeg) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n || !gs[p]) return;
+    gbeg[gid[p]] = (uint32_t)p;
+}
+
+__global__ void k_group_fin(int64_t n, int64_t ng, const uint32_t *__restrict__ gbeg,
+                            uint32_t *gend, const uint32_t *__restrict__ px,
+                            const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
+                            uint32_t *gbox) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    uint32_t b = gbeg[g];
+    uint32_t e = (g + 1 < ng) ? gbeg[g + 1] : (uint32_t)n;
+    gend[g] = e;
+    uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
+    for (uint32_t q = b; q < e; ++q) {
+        uint32_t v[3] = {px[q], py[q], pz[q]};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = min(lo[a], v[a]);
+            hi[a] = max(hi[a], v[a]);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        gbox[6 * g + a] = lo[a];
+        gbox[6 * g + 3 + a] = hi[a];
+    }
+}
+
+__global__ void k_records(int64_t n, int64_t nchild, const uint32_t *__restrict__ child,
+                          const uint32_t *__restrict__ px, const uint32_t *__restrict__ py,
+                          const uint32_t *__restrict__ pz, const float *__restrict__ pm32,
+                          const double *__restrict__ pm64, const uint8_t *__restrict__ nlev,
+                          const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ nccnt,
+                          const double *__restrict__ nM, const uint32_t *__restrict__ ncom,
+                          CRec *crec) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchild) return;
+    uint32_t item = child[c];
+    CRec r;
+    if (item < n) {
+        r.x = px[item];
+        r.y = py[item];
+        r.z = pz[item];
+        r.m = pm32[item];
+        r.M = pm64[item];
+        r.info = 0;
+        r.ref = item;
+    } else {
+        int64_t j = item - n;
+        r.x = ncom[3 * j + 0];
+        r.y = ncom[3 * j + 1];
+        r.z = ncom[3 * j + 2];
+        r.M = nM[j];
+        r.m = __double2float_rn(r.M);
+        r.info = (1u << 31) | ((uint32_t)nlev[j] << 26) | (nccnt[j] & 0x3ffffffu);
+        r.ref = ncbeg[j];
+    }
+    crec[c] = r;
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
+
+// bump allocator inside one device allocation
+struct Bump {
+    char *base;
+    size_t off = 0, cap;
+    Bump(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
+    template <class T>
+    T *take(int64_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += (size_t)(count > 0 ? count : 1) * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace
+
+// Bytes of the persistent arrays of a tree with n particles.
+static size_t tree_bytes(int64_t n, bool alloc) {
+    (void)alloc;
+    int64_t m = n;            // nodes <= n
+    int64_t c = n + m;        // children = (n - 1) + nodes <= 2n
+    size_t b = 0;
+    auto add = [&](size_t sz, int64_t cnt) { b += ((size_t)(cnt > 0 ? cnt : 1) * sz + 255) & ~(size_t)255; };
+    add(8, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n); add(8, n);    // particles
+    add(1, m); add(4, m); add(4, m); add(4, m); add(4, m); add(4, m);               // nlev..npos
+    add(4, m); add(4, m); add(4, m); add(8, m); add(8, 3 * m); add(4, 3 * m);       // npar.. ncom
+    add(4, n); add(4, n);                                                           // pnext, owner
+    add(4, c); add(32, c);                                                          // child, crec
+    add(4, n); add(4, n); add(4, 6 * n);                                            // groups
+    add(4, 3 * n); add(4, 3 * n); add(4, n); add(4, n);                             // force arrays
+    return b + 4096;
+}
+
+og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
+    cudaStream_t s = t->ctx->stream;
+    const int64_t n = t->n;
+    const og_params &p = t->prm;
+    cudaError_t err;
+
+    // ---- persistent arrays
+    size_t tb = tree_bytes(n, true);
+    if ((err = cudaMallocAsync(&t->arena, tb, s)) != cudaSuccess) {
+        t->arena = nullptr;
+        return err == cudaErrorMemoryAllocation ? (set_error("device allocation of %zu bytes failed", tb), OG_ERR_OOM)
+                                                : cuda_fail(err, "cudaMallocAsync");
+    }
+    t->arena_bytes = tb;
+    Bump A(t->arena, tb);
+    const int64_t mcap = n, ccap = 2 * n;
+    t->skey = A.take<uint64_t>(n);
+    t->perm = A.take<uint32_t>(n);
+    t->px = A.take<uint32_t>(n);
+    t->py = A.take<uint32_t>(n);
+    t->pz = A.take<uint32_t>(n);
+    t->pm32 = A.take<float>(n);
+    t->pm64 = A.take<double>(n);
+    t->nlev = A.take<uint8_t>(mcap);
+    t->nbeg = A.take<uint32_t>(mcap);
+    t->nend = A.take<uint32_t>(mcap);
+    t->ncbeg = A.take<uint32_t>(mcap);
+    t->nccnt = A.take<uint32_t>(mcap);
+    t->npos = A.take<uint32_t>(mcap);
+    t->npar = A.take<int32_t>(mcap);
+    t->nnext = A.take<int32_t>(mcap);
+    t->nsib = A.take<int32_t>(mcap);
+    t->nM = A.take<double>(mcap);
+    t->nS = A.take<double>(3 * mcap);
+    t->ncom = A.take<uint32_t>(3 * mcap);
+    t->pnext = A.take<int32_t>(n);
+    t->owner = A.take<uint32_t>(n);
+    t->child = A.take<uint32_t>(ccap);
+    t->crec = A.take<CRec>(ccap);
+    t->gbeg = A.take<uint32_t>(n);
+    t->gend = A.take<uint32_t>(n);
+    t->gbox = A.take<uint32_t>(6 * n);
+    t->a_sorted = A.take<float>(3 * n);
+    t->a_old_sorted = A.take<float>(3 * n);
+    t->npp_sorted = A.take<uint32_t>(n);
+    t->npn_sorted = A.take<uint32_t>(n);
+    if (A.off > tb) { set_error("internal: arena overflow"); return OG_ERR_STATE; }
+
+    // ---- scratch
+    size_t sb_bytes = 0;
+    {
+        auto add = [&](size_t sz, int64_t cnt) { sb_bytes += ((size_t)(cnt > 0 ? cnt : 1) * sz + 255) & ~(size_t)255; };
+        add(4, n); add(4, n); add(4, n);        // qx qy qz
+        add(8, n); add(4, n); add(8, n); add(4, n);  // keys, idx, alt
+        add(1, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // lv sb se first nid sid
+        add(4, n); add(4, n); add(4, n);        // occ nnc arrive
+        add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs gid
+        sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + 8) + 4096;
+    }
+    void *scratch = nullptr;
+    if ((err = cudaMallocAsync(&scratch, sb_bytes, s)) != cudaSuccess)
+        return err == cudaErrorMemoryAllocation ? (set_error("device allocation of %zu bytes failed", sb_bytes), OG_ERR_OOM)
+                                                : cuda_fail(err, "cudaMallocAsync");
+    Bump B(scratch, sb_bytes);
+    uint32_t *qx = B.take<uint32_t>(n), *qy = B.take<uint32_t>(n), *qz = B.take<uint32_t>(n);
+    uint64_t *keys = B.take<uint64_t>(n);
+    uint32_t *idx = B.take<uint32_t>(n);
+    uint64_t *keys_alt = B.take<uint64_t>(n);
+    uint32_t *idx_alt = B.take<uint32_t>(n);
+    uint8_t *lv = B.take<uint8_t>(n);
+    uint32_t *sbeg = B.take<uint32_t>(n), *send = B.take<uint32_t>(n);
+    uint32_t *first = B.take<uint32_t>(n), *nid = B.take<uint32_t>(n), *sid = B.take<uint32_t>(n);
+    uint32_t *occ = B.take<uint32_t>(n), *nnc = B.take<uint32_t>(n), *arrive = B.take<uint32_t>(n);
+    uint32_t *fp = B.take<uint32_t>(n), *rs = B.take<uint32_t>(n), *gs = B.take<uint32_t>(n);
+    uint32_t *gid = B.take<uint32_t>(n);
+    void *sort_scratch = B.take<char>((int64_t)radix_sort_scratch_bytes(n));
+    void *scan_scratch = B.take<char>((int64_t)scan_scratch_bytes(2 * n + 8));
+    uint32_t *d_tot = B.take<uint32_t>(4);
+    uint32_t *status = t->ctx->d_status;
+
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+
+    // a1, a2
+    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, d_mass, n, p.box, qx, qy, qz, keys, idx, status);
+    // a3
+    bool in_alt = false;
+    radix_sort_pairs(keys, idx, keys_alt, idx_alt, n, 63, sort_scratch, s, &in_alt);
+    const uint64_t *skey_src = in_alt ? keys_alt : keys;
+    const uint32_t *perm_src = in_alt ? idx_alt : idx;
+    cudaMemcpyAsync(t->skey, skey_src, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    k_permute<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, d_mass, t->px, t->py, t->pz, t->pm32,
+                                     t->pm64);
+    // a4: nodes from splits
+    uint32_t h_tot[4] = {0, 0, 0, 0};
+    int64_t nsplit = n - 1;
+    if (nsplit > 0) {
+        k_split_levels<<<nblk(nsplit), kT, 0, s>>>(t->skey, n, lv);
+        k_split_nodes<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, n, sbeg, send, first);
+        scan_exclusive_u32(first, nid, nsplit, d_tot, scan_scratch, s);
+        cudaMemcpyAsync(h_tot, d_tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) {
+            cudaFreeAsync(scratch, s);
+            return cuda_fail(err, "build (sort)");
+        }
+    }
+    const int64_t m = 1 + (int64_t)h_tot[0];
+    t->nnodes = m;
+    k_node_init<<<nblk(nsplit > 0 ? nsplit : 1), kT, 0, s>>>(n, first, nid, lv, sbeg, send, t->nlev,
+                                                             t->nbeg, t->nend);
+    if (nsplit > 0)
+        k_split_node_id<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, sbeg, first, nid, n, sid);
+    cudaMemsetAsync(occ, 0, m * sizeof(uint32_t), s);
+    cudaMemsetAsync(nnc, 0, m * sizeof(uint32_t), s);
+    cudaMemsetAsync(arrive, 0, m * sizeof(uint32_t), s);
+    k_link<<<nblk(n + m), kT, 0, s>>>(n, m, t->skey, lv, sid, t->nlev, t->nbeg, t->nend, t->npar,
+                                      t->owner, occ, nnc, status);
+    k_ccnt<<<nblk(m), kT, 0, s>>>(m, t->nlev, t->nbeg, t->nend, occ, t->nccnt);
+    scan_exclusive_u32(t->nccnt, t->ncbeg, m, d_tot + 1, scan_scratch, s);
+    const int64_t nchild = (n - 1) + m;
+    t->nchild = nchild;
+    k_place<<<nblk(n + m), kT, 0, s>>>(n, m, t->skey, t->nlev, t->nbeg, t->ncbeg, occ, t->npar,
+                                       t->owner, t->child, t->npos, nchild, status);
+    k_threading<<<nblk(nchild), kT, 0, s>>>(n, m, nchild, t->child, t->ncbeg, t->nccnt, t->npar,
+                                            t->npos, t->owner, t->nnext, t->nsib, t->pnext, status);
+    // a5
+    k_moments<<<nblk(8 * m), kT, 0, s>>>(n, m, t->nlev, t->nbeg, t->nend, t->ncbeg, occ, t->child,
+                                         t->npar, nnc, arrive, t->px, t->py, t->pz, t->pm64, t->nM,
+                                         t->nS, t->ncom, nchild, status);
+    // a6: groups
+    const int G = p.group_max;
+    k_frontier<<<nblk(n), kT, 0, s>>>(n, G, t->owner, t->npar, t->nbeg, t->nend, fp);
+    k_runmark<<<nblk(n), kT, 0, s>>>(n, fp, rs);
+    scan_inclusive_max_u32(rs, rs, n, scan_scratch, s);
+    k_groupmark<<<nblk(n), kT, 0, s>>>(n, G, rs, gs);
+    scan_exclusive_u32(gs, gid, n, d_tot + 2, scan_scratch, s);
+    k_group_init<<<nblk(n), kT, 0, s>>>(n, gs, gid, t->gbeg);
+    cudaMemcpyAsync(h_tot + 1, d_tot + 1, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) {
+        cudaFreeAsync(scratch, s);
+        return cuda_fail(err, "build (topology)");
+    }
+    if ((int64_t)h_tot[1] != nchild) {
+        cudaFreeAsync(scratch, s);
+        set_error("internal: child count %u != %lld", h_tot[1], (long long)nchild);
+        return OG_ERR_STATE;
+    }
+    t->ngroups = h_tot[2];
+    k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
+                                                t->pz, t->gbox);
+    k_records<<<nblk(nchild), kT, 0, s>>>(n, nchild, t->child, t->px, t->py, t->pz, t->pm32,
+                                          t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nM, t->ncom,
+                                          t->crec);
+    cudaEventRecord(e1, s);
+    cudaFreeAsync(scratch, s);
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "build");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    t->ms_build = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((err = cudaGetLastError()) != cudaSuccess) return cuda_fail(err, "build launch");
+    return OG_OK;
+}
+
+}  // namespace og

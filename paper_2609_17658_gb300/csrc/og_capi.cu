@@ -1,0 +1,388 @@
+// og_capi.cu -- the C-ABI entry points of include/og.h.
+//
+// Host-side responsibilities: argument validation, the context (device,
+// stream, stream-ordered memory pool, device status word), host<->device
+// copies for host-pointer calls, the two-pass relative opening
+// (Sect. 4.1.2: the relative criterion needs the previous acceleration; a
+// Barnes-Hut pass supplies it when the caller has none), and the final
+// reordering to the caller's particle order.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "og_internal.h"
+
+namespace og {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+og_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? OG_ERR_OOM : OG_ERR_CUDA;
+}
+
+namespace {
+
+constexpr int kT = 256;
+inline unsigned nblk(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
+
+__global__ void k_gather_aold(int64_t n, const uint32_t *__restrict__ perm,
+                              const float *__restrict__ a_old, float *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = perm[i];
+    out[i] = a_old[3ull * j + 0];
+    out[n + i] = a_old[3ull * j + 1];
+    out[2 * n + i] = a_old[3ull * j + 2];
+}
+
+__global__ void k_unpermute(int64_t n, const uint32_t *__restrict__ perm,
+                            const float *__restrict__ acc_sorted,
+                            const uint32_t *__restrict__ npp_s, const uint32_t *__restrict__ npn_s,
+                            float *acc, uint32_t *npp, uint32_t *npn) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = perm[i];
+    acc[3ull * j + 0] = acc_sorted[i];
+    acc[3ull * j + 1] = acc_sorted[n + i];
+    acc[3ull * j + 2] = acc_sorted[2 * n + i];
+    if (npp) npp[j] = npp_s[i];
+    if (npn) npn[j] = npn_s[i];
+}
+
+og_status check_status(og_ctx *c) {
+    uint32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st == 0) return OG_OK;
+    cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (st & ST_BAD_INPUT) {
+        set_error("non-finite position or negative/non-finite mass");
+        return OG_ERR_ARG;
+    }
+    if (st & ST_STACK_OVF) {
+        set_error("walk stack overflow");
+        return OG_ERR_OVERFLOW;
+    }
+    if (st & ST_LIST_OVF) {
+        set_error("debug list buffer overflow");
+        return OG_ERR_OVERFLOW;
+    }
+    set_error("internal consistency check failed (status 0x%x)", st);
+    return OG_ERR_STATE;
+}
+
+og_status validate(const og_params *p, int64_t n) {
+    if (!p) { set_error("params is NULL"); return OG_ERR_ARG; }
+    if (n < 1 || n > kMaxN) { set_error("N = %lld out of range [1, %lld]", (long long)n, (long long)kMaxN); return OG_ERR_ARG; }
+    if (!(p->box > 0.0) || !std::isfinite(p->box)) { set_error("box must be finite and > 0"); return OG_ERR_ARG; }
+    if (!std::isfinite(p->G) || !std::isfinite(p->eps) || p->eps < 0.0) { set_error("G and eps must be finite, eps >= 0"); return OG_ERR_ARG; }
+    if (!std::isfinite(p->r_s)) { set_error("r_s must be finite"); return OG_ERR_ARG; }
+    if (p->r_s > 0.0) {
+        double rc = p->rcut_over_rs * p->r_s;
+        if (!(rc > 0.0) || !(rc < 0.5 * p->box)) { set_error("cutoff radius must satisfy 0 < r_cut < box/2"); return OG_ERR_ARG; }
+    }
+    if (p->opening != OG_OPEN_BH && p->opening != OG_OPEN_REL) { set_error("unknown opening criterion"); return OG_ERR_ARG; }
+    if (!(p->theta >= 0.0) || !std::isfinite(p->theta)) { set_error("theta must be >= 0"); return OG_ERR_ARG; }
+    if (!(p->alpha >= 0.0) || !std::isfinite(p->alpha)) { set_error("alpha must be >= 0"); return OG_ERR_ARG; }
+    if (!(p->theta_first_pass >= 0.0)) { set_error("theta_first_pass must be >= 0"); return OG_ERR_ARG; }
+    if (p->leaf_max != 1) { set_error("leaf_max must be 1 (one particle per leaf cell)"); return OG_ERR_ARG; }
+    if (p->group_max < 0 || p->group_max > 32) { set_error("group_max must be in [0, 32]"); return OG_ERR_ARG; }
+    return OG_OK;
+}
+
+}  // namespace
+}  // namespace og
+
+using namespace og;
+
+extern "C" {
+
+const char *og_last_error(void) { return g_err; }
+
+og_status og_params_default(og_params *p) {
+    if (!p) return OG_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->box = 1.0;
+    p->G = 1.0;
+    p->eps = 0.0;
+    p->r_s = 0.0;
+    p->rcut_over_rs = 4.5;
+    p->theta = 0.5;
+    p->alpha = 0.005;
+    p->theta_first_pass = 0.5;
+    p->opening = OG_OPEN_BH;
+    p->leaf_max = 1;
+    p->group_max = 32;
+    p->flags = 0;
+    return OG_OK;
+}
+
+og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
+    if (!out) { set_error("ctx is NULL"); return OG_ERR_ARG; }
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) { set_error("no CUDA device %d", device); return OG_ERR_ARG; }
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    og_ctx *c = new (std::nothrow) og_ctx();
+    if (!c) { set_error("host allocation failed"); return OG_ERR_OOM; }
+    c->device = device;
+    c->hbm_budget = hbm_budget_bytes;
+    if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    c->stream = c->own_stream;
+    // keep freed blocks in the stream-ordered pool: repeated builds reuse them
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if ((e = cudaMalloc(&c->d_status, 256)) != cudaSuccess) {
+        cudaStreamDestroy(c->own_stream);
+        delete c;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    c->d_counters = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(c->d_status) + 64);
+    cudaMemset(c->d_status, 0, 256);
+    cudaDeviceSynchronize();
+    *out = c;
+    return OG_OK;
+}
+
+og_status og_destroy(og_ctx *c) {
+    if (!c) return OG_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_status);
+    cudaStreamDestroy(c->own_stream);
+    delete c;
+    return OG_OK;
+}
+
+og_status og_set_stream(og_ctx *c, void *stream) {
+    if (!c) { set_error("ctx is NULL"); return OG_ERR_ARG; }
+    c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+    return OG_OK;
+}
+
+og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_t n,
+                        const og_params *p, og_tree **out) {
+    if (!out) { set_error("out is NULL"); return OG_ERR_ARG; }
+    *out = nullptr;
+    if (!c || !pos || !mass) { set_error("NULL argument"); return OG_ERR_ARG; }
+    og_status st = validate(p, n);
+    if (st) return st;
+    cudaSetDevice(c->device);
+    og_tree *t = new (std::nothrow) og_tree();
+    if (!t) { set_error("host allocation failed"); return OG_ERR_OOM; }
+    t->ctx = c;
+    t->prm = *p;
+    if (t->prm.group_max == 0) t->prm.group_max = 32;
+    t->n = n;
+    cudaStream_t s = c->stream;
+    const double *d_pos = pos, *d_mass = mass;
+    void *staging = nullptr;
+    cudaError_t e;
+    if (!(p->flags & OG_DEVICE_PTRS)) {
+        size_t bytes = (size_t)n * 4 * sizeof(double);
+        if ((e = cudaMallocAsync(&staging, bytes, s)) != cudaSuccess) {
+            delete t;
+            return cuda_fail(e, "cudaMallocAsync (inputs)");
+        }
+        double *dp = static_cast<double *>(staging);
+        cudaMemcpyAsync(dp, pos, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dp + 3 * n, mass, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s);
+        d_pos = dp;
+        d_mass = dp + 3 * n;
+    }
+    st = build_tree(t, d_pos, d_mass);
+    if (staging) cudaFreeAsync(staging, s);
+    if (st == OG_OK) st = check_status(c);
+    if (st != OG_OK) {
+        og_tree_free(t);
+        return st;
+    }
+    *out = t;
+    return OG_OK;
+}
+
+og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_pp,
+                        uint32_t *n_pn) {
+    if (!t || !acc) { set_error("NULL argument"); return OG_ERR_ARG; }
+    og_ctx *c = t->ctx;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int64_t n = t->n;
+    const bool dev = (t->prm.flags & OG_DEVICE_PTRS) != 0;
+    cudaError_t e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    t->interactions = 0;
+    float ms_walk = 0, ms;
+
+    // debug lists
+    if (t->prm.flags & OG_DEBUG_DUMP_LISTS) {
+        if (!t->lists) {
+            t->list_cap = (int64_t)1 << 28;
+            if ((e = cudaMalloc(&t->lists, (size_t)t->list_cap * 2 * sizeof(uint32_t))) != cudaSuccess) {
+                t->lists = nullptr;
+                return cuda_fail(e, "cudaMalloc (lists)");
+            }
+        }
+        t->list_len = 0;
+    }
+    // previous accelerations
+    const float *a_old_sorted = nullptr;
+    void *tmp = nullptr;
+    if (t->prm.opening == OG_OPEN_REL) {
+        if (a_old) {
+            const float *d_aold = a_old;
+            if (!dev) {
+                if ((e = cudaMallocAsync(&tmp, (size_t)n * 3 * sizeof(float), s)) != cudaSuccess)
+                    return cuda_fail(e, "cudaMallocAsync (a_old)");
+                cudaMemcpyAsync(tmp, a_old, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+                d_aold = static_cast<const float *>(tmp);
+            }
+            k_gather_aold<<<nblk(n), kT, 0, s>>>(n, t->perm, d_aold, t->a_old_sorted);
+        } else {
+            // first pass: Barnes-Hut with theta_first_pass
+            WalkParams w1 = make_walk_params(t->prm, OG_OPEN_BH, t->prm.theta_first_pass);
+            w1.dump = false;
+            og_status st = walk_pass(t, w1, nullptr, t->a_old_sorted, &ms);
+            if (st) return st;
+            ms_walk += ms;
+        }
+        a_old_sorted = t->a_old_sorted;
+    }
+    WalkParams w = make_walk_params(t->prm, t->prm.opening, t->prm.theta);
+    int64_t inter_before = t->interactions;
+    og_status st = walk_pass(t, w, a_old_sorted, t->a_sorted, &ms);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (st) return st;
+    (void)inter_before;
+    ms_walk += ms;
+    // back to caller order
+    float *d_acc = acc;
+    uint32_t *d_npp = n_pp, *d_npn = n_pn;
+    void *out_tmp = nullptr;
+    if (!dev) {
+        size_t bytes = (size_t)n * 3 * sizeof(float) + 2 * (size_t)n * sizeof(uint32_t) + 512;
+        if ((e = cudaMallocAsync(&out_tmp, bytes, s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (out)");
+        d_acc = static_cast<float *>(out_tmp);
+        d_npp = n_pp ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) : nullptr;
+        d_npn = n_pn ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) + n : nullptr;
+    }
+    k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+                                       d_acc, d_npp, d_npn);
+    if (!dev) {
+        cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (n_pp) cudaMemcpyAsync(n_pp, d_npp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (n_pn) cudaMemcpyAsync(n_pn, d_npn, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(out_tmp, s);
+    }
+    cudaEventRecord(e1, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "force");
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t->ms_force = ms;
+    t->ms_walk = ms_walk;
+    return check_status(c);
+}
+
+og_status og_tree_info_get(const og_tree *t, og_tree_info *info) {
+    if (!t || !info) { set_error("NULL argument"); return OG_ERR_ARG; }
+    info->n = t->n;
+    info->nodes = t->nnodes;
+    info->children = t->nchild;
+    info->groups = t->ngroups;
+    info->list_entries = t->list_len;
+    info->interactions = t->interactions;
+    info->interactions_last_pass = t->interactions_last;
+    info->ms_build = t->ms_build;
+    info->ms_force = t->ms_force;
+    info->ms_walk = t->ms_walk;
+    return OG_OK;
+}
+
+og_status og_tree_export(const og_tree *t, int field, void *dst, size_t bytes) {
+    if (!t || !dst) { set_error("NULL argument"); return OG_ERR_ARG; }
+    const int64_t n = t->n, m = t->nnodes, g = t->ngroups, c = t->nchild;
+    const void *src = nullptr;
+    size_t need = 0;
+    switch (field) {
+    case OG_F_SKEY: src = t->skey; need = n * 8; break;
+    case OG_F_PERM: src = t->perm; need = n * 4; break;
+    case OG_F_SPOS: need = 3 * n * 4; break;
+    case OG_F_LEVEL: src = t->nlev; need = m; break;
+    case OG_F_NBEG: src = t->nbeg; need = m * 4; break;
+    case OG_F_NEND: src = t->nend; need = m * 4; break;
+    case OG_F_PARENT: src = t->npar; need = m * 4; break;
+    case OG_F_CBEG: src = t->ncbeg; need = m * 4; break;
+    case OG_F_CCNT: src = t->nccnt; need = m * 4; break;
+    case OG_F_CHILD: src = t->child; need = c * 4; break;
+    case OG_F_MASS: src = t->nM; need = m * 8; break;
+    case OG_F_COM: src = t->ncom; need = 3 * m * 4; break;
+    case OG_F_NEXTNODE: src = t->nnext; need = m * 4; break;
+    case OG_F_SIBLING: src = t->nsib; need = m * 4; break;
+    case OG_F_PNEXT: src = t->pnext; need = n * 4; break;
+    case OG_F_GBEG: src = t->gbeg; need = g * 4; break;
+    case OG_F_GEND: src = t->gend; need = g * 4; break;
+    case OG_F_GBOX: src = t->gbox; need = 6 * g * 4; break;
+    case OG_F_LISTS: src = t->lists; need = t->list_len * 8; break;
+    default: set_error("unknown field %d", field); return OG_ERR_ARG;
+    }
+    if (bytes != need) { set_error("field %d needs %zu bytes, got %zu", field, need, bytes); return OG_ERR_ARG; }
+    if (need == 0) return OG_OK;
+    cudaSetDevice(t->ctx->device);
+    cudaStream_t s = t->ctx->stream;
+    if (field == OG_F_SPOS) {
+        char *d = static_cast<char *>(dst);
+        cudaMemcpyAsync(d, t->px, n * 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(d + n * 4, t->py, n * 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(d + 2 * n * 4, t->pz, n * 4, cudaMemcpyDeviceToHost, s);
+    } else {
+        cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "export");
+    return OG_OK;
+}
+
+og_status og_tree_free(og_tree *t) {
+    if (!t) return OG_OK;
+    cudaSetDevice(t->ctx->device);
+    if (t->arena) cudaFreeAsync(t->arena, t->ctx->stream);
+    if (t->lists) {
+        cudaStreamSynchronize(t->ctx->stream);
+        cudaFree(t->lists);
+    }
+    delete t;
+    return OG_OK;
+}
+
+og_status og_tree_refit(og_tree *t, const double *pos) {
+    (void)pos;
+    if (!t) { set_error("NULL argument"); return OG_ERR_ARG; }
+    set_error("og_tree_refit: not available in this build");
+    return OG_ERR_STATE;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// og_internal.h -- internal types shared by the library's translation units.
+//
+// Device data of one tree (all in HBM, structure of arrays, sorted order):
+//   skey[n] u64, perm[n] u32, px/py/pz[n] u32 fixed point, pm32[n] f32, pm64[n] f64
+//   nodes (id 0 = root; others in the order of their first split):
+//     nlev[m] u8, nbeg/nend[m] u32, npar[m] i32, ncbeg/nccnt[m] u32, npos[m] u32
+//     nM[m] f64, nS[3m] f64 (sum m x), ncom[3m] u32, nnext/nsib[m] i32
+//   child[c] u32 unified refs (particle < n, node + n), crec[c] 32-byte walk records
+//   groups: gbeg/gend[g] u32, gbox[6g] u32
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/og.h"
+
+namespace og {
+
+constexpr int kLevels = 21;          // Morton levels: 21 bits per axis
+constexpr int64_t kMaxN = (1ll << 26) - 1;
+
+// status bits raised by kernels in the context's device status word
+enum : uint32_t {
+    ST_BAD_INPUT = 1u << 0,   // non-finite position or negative / non-finite mass
+    ST_STACK_OVF = 1u << 1,   // walk stack overflow
+    ST_LIST_OVF = 1u << 2,    // debug list buffer overflow
+    ST_INTERNAL = 1u << 3,    // an internal consistency check failed
+};
+
+// 32-byte record of one child slot, read by the walk (particle or node)
+struct __align__(16) CRec {
+    uint32_t x, y, z;   // particle position or node centre of mass (fixed point)
+    float m;            // mass (f32) used by the pair arithmetic
+    double M;           // mass (f64) used by the relative opening test
+    uint32_t info;      // bit 31: node; bits 26..30: level; bits 0..25: child count
+    uint32_t ref;       // particle: sorted index; node: first entry in the child array
+};
+static_assert(sizeof(CRec) == 32, "CRec must be 32 bytes");
+
+struct Alloc;  // stream-ordered device allocator of a context
+
+}  // namespace og
+
+struct og_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    size_t hbm_budget = 0;
+    uint32_t *d_status = nullptr;     // device status word
+    unsigned long long *d_counters = nullptr;  // scratch counters (work queues, totals)
+    void *serve = nullptr;            // serving state (og_serve.cu)
+};
+
+struct og_tree {
+    og_ctx *ctx = nullptr;
+    og_params prm{};
+    int64_t n = 0, nnodes = 0, nchild = 0, ngroups = 0;
+    // sorted particles
+    uint64_t *skey = nullptr;
+    uint32_t *perm = nullptr;
+    uint32_t *px = nullptr, *py = nullptr, *pz = nullptr;
+    float *pm32 = nullptr;
+    double *pm64 = nullptr;
+    // nodes
+    uint8_t *nlev = nullptr;
+    uint32_t *nbeg = nullptr, *nend = nullptr, *ncbeg = nullptr, *nccnt = nullptr;
+    uint32_t *npos = nullptr;
+    int32_t *npar = nullptr, *nnext = nullptr, *nsib = nullptr;
+    double *nM = nullptr, *nS = nullptr;
+    uint32_t *ncom = nullptr;
+    int32_t *pnext = nullptr;
+    uint32_t *owner = nullptr;        // node a particle hangs from
+    uint32_t *child = nullptr;
+    og::CRec *crec = nullptr;
+    // groups
+    uint32_t *gbeg = nullptr, *gend = nullptr, *gbox = nullptr;
+    // force work arrays (sorted order)
+    float *a_sorted = nullptr;        // last pass accelerations, [3][n]
+    float *a_old_sorted = nullptr;    // previous accelerations, [3][n]
+    uint32_t *npp_sorted = nullptr, *npn_sorted = nullptr;
+    // debug lists
+    uint32_t *lists = nullptr;
+    int64_t list_cap = 0, list_len = 0;
+    // stats
+    int64_t interactions = 0, interactions_last = 0;
+    double ms_build = 0, ms_force = 0, ms_walk = 0;
+    // one allocation holds every array above
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+};
+
+namespace og {
+
+// thread-local last error
+void set_error(const char *fmt, ...);
+og_status cuda_fail(cudaError_t e, const char *what);
+
+// device scans (og_scan.cu); n elements, exclusive, total written to *d_total
+// when d_total != nullptr.  scratch must hold scan_scratch_bytes(n).
+size_t scan_scratch_bytes(int64_t n);
+void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total,
+                        void *scratch, cudaStream_t s);
+void scan_inclusive_max_u32(const uint32_t *in, uint32_t *out, int64_t n, void *scratch,
+                            cudaStream_t s);
+
+// radix sort of (key, value) pairs, stable, keys of `bits` significant bits
+size_t radix_sort_scratch_bytes(int64_t n);
+void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                      int64_t n, int bits, void *scratch, cudaStream_t s, bool *result_in_alt);
+
+// build stages (og_build.cu)
+og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass);
+
+// force (og_walk.cu)
+struct WalkParams {
+    int opening;       // OG_OPEN_BH / OG_OPEN_REL
+    bool split;        // erfc split and cutoff active
+    bool dump;         // keep lists
+    double th2;        // theta^2
+    double G;          // gravitational constant (relative test)
+    double alpha;      // relative-criterion tolerance
+    double s2;         // (L / 2^32)^2
+    float rc2;         // cutoff^2 in grid units (single precision)
+    unsigned long long rprune;  // prune threshold, squared grid units
+    float h;           // softening length, grid units
+    float inv_h;
+    float inv_2rs;     // 1 / (2 r_s), grid units
+    float out_scale;   // G (2^32/L)^2
+};
+og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted,
+                    float *acc_sorted, float *ms_out);
+WalkParams make_walk_params(const og_params &p, int opening, double theta);
+
+}  // namespace og

@@ -1,0 +1,159 @@
+// og_scan.cu -- device-wide prefix scans (tile reduce, scan of tile totals, downsweep).
+//
+// Tiles of 4096 elements: 512 threads x 8 consecutive items, staged through
+// shared memory so that global loads and stores stay coalesced.  Used for
+// compaction offsets (node ids, child offsets, group ids, run starts).
+#include "og_internal.h"
+
+namespace og {
+namespace {
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+struct OpSum {
+    static __device__ __forceinline__ uint32_t id() { return 0u; }
+    static __device__ __forceinline__ uint32_t op(uint32_t a, uint32_t b) { return a + b; }
+};
+struct OpMax {
+    static __device__ __forceinline__ uint32_t id() { return 0u; }
+    static __device__ __forceinline__ uint32_t op(uint32_t a, uint32_t b) { return a > b ? a : b; }
+};
+
+template <class Op>
+__device__ __forceinline__ uint32_t warp_inclusive(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v = Op::op(o, v);
+    }
+    return v;
+}
+
+// Block-wide scan of one value per thread.  Returns the exclusive prefix,
+// writes the block total to *total.  s_warp holds 32 words.
+template <class Op>
+__device__ uint32_t block_exclusive(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    uint32_t inc = warp_inclusive<Op>(v);
+    uint32_t exc_in_warp = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) exc_in_warp = Op::id();
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nwarps ? s_warp[lane] : Op::id();
+        uint32_t wi = warp_inclusive<Op>(w);
+        if (lane < nwarps) s_warp[lane] = wi;
+    }
+    __syncthreads();
+    uint32_t warp_pre = warp > 0 ? s_warp[warp - 1] : Op::id();
+    *total = s_warp[nwarps - 1];
+    __syncthreads();
+    return Op::op(warp_pre, exc_in_warp);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kScanThreads) k_tile_reduce(const uint32_t *__restrict__ in,
+                                                               int64_t n, uint32_t *tile_tot) {
+    __shared__ uint32_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t acc = Op::id();
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) acc = Op::op(acc, in[i]);
+    }
+    uint32_t tot;
+    block_exclusive<Op>(acc, s_warp, &tot);
+    if (threadIdx.x == 0) tile_tot[blockIdx.x] = tot;
+}
+
+// exclusive scan of the tile totals in one block, any number of tiles
+template <class Op>
+__global__ void __launch_bounds__(1024) k_tile_scan(uint32_t *tile_tot, int64_t ntiles,
+                                                    uint32_t *d_total) {
+    __shared__ uint32_t s_warp[32];
+    uint32_t carry = Op::id();
+    for (int64_t b = 0; b < ntiles; b += blockDim.x) {
+        int64_t i = b + threadIdx.x;
+        uint32_t v = i < ntiles ? tile_tot[i] : Op::id();
+        uint32_t tot;
+        uint32_t exc = block_exclusive<Op>(v, s_warp, &tot);
+        if (i < ntiles) tile_tot[i] = Op::op(carry, exc);
+        carry = Op::op(carry, tot);
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
+template <class Op, bool kExclusive>
+__global__ void __launch_bounds__(kScanThreads) k_tile_downsweep(const uint32_t *__restrict__ in,
+                                                                  uint32_t *out, int64_t n,
+                                                                  const uint32_t *tile_pre) {
+    __shared__ uint32_t s_items[kScanTile];
+    __shared__ uint32_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        s_items[k * kScanThreads + threadIdx.x] = i < n ? in[i] : Op::id();
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t acc = Op::id();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = s_items[threadIdx.x * kScanItems + k];
+        acc = Op::op(acc, v[k]);
+    }
+    uint32_t tot;
+    uint32_t r = Op::op(tile_pre[blockIdx.x], block_exclusive<Op>(acc, s_warp, &tot));
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (kExclusive) {
+            s_items[threadIdx.x * kScanItems + k] = r;
+            r = Op::op(r, v[k]);
+        } else {
+            r = Op::op(r, v[k]);
+            s_items[threadIdx.x * kScanItems + k] = r;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = s_items[k * kScanThreads + threadIdx.x];
+    }
+}
+
+template <class Op, bool kExclusive>
+void scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, void *scratch,
+               cudaStream_t s) {
+    if (n <= 0) {
+        if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s);
+        return;
+    }
+    int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    uint32_t *tile = static_cast<uint32_t *>(scratch);
+    k_tile_reduce<Op><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tile);
+    k_tile_scan<Op><<<1, 1024, 0, s>>>(tile, ntiles, d_total);
+    k_tile_downsweep<Op, kExclusive><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tile);
+}
+
+}  // namespace
+
+size_t scan_scratch_bytes(int64_t n) {
+    int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    return (size_t)(ntiles + 1) * sizeof(uint32_t) + 256;
+}
+
+void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total,
+                        void *scratch, cudaStream_t s) {
+    scan_impl<OpSum, true>(in, out, n, d_total, scratch, s);
+}
+
+void scan_inclusive_max_u32(const uint32_t *in, uint32_t *out, int64_t n, void *scratch,
+                            cudaStream_t s) {
+    scan_impl<OpMax, false>(in, out, n, nullptr, scratch, s);
+}
+
+}  // namespace og

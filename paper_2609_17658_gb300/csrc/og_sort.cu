@@ -1,0 +1,211 @@
+// og_sort.cu -- stable LSD radix sort of (63-bit Morton key, u32 index) pairs.
+//
+// The paper inserts particles "sequentially following their Peano-Hilbert
+// ordering" (Sect. 4.1.1); here the order is a Morton order produced by a
+// least-significant-digit radix sort, 8 bits per pass.  Each pass is
+//   1. upsweep:   per 4096-key tile, a 256-bin digit histogram (shared-memory
+//                 atomics, one sub-histogram per warp), stored digit-major;
+//   2. scan:      exclusive scan over (digit, tile) -> global offsets;
+//   3. downsweep: stable in-tile ranking with __match_any_sync (each warp owns
+//                 512 consecutive keys, 16 rounds of 32), keys staged in shared
+//                 memory in digit order, then written out so that runs of one
+//                 digit stay contiguous in global memory.
+// Passes whose digit is the same for every key (found from one histogram of
+// all passes) are skipped.
+#include "og_internal.h"
+
+namespace og {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;        // 4096 keys per tile
+constexpr int kPerWarp = 32 * kItems;           // 512 consecutive keys per warp
+constexpr int kRadix = 256;
+
+__global__ void __launch_bounds__(kThreads) k_upsweep(const uint64_t *__restrict__ keys, int64_t n,
+                                                      int shift, uint32_t *counts,
+                                                      int64_t ntiles) {
+    __shared__ uint32_t hist[kWarps][kRadix];
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&hist[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+#pragma unroll 4
+    for (int k = 0; k < kItems; ++k) {
+        int64_t i = base + (int64_t)k * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&hist[warp][(uint32_t)(keys[i] >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) tot += hist[w][threadIdx.x];
+    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = tot;
+}
+
+// histogram of all eight digit positions over all keys (to skip trivial passes)
+__global__ void __launch_bounds__(kThreads) k_all_digits(const uint64_t *__restrict__ keys,
+                                                         int64_t n, uint32_t *hist8) {
+    __shared__ uint32_t h[8][kRadix];
+    for (int i = threadIdx.x; i < 8 * kRadix; i += kThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) atomicAdd(&h[p][(uint32_t)(k >> (8 * p)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 8 * kRadix; i += kThreads) {
+        uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(&hist8[i], v);
+    }
+}
+
+struct DownSmem {
+    uint64_t keys[kTile];
+    uint32_t vals[kTile];
+    uint32_t wcnt[kWarps][kRadix];
+    uint32_t dstart[kRadix];
+    uint32_t gofs[kRadix];
+    uint32_t warp_tot[kWarps];
+};
+
+__global__ void __launch_bounds__(kThreads) k_downsweep(const uint64_t *__restrict__ kin,
+                                                        const uint32_t *__restrict__ vin,
+                                                        uint64_t *__restrict__ kout,
+                                                        uint32_t *__restrict__ vout, int64_t n,
+                                                        int shift, const uint32_t *offsets,
+                                                        int64_t ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DownSmem &S = *reinterpret_cast<DownSmem *>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&S.wcnt[0][0])[i] = 0;
+    __syncthreads();
+
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    uint64_t k[kItems];
+    uint32_t v[kItems];
+    uint32_t rank[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        int64_t i = base + warp * kPerWarp + r * 32 + lane;
+        bool valid = i < n;
+        k[r] = valid ? kin[i] : 0ull;
+        v[r] = valid ? vin[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        int64_t i = base + warp * kPerWarp + r * 32 + lane;
+        uint32_t d = (i < n) ? ((uint32_t)(k[r] >> shift) & 0xffu) : (uint32_t)kRadix;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        uint32_t before = (d < kRadix) ? S.wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (lane == leader && d < kRadix) S.wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    // per digit: exclusive offsets of the warps, then the digit's tile total
+    const int t = threadIdx.x;  // one thread per digit
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        uint32_t c = S.wcnt[w][t];
+        S.wcnt[w][t] = run;
+        run += c;
+    }
+    // block exclusive scan of the digit totals
+    uint32_t inc = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) S.warp_tot[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += S.warp_tot[w];
+    S.dstart[t] = wpre + inc - run;
+    S.gofs[t] = offsets[(int64_t)t * ntiles + blockIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        int64_t i = base + warp * kPerWarp + r * 32 + lane;
+        if (i < n) {
+            uint32_t d = (uint32_t)(k[r] >> shift) & 0xffu;
+            uint32_t pos = S.dstart[d] + S.wcnt[warp][d] + rank[r];
+            S.keys[pos] = k[r];
+            S.vals[pos] = v[r];
+        }
+    }
+    __syncthreads();
+    const int64_t cnt = (n - base) < kTile ? (n - base) : kTile;
+    for (int p = threadIdx.x; p < cnt; p += kThreads) {
+        uint64_t key = S.keys[p];
+        uint32_t d = (uint32_t)(key >> shift) & 0xffu;
+        uint32_t g = S.gofs[d] + ((uint32_t)p - S.dstart[d]);
+        kout[g] = key;
+        vout[g] = S.vals[p];
+    }
+}
+
+}  // namespace
+
+size_t radix_sort_scratch_bytes(int64_t n) {
+    int64_t ntiles = (n + kTile - 1) / kTile;
+    size_t counts = (size_t)kRadix * ntiles * sizeof(uint32_t);
+    return counts + scan_scratch_bytes((int64_t)kRadix * ntiles) + 8 * kRadix * sizeof(uint32_t) +
+           1024;
+}
+
+void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                      int64_t n, int bits, void *scratch, cudaStream_t s, bool *result_in_alt) {
+    *result_in_alt = false;
+    if (n <= 1) return;
+    int64_t ntiles = (n + kTile - 1) / kTile;
+    char *p = static_cast<char *>(scratch);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(p);
+    p += (size_t)kRadix * ntiles * sizeof(uint32_t);
+    uint32_t *hist8 = reinterpret_cast<uint32_t *>(p);
+    p += 8 * kRadix * sizeof(uint32_t);
+    void *scan_scratch = p;
+
+    // which passes are trivial (all keys share the digit)?
+    cudaMemsetAsync(hist8, 0, 8 * kRadix * sizeof(uint32_t), s);
+    int grid = (int)((n + kThreads * 16 - 1) / (kThreads * 16));
+    if (grid > 1184) grid = 1184;
+    k_all_digits<<<grid, kThreads, 0, s>>>(keys, n, hist8);
+    uint32_t h[8 * kRadix];
+    cudaMemcpyAsync(h, hist8, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(DownSmem));
+        attr_set = true;
+    }
+    uint64_t *kin = keys, *kout = keys_alt;
+    uint32_t *vin = vals, *vout = vals_alt;
+    int npasses = (bits + 7) / 8;
+    for (int pass = 0; pass < npasses; ++pass) {
+        bool trivial = false;
+        for (int d = 0; d < kRadix; ++d)
+            if (h[pass * kRadix + d] == (uint32_t)n) trivial = true;
+        if (trivial) continue;
+        int shift = 8 * pass;
+        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles);
+        scan_exclusive_u32(counts, counts, (int64_t)kRadix * ntiles, nullptr, scan_scratch, s);
+        k_downsweep<<<(unsigned)ntiles, kThreads, sizeof(DownSmem), s>>>(kin, vin, kout, vout, n,
+                                                                         shift, counts, ntiles);
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        uint32_t *tv = vin; vin = vout; vout = tv;
+    }
+    *result_in_alt = (kin == keys_alt);
+}
+
+}  // namespace og

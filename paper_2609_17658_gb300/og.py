@@ -1,0 +1,284 @@
+"""Thin ctypes binding of the C-ABI in include/og.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does no
+arithmetic of its own: arrays are checked for dtype/shape/contiguity, their
+pointers are passed through, and a negative status raises OGError with the
+library's message.  Host arrays are numpy; device arrays are torch CUDA
+tensors (the OG_DEVICE_PTRS flag is then set for the call).
+
+The shared library must have been built (``paper_2609_17658_gb300.build``);
+a missing library raises immediately -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OG_OK = 0
+OG_PENDING = 1
+OG_ERR_ARG = -1
+OG_ERR_OOM = -2
+OG_ERR_CUDA = -3
+OG_ERR_TIMEOUT = -4
+OG_ERR_BUDGET = -5
+OG_ERR_OVERFLOW = -6
+OG_ERR_STATE = -7
+
+OG_OPEN_BH = 0
+OG_OPEN_REL = 1
+OG_DEVICE_PTRS = 1
+OG_DEBUG_DUMP_LISTS = 2
+
+(OG_F_SKEY, OG_F_PERM, OG_F_SPOS, OG_F_LEVEL, OG_F_NBEG, OG_F_NEND, OG_F_PARENT, OG_F_CBEG,
+ OG_F_CCNT, OG_F_CHILD, OG_F_MASS, OG_F_COM, OG_F_NEXTNODE, OG_F_SIBLING, OG_F_PNEXT,
+ OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS) = range(19)
+
+
+class OGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"og status {status}: {msg}")
+        self.status = status
+
+
+class og_params(C.Structure):
+    _fields_ = [("box", C.c_double), ("G", C.c_double), ("eps", C.c_double),
+                ("r_s", C.c_double), ("rcut_over_rs", C.c_double), ("theta", C.c_double),
+                ("alpha", C.c_double), ("theta_first_pass", C.c_double),
+                ("opening", C.c_int32), ("leaf_max", C.c_int32), ("group_max", C.c_int32),
+                ("flags", C.c_int32)]
+
+
+class og_tree_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nodes", C.c_int64), ("children", C.c_int64),
+                ("groups", C.c_int64), ("list_entries", C.c_int64),
+                ("interactions", C.c_int64), ("interactions_last_pass", C.c_int64),
+                ("ms_build", C.c_double), ("ms_force", C.c_double), ("ms_walk", C.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libog.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run paper_2609_17658_gb300.build)")
+        L = C.CDLL(path)
+        P, i64, sz = C.c_void_p, C.c_int64, C.c_size_t
+        L.og_create.argtypes = [C.POINTER(P), C.c_int, sz]
+        L.og_destroy.argtypes = [P]
+        L.og_set_stream.argtypes = [P, P]
+        L.og_params_default.argtypes = [C.POINTER(og_params)]
+        L.og_tree_build.argtypes = [P, P, P, i64, C.POINTER(og_params), C.POINTER(P)]
+        L.og_tree_refit.argtypes = [P, P]
+        L.og_tree_force.argtypes = [P, P, P, P, P]
+        L.og_tree_info_get.argtypes = [P, C.POINTER(og_tree_info)]
+        L.og_tree_export.argtypes = [P, C.c_int, P, sz]
+        L.og_tree_free.argtypes = [P]
+        L.og_last_error.restype = C.c_char_p
+        for name in ("og_create", "og_destroy", "og_set_stream", "og_params_default",
+                     "og_tree_build", "og_tree_refit", "og_tree_force", "og_tree_info_get",
+                     "og_tree_export", "og_tree_free"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def og_last_error() -> str:
+    return lib().og_last_error().decode(errors="replace")
+
+
+def _check(st: int):
+    if st < 0:
+        raise OGError(st, og_last_error())
+    return st
+
+
+def params_from_dict(p: dict, flags: int = 0) -> og_params:
+    q = og_params()
+    _check(lib().og_params_default(C.byref(q)))
+    for k in ("box", "G", "eps", "r_s", "rcut_over_rs", "theta", "alpha", "theta_first_pass"):
+        if k in p:
+            setattr(q, k, float(p[k]))
+    for k in ("opening", "leaf_max", "group_max", "flags"):
+        if k in p:
+            setattr(q, k, int(p[k]))
+    q.flags = int(q.flags) | int(flags)
+    return q
+
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+def _host_ptr(a: np.ndarray, dtype, shape_tail=()):
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    if shape_tail and a.shape[1:] != shape_tail:
+        raise ValueError(f"expected shape (N, {shape_tail})")
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(t, dtype_name: str):
+    if str(t.dtype) != f"torch.{dtype_name}" or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous CUDA tensor of {dtype_name}")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---- C entry points -------------------------------------------------------
+
+def og_create(device: int = 0, hbm_budget_bytes: int = 0) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().og_create(C.byref(h), int(device), int(hbm_budget_bytes)))
+    return h
+
+
+def og_destroy(ctx) -> None:
+    _check(lib().og_destroy(ctx))
+
+
+def og_set_stream(ctx, stream_handle: int | None) -> None:
+    _check(lib().og_set_stream(ctx, C.c_void_p(stream_handle) if stream_handle else None))
+
+
+def og_tree_build(ctx, pos, mass, params: dict) -> C.c_void_p:
+    """pos: float64 [N,3], mass: float64 [N] (numpy host or torch CUDA)."""
+    dev = _is_torch_cuda(pos)
+    if dev:
+        pp, mp = _dev_ptr(pos, "float64"), _dev_ptr(mass, "float64")
+        n = int(pos.shape[0])
+    else:
+        pp, mp = _host_ptr(pos, np.float64, (3,)), _host_ptr(mass, np.float64)
+        n = int(pos.shape[0])
+    if int(mass.shape[0]) != n:
+        raise ValueError("mass and pos lengths differ")
+    prm = params_from_dict(params, OG_DEVICE_PTRS if dev else 0)
+    if not dev:
+        prm.flags = int(prm.flags) & ~OG_DEVICE_PTRS
+    h = C.c_void_p()
+    _check(lib().og_tree_build(ctx, pp, mp, n, C.byref(prm), C.byref(h)))
+    return h
+
+
+def og_tree_force(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
+    """Fill acc (float32 [N,3]) and optionally n_pp, n_pn (uint32 [N] / int32 CUDA)."""
+    if _is_torch_cuda(acc):
+        ap = _dev_ptr(acc, "float32")
+        op = None if a_old is None else _dev_ptr(a_old, "float32")
+        pp = None if n_pp is None else _dev_ptr(n_pp, "int32")
+        np_ = None if n_pn is None else _dev_ptr(n_pn, "int32")
+    else:
+        ap = _host_ptr(acc, np.float32, (3,))
+        op = None if a_old is None else _host_ptr(a_old, np.float32, (3,))
+        pp = None if n_pp is None else _host_ptr(n_pp, np.uint32)
+        np_ = None if n_pn is None else _host_ptr(n_pn, np.uint32)
+    _check(lib().og_tree_force(tree, op, ap, pp, np_))
+
+
+def og_tree_info_get(tree) -> dict:
+    info = og_tree_info()
+    _check(lib().og_tree_info_get(tree, C.byref(info)))
+    return {k: getattr(info, k) for k, _ in og_tree_info._fields_}
+
+
+_FIELD_SPEC = {
+    OG_F_SKEY: ("n", np.uint64, ()), OG_F_PERM: ("n", np.uint32, ()),
+    OG_F_SPOS: ("n", np.uint32, "3n"), OG_F_LEVEL: ("nodes", np.uint8, ()),
+    OG_F_NBEG: ("nodes", np.uint32, ()), OG_F_NEND: ("nodes", np.uint32, ()),
+    OG_F_PARENT: ("nodes", np.int32, ()), OG_F_CBEG: ("nodes", np.uint32, ()),
+    OG_F_CCNT: ("nodes", np.uint32, ()), OG_F_CHILD: ("children", np.uint32, ()),
+    OG_F_MASS: ("nodes", np.float64, ()), OG_F_COM: ("nodes", np.uint32, (3,)),
+    OG_F_NEXTNODE: ("nodes", np.int32, ()), OG_F_SIBLING: ("nodes", np.int32, ()),
+    OG_F_PNEXT: ("n", np.int32, ()), OG_F_GBEG: ("groups", np.uint32, ()),
+    OG_F_GEND: ("groups", np.uint32, ()), OG_F_GBOX: ("groups", np.uint32, (6,)),
+    OG_F_LISTS: ("list_entries", np.uint32, (2,)),
+}
+
+
+def og_tree_export(tree, field: int) -> np.ndarray:
+    info = og_tree_info_get(tree)
+    key, dt, tail = _FIELD_SPEC[field]
+    cnt = int(info[key])
+    if tail == "3n":
+        out = np.zeros((3, cnt), dtype=dt)
+    else:
+        out = np.zeros((cnt,) + tuple(tail), dtype=dt)
+    _check(lib().og_tree_export(tree, int(field), out.ctypes.data_as(C.c_void_p), out.nbytes))
+    return out
+
+
+def og_tree_free(tree) -> None:
+    _check(lib().og_tree_free(tree))
+
+
+def og_tree_refit(tree, pos) -> None:
+    pp = _dev_ptr(pos, "float64") if _is_torch_cuda(pos) else _host_ptr(pos, np.float64, (3,))
+    _check(lib().og_tree_refit(tree, pp))
+
+
+# ---- convenience wrappers -------------------------------------------------
+
+class Context:
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.h = og_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.h is not None:
+            og_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tree:
+    """One system's device-resident tree (og_tree_build / og_tree_force)."""
+
+    def __init__(self, ctx: Context, pos, mass, params: dict):
+        self.ctx = ctx
+        self.n = int(pos.shape[0])
+        self.h = og_tree_build(ctx.h, pos, mass, params)
+
+    def force(self, a_old=None, counts: bool = True):
+        acc = np.zeros((self.n, 3), dtype=np.float32)
+        npp = np.zeros(self.n, dtype=np.uint32) if counts else None
+        npn = np.zeros(self.n, dtype=np.uint32) if counts else None
+        ao = None if a_old is None else np.ascontiguousarray(a_old, dtype=np.float32)
+        og_tree_force(self.h, acc, ao, npp, npn)
+        return acc, npp, npn
+
+    def info(self) -> dict:
+        return og_tree_info_get(self.h)
+
+    def export(self, field: int) -> np.ndarray:
+        return og_tree_export(self.h, field)
+
+    def free(self):
+        if self.h is not None:
+            og_tree_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
