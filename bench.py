@@ -1,0 +1,317 @@
+"""Benchmark of the short-range TreePM tree force on GB300.
+
+One step = the whole hot path on one system: fixed point + Morton keys, radix
+sort, octree topology + threading, moments, groups, the Barnes-Hut first pass
+and the relative-criterion pass of the walk, and the reordering of the
+accelerations to the caller's order.  Default workload: 2,097,152 particles,
+70 % in 2000 NFW haloes + 30 % uniform, eps = 1/6400, r_s = 1.25/256,
+cutoff 4.5 r_s, relative opening alpha = 0.005 after a BH theta = 0.5 pass.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With torchrun each rank runs its own system
+(a different seed; the path has no exchange step), so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import og_inputs as gi  # noqa: E402
+
+METRIC = "tree-force particles/s & interactions/s at 2.1M; served p50/p99 latency"
+UNIT = "particles/s"
+# Algorithmic FP32 work of one interaction in the walk's evaluation loop (the
+# instruction mix of eval_chunk, counting an FMA as 2 flops and a
+# multi-function unit op or a conversion as 1): see the design notes.
+FLOPS_PER_INTERACTION = 38
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clustered-2m")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.idx = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(pos, mass, prm, budget_s=20.0):
+    """The FP64 oracle on the host cores: full tree build plus the walk of a
+    bounded sample of groups, extrapolated to the whole system."""
+    import oracle
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ot = oracle.Tree(pos, mass, prm)
+    t_build = time.perf_counter() - t0
+    ng = ot.ngroups
+    gb, ge = ot.get(oracle.F_GBEG), ot.get(oracle.F_GEND)
+    r = np.random.default_rng(1)
+    k = 64
+    done_groups, targets, t_force = 0, 0, 0.0
+    order = r.permutation(ng)
+    while t_force < budget_s * 0.5 and done_groups < ng:
+        sel = np.sort(order[done_groups:done_groups + k])
+        t0 = time.perf_counter()
+        a1, _, _ = ot.force(opening=gi.OPEN_BH, theta=prm["theta_first_pass"], groups=sel,
+                            nthreads=nthreads)
+        if prm["opening"] == gi.OPEN_REL:
+            a_old = np.nan_to_num(a1).astype(np.float32)
+            ot.force(opening=gi.OPEN_REL, a_old=a_old, groups=sel, nthreads=nthreads)
+        t_force += time.perf_counter() - t0
+        done_groups += len(sel)
+        targets += int((ge[sel] - gb[sel]).sum())
+        k *= 2
+    n = len(mass)
+    t_total = t_build + t_force * (n / max(targets, 1))
+    return {"value": n / t_total, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"full FP64 tree build of all {n} particles ({t_build:.2f} s) + both walk "
+                      f"passes for {targets} targets in {done_groups} random groups "
+                      f"({t_force:.2f} s), force time scaled to all {n} targets"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle (the paper's method as the CPU program
+    of this repository) timed on the host cores, each step a bounded sample."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    pos, mass, prm = gi.config(args.workload)
+    vals = []
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(pos, mass, prm, budget_s=8.0)
+        if s >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": len(mass) / v * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"{args.workload}: N={len(mass)}", "l2": "n/a (CPU)"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                            "sample": cb["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    from paper_2609_17658_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_2609_17658_gb300 import og
+
+    pos, mass, prm = gi.config(args.workload, seed=12346 + 1000 * rank)
+    n = len(mass)
+    dev = torch.device(f"cuda:{local}")
+    stream = torch.cuda.current_stream(dev)
+    ctx = og.Context(local)
+    og.og_set_stream(ctx.h, stream.cuda_stream)
+    dpos = torch.from_numpy(pos).to(dev)
+    dmass = torch.from_numpy(mass).to(dev)
+    acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    npp = torch.empty(n, dtype=torch.int32, device=dev)
+    npn = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        h = og.og_tree_build(ctx.h, dpos, dmass, prm)
+        og.og_tree_force(h, acc, None, npp, npn)
+        info = og.og_tree_info_get(h)
+        og.og_tree_free(h)
+        return info
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    gpu_id = f"GPU-{uuid}" if uuid is not None else os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.3)
+    ms_steps, ms_walk, inter, ms_build = [], [], [], []
+    launches0 = og.og_kernel_launches()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_steps.append(e0.elapsed_time(e1))
+        ms_walk.append(info["ms_walk"])
+        ms_build.append(info["ms_build"])
+        inter.append(info["interactions"])
+    launches = og.og_kernel_launches() - launches0
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    total_ms = float(sum(ms_steps))
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * n / (ms_per_step * 1e-3)
+    inter_step = float(np.mean(inter))
+    walk_ms = float(np.mean(ms_walk))
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        # pinned host buffers, as a serving process would keep them
+        h_pos = torch.from_numpy(pos).pin_memory().numpy()
+        h_mass = torch.from_numpy(mass).pin_memory().numpy()
+        h_acc = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+        h_pp = torch.empty(n, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        h_pn = torch.empty(n, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        og.og_set_stream(ctx.h, None)
+        ts = []
+        for k in range(max(2, args.steps) + 1):
+            t0 = time.perf_counter()
+            h = og.og_tree_build(ctx.h, h_pos, h_mass, prm)
+            og.og_tree_force(h, h_acc, None, h_pp, h_pn)
+            og.og_tree_free(h)
+            if k > 0:
+                ts.append(time.perf_counter() - t0)
+        og.og_set_stream(ctx.h, stream.cuda_stream)
+        e2e = {"value": n / statistics.median(ts), "unit": UNIT,
+               "h2d_bytes_per_step": int(pos.nbytes + mass.nbytes),
+               "d2h_bytes_per_step": int(h_acc.nbytes + h_pp.nbytes + h_pn.nbytes)}
+        if ws > 1:
+            e2e["value"] *= ws
+
+    # roofline of the dominant kernel (the walk): FP32 ALU bound
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    achieved = inter_step * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_walk (both passes)",
+            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
+            "frac_at_observed_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 *
+                                                   clocks["sm_mhz"] * 1e6 / 1e12)
+                                       if clocks.get("sm_mhz") else None)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(pos, mass, prm)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+               "data": "synthetic",
+               "config": {"workload": f"{args.workload}: N={n} per GPU, 70% in 2000 NFW haloes "
+                                      f"+ 30% uniform, eps=1/6400, r_s=1.25/256, cutoff 4.5 r_s, "
+                                      f"relative alpha=0.005 after BH theta=0.5",
+                          "l2": "flushed between steps (256 MB write)"},
+               "interactions_per_s": ws * inter_step / (ms_per_step * 1e-3),
+               "interactions_per_step": inter_step,
+               "walk_ms_per_step": walk_ms,
+               "build_ms_per_step": float(np.mean(ms_build)),
+               "walk_interactions_per_s": inter_step / (walk_ms * 1e-3),
+               "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+               "roofline": roof, "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

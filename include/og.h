@@ -167,6 +167,10 @@ og_status og_tree_free(og_tree *t);
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *og_last_error(void);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (for benchmarks that count their own launches in a timed region). */
+int64_t og_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -496,7 +496,7 @@ static size_t tree_bytes(int64_t n, bool alloc) {
     add(4, m); add(4, m); add(4, m); add(8, m); add(8, 3 * m); add(4, 3 * m);       // npar.. ncom
     add(4, n); add(4, n);                                                           // pnext, owner
     add(4, c); add(32, c);                                                          // child, crec
-    add(4, n); add(4, n); add(4, 6 * n);                                            // groups
+    add(4, n); add(4, n); add(4, 6 * n); add(4, n); add(4, n);                      // groups
     add(4, 3 * n); add(4, 3 * n); add(4, n); add(4, n);                             // force arrays
     return b + 4096;
 }
@@ -543,6 +543,8 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     t->gbeg = A.take<uint32_t>(n);
     t->gend = A.take<uint32_t>(n);
     t->gbox = A.take<uint32_t>(6 * n);
+    t->gcost = A.take<uint32_t>(n);
+    t->gorder = A.take<uint32_t>(n);
     t->a_sorted = A.take<float>(3 * n);
     t->a_old_sorted = A.take<float>(3 * n);
     t->npp_sorted = A.take<uint32_t>(n);
@@ -587,7 +589,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     cudaEventRecord(e0, s);
 
     // a1, a2
-    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, d_mass, n, p.box, qx, qy, qz, keys, idx, status);
+    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, d_mass, n, p.box, qx, qy, qz, keys, idx, status); note_launch();
     // a3
     bool in_alt = false;
     radix_sort_pairs(keys, idx, keys_alt, idx_alt, n, 63, sort_scratch, s, &in_alt);
@@ -596,13 +598,13 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     cudaMemcpyAsync(t->skey, skey_src, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
     k_permute<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, d_mass, t->px, t->py, t->pz, t->pm32,
-                                     t->pm64);
+                                     t->pm64); note_launch();
     // a4: nodes from splits
     uint32_t h_tot[4] = {0, 0, 0, 0};
     int64_t nsplit = n - 1;
     if (nsplit > 0) {
-        k_split_levels<<<nblk(nsplit), kT, 0, s>>>(t->skey, n, lv);
-        k_split_nodes<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, n, sbeg, send, first);
+        k_split_levels<<<nblk(nsplit), kT, 0, s>>>(t->skey, n, lv); note_launch();
+        k_split_nodes<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, n, sbeg, send, first); note_launch();
         scan_exclusive_u32(first, nid, nsplit, d_tot, scan_scratch, s);
         cudaMemcpyAsync(h_tot, d_tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if ((err = cudaStreamSynchronize(s)) != cudaSuccess) {
@@ -613,34 +615,34 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     const int64_t m = 1 + (int64_t)h_tot[0];
     t->nnodes = m;
     k_node_init<<<nblk(nsplit > 0 ? nsplit : 1), kT, 0, s>>>(n, first, nid, lv, sbeg, send, t->nlev,
-                                                             t->nbeg, t->nend);
+                                                             t->nbeg, t->nend); note_launch();
     if (nsplit > 0)
-        k_split_node_id<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, sbeg, first, nid, n, sid);
+        k_split_node_id<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, sbeg, first, nid, n, sid); note_launch();
     cudaMemsetAsync(occ, 0, m * sizeof(uint32_t), s);
     cudaMemsetAsync(nnc, 0, m * sizeof(uint32_t), s);
     cudaMemsetAsync(arrive, 0, m * sizeof(uint32_t), s);
     k_link<<<nblk(n + m), kT, 0, s>>>(n, m, t->skey, lv, sid, t->nlev, t->nbeg, t->nend, t->npar,
-                                      t->owner, occ, nnc, status);
-    k_ccnt<<<nblk(m), kT, 0, s>>>(m, t->nlev, t->nbeg, t->nend, occ, t->nccnt);
+                                      t->owner, occ, nnc, status); note_launch();
+    k_ccnt<<<nblk(m), kT, 0, s>>>(m, t->nlev, t->nbeg, t->nend, occ, t->nccnt); note_launch();
     scan_exclusive_u32(t->nccnt, t->ncbeg, m, d_tot + 1, scan_scratch, s);
     const int64_t nchild = (n - 1) + m;
     t->nchild = nchild;
     k_place<<<nblk(n + m), kT, 0, s>>>(n, m, t->skey, t->nlev, t->nbeg, t->ncbeg, occ, t->npar,
-                                       t->owner, t->child, t->npos, nchild, status);
+                                       t->owner, t->child, t->npos, nchild, status); note_launch();
     k_threading<<<nblk(nchild), kT, 0, s>>>(n, m, nchild, t->child, t->ncbeg, t->nccnt, t->npar,
-                                            t->npos, t->owner, t->nnext, t->nsib, t->pnext, status);
+                                            t->npos, t->owner, t->nnext, t->nsib, t->pnext, status); note_launch();
     // a5
     k_moments<<<nblk(8 * m), kT, 0, s>>>(n, m, t->nlev, t->nbeg, t->nend, t->ncbeg, occ, t->child,
                                          t->npar, nnc, arrive, t->px, t->py, t->pz, t->pm64, t->nM,
-                                         t->nS, t->ncom, nchild, status);
+                                         t->nS, t->ncom, nchild, status); note_launch();
     // a6: groups
     const int G = p.group_max;
-    k_frontier<<<nblk(n), kT, 0, s>>>(n, G, t->owner, t->npar, t->nbeg, t->nend, fp);
-    k_runmark<<<nblk(n), kT, 0, s>>>(n, fp, rs);
+    k_frontier<<<nblk(n), kT, 0, s>>>(n, G, t->owner, t->npar, t->nbeg, t->nend, fp); note_launch();
+    k_runmark<<<nblk(n), kT, 0, s>>>(n, fp, rs); note_launch();
     scan_inclusive_max_u32(rs, rs, n, scan_scratch, s);
-    k_groupmark<<<nblk(n), kT, 0, s>>>(n, G, rs, gs);
+    k_groupmark<<<nblk(n), kT, 0, s>>>(n, G, rs, gs); note_launch();
     scan_exclusive_u32(gs, gid, n, d_tot + 2, scan_scratch, s);
-    k_group_init<<<nblk(n), kT, 0, s>>>(n, gs, gid, t->gbeg);
+    k_group_init<<<nblk(n), kT, 0, s>>>(n, gs, gid, t->gbeg); note_launch();
     cudaMemcpyAsync(h_tot + 1, d_tot + 1, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) {
         cudaFreeAsync(scratch, s);
@@ -653,10 +655,10 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     }
     t->ngroups = h_tot[2];
     k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
-                                                t->pz, t->gbox);
+                                                t->pz, t->gbox); note_launch();
     k_records<<<nblk(nchild), kT, 0, s>>>(n, nchild, t->child, t->px, t->py, t->pz, t->pm32,
                                           t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nM, t->ncom,
-                                          t->crec);
+                                          t->crec); note_launch();
     cudaEventRecord(e1, s);
     cudaFreeAsync(scratch, s);
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "build");

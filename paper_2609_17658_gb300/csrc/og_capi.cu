@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "og_internal.h"
@@ -17,6 +18,9 @@
 namespace og {
 
 static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -110,6 +114,8 @@ using namespace og;
 extern "C" {
 
 const char *og_last_error(void) { return g_err; }
+
+int64_t og_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 og_status og_params_default(og_params *p) {
     if (!p) return OG_ERR_ARG;
@@ -260,12 +266,12 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
                 cudaMemcpyAsync(tmp, a_old, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
                 d_aold = static_cast<const float *>(tmp);
             }
-            k_gather_aold<<<nblk(n), kT, 0, s>>>(n, t->perm, d_aold, t->a_old_sorted);
+            k_gather_aold<<<nblk(n), kT, 0, s>>>(n, t->perm, d_aold, t->a_old_sorted); note_launch();
         } else {
             // first pass: Barnes-Hut with theta_first_pass
             WalkParams w1 = make_walk_params(t->prm, OG_OPEN_BH, t->prm.theta_first_pass);
             w1.dump = false;
-            og_status st = walk_pass(t, w1, nullptr, t->a_old_sorted, &ms);
+            og_status st = walk_pass(t, w1, nullptr, t->a_old_sorted, &ms, false);
             if (st) return st;
             ms_walk += ms;
         }
@@ -273,7 +279,7 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
     }
     WalkParams w = make_walk_params(t->prm, t->prm.opening, t->prm.theta);
     int64_t inter_before = t->interactions;
-    og_status st = walk_pass(t, w, a_old_sorted, t->a_sorted, &ms);
+    og_status st = walk_pass(t, w, a_old_sorted, t->a_sorted, &ms, true);
     if (tmp) cudaFreeAsync(tmp, s);
     if (st) return st;
     (void)inter_before;
@@ -290,7 +296,7 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
         d_npn = n_pn ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) + n : nullptr;
     }
     k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
-                                       d_acc, d_npp, d_npn);
+                                       d_acc, d_npp, d_npn); note_launch();
     if (!dev) {
         cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
         if (n_pp) cudaMemcpyAsync(n_pp, d_npp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);

@@ -75,6 +75,9 @@ struct og_tree {
     og::CRec *crec = nullptr;
     // groups
     uint32_t *gbeg = nullptr, *gend = nullptr, *gbox = nullptr;
+    uint32_t *gcost = nullptr;        // list length of each group in the last walk pass
+    uint32_t *gorder = nullptr;       // groups by decreasing cost
+    bool have_cost = false;
     // force work arrays (sorted order)
     float *a_sorted = nullptr;        // last pass accelerations, [3][n]
     float *a_old_sorted = nullptr;    // previous accelerations, [3][n]
@@ -94,6 +97,8 @@ namespace og {
 
 // thread-local last error
 void set_error(const char *fmt, ...);
+// count of kernels launched by this library in this process
+void note_launch();
 og_status cuda_fail(cudaError_t e, const char *what);
 
 // device scans (og_scan.cu); n elements, exclusive, total written to *d_total
@@ -118,18 +123,24 @@ struct WalkParams {
     bool split;        // erfc split and cutoff active
     bool dump;         // keep lists
     double th2;        // theta^2
+    float th2f;        // theta^2 in single precision (opening filter)
     double G;          // gravitational constant (relative test)
+    float Gf;
     double alpha;      // relative-criterion tolerance
     double s2;         // (L / 2^32)^2
     float rc2;         // cutoff^2 in grid units (single precision)
     unsigned long long rprune;  // prune threshold, squared grid units
+    unsigned long long hnear2;  // entries closer than this (squared grid units) may need softening
     float h;           // softening length, grid units
     float inv_h;
     float inv_2rs;     // 1 / (2 r_s), grid units
+    float kexp;        // -log2(e) / (4 r_s^2), grid units
     float out_scale;   // G (2^32/L)^2
 };
+// One walk launch over all groups.  use_order: take the groups longest list
+// first, by the list lengths of the previous pass on this tree (if any).
 og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted,
-                    float *acc_sorted, float *ms_out);
+                    float *acc_sorted, float *ms_out, bool use_order);
 WalkParams make_walk_params(const og_params &p, int opening, double theta);
 
 }  // namespace og

@@ -134,9 +134,9 @@ void scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, 
     }
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     uint32_t *tile = static_cast<uint32_t *>(scratch);
-    k_tile_reduce<Op><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tile);
-    k_tile_scan<Op><<<1, 1024, 0, s>>>(tile, ntiles, d_total);
-    k_tile_downsweep<Op, kExclusive><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tile);
+    k_tile_reduce<Op><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tile); note_launch();
+    k_tile_scan<Op><<<1, 1024, 0, s>>>(tile, ntiles, d_total); note_launch();
+    k_tile_downsweep<Op, kExclusive><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tile); note_launch();
 }
 
 }  // namespace

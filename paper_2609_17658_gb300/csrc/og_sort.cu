@@ -178,7 +178,7 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     cudaMemsetAsync(hist8, 0, 8 * kRadix * sizeof(uint32_t), s);
     int grid = (int)((n + kThreads * 16 - 1) / (kThreads * 16));
     if (grid > 1184) grid = 1184;
-    k_all_digits<<<grid, kThreads, 0, s>>>(keys, n, hist8);
+    k_all_digits<<<grid, kThreads, 0, s>>>(keys, n, hist8); note_launch();
     uint32_t h[8 * kRadix];
     cudaMemcpyAsync(h, hist8, sizeof(h), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
@@ -198,10 +198,10 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
             if (h[pass * kRadix + d] == (uint32_t)n) trivial = true;
         if (trivial) continue;
         int shift = 8 * pass;
-        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles);
+        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles); note_launch();
         scan_exclusive_u32(counts, counts, (int64_t)kRadix * ntiles, nullptr, scan_scratch, s);
         k_downsweep<<<(unsigned)ntiles, kThreads, sizeof(DownSmem), s>>>(kin, vin, kout, vout, n,
-                                                                         shift, counts, ntiles);
+                                                                         shift, counts, ntiles); note_launch();
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
     }

@@ -3,8 +3,7 @@
 // The paper walks the tree once per target particle with a threaded
 // (nextnode / sibling) loop and, on GPUs, processes neighbours in chunks of
 // 32.  Here one warp walks the tree once for a whole group of up to 32
-// spatially close targets (one target per lane) and shares the resulting
-// interaction list:
+// spatially close targets and shares the resulting interaction list:
 //
 //   list building   the warp keeps a stack of child-array ranges of opened
 //                   nodes in shared memory.  Each round the 32 lanes take the
@@ -13,19 +12,27 @@
 //                   integer bounding box:
 //                     particle -> PP entry unless beyond the prune distance;
 //                     node     -> pruned, opened (range pushed), or PN entry.
-//                   The prune test is exact integer geometry; the boundary
-//                   check is an exact integer test; the Barnes-Hut / relative
-//                   opening test is FP64 with a fixed operation order and no
-//                   fused operations, so the lists equal the oracle's.
-//   evaluation      accepted entries (x, y, z, m) are appended to a shared
-//                   chunk; when it fills, every lane evaluates the chunk for
-//                   its target: exact int32 minimum-image separation, converted
-//                   to FP32, r^2 by FMA, cutoff, rsqrt, spline softening inside
-//                   h, erfc split factor, FP32 accumulation over the chunk, then
-//                   a compensated (Kahan) add of the chunk sum into the totals.
+//                   Prune and boundary tests are exact integer geometry.  The
+//                   Barnes-Hut / relative test is decided in FP32 when the
+//                   FP32 value is farther from the threshold than its proven
+//                   error bound, and otherwise by the exact FP64 expression
+//                   (fixed operation order, no fused operations), so every
+//                   decision equals the FP64 decision of the oracle.
+//   evaluation      entries (x, y, z, m) go to one of two shared-memory chunks:
+//                   "far" entries (integer distance from the group box >= h,
+//                   so no target can need the softened kernel) and "near"
+//                   entries.  A full chunk is evaluated by every lane for its
+//                   target: exact int32 minimum-image separation, converted to
+//                   FP32, r^2 by FMA, cutoff, rsqrt, erfc split factor, spline
+//                   softening for near entries only, FP32 accumulation over the
+//                   chunk, then a compensated (Kahan) add into the totals.
+//                   Groups of at most 16 (8) targets replicate each target on
+//                   2 (4) lanes that split the chunk's entries; the replicas'
+//                   totals are added in a fixed order at the end.
 //
-// Work distribution: persistent blocks, warps take groups from a global
-// atomic counter (groups in clustered regions cost far more than others).
+// Work distribution: persistent blocks; warps take groups from a global
+// atomic counter, in decreasing order of the previous pass's list length
+// when that is known (longest first shortens the tail of the launch).
 #include "og_internal.h"
 
 namespace og {
@@ -33,7 +40,8 @@ namespace {
 
 constexpr int kWarps = 4;          // warps per block
 constexpr int kStackCap = 768;     // ranges per warp stack
-constexpr int kChunk = 256;        // entries per shared chunk
+constexpr int kChunk = 256;        // far entries per shared chunk
+constexpr int kNearChunk = 64;     // near entries per shared chunk
 
 // Abramowitz & Stegun 7.1.26: erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
 // t = 1 / (1 + p x), |error| <= 1.5e-7 for x >= 0.
@@ -42,9 +50,16 @@ constexpr float kAs1 = 0.254829592f, kAs2 = -0.284496736f, kAs3 = 1.421413741f;
 constexpr float kAs4 = -1.453152027f, kAs5 = 1.061405429f;
 constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 
+// relative margin of the FP32 opening filter (the FP32 evaluation errs by
+// less than 2^-20; inside this band the FP64 expression decides)
+constexpr float kFilterHi = 1.0f + 1.0f / 65536.0f;
+constexpr float kFilterLo = 1.0f - 1.0f / 65536.0f;
+
 struct WalkArgs {
     int64_t n, ngroups;
     const uint32_t *gbeg, *gend, *gbox;
+    const uint32_t *gorder;       // processing order of the groups, or null (key order)
+    uint32_t *gcost;              // out: list length per group
     const CRec *crec;
     int64_t nchild, max_rounds;
     uint32_t root_cbeg, root_ccnt;
@@ -60,6 +75,24 @@ struct WalkArgs {
     uint32_t *status;
     WalkParams p;
 };
+
+// multi-function-unit approximations (PTX .approx with flush-to-zero); the
+// operands here are never subnormal: r^2 >= 1 in grid units, see eval_chunk
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 __device__ __forceinline__ uint32_t point_gap(uint32_t c, uint32_t lo, uint32_t hi) {
     if (c >= lo && c <= hi) return 0u;
@@ -77,41 +110,50 @@ __device__ __forceinline__ unsigned long long sq64(uint32_t g) {
     return (unsigned long long)g * (unsigned long long)g;
 }
 
-template <bool kSplit>
-__device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, uint32_t xi, uint32_t yi,
-                                           uint32_t zi, const WalkParams &p, float &ax, float &ay,
-                                           float &az) {
-    const float rc2 = p.rc2, h = p.h, inv_h = p.inv_h, inv_2rs = p.inv_2rs;
+// Chunk evaluation for one target per lane.  Entries e = rep, rep + R, ...
+// are this lane's share.  r^2 is guarded from below by 1 (a nonzero integer
+// separation has r^2 >= 1 in grid units); a zero separation then contributes
+// f * 0 = 0 exactly, the self term included.
+template <bool kSplit, bool kNear>
+__device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, int R, uint32_t xi,
+                                           uint32_t yi, uint32_t zi, const WalkParams &p,
+                                           float &ax, float &ay, float &az) {
+    const float rc2 = p.rc2, inv_2rs = p.inv_2rs, kexp = p.kexp;
+    const float h = p.h, inv_h = p.inv_h;
     const float hinv3 = inv_h * inv_h * inv_h;
 #pragma unroll 4
-    for (int e = 0; e < cnt; ++e) {
+    for (int e = rep; e < cnt; e += R) {
         const uint4 s = ch[e];
-        const float fx = __int2float_rn((int)(s.x - xi));
-        const float fy = __int2float_rn((int)(s.y - yi));
-        const float fz = __int2float_rn((int)(s.z - zi));
+        const float fx = (float)(int)(s.x - xi);
+        const float fy = (float)(int)(s.y - yi);
+        const float fz = (float)(int)(s.z - zi);
         const float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, __fmul_rn(fz, fz)));
-        const bool in = (r2 > 0.0f) && (r2 < rc2);
-        const float rinv = rsqrtf(r2);
-        const float r = r2 * rinv;
-        float g = rinv * rinv * rinv;
-        if (r < h) {
-            const float u = r * inv_h;
-            const float u2 = u * u;
-            if (u < 0.5f)
-                g = hinv3 * (32.0f / 3.0f + u2 * (32.0f * u - 192.0f / 5.0f));
-            else
-                g = hinv3 * (64.0f / 3.0f - 48.0f * u + 192.0f / 5.0f * u2 -
-                             32.0f / 3.0f * u2 * u - (1.0f / 15.0f) / (u2 * u));
-        }
-        float S = 1.0f;
+        float m = __uint_as_float(s.w);
+        if (kSplit) m = (r2 < rc2) ? m : 0.0f;
+        const float r2c = fmaxf(r2, 1.0f);
+        const float rinv = rsqrt_ftz(r2c);
+        float mS = m;
+        float r = 0.0f;
+        if (kSplit || kNear) r = r2c * rinv;
         if (kSplit) {
             const float us = r * inv_2rs;
-            const float t = __fdividef(1.0f, fmaf(kAsP, us, 1.0f));
+            const float t = rcp_ftz(fmaf(kAsP, us, 1.0f));
             const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, kAs5, kAs4), kAs3), kAs2), kAs1);
-            const float ex = __expf(-us * us);
-            S = ex * fmaf(kTwoOverSqrtPi, us, poly);
+            const float ex = ex2_ftz(r2c * kexp);
+            mS = m * (ex * fmaf(kTwoOverSqrtPi, us, poly));
         }
-        const float f = in ? __uint_as_float(s.w) * g * S : 0.0f;
+        float g = rinv * rinv * rinv;
+        if (kNear) {
+            // cubic-spline softened kernel inside h (Monaghan 1985 form)
+            const float u = r * inv_h;
+            const float u2 = u * u;
+            const float gin = hinv3 * fmaf(u2, fmaf(32.0f, u, -192.0f / 5.0f), 32.0f / 3.0f);
+            const float gout = hinv3 * (fmaf(u, fmaf(u, fmaf(u, -32.0f / 3.0f, 192.0f / 5.0f), -48.0f),
+                                             64.0f / 3.0f) -
+                                        (1.0f / 15.0f) * rcp_ftz(u2 * u));
+            g = (r < h) ? ((u < 0.5f) ? gin : gout) : g;
+        }
+        const float f = mS * g;
         ax = fmaf(f, fx, ax);
         ay = fmaf(f, fy, ay);
         az = fmaf(f, fz, az);
@@ -125,12 +167,54 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
     sum = t;
 }
 
+struct Acc {
+    float sx = 0.f, sy = 0.f, sz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+    __device__ __forceinline__ void add(float tx, float ty, float tz) {
+        kahan_add(sx, kx, tx);
+        kahan_add(sy, ky, ty);
+        kahan_add(sz, kz, tz);
+    }
+};
+
+// Barnes-Hut: open iff l2 > th2 * d2 with d2 = (dx*dx + dy*dy) + dz*dz in FP64.
+__device__ __forceinline__ bool open_bh(uint32_t gx, uint32_t gy, uint32_t gz, float l2f,
+                                        double l2, const WalkParams &p) {
+    const float fx = (float)gx, fy = (float)gy, fz = (float)gz;
+    const float d2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+    const float q = p.th2f * d2f;
+    if (l2f > q * kFilterHi) return true;
+    if (l2f < q * kFilterLo) return false;
+    const double dx = (double)gx, dy = (double)gy, dz = (double)gz;
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return l2 > __dmul_rn(p.th2, d2);
+}
+
+// relative: open iff (G M) l2 > arel (d2 d2), arel = (alpha a_min) s^2, in FP64.
+__device__ __forceinline__ bool open_rel(uint32_t gx, uint32_t gy, uint32_t gz, float l2f,
+                                         double l2, float Mf, double M, float arelf, double arel,
+                                         const WalkParams &p) {
+    const float fx = (float)gx, fy = (float)gy, fz = (float)gz;
+    const float d2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+    const float lhs = (p.Gf * Mf) * l2f;
+    const float rhs = (arelf * d2f) * d2f;
+    const bool normal = lhs >= 1e-30f && lhs <= 1e30f && rhs >= 1e-30f && rhs <= 1e30f;
+    if (normal) {
+        if (lhs > rhs * kFilterHi) return true;
+        if (lhs < rhs * kFilterLo) return false;
+    }
+    const double dx = (double)gx, dy = (double)gy, dz = (double)gz;
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return __dmul_rn(__dmul_rn(p.G, M), l2) > __dmul_rn(arel, __dmul_rn(d2, d2));
+}
+
 template <int kOpen, bool kSplit, bool kDump>
 __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint2 *stk = reinterpret_cast<uint2 *>(smem) + warp * kStackCap;
-    uint4 *ch = reinterpret_cast<uint4 *>(smem + kWarps * kStackCap * sizeof(uint2)) + warp * kChunk;
+    uint4 *chf = reinterpret_cast<uint4 *>(smem + kWarps * kStackCap * sizeof(uint2)) +
+                 warp * (kChunk + kNearChunk);
+    uint4 *chn = chf + kChunk;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
     const WalkParams &p = a.p;
@@ -140,22 +224,28 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         if (lane == 0) gq = atomicAdd(a.work, 1ull);
         gq = __shfl_sync(FULL, gq, 0);
         if (gq >= (unsigned long long)a.ngroups) break;
-        const int64_t g = (int64_t)gq;
+        const int64_t g = a.gorder ? (int64_t)a.gorder[gq] : (int64_t)gq;
         const uint32_t gb = a.gbeg[g], ge = a.gend[g];
+        const uint32_t gsize = ge - gb;
         uint32_t lo[3], hi[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             lo[k] = a.gbox[6 * g + k];
             hi[k] = a.gbox[6 * g + 3 + k];
         }
-        const uint32_t i = gb + lane;
-        const bool active = i < ge;
+        // lane -> (target, replica): P lanes per replica, R = 32 / P replicas
+        const int P = gsize > 16u ? 32 : (gsize > 8u ? 16 : 8);
+        const int R = 32 / P;
+        const int tl = lane & (P - 1), rep = lane / P;
+        const uint32_t i = gb + tl;
+        const bool active = (uint32_t)tl < gsize;
         const uint32_t xi = active ? a.px[i] : 0u;
         const uint32_t yi = active ? a.py[i] : 0u;
         const uint32_t zi = active ? a.pz[i] : 0u;
         // relative criterion: arel = (alpha * a_min) * s^2, a_min = min over the group
         // of |a_old| in FP64 of the single-precision components
-        double arel_coef = 0.0;
+        double arel = 0.0;
+        float arelf = 0.0f;
         if (kOpen == OG_OPEN_REL) {
             double an = __longlong_as_double(0x7ff0000000000000ll);  // +inf
             if (active) {
@@ -165,15 +255,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             }
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) an = fmin(an, __shfl_xor_sync(FULL, an, d));
-            arel_coef = __dmul_rn(__dmul_rn(p.alpha, an), p.s2);
+            arel = __dmul_rn(__dmul_rn(p.alpha, an), p.s2);
+            arelf = __double2float_rn(arel);
         }
 
         if (lane == 0) stk[0] = make_uint2(a.root_cbeg, a.root_ccnt);
         __syncwarp();
-        int sp = 1, cc = 0;
+        int sp = 1, cf = 0, cn = 0;
         int64_t rounds = 0;
         uint32_t cnt_pp = 0, cnt_pn = 0;
-        float sx = 0.f, sy = 0.f, sz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+        Acc acc;
         bool overflow = false;
 
         while (sp > 0) {
@@ -185,9 +276,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
                 break;
             }
             const int nr = sp < 32 ? sp : 32;
-            uint2 R = make_uint2(0u, 0u);
-            if (lane < nr) R = stk[sp - 1 - lane];
-            const uint32_t cnt = R.y;
+            uint2 Rg = make_uint2(0u, 0u);
+            if (lane < nr) Rg = stk[sp - 1 - lane];
+            const uint32_t cnt = Rg.y;
             uint32_t incl = cnt;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -205,78 +296,60 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             const int sp_new = sp - nfull;
             if (lane == nfull && lane < nr && excl < 32u) {
                 const uint32_t used = 32u - excl;
-                stk[sp - 1 - nfull] = make_uint2(R.x + used, R.y - used);
+                stk[sp - 1 - nfull] = make_uint2(Rg.x + used, Rg.y - used);
             }
             // this lane's child slot
             const unsigned upto = lane == 31 ? smask : (smask & ((2u << lane) - 1u));
             const int rj = __popc(upto) - 1;
-            const uint32_t rcb = __shfl_sync(FULL, R.x, rj < 0 ? 0 : rj);
+            const uint32_t rcb = __shfl_sync(FULL, Rg.x, rj < 0 ? 0 : rj);
             const uint32_t rex = __shfl_sync(FULL, excl, rj < 0 ? 0 : rj);
             const bool has = lane < ntake;
             const uint32_t ci = rcb + ((uint32_t)lane - rex);
 
-            bool emit = false, open = false, isnode = false;
-            CRec r;
-            r.x = r.y = r.z = 0u;
-            r.m = 0.f;
-            r.M = 0.0;
-            r.info = 0u;
-            r.ref = 0u;
+            bool emit = false, open = false, isnode = false, near = false;
+            uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+            uint32_t push_ref = 0u, push_cnt = 0u;
             if (has && ci < a.nchild) {
-                r = a.crec[ci];
+                const CRec r = a.crec[ci];
+                ent = make_uint4(r.x, r.y, r.z, __float_as_uint(r.m));
                 isnode = (r.info >> 31) != 0u;
+                const uint32_t gx = point_gap(r.x, lo[0], hi[0]);
+                const uint32_t gy = point_gap(r.y, lo[1], hi[1]);
+                const uint32_t gz = point_gap(r.z, lo[2], hi[2]);
+                const unsigned long long pg2 = sq64(gx) + sq64(gy) + sq64(gz);
+                near = pg2 < p.hnear2;
                 if (!isnode) {
-                    if (!kSplit) {
-                        emit = true;
-                    } else {
-                        unsigned long long g2 = sq64(point_gap(r.x, lo[0], hi[0])) +
-                                                sq64(point_gap(r.y, lo[1], hi[1])) +
-                                                sq64(point_gap(r.z, lo[2], hi[2]));
-                        emit = g2 <= p.rprune;
-                    }
+                    emit = !kSplit || pg2 <= p.rprune;
                 } else {
                     const uint32_t lev = (r.info >> 26) & 31u;
                     const uint32_t side = 1u << (32u - lev);
                     const uint32_t msk = ~(side - 1u);
-                    const uint32_t com[3] = {r.x, r.y, r.z};
-                    uint32_t org[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) org[k] = com[k] & msk;
+                    const uint32_t ox = r.x & msk, oy = r.y & msk, oz = r.z & msk;
                     bool pruned = false;
                     if (kSplit) {
-                        unsigned long long g2 = 0;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k)
-                            g2 += sq64(box_gap(lo[k], hi[k], org[k], org[k] + (side - 1u)));
+                        const unsigned long long g2 = sq64(box_gap(lo[0], hi[0], ox, ox + (side - 1u))) +
+                                                      sq64(box_gap(lo[1], hi[1], oy, oy + (side - 1u))) +
+                                                      sq64(box_gap(lo[2], hi[2], oz, oz + (side - 1u)));
                         pruned = g2 > p.rprune;
                     }
                     if (!pruned) {
-                        // boundary check: box meets the cell enlarged to 0.6 side
-                        bool near = true;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const uint32_t centre = org[k] + (side >> 1);
-                            const unsigned long long dc = point_gap(centre, lo[k], hi[k]);
-                            if (10ull * dc > 6ull * (unsigned long long)side) near = false;
-                        }
-                        if (near) {
+                        // boundary check: the box meets the cell enlarged to 0.6 side
+                        const unsigned long long lim = 6ull * (unsigned long long)side;
+                        const bool bnear =
+                            10ull * point_gap(ox + (side >> 1), lo[0], hi[0]) <= lim &&
+                            10ull * point_gap(oy + (side >> 1), lo[1], hi[1]) <= lim &&
+                            10ull * point_gap(oz + (side >> 1), lo[2], hi[2]) <= lim;
+                        if (bnear) {
                             open = true;
                         } else {
-                            const double dx = (double)point_gap(com[0], lo[0], hi[0]);
-                            const double dy = (double)point_gap(com[1], lo[1], hi[1]);
-                            const double dz = (double)point_gap(com[2], lo[2], hi[2]);
-                            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                                        __dmul_rn(dz, dz));
-                            const double l2 = (double)side * (double)side;
-                            if (kOpen == OG_OPEN_BH) {
-                                open = l2 > __dmul_rn(p.th2, d2);
-                            } else {
-                                const double lhs = __dmul_rn(__dmul_rn(p.G, r.M), l2);
-                                const double rhs = __dmul_rn(arel_coef, __dmul_rn(d2, d2));
-                                open = lhs > rhs;
-                            }
+                            const float l2f = __uint_as_float((uint32_t)(127 + 64 - 2 * lev) << 23);
+                            const double l2 = __longlong_as_double((long long)(1023 + 64 - 2 * lev) << 52);
+                            if (kOpen == OG_OPEN_BH) open = open_bh(gx, gy, gz, l2f, l2, p);
+                            else open = open_rel(gx, gy, gz, l2f, l2, r.m, r.M, arelf, arel, p);
                         }
                         emit = !open;
+                        push_ref = r.ref;
+                        push_cnt = r.info & 0x3ffffffu;
                     }
                 }
             }
@@ -288,30 +361,42 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
                 break;
             }
             if (open) {
-                const uint32_t cnt_c = r.info & 0x3ffffffu;
                 // a node always has children; a zero count would stall the walk
-                stk[sp_new + __popc(bo & lt)] = make_uint2(r.ref, cnt_c > 0u ? cnt_c : 1u);
-                if (cnt_c == 0u || (uint64_t)r.ref + cnt_c > (uint64_t)a.nchild) atomicOr(a.status, ST_INTERNAL);
+                stk[sp_new + __popc(bo & lt)] = make_uint2(push_ref, push_cnt > 0u ? push_cnt : 1u);
+                if (push_cnt == 0u || (uint64_t)push_ref + push_cnt > (uint64_t)a.nchild)
+                    atomicOr(a.status, ST_INTERNAL);
             }
             sp = sp_new + npush;
-            // append entries
+            // append entries to the far / near chunks
             const unsigned be = __ballot_sync(FULL, emit);
             const unsigned bn = __ballot_sync(FULL, isnode);
-            const int nem = __popc(be);
+            const unsigned bnear = __ballot_sync(FULL, emit && near);
+            const unsigned bfar = be & ~bnear;
             cnt_pn += __popc(be & bn);
             cnt_pp += __popc(be & ~bn);
-            if (cc + nem > kChunk) {
+            const int nfar = __popc(bfar), nnear = __popc(bnear);
+            if (cf + nfar > kChunk) {
                 __syncwarp();
                 float tx = 0.f, ty = 0.f, tz = 0.f;
-                eval_chunk<kSplit>(ch, cc, xi, yi, zi, p, tx, ty, tz);
-                kahan_add(sx, kx, tx);
-                kahan_add(sy, ky, ty);
-                kahan_add(sz, kz, tz);
-                cc = 0;
+                eval_chunk<kSplit, false>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz);
+                acc.add(tx, ty, tz);
+                cf = 0;
                 __syncwarp();
             }
-            if (emit) ch[cc + __popc(be & lt)] = make_uint4(r.x, r.y, r.z, __float_as_uint(r.m));
-            if (kDump && nem > 0) {
+            if (cn + nnear > kNearChunk) {
+                __syncwarp();
+                float tx = 0.f, ty = 0.f, tz = 0.f;
+                eval_chunk<kSplit, true>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz);
+                acc.add(tx, ty, tz);
+                cn = 0;
+                __syncwarp();
+            }
+            if (emit) {
+                if (near) chn[cn + __popc(bnear & lt)] = ent;
+                else chf[cf + __popc(bfar & lt)] = ent;
+            }
+            if (kDump && (nfar + nnear) > 0) {
+                const int nem = nfar + nnear;
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(a.list_cursor, (unsigned long long)nem);
                 base = __shfl_sync(FULL, base, 0);
@@ -325,7 +410,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
                     }
                 }
             }
-            cc += nem;
+            cf += nfar;
+            cn += nnear;
             __syncwarp();
         }
         if (overflow) {
@@ -336,28 +422,38 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         __syncwarp();
         {
             float tx = 0.f, ty = 0.f, tz = 0.f;
-            eval_chunk<kSplit>(ch, cc, xi, yi, zi, p, tx, ty, tz);
-            kahan_add(sx, kx, tx);
-            kahan_add(sy, ky, ty);
-            kahan_add(sz, kz, tz);
+            eval_chunk<kSplit, false>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz);
+            acc.add(tx, ty, tz);
+            tx = ty = tz = 0.f;
+            eval_chunk<kSplit, true>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz);
+            acc.add(tx, ty, tz);
         }
         __syncwarp();
-        if (active) {
-            a.acc[i] = __fsub_rn(sx, kx) * p.out_scale;
-            a.acc[a.n + i] = __fsub_rn(sy, ky) * p.out_scale;
-            a.acc[2 * a.n + i] = __fsub_rn(sz, kz) * p.out_scale;
+        float vx = __fsub_rn(acc.sx, acc.kx), vy = __fsub_rn(acc.sy, acc.ky),
+              vz = __fsub_rn(acc.sz, acc.kz);
+        // replicas of a target: fixed-order pairwise sums
+        for (int o = P; o < 32; o <<= 1) {
+            vx = __fadd_rn(vx, __shfl_xor_sync(FULL, vx, o));
+            vy = __fadd_rn(vy, __shfl_xor_sync(FULL, vy, o));
+            vz = __fadd_rn(vz, __shfl_xor_sync(FULL, vz, o));
+        }
+        if (active && rep == 0) {
+            a.acc[i] = vx * p.out_scale;
+            a.acc[a.n + i] = vy * p.out_scale;
+            a.acc[2 * a.n + i] = vz * p.out_scale;
             a.npp[i] = cnt_pp - 1u;
             a.npn[i] = cnt_pn;
         }
-        if (lane == 0)
-            atomicAdd(a.inter, (unsigned long long)(ge - gb) *
-                                   (unsigned long long)(cnt_pp - 1u + cnt_pn));
+        if (lane == 0) {
+            a.gcost[g] = cnt_pp + cnt_pn;
+            atomicAdd(a.inter, (unsigned long long)gsize * (unsigned long long)(cnt_pp - 1u + cnt_pn));
+        }
     }
 }
 
 template <int kOpen, bool kSplit, bool kDump>
 void launch_walk(const WalkArgs &a, cudaStream_t s, int sms) {
-    const size_t smem = kWarps * (kStackCap * sizeof(uint2) + kChunk * sizeof(uint4));
+    const size_t smem = kWarps * (kStackCap * sizeof(uint2) + (kChunk + kNearChunk) * sizeof(uint4));
     static bool attr = false;
     static int per_sm = 1;
     if (!attr) {
@@ -372,7 +468,15 @@ void launch_walk(const WalkArgs &a, cudaStream_t s, int sms) {
     int64_t grid = (int64_t)sms * per_sm;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    k_walk<kOpen, kSplit, kDump><<<(unsigned)grid, kWarps * 32, smem, s>>>(a);
+    k_walk<kOpen, kSplit, kDump><<<(unsigned)grid, kWarps * 32, smem, s>>>(a); note_launch();
+}
+
+__global__ void k_cost_keys(int64_t ng, const uint32_t *__restrict__ gcost, uint64_t *keys,
+                            uint32_t *vals) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    keys[g] = (uint64_t)(0xffffffffu - gcost[g]);  // decreasing cost, ties in key order
+    vals[g] = (uint32_t)g;
 }
 
 }  // namespace
@@ -384,29 +488,39 @@ WalkParams make_walk_params(const og_params &p, int opening, double theta) {
     w.split = p.r_s > 0.0;
     w.dump = (p.flags & OG_DEBUG_DUMP_LISTS) != 0;
     w.th2 = theta * theta;
+    w.th2f = (float)w.th2;
     w.G = p.G;
+    w.Gf = (float)p.G;
     const double s = p.box / two32;
     w.s2 = s * s;
     w.alpha = p.alpha;
     if (w.split) {
         const double rcg = (p.rcut_over_rs * p.r_s) / p.box * two32;
+        const double rsg = p.r_s / p.box * two32;
         w.rc2 = (float)(rcg * rcg);
         w.rprune = (unsigned long long)(rcg * rcg * (1.0 + 1.0 / 1024.0));
-        w.inv_2rs = (float)(1.0 / (2.0 * p.r_s / p.box * two32));
+        w.inv_2rs = (float)(1.0 / (2.0 * rsg));
+        // exp(-r^2 / (4 r_s^2)) = 2^(r^2 * kexp)
+        w.kexp = (float)(-1.4426950408889634 / (4.0 * rsg * rsg));
     } else {
         w.rc2 = __builtin_huge_valf();
         w.rprune = ~0ull;
         w.inv_2rs = 0.0f;
+        w.kexp = 0.0f;
     }
     const double hg = 2.8 * p.eps / p.box * two32;
     w.h = (float)hg;
     w.inv_h = hg > 0.0 ? (float)(1.0 / hg) : 0.0f;
+    // an entry is "near" when its integer distance to the group box is below
+    // h (with a generous rounding margin); only near entries may need softening
+    const double hn = hg * (1.0 + 1.0 / 256.0) + 2.0;
+    w.hnear2 = hg > 0.0 ? (unsigned long long)(hn * hn) : 0ull;
     w.out_scale = (float)(p.G * (two32 / p.box) * (two32 / p.box));
     return w;
 }
 
 og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted, float *acc_sorted,
-                    float *ms_out) {
+                    float *ms_out, bool use_order) {
     cudaStream_t s = t->ctx->stream;
     WalkArgs a{};
     a.n = t->n;
@@ -414,16 +528,37 @@ og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted,
     a.gbeg = t->gbeg;
     a.gend = t->gend;
     a.gbox = t->gbox;
+    a.gcost = t->gcost;
+    a.gorder = nullptr;
     a.crec = t->crec;
     a.nchild = t->nchild;
     a.max_rounds = t->nchild + 2;
     uint32_t root[2];
-    // root child range (cbeg[0] = 0 by construction of the scan; ccnt read back)
     cudaMemcpyAsync(root, t->ncbeg, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(root + 1, t->nccnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
+    cudaError_t err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return cuda_fail(err, "walk setup");
     a.root_cbeg = root[0];
     a.root_ccnt = root[1];
+    void *sort_tmp = nullptr;
+    if (use_order && t->have_cost && t->ngroups > 1) {
+        // longest list first, from the costs of the previous pass on this tree
+        const int64_t ng = t->ngroups;
+        size_t bytes = (size_t)ng * 24 + radix_sort_scratch_bytes(ng) + 1024;
+        if ((err = cudaMallocAsync(&sort_tmp, bytes, s)) != cudaSuccess)
+            return cuda_fail(err, "cudaMallocAsync (group order)");
+        char *q = static_cast<char *>(sort_tmp);
+        uint64_t *k0 = reinterpret_cast<uint64_t *>(q);
+        uint64_t *k1 = k0 + ng;
+        uint32_t *v0 = reinterpret_cast<uint32_t *>(k1 + ng);
+        uint32_t *v1 = v0 + ng;
+        void *scr = v1 + ng + 64;
+        k_cost_keys<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(ng, t->gcost, k0, v0); note_launch();
+        bool alt = false;
+        radix_sort_pairs(k0, v0, k1, v1, ng, 32, scr, s, &alt);
+        cudaMemcpyAsync(t->gorder, alt ? v1 : v0, ng * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        a.gorder = t->gorder;
+    }
     a.px = t->px;
     a.py = t->py;
     a.pz = t->pz;
@@ -464,9 +599,10 @@ og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted,
         }
     }
     cudaEventRecord(e1, s);
+    if (sort_tmp) cudaFreeAsync(sort_tmp, s);
     unsigned long long h[3] = {0, 0, 0};
     cudaMemcpyAsync(h, t->ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost, s);
-    cudaError_t err = cudaStreamSynchronize(s);
+    err = cudaStreamSynchronize(s);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
@@ -474,6 +610,7 @@ og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted,
     if (err != cudaSuccess) return cuda_fail(err, "walk");
     if ((err = cudaGetLastError()) != cudaSuccess) return cuda_fail(err, "walk launch");
     if (ms_out) *ms_out = ms;
+    t->have_cost = true;
     t->interactions_last = (int64_t)h[1];
     t->interactions += (int64_t)h[1];
     if (wp.dump) t->list_len = (int64_t)(h[2] < (unsigned long long)t->list_cap ? h[2] : t->list_cap);

@@ -86,6 +86,7 @@ def lib():
         L.og_tree_export.argtypes = [P, C.c_int, P, sz]
         L.og_tree_free.argtypes = [P]
         L.og_last_error.restype = C.c_char_p
+        L.og_kernel_launches.restype = C.c_int64
         for name in ("og_create", "og_destroy", "og_set_stream", "og_params_default",
                      "og_tree_build", "og_tree_refit", "og_tree_force", "og_tree_info_get",
                      "og_tree_export", "og_tree_free"):
@@ -96,6 +97,10 @@ def lib():
 
 def og_last_error() -> str:
     return lib().og_last_error().decode(errors="replace")
+
+
+def og_kernel_launches() -> int:
+    return int(lib().og_kernel_launches())
 
 
 def _check(st: int):
@@ -148,6 +153,7 @@ def og_destroy(ctx) -> None:
 
 
 def og_set_stream(ctx, stream_handle: int | None) -> None:
+    """Order the context's work on a CUDA stream handle (e.g. torch's cuda_stream)."""
     _check(lib().og_set_stream(ctx, C.c_void_p(stream_handle) if stream_handle else None))
 
 
