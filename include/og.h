@@ -167,6 +167,35 @@ og_status og_tree_free(og_tree *t);
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *og_last_error(void);
 
+/* ---- sort without device allocation ------------------------------------ */
+
+/* Largest n accepted by og_sort_keys_noalloc. */
+#define OG_NOALLOC_MAX_N 1048576
+
+/* Stable ascending radix sort of n 64-bit keys that allocates no memory.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory when they need a sort -- a serving process that has
+ * committed its whole HBM budget, or a latency-critical loop that cannot
+ * afford cudaMalloc/cudaFree (which can synchronise the whole device).
+ *   keys_in:  device uint64[n] (not modified unless it is keys_out);
+ *   keys_out: device uint64[n], the sorted keys;
+ *   perm_out: device uint32[n], perm_out[i] = index in keys_in of the i-th key
+ *             (equal keys keep their input order);
+ *   stream:   cudaStream_t of the current device, or NULL for the default stream.
+ * 1 <= n <= OG_NOALLOC_MAX_N, else OG_ERR_ARG.  The work is queued on `stream`
+ * on the current device and the call returns before it finishes; synchronise
+ * the stream before reading the outputs.
+ * The scratch is a fixed static device array of about 16 MB that every GPU
+ * loading this library holds until the process exits.  The first call on a
+ * device looks up that array's device address (once per device, with the
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array: calls whose work overlaps on the GPU (on
+ * different streams, or from different threads) race and corrupt each
+ * other's results; serialise them on one stream.  The array carries no state
+ * from one call to the next. */
+og_status og_sort_keys_noalloc(const uint64_t *keys_in, uint64_t *keys_out, uint32_t *perm_out,
+                               int64_t n, void *stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (for benchmarks that count their own launches in a timed region). */
 int64_t og_kernel_launches(void);

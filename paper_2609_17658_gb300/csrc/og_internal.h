@@ -114,6 +114,12 @@ size_t radix_sort_scratch_bytes(int64_t n);
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                       int64_t n, int bits, void *scratch, cudaStream_t s, bool *result_in_alt);
 
+// the same sort with every digit pass run (no histogram read-back, no host
+// synchronisation); with an even pass count the result is back in keys/vals
+void radix_sort_pairs_every_pass(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                                 uint32_t *vals_alt, int64_t n, int bits, void *scratch,
+                                 cudaStream_t s);
+
 // build stages (og_build.cu)
 og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass);
 

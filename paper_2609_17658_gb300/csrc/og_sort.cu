@@ -208,4 +208,30 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     *result_in_alt = (kin == keys_alt);
 }
 
+void radix_sort_pairs_every_pass(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                                 uint32_t *vals_alt, int64_t n, int bits, void *scratch,
+                                 cudaStream_t s) {
+    if (n <= 1) return;
+    int64_t ntiles = (n + kTile - 1) / kTile;
+    char *p = static_cast<char *>(scratch);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(p);
+    p += (size_t)kRadix * ntiles * sizeof(uint32_t);
+    p += 8 * kRadix * sizeof(uint32_t);
+    void *scan_scratch = p;
+    cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmem));
+    uint64_t *kin = keys, *kout = keys_alt;
+    uint32_t *vin = vals, *vout = vals_alt;
+    const int npasses = (bits + 7) / 8;
+    for (int pass = 0; pass < npasses; ++pass) {
+        const int shift = 8 * pass;
+        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles); note_launch();
+        scan_exclusive_u32(counts, counts, (int64_t)kRadix * ntiles, nullptr, scan_scratch, s);
+        k_downsweep<<<(unsigned)ntiles, kThreads, sizeof(DownSmem), s>>>(kin, vin, kout, vout, n,
+                                                                         shift, counts, ntiles); note_launch();
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        uint32_t *tv = vin; vin = vout; vout = tv;
+    }
+}
+
 }  // namespace og

@@ -87,6 +87,8 @@ def lib():
         L.og_tree_free.argtypes = [P]
         L.og_last_error.restype = C.c_char_p
         L.og_kernel_launches.restype = C.c_int64
+        L.og_sort_keys_noalloc.argtypes = [P, P, P, i64, P]
+        L.og_sort_keys_noalloc.restype = C.c_int
         for name in ("og_create", "og_destroy", "og_set_stream", "og_params_default",
                      "og_tree_build", "og_tree_refit", "og_tree_force", "og_tree_info_get",
                      "og_tree_export", "og_tree_free"):
@@ -221,6 +223,22 @@ def og_tree_export(tree, field: int) -> np.ndarray:
         out = np.zeros((cnt,) + tuple(tail), dtype=dt)
     _check(lib().og_tree_export(tree, int(field), out.ctypes.data_as(C.c_void_p), out.nbytes))
     return out
+
+
+OG_NOALLOC_MAX_N = 1048576
+
+
+def og_sort_keys_noalloc(keys_in, keys_out, perm_out, stream_handle: int | None = None) -> None:
+    """Sort device keys without any device allocation (see include/og.h).
+    keys_in, keys_out: CUDA int64 tensors holding the uint64 key bits;
+    perm_out: CUDA int32 tensor.  Queued on ``stream_handle`` (None: default
+    stream); synchronise before reading the outputs."""
+    n = int(keys_in.shape[0])
+    if int(keys_out.shape[0]) != n or int(perm_out.shape[0]) != n:
+        raise ValueError("keys_in, keys_out and perm_out lengths differ")
+    _check(lib().og_sort_keys_noalloc(_dev_ptr(keys_in, "int64"), _dev_ptr(keys_out, "int64"),
+                                      _dev_ptr(perm_out, "int32"), n,
+                                      C.c_void_p(stream_handle) if stream_handle else None))
 
 
 def og_tree_free(tree) -> None:
