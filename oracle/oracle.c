@@ -34,8 +34,8 @@
  * design notes of the repository):
  *   - units: G and the box length L are parameters; positions are reduced to
  *     the torus [0, L)^3.
- *   - fixed point: u = floor(frac(x/L) * 2^32); a value that rounds to 2^32
- *     is the point 0 of the torus.
+ *   - fixed point: u = floor(frac(t) * 2^32) with t = x/L in FP64, evaluated
+ *     exactly as floor(t * 2^32) mod 2^32 (no rounding after the division).
  *   - minimum image: dx = x_j - x_i as a 32-bit two's-complement difference;
  *     an exact half-box separation maps to -L/2.
  *   - softening: h = 2.8 eps (Sect. 4.1.3, Plummer-equivalent eps).  The
@@ -62,10 +62,13 @@
  *     bucket sums its particles sequentially in key order.  The centre of
  *     mass is rounded half-to-even to the integer grid.  No fused multiply
  *     adds (compiled with -ffp-contract=off).
- *   - groups: at every node with more than G particles (and at the root),
- *     maximal runs of consecutive "small" children (particles, or nodes with
- *     at most G particles) are cut, in key order, into groups of G (the last
- *     one shorter); children with more than G particles are recursed into.
+ *   - groups: children with more than G particles are recursed into.  At a
+ *     node that holds at most 8 G particles (and at the root), maximal runs of
+ *     consecutive "small" children (particles, or nodes with at most G
+ *     particles) are cut, in key order, into groups of G (the last one
+ *     shorter).  At a node with more than 8 G particles the small children
+ *     are not merged: each one is a group of its own, so that a group never
+ *     spans the octants of a cell much larger than its own neighbourhood.
  *   - geometry of a group: the integer bounding box of its members.  All
  *     distances between a group box and a point or a cell are taken per axis
  *     on the circle of 2^32 grid units (0 when overlapping).
@@ -106,10 +109,16 @@ int ora_quantize1(double v, double box, uint32_t *out)
 {
     if (!isfinite(v)) return ORA_ERR_ARG;
     double t = v / box;
-    t = t - floor(t);
-    double q = floor(t * TWO32);
-    if (q >= TWO32) q = 0.0; /* frac rounded up to 1: the same torus point as 0 */
-    *out = (uint32_t)q;
+    if (fabs(t) < 2147483648.0) {
+        /* t * 2^32 is exact and below 2^63 in magnitude: floor it, keep the low
+           32 bits (the same as floor(frac(t) * 2^32), exactly, for either sign) */
+        int64_t q = (int64_t)floor(t * TWO32);
+        *out = (uint32_t)(uint64_t)q;
+    } else {
+        /* |t| >= 2^31: t - floor(t) is exact */
+        double f = t - floor(t);
+        *out = (uint32_t)floor(f * TWO32);
+    }
     return ORA_OK;
 }
 
@@ -346,6 +355,7 @@ static void make_groups(ora_tree *t, int64_t id)
     const int64_t n = t->n;
     int64_t G = t->p.group_max;
     int64_t rb = -1, re = -1;
+    const int merge = t->end[id] - t->beg[id] <= 8 * G;
     for (int64_t k = 0; k < t->ccnt[id]; ++k) {
         int64_t c = t->child[t->cbeg[id] + k];
         int64_t cb, ce;
@@ -362,6 +372,10 @@ static void make_groups(ora_tree *t, int64_t id)
                 make_groups(t, j);
                 continue;
             }
+        }
+        if (!merge) {
+            emit_run(t, cb, ce);
+            continue;
         }
         if (rb < 0) rb = cb;
         re = ce;

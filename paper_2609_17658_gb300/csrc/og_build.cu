@@ -24,6 +24,7 @@
 //
 // Every decision is integer or IEEE FP64 with a fixed operation order, so the
 // result is identical to the oracle's recursive construction.
+#include <cmath>
 #include <cstdio>
 
 #include "og_internal.h"
@@ -52,26 +53,31 @@ __device__ __forceinline__ int digit_at(uint64_t key, int lev) {
     return (int)((key >> (3 * (kLevels - lev))) & 7u);
 }
 
-__device__ __forceinline__ uint32_t quantize(double v, double box, uint32_t *status) {
+// u = floor(frac(t) * 2^32), t = x / L, evaluated exactly as
+// floor(t * 2^32) mod 2^32: t * 2^32 is an exact scaling and, for |t| < 2^31,
+// fits a signed 64-bit integer after the round-down conversion.  When L is a
+// power of two, x * (1/L) equals the correctly rounded quotient exactly.
+__device__ __forceinline__ uint32_t quantize(double v, double box, double inv_box, bool pow2,
+                                             uint32_t *status) {
     if (!isfinite(v)) {
         atomicOr(status, ST_BAD_INPUT);
         return 0;
     }
-    double t = __ddiv_rn(v, box);
-    t = __dsub_rn(t, floor(t));
-    double q = floor(__dmul_rn(t, 4294967296.0));
-    if (q >= 4294967296.0) q = 0.0;
-    return (uint32_t)q;
+    const double t = pow2 ? v * inv_box : __ddiv_rn(v, box);
+    if (fabs(t) < 2147483648.0) return (uint32_t)(unsigned long long)__double2ll_rd(t * 4294967296.0);
+    const double f = t - floor(t);  // exact for |t| >= 1
+    return (uint32_t)floor(f * 4294967296.0);
 }
 
 __global__ void k_quantize_keys(const double *__restrict__ pos, const double *__restrict__ mass,
-                                int64_t n, double box, uint32_t *qx, uint32_t *qy, uint32_t *qz,
-                                uint64_t *key, uint32_t *idx, uint32_t *status) {
+                                int64_t n, double box, double inv_box, bool pow2, uint32_t *qx,
+                                uint32_t *qy, uint32_t *qz, uint64_t *key, uint32_t *idx,
+                                uint32_t *status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint32_t x = quantize(pos[3 * i + 0], box, status);
-    uint32_t y = quantize(pos[3 * i + 1], box, status);
-    uint32_t z = quantize(pos[3 * i + 2], box, status);
+    uint32_t x = quantize(pos[3 * i + 0], box, inv_box, pow2, status);
+    uint32_t y = quantize(pos[3 * i + 1], box, inv_box, pow2, status);
+    uint32_t z = quantize(pos[3 * i + 2], box, inv_box, pow2, status);
     double m = mass[i];
     if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
     qx[i] = x;
@@ -283,113 +289,129 @@ __global__ void k_threading(int64_t n, int64_t m, int64_t nchild, const uint32_t
     else nsib[item - n] = after;
 }
 
-// a5: moments.  One team of 8 lanes per node; lane s holds octant slot s.
-__global__ void __launch_bounds__(kT) k_moments(
-    int64_t n, int64_t m, const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ nbeg,
-    const uint32_t *__restrict__ nend, const uint32_t *__restrict__ ncbeg,
-    const uint32_t *__restrict__ occ, const uint32_t *__restrict__ child,
-    const int32_t *__restrict__ npar, const uint32_t *__restrict__ nnc, uint32_t *arrive,
-    const uint32_t *__restrict__ px, const uint32_t *__restrict__ py,
-    const uint32_t *__restrict__ pz, const double *__restrict__ pm64, double *nM, double *nS,
-    uint32_t *ncom, int64_t nchild, uint32_t *status) {
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const int sub = lane & 7;
-    const unsigned tmask = 0xffu << (lane & 24);
-    int64_t node = gt >> 3;
-    if (node >= m) return;  // whole team leaves together
-    if (nnc[node] != 0) return;
-    for (int guard = 0;; ++guard) {
-        if (guard > kLevels + 2) {
-            if (sub == 0) atomicOr(status, ST_INTERNAL);
-            break;
-        }
-        const int L = nlev[node];
-        double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
-        if (L == kLevels) {
-            if (sub == 0) {
-                for (uint32_t q = nbeg[node]; q < nend[node]; ++q) {
-                    double mq = pm64[q];
-                    M = __dadd_rn(M, mq);
-                    Sx = __dadd_rn(Sx, __dmul_rn(mq, (double)px[q]));
-                    Sy = __dadd_rn(Sy, __dmul_rn(mq, (double)py[q]));
-                    Sz = __dadd_rn(Sz, __dmul_rn(mq, (double)pz[q]));
-                }
-            }
-        } else {
-            const uint32_t o = occ[node];
-            const uint32_t slot = ncbeg[node] + __popc(o & ((1u << sub) - 1u));
-            if (((o >> sub) & 1u) && slot < (uint64_t)nchild) {
-                uint32_t item = child[slot];
-                if (item < n) {
-                    double mq = pm64[item];
-                    M = mq;
-                    Sx = __dmul_rn(mq, (double)px[item]);
-                    Sy = __dmul_rn(mq, (double)py[item]);
-                    Sz = __dmul_rn(mq, (double)pz[item]);
-                } else {
-                    int64_t j = item - n;
-                    M = __ldcg(&nM[j]);
-                    Sx = __ldcg(&nS[3 * j + 0]);
-                    Sy = __ldcg(&nS[3 * j + 1]);
-                    Sz = __ldcg(&nS[3 * j + 2]);
-                }
-            }
-#pragma unroll
-            for (int d = 1; d < 8; d <<= 1) {
-                M = __dadd_rn(M, __shfl_xor_sync(tmask, M, d));
-                Sx = __dadd_rn(Sx, __shfl_xor_sync(tmask, Sx, d));
-                Sy = __dadd_rn(Sy, __shfl_xor_sync(tmask, Sy, d));
-                Sz = __dadd_rn(Sz, __shfl_xor_sync(tmask, Sz, d));
-            }
-        }
-        int go = 0;
-        if (sub == 0) {
-            nM[node] = M;
-            nS[3 * node + 0] = Sx;
-            nS[3 * node + 1] = Sy;
-            nS[3 * node + 2] = Sz;
-            uint32_t c[3];
-            if (M > 0.0) {
-                c[0] = (uint32_t)rint(__ddiv_rn(Sx, M));
-                c[1] = (uint32_t)rint(__ddiv_rn(Sy, M));
-                c[2] = (uint32_t)rint(__ddiv_rn(Sz, M));
-            } else {
-                // massless node: the cell centre
-                const uint32_t q = nbeg[node];
-                const uint32_t pc[3] = {px[q], py[q], pz[q]};
-                for (int a = 0; a < 3; ++a) {
-                    uint64_t mask = L == 0 ? 0ull : ~((1ull << (32 - L)) - 1ull);
-                    c[a] = (uint32_t)(((uint64_t)pc[a] & mask) + (1ull << (31 - L)));
-                }
-            }
-            ncom[3 * node + 0] = c[0];
-            ncom[3 * node + 1] = c[1];
-            ncom[3 * node + 2] = c[2];
-            __threadfence();
-            if (node != 0) {
-                int32_t par = npar[node];
-                uint32_t old = atomicAdd(&arrive[par], 1u);
-                go = (old + 1 == nnc[par]) ? 1 : 0;
-            }
-        }
-        go = __shfl_sync(tmask, go, lane & 24);
-        if (!go) break;
-        __threadfence();
-        node = npar[node];
-    }
+// a5: moments, level by level from the deepest level up, one thread per node:
+// every FP64 instruction then serves 32 nodes (the FP64 rate of the chip is
+// 1/64 of its FP32 rate).  Slot s holds the child in octant s (a particle or
+// a node) or +0.0; the slots combine as ((0+1)+(2+3))+((4+5)+(6+7)).
+__global__ void k_level_hist(int64_t m, const uint8_t *__restrict__ nlev, uint32_t *lcount) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < m) atomicAdd(&lcount[nlev[id]], 1u);
 }
 
+__global__ void k_level_offsets(uint32_t *lcount, uint32_t *loff, uint32_t *lcursor) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t run = 0;
+    for (int l = 0; l <= kLevels; ++l) {
+        loff[l] = run;
+        lcursor[l] = 0;
+        run += lcount[l];
+    }
+    loff[kLevels + 1] = run;
+}
+
+__global__ void k_level_scatter(int64_t m, const uint8_t *__restrict__ nlev,
+                                const uint32_t *__restrict__ loff, uint32_t *lcursor,
+                                uint32_t *lnodes) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= m) return;
+    const int l = nlev[id];
+    lnodes[loff[l] + atomicAdd(&lcursor[l], 1u)] = (uint32_t)id;
+}
+
+struct Slot {
+    double M, x, y, z;
+};
+
+__device__ __forceinline__ Slot slot_add(const Slot &a, const Slot &b) {
+    return {__dadd_rn(a.M, b.M), __dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y), __dadd_rn(a.z, b.z)};
+}
+
+__global__ void __launch_bounds__(kT) k_moments_level(
+    int64_t n, int64_t m, int level, const uint32_t *__restrict__ lnodes, uint32_t cnt,
+    const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
+    const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
+    const uint32_t *__restrict__ child, const uint32_t *__restrict__ px,
+    const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
+    const double *__restrict__ pm64, double *nM, double *nS, uint32_t *ncom, int64_t nchild,
+    uint32_t *status) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    const uint32_t node = lnodes[k];
+    if (node >= (uint64_t)m) {
+        atomicOr(status, ST_INTERNAL);
+        return;
+    }
+    Slot tot = {0.0, 0.0, 0.0, 0.0};
+    if (level == kLevels) {
+        // bucket of coincident keys: sequential in key order
+        for (uint32_t q = nbeg[node]; q < nend[node]; ++q) {
+            const double mq = pm64[q];
+            tot.M = __dadd_rn(tot.M, mq);
+            tot.x = __dadd_rn(tot.x, __dmul_rn(mq, (double)px[q]));
+            tot.y = __dadd_rn(tot.y, __dmul_rn(mq, (double)py[q]));
+            tot.z = __dadd_rn(tot.z, __dmul_rn(mq, (double)pz[q]));
+        }
+    } else {
+        const uint32_t o = occ[node];
+        const uint32_t cb = ncbeg[node];
+        Slot sl[8];
+#pragma unroll
+        for (int sidx = 0; sidx < 8; ++sidx) {
+            sl[sidx] = {0.0, 0.0, 0.0, 0.0};
+            const uint32_t slot = cb + __popc(o & ((1u << sidx) - 1u));
+            if (((o >> sidx) & 1u) && slot < (uint64_t)nchild) {
+                const uint32_t item = child[slot];
+                if (item < n) {
+                    const double mq = pm64[item];
+                    sl[sidx] = {mq, __dmul_rn(mq, (double)px[item]), __dmul_rn(mq, (double)py[item]),
+                                __dmul_rn(mq, (double)pz[item])};
+                } else {
+                    const int64_t j = item - n;
+                    sl[sidx] = {nM[j], nS[3 * j + 0], nS[3 * j + 1], nS[3 * j + 2]};
+                }
+            }
+        }
+        tot = slot_add(slot_add(slot_add(sl[0], sl[1]), slot_add(sl[2], sl[3])),
+                       slot_add(slot_add(sl[4], sl[5]), slot_add(sl[6], sl[7])));
+    }
+    nM[node] = tot.M;
+    nS[3 * node + 0] = tot.x;
+    nS[3 * node + 1] = tot.y;
+    nS[3 * node + 2] = tot.z;
+    uint32_t c[3];
+    if (tot.M > 0.0) {
+        c[0] = (uint32_t)rint(__ddiv_rn(tot.x, tot.M));
+        c[1] = (uint32_t)rint(__ddiv_rn(tot.y, tot.M));
+        c[2] = (uint32_t)rint(__ddiv_rn(tot.z, tot.M));
+    } else {
+        // massless node: the cell centre
+        const uint32_t q = nbeg[node];
+        const uint32_t pc[3] = {px[q], py[q], pz[q]};
+        const uint64_t mask = level == 0 ? 0ull : ~((1ull << (32 - level)) - 1ull);
+        for (int a = 0; a < 3; ++a) c[a] = (uint32_t)(((uint64_t)pc[a] & mask) + (1ull << (31 - level)));
+    }
+    ncom[3 * node + 0] = c[0];
+    ncom[3 * node + 1] = c[1];
+    ncom[3 * node + 2] = c[2];
+}
+
+// frontier node of p: the deepest node with more than G particles containing
+// p (or the root); unit: the child of the frontier node that contains p
+// (its first particle), or p itself when p hangs directly from it
 __global__ void k_frontier(int64_t n, int G, const uint32_t *__restrict__ owner,
                            const int32_t *__restrict__ npar, const uint32_t *__restrict__ nbeg,
-                           const uint32_t *__restrict__ nend, uint32_t *fp) {
+                           const uint32_t *__restrict__ nend, uint32_t *fp, uint32_t *unit) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     uint32_t node = owner[p];
+    int64_t prev = -1;
     for (int guard = 0; node != 0 && nend[node] - nbeg[node] <= (uint32_t)G && guard <= kLevels + 2;
-         ++guard)
+         ++guard) {
+        prev = node;
         node = (uint32_t)npar[node];
+    }
     fp[p] = node;
+    unit[p] = prev < 0 ? (uint32_t)p : nbeg[prev];
 }
 
 __global__ void k_runmark(int64_t n, const uint32_t *__restrict__ fp, uint32_t *rs) {
@@ -398,10 +420,19 @@ __global__ void k_runmark(int64_t n, const uint32_t *__restrict__ fp, uint32_t *
     rs[p] = (p == 0 || fp[p] != fp[p - 1]) ? (uint32_t)p : 0u;
 }
 
-__global__ void k_groupmark(int64_t n, int G, const uint32_t *__restrict__ runstart, uint32_t *gs) {
+// group starts: inside a frontier node of at most 8G particles, runs of
+// consecutive particles are cut every G; inside a larger frontier node every
+// unit (a small child node or a single particle) starts a group of its own
+__global__ void k_groupmark(int64_t n, int G, const uint32_t *__restrict__ runstart,
+                            const uint32_t *__restrict__ fp, const uint32_t *__restrict__ unit,
+                            const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
+                            uint32_t *gs) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    gs[p] = ((p - runstart[p]) % G == 0) ? 1u : 0u;
+    const uint32_t f = fp[p];
+    const bool merge = (uint64_t)(nend[f] - nbeg[f]) <= 8ull * (uint64_t)G;
+    if (merge) gs[p] = ((p - runstart[p]) % G == 0) ? 1u : 0u;
+    else gs[p] = (unit[p] == (uint32_t)p) ? 1u : 0u;
 }
 
 __global__ void k_group_init(int64_t n, const uint32_t *__restrict__ gs,
@@ -558,8 +589,8 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         add(4, n); add(4, n); add(4, n);        // qx qy qz
         add(8, n); add(4, n); add(8, n); add(4, n);  // keys, idx, alt
         add(1, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // lv sb se first nid sid
-        add(4, n); add(4, n); add(4, n);        // occ nnc arrive
-        add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs gid
+        add(4, n); add(4, n); add(4, n); add(4, n); add(4, 3 * 24);  // occ nnc arrive lnodes levels
+        add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs gid unit
         sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + 8) + 4096;
     }
     void *scratch = nullptr;
@@ -576,8 +607,12 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     uint32_t *sbeg = B.take<uint32_t>(n), *send = B.take<uint32_t>(n);
     uint32_t *first = B.take<uint32_t>(n), *nid = B.take<uint32_t>(n), *sid = B.take<uint32_t>(n);
     uint32_t *occ = B.take<uint32_t>(n), *nnc = B.take<uint32_t>(n), *arrive = B.take<uint32_t>(n);
+    uint32_t *lnodes = B.take<uint32_t>(n);
+    uint32_t *lcount = B.take<uint32_t>(3 * (kLevels + 2));
+    uint32_t *loff = lcount + (kLevels + 2), *lcursor = lcount + 2 * (kLevels + 2);
     uint32_t *fp = B.take<uint32_t>(n), *rs = B.take<uint32_t>(n), *gs = B.take<uint32_t>(n);
     uint32_t *gid = B.take<uint32_t>(n);
+    uint32_t *unit = B.take<uint32_t>(n);
     void *sort_scratch = B.take<char>((int64_t)radix_sort_scratch_bytes(n));
     void *scan_scratch = B.take<char>((int64_t)scan_scratch_bytes(2 * n + 8));
     uint32_t *d_tot = B.take<uint32_t>(4);
@@ -589,7 +624,10 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     cudaEventRecord(e0, s);
 
     // a1, a2
-    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, d_mass, n, p.box, qx, qy, qz, keys, idx, status); note_launch();
+    int box_exp = 0;
+    const bool box_pow2 = std::frexp(p.box, &box_exp) == 0.5;
+    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, d_mass, n, p.box, 1.0 / p.box, box_pow2, qx, qy, qz,
+                                           keys, idx, status); note_launch();
     // a3
     bool in_alt = false;
     radix_sort_pairs(keys, idx, keys_alt, idx_alt, n, 63, sort_scratch, s, &in_alt);
@@ -631,19 +669,22 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
                                        t->owner, t->child, t->npos, nchild, status); note_launch();
     k_threading<<<nblk(nchild), kT, 0, s>>>(n, m, nchild, t->child, t->ncbeg, t->nccnt, t->npar,
                                             t->npos, t->owner, t->nnext, t->nsib, t->pnext, status); note_launch();
-    // a5
-    k_moments<<<nblk(8 * m), kT, 0, s>>>(n, m, t->nlev, t->nbeg, t->nend, t->ncbeg, occ, t->child,
-                                         t->npar, nnc, arrive, t->px, t->py, t->pz, t->pm64, t->nM,
-                                         t->nS, t->ncom, nchild, status); note_launch();
+    // a5 (part 1): node ids by level
+    cudaMemsetAsync(lcount, 0, (kLevels + 2) * sizeof(uint32_t), s);
+    k_level_hist<<<nblk(m), kT, 0, s>>>(m, t->nlev, lcount); note_launch();
+    k_level_offsets<<<1, 32, 0, s>>>(lcount, loff, lcursor); note_launch();
+    k_level_scatter<<<nblk(m), kT, 0, s>>>(m, t->nlev, loff, lcursor, lnodes); note_launch();
     // a6: groups
     const int G = p.group_max;
-    k_frontier<<<nblk(n), kT, 0, s>>>(n, G, t->owner, t->npar, t->nbeg, t->nend, fp); note_launch();
+    k_frontier<<<nblk(n), kT, 0, s>>>(n, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit); note_launch();
     k_runmark<<<nblk(n), kT, 0, s>>>(n, fp, rs); note_launch();
     scan_inclusive_max_u32(rs, rs, n, scan_scratch, s);
-    k_groupmark<<<nblk(n), kT, 0, s>>>(n, G, rs, gs); note_launch();
+    k_groupmark<<<nblk(n), kT, 0, s>>>(n, G, rs, fp, unit, t->nbeg, t->nend, gs); note_launch();
     scan_exclusive_u32(gs, gid, n, d_tot + 2, scan_scratch, s);
     k_group_init<<<nblk(n), kT, 0, s>>>(n, gs, gid, t->gbeg); note_launch();
     cudaMemcpyAsync(h_tot + 1, d_tot + 1, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    uint32_t h_lcount[kLevels + 2];
+    cudaMemcpyAsync(h_lcount, lcount, (kLevels + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) {
         cudaFreeAsync(scratch, s);
         return cuda_fail(err, "build (topology)");
@@ -654,6 +695,22 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         return OG_ERR_STATE;
     }
     t->ngroups = h_tot[2];
+    // a5 (part 2): moments from the deepest level up; each launch reads only
+    // nodes of deeper levels, finished by the previous launches
+    {
+        uint32_t off = 0;
+        uint32_t offs[kLevels + 1];
+        for (int l = 0; l <= kLevels; ++l) {
+            offs[l] = off;
+            off += h_lcount[l];
+        }
+        for (int l = kLevels; l >= 0; --l) {
+            if (h_lcount[l] == 0) continue;
+            k_moments_level<<<nblk(h_lcount[l]), kT, 0, s>>>(
+                n, m, l, lnodes + offs[l], h_lcount[l], t->nbeg, t->nend, t->ncbeg, occ, t->child,
+                t->px, t->py, t->pz, t->pm64, t->nM, t->nS, t->ncom, nchild, status); note_launch();
+        }
+    }
     k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
                                                 t->pz, t->gbox); note_launch();
     k_records<<<nblk(nchild), kT, 0, s>>>(n, nchild, t->child, t->px, t->py, t->pz, t->pm32,

@@ -13,7 +13,7 @@
 #include <stdint.h>
 #include <string>
 
-#include "../../include/og.h"
+#include "og.h"
 
 namespace og {
 

@@ -26,9 +26,10 @@
 //                   FP32, r^2 by FMA, cutoff, rsqrt, erfc split factor, spline
 //                   softening for near entries only, FP32 accumulation over the
 //                   chunk, then a compensated (Kahan) add into the totals.
-//                   Groups of at most 16 (8) targets replicate each target on
-//                   2 (4) lanes that split the chunk's entries; the replicas'
-//                   totals are added in a fixed order at the end.
+//                   A group of g <= 16 targets replicates each target on
+//                   32 / P lanes (P the next power of two >= g) that split the
+//                   chunk's entries; the replicas' totals are added in a fixed
+//                   order at the end.
 //
 // Work distribution: persistent blocks; warps take groups from a global
 // atomic counter, in decreasing order of the previous pass's list length
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             hi[k] = a.gbox[6 * g + 3 + k];
         }
         // lane -> (target, replica): P lanes per replica, R = 32 / P replicas
-        const int P = gsize > 16u ? 32 : (gsize > 8u ? 16 : 8);
+        const int P = gsize > 16u ? 32 : gsize > 8u ? 16 : gsize > 4u ? 8 : gsize > 2u ? 4 : gsize > 1u ? 2 : 1;
         const int R = 32 / P;
         const int tl = lane & (P - 1), rep = lane / P;
         const uint32_t i = gb + tl;

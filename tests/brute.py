@@ -17,9 +17,9 @@ TWO32 = 1 << 32
 def quantize_exact(v: float, box: float = 1.0) -> int:
     """floor(frac(v/box) * 2^32) with the FP64 quotient and exact rationals after it."""
     t = Fraction(v / box)
-    frac = t - (t.numerator // t.denominator)
+    frac = t - (t.numerator // t.denominator)          # in [0, 1) for either sign
     q = (frac * TWO32).numerator // (frac * TWO32).denominator
-    return 0 if q >= TWO32 else int(q)
+    return int(q)
 
 
 def morton_string(x: int, y: int, z: int) -> int:
@@ -61,22 +61,34 @@ def deepest_containing(nodes, lo, hi):
 
 def groups_flat(nodes, n: int, G: int):
     """Groups from the flat reading: each particle's frontier node is the
-    deepest node with more than G particles containing it (the root if none);
-    maximal runs of consecutive particles with the same frontier node are cut
-    into pieces of G."""
+    deepest node with more than G particles containing it (the root if none).
+    When the frontier node holds at most 8G particles, maximal runs of
+    consecutive particles with the same frontier node are cut into pieces of
+    G; otherwise the particles of each child of the frontier node (a node of
+    at most G particles, or a single particle) form one group."""
     big = [nd for nd in nodes if nd[2] - nd[1] > G or nd[0] == 0]
     big.sort(key=lambda t: (t[1], t[0]))
-    front = []
+    front, unit = [], []
     for i in range(n):
-        front.append(deepest_containing(big, i, i + 1))
+        f = deepest_containing(big, i, i + 1)
+        front.append(f)
+        # the child of f containing i: the shallowest node below f containing i
+        below = [nd for nd in nodes if nd[0] > f[0] and nd[1] <= i < nd[2]
+                 and f[1] <= nd[1] and nd[2] <= f[2]]
+        unit.append(min(below, key=lambda t: t[0]) if below else ("p", i))
     groups = []
     i = 0
     while i < n:
         j = i
-        while j < n and front[j] == front[i]:
-            j += 1
-        for s in range(i, j, G):
-            groups.append((s, min(s + G, j)))
+        if front[i][2] - front[i][1] <= 8 * G:
+            while j < n and front[j] == front[i]:
+                j += 1
+            for s in range(i, j, G):
+                groups.append((s, min(s + G, j)))
+        else:
+            while j < n and front[j] == front[i] and unit[j] == unit[i]:
+                j += 1
+            groups.append((i, j))
         i = j
     return groups
 

@@ -28,7 +28,7 @@ def test_quantize_special_values():
     assert oracle.quantize1(0.0) == 0
     assert oracle.quantize1(0.5) == 1 << 31
     assert oracle.quantize1(1.0) == 0                      # periodic wrap
-    assert oracle.quantize1(-1e-20) == 0                   # frac rounds up to 1 -> 0
+    assert oracle.quantize1(-1e-20) == (1 << 32) - 1       # exact: just below the torus point 0
     assert oracle.quantize1(1.0 - 2.0 ** -53) == (1 << 32) - 1
     assert oracle.quantize1(0.25, box=0.5) == 1 << 31
     assert oracle.quantize1(2.75) == 3 << 30
@@ -39,7 +39,10 @@ def test_quantize_special_values():
 
 def test_quantize_matches_exact_rationals():
     r = np.random.default_rng(1)
-    for v in np.concatenate([r.random(300) * 3.0, r.random(50) * 1e-6, [1e-300, 0.999999999]]):
+    vals = np.concatenate([r.random(300) * 3.0, r.random(50) * 1e-6, [1e-300, 0.999999999],
+                           -r.random(100) * 3.0, -r.random(50) * 1e-12, [-1e-300, -2.0 ** -60],
+                           r.random(20) * 1e12, -r.random(20) * 1e12, [2.0 ** 31 + 0.25, -2.0 ** 31 - 0.25]])
+    for v in vals:
         assert oracle.quantize1(float(v)) == brute.quantize_exact(float(v))
     for box in (0.37, 3.0, 1e3):
         for v in r.random(50) * box * 2:
