@@ -293,9 +293,21 @@ __global__ void k_threading(int64_t n, int64_t m, int64_t nchild, const uint32_t
 // every FP64 instruction then serves 32 nodes (the FP64 rate of the chip is
 // 1/64 of its FP32 rate).  Slot s holds the child in octant s (a particle or
 // a node) or +0.0; the slots combine as ((0+1)+(2+3))+((4+5)+(6+7)).
-__global__ void k_level_hist(int64_t m, const uint8_t *__restrict__ nlev, uint32_t *lcount) {
-    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id < m) atomicAdd(&lcount[nlev[id]], 1u);
+constexpr int kLvItems = 16;  // nodes per thread in the level bucketing
+
+// per-block shared-memory histograms, one global atomic per level and block
+__global__ void __launch_bounds__(kT) k_level_hist(int64_t m, const uint8_t *__restrict__ nlev,
+                                                   uint32_t *lcount) {
+    __shared__ uint32_t h[kLevels + 1];
+    if (threadIdx.x <= kLevels) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * kLvItems;
+    for (int k = 0; k < kLvItems; ++k) {
+        const int64_t id = base + (int64_t)k * blockDim.x + threadIdx.x;
+        if (id < m) atomicAdd(&h[nlev[id]], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x <= kLevels && h[threadIdx.x]) atomicAdd(&lcount[threadIdx.x], h[threadIdx.x]);
 }
 
 __global__ void k_level_offsets(uint32_t *lcount, uint32_t *loff, uint32_t *lcursor) {
@@ -309,13 +321,29 @@ __global__ void k_level_offsets(uint32_t *lcount, uint32_t *loff, uint32_t *lcur
     loff[kLevels + 1] = run;
 }
 
-__global__ void k_level_scatter(int64_t m, const uint8_t *__restrict__ nlev,
-                                const uint32_t *__restrict__ loff, uint32_t *lcursor,
-                                uint32_t *lnodes) {
-    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= m) return;
-    const int l = nlev[id];
-    lnodes[loff[l] + atomicAdd(&lcursor[l], 1u)] = (uint32_t)id;
+__global__ void __launch_bounds__(kT) k_level_scatter(int64_t m, const uint8_t *__restrict__ nlev,
+                                                      const uint32_t *__restrict__ loff,
+                                                      uint32_t *lcursor, uint32_t *lnodes) {
+    __shared__ uint32_t h[kLevels + 1], hb[kLevels + 1];
+    if (threadIdx.x <= kLevels) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * kLvItems;
+    uint32_t pos[kLvItems];
+    uint8_t lev[kLvItems];
+#pragma unroll
+    for (int k = 0; k < kLvItems; ++k) {
+        const int64_t id = base + (int64_t)k * blockDim.x + threadIdx.x;
+        lev[k] = id < m ? nlev[id] : 0;
+        pos[k] = id < m ? atomicAdd(&h[lev[k]], 1u) : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x <= kLevels) hb[threadIdx.x] = h[threadIdx.x] ? atomicAdd(&lcursor[threadIdx.x], h[threadIdx.x]) : 0u;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kLvItems; ++k) {
+        const int64_t id = base + (int64_t)k * blockDim.x + threadIdx.x;
+        if (id < m) lnodes[loff[lev[k]] + hb[lev[k]] + pos[k]] = (uint32_t)id;
+    }
 }
 
 struct Slot {
@@ -671,9 +699,10 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
                                             t->npos, t->owner, t->nnext, t->nsib, t->pnext, status); note_launch();
     // a5 (part 1): node ids by level
     cudaMemsetAsync(lcount, 0, (kLevels + 2) * sizeof(uint32_t), s);
-    k_level_hist<<<nblk(m), kT, 0, s>>>(m, t->nlev, lcount); note_launch();
+    const unsigned lv_blocks = (unsigned)((m + (int64_t)kT * kLvItems - 1) / ((int64_t)kT * kLvItems));
+    k_level_hist<<<lv_blocks, kT, 0, s>>>(m, t->nlev, lcount); note_launch();
     k_level_offsets<<<1, 32, 0, s>>>(lcount, loff, lcursor); note_launch();
-    k_level_scatter<<<nblk(m), kT, 0, s>>>(m, t->nlev, loff, lcursor, lnodes); note_launch();
+    k_level_scatter<<<lv_blocks, kT, 0, s>>>(m, t->nlev, loff, lcursor, lnodes); note_launch();
     // a6: groups
     const int G = p.group_max;
     k_frontier<<<nblk(n), kT, 0, s>>>(n, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit); note_launch();
