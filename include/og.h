@@ -133,6 +133,35 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
 
 og_status og_tree_info_get(const og_tree *t, og_tree_info *info);
 
+/* ---- many independent boxes in one launch ------------------------------ */
+
+/* One independent periodic system of a batch. */
+typedef struct {
+    const double *pos;       /* double[n][3] */
+    const double *mass;      /* double[n] */
+    int64_t n;               /* >= 1 */
+    og_params params;        /* per-box box size, G, eps, r_s, theta, alpha; the opening
+                                criterion, split on/off (r_s > 0), group_max and flags must
+                                agree across the batch */
+    const float *a_old;      /* float[n][3] for OG_OPEN_REL, or NULL (NULL for every box or none) */
+    float *acc;              /* float[n][3] out */
+    uint32_t *n_pp, *n_pn;   /* uint32[n] out, or NULL */
+} og_box;
+
+typedef struct {
+    int64_t boxes, particles, groups, interactions;
+    double ms_total, ms_build, ms_walk;   /* device time of the whole call, the build, the walk */
+} og_batch_info;
+
+/* Short-range accelerations of many independent boxes at once: one forest
+ * (every box its own root, particles sorted by box then key), and one walk
+ * launch per pass over the groups of all boxes, longest lists first.  Each
+ * box's result equals og_tree_build + og_tree_force on that box alone
+ * (same tree, lists and summation order).  Pointers follow OG_DEVICE_PTRS
+ * of boxes[0].params.flags.  The total particle count must be < 2^26.
+ * info may be NULL. */
+og_status og_batch_force(og_ctx *ctx, int64_t nbox, const og_box *boxes, og_batch_info *info);
+
 /* Copy one internal array of the tree to host memory (test and debug use).
  * field: one of og_field; bytes must equal the field's size:
  *   OG_F_SKEY     uint64[n]      sorted Morton keys

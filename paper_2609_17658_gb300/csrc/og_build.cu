@@ -2,7 +2,11 @@
 //
 // The paper builds the tree by inserting particles one at a time in
 // space-filling-curve order and then computing moments bottom-up.  Here the
-// same tree is built fully in parallel from the sorted keys:
+// same tree is built fully in parallel from the sorted keys, for a forest of
+// B independent periodic boxes (segments) at once: the particles of all boxes
+// are concatenated, sorted by (box, key), and every box gets its own root
+// (node ids 0..B-1).  A single system is the forest with B = 1.  Splits
+// between two boxes are separators: no node spans them.
 //
 //   a1/a2  k_quantize_keys   f64 positions -> u32 fixed point -> 63-bit Morton key
 //   a3     radix sort (og_sort.cu), k_permute gathers sorted SoA positions/masses
@@ -26,6 +30,7 @@
 // result is identical to the oracle's recursive construction.
 #include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "og_internal.h"
 
@@ -33,6 +38,7 @@ namespace og {
 namespace {
 
 constexpr int kT = 256;
+constexpr uint8_t kSep = 0xff;  // split level of a boundary between two boxes
 
 __device__ __forceinline__ uint64_t spread21(uint32_t v) {
     uint64_t x = v & 0x1fffffu;
@@ -69,12 +75,28 @@ __device__ __forceinline__ uint32_t quantize(double v, double box, double inv_bo
     return (uint32_t)floor(f * 4294967296.0);
 }
 
+// segment (box) of every particle of the concatenated input
+__global__ void k_fill_seg(int64_t n, int64_t B, const uint32_t *__restrict__ seg_off, uint32_t *pseg) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t lo = 0, hi = B;  // seg_off[lo] <= i < seg_off[hi]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) / 2;
+        if ((uint64_t)seg_off[mid] <= (uint64_t)i) lo = mid; else hi = mid;
+    }
+    pseg[i] = (uint32_t)lo;
+}
+
 __global__ void k_quantize_keys(const double *__restrict__ pos, const double *__restrict__ mass,
-                                int64_t n, double box, double inv_box, bool pow2, uint32_t *qx,
-                                uint32_t *qy, uint32_t *qz, uint64_t *key, uint32_t *idx,
+                                int64_t n, const uint32_t *__restrict__ pseg,
+                                const SegGeom *__restrict__ geom, uint32_t *qx, uint32_t *qy,
+                                uint32_t *qz, uint64_t *key, uint64_t *key_copy, uint32_t *idx,
                                 uint32_t *status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const SegGeom g = geom[pseg ? pseg[i] : 0];
+    const double box = g.box, inv_box = g.inv_box;
+    const bool pow2 = g.pow2 != 0;
     uint32_t x = quantize(pos[3 * i + 0], box, inv_box, pow2, status);
     uint32_t y = quantize(pos[3 * i + 1], box, inv_box, pow2, status);
     uint32_t z = quantize(pos[3 * i + 2], box, inv_box, pow2, status);
@@ -83,8 +105,28 @@ __global__ void k_quantize_keys(const double *__restrict__ pos, const double *__
     qx[i] = x;
     qy[i] = y;
     qz[i] = z;
-    key[i] = (spread21(x >> 11) << 2) | (spread21(y >> 11) << 1) | spread21(z >> 11);
+    const uint64_t k = (spread21(x >> 11) << 2) | (spread21(y >> 11) << 1) | spread21(z >> 11);
+    key[i] = k;
+    if (key_copy) key_copy[i] = k;
     idx[i] = (uint32_t)i;
+}
+
+// after the key sort: sort key = box index of each particle (stable second pass)
+__global__ void k_seg_keys(int64_t n, const uint32_t *__restrict__ idx,
+                           const uint32_t *__restrict__ pseg, uint64_t *segkey) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    segkey[i] = pseg[idx[i]];
+}
+
+__global__ void k_gather_keys(int64_t n, const uint32_t *__restrict__ perm,
+                              const uint64_t *__restrict__ key0, const uint32_t *__restrict__ pseg,
+                              uint64_t *skey, uint32_t *sseg) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    skey[i] = key0[j];
+    sseg[i] = pseg[j];
 }
 
 __global__ void k_permute(int64_t n, const uint32_t *__restrict__ perm,
@@ -102,26 +144,35 @@ __global__ void k_permute(int64_t n, const uint32_t *__restrict__ perm,
     pm32[i] = __double2float_rn(m);
 }
 
-__global__ void k_split_levels(const uint64_t *__restrict__ skey, int64_t n, uint8_t *lv) {
+__global__ void k_split_levels(const uint64_t *__restrict__ skey, const uint32_t *__restrict__ sseg,
+                               int64_t n, uint8_t *lv) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
-    lv[i] = (uint8_t)lcp_levels(skey[i], skey[i + 1]);
+    lv[i] = (sseg[i] != sseg[i + 1]) ? kSep : (uint8_t)lcp_levels(skey[i], skey[i + 1]);
 }
 
 // Node of split i: the maximal key range around i whose keys share lv[i]
 // leading digits.  It is the node's first split iff no split of the same
 // level lies between the range start and i.
 __global__ void k_split_nodes(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ lv,
+                              const uint32_t *__restrict__ sseg, const uint32_t *__restrict__ seg_off,
                               int64_t n, uint32_t *sb, uint32_t *se, uint32_t *first) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
+    if (lv[i] == kSep) {
+        sb[i] = se[i] = 0;
+        first[i] = 0;
+        return;
+    }
     const int L = lv[i];
     const uint64_t ki = skey[i];
+    const uint32_t sg = sseg[i];
+    const int64_t lo_bound = seg_off[sg], hi_bound = seg_off[sg + 1];  // this box's particles
     // smallest b <= i with lcp(skey[b], ki) >= L: gallop left, then bisect
-    int64_t ok = i, step = 1, bad = -1;
+    int64_t ok = i, step = 1, bad = lo_bound - 1;
     while (true) {
         int64_t j = i - step;
-        if (j < 0) { bad = -1; break; }
+        if (j < lo_bound) { bad = lo_bound - 1; break; }
         if (lcp_levels(skey[j], ki) >= L) { ok = j; step <<= 1; }
         else { bad = j; break; }
     }
@@ -133,10 +184,10 @@ __global__ void k_split_nodes(const uint64_t *__restrict__ skey, const uint8_t *
     // largest e-1 >= i+1 with lcp(ki, skey[e-1]) >= L
     ok = i + 1;
     step = 1;
-    int64_t badr = n;
+    int64_t badr = hi_bound;
     while (true) {
         int64_t j = i + 1 + step;
-        if (j >= n) { badr = n; break; }
+        if (j >= hi_bound) { badr = hi_bound; break; }
         if (lcp_levels(ki, skey[j]) >= L) { ok = j; step <<= 1; }
         else { badr = j; break; }
     }
@@ -149,18 +200,19 @@ __global__ void k_split_nodes(const uint64_t *__restrict__ skey, const uint8_t *
     first[i] = (L >= 1 && (b == i || lcp_levels(skey[b], ki) > L)) ? 1u : 0u;
 }
 
-__global__ void k_node_init(int64_t n, const uint32_t *__restrict__ first,
-                            const uint32_t *__restrict__ nid, const uint8_t *__restrict__ lv,
-                            const uint32_t *__restrict__ sb, const uint32_t *__restrict__ se,
-                            uint8_t *nlev, uint32_t *nbeg, uint32_t *nend) {
+__global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ seg_off,
+                            const uint32_t *__restrict__ first, const uint32_t *__restrict__ nid,
+                            const uint8_t *__restrict__ lv, const uint32_t *__restrict__ sb,
+                            const uint32_t *__restrict__ se, uint8_t *nlev, uint32_t *nbeg,
+                            uint32_t *nend) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) {
-        nlev[0] = 0;
-        nbeg[0] = 0;
-        nend[0] = (uint32_t)n;
+    if (i < B) {  // the root of box i covers the whole box
+        nlev[i] = 0;
+        nbeg[i] = seg_off[i];
+        nend[i] = seg_off[i + 1];
     }
     if (i >= n - 1 || !first[i]) return;
-    uint32_t id = 1 + nid[i];
+    uint32_t id = (uint32_t)B + nid[i];
     nlev[id] = lv[i];
     nbeg[id] = sb[i];
     nend[id] = se[i];
@@ -168,12 +220,14 @@ __global__ void k_node_init(int64_t n, const uint32_t *__restrict__ first,
 
 __global__ void k_split_node_id(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ lv,
                                 const uint32_t *__restrict__ sb, const uint32_t *__restrict__ first,
-                                const uint32_t *__restrict__ nid, int64_t n, uint32_t *sid) {
+                                const uint32_t *__restrict__ nid, const uint32_t *__restrict__ sseg,
+                                int64_t n, int64_t B, uint32_t *sid) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     const int L = lv[i];
-    if (L == 0) { sid[i] = 0; return; }
-    if (first[i]) { sid[i] = 1 + nid[i]; return; }
+    if (L == kSep) { sid[i] = 0xffffffffu; return; }
+    if (L == 0) { sid[i] = sseg[i]; return; }  // the root of this box
+    if (first[i]) { sid[i] = (uint32_t)B + nid[i]; return; }
     // first split f in [b, i]: smallest j with lcp(skey[b], skey[j+1]) == L
     const int64_t b = sb[i];
     const uint64_t kb = skey[b];
@@ -182,36 +236,42 @@ __global__ void k_split_node_id(const uint64_t *__restrict__ skey, const uint8_t
         int64_t mid = lo + (hi - lo) / 2;
         if (lcp_levels(kb, skey[mid + 1]) <= L) hi = mid; else lo = mid + 1;
     }
-    sid[i] = 1 + nid[lo];
+    sid[i] = (uint32_t)B + nid[lo];
 }
 
-__global__ void k_link(int64_t n, int64_t m, const uint64_t *__restrict__ skey,
+__device__ __forceinline__ int split_at(const uint8_t *lv, int64_t j, int64_t n) {
+    if (j < 0 || j >= n - 1) return -1;
+    const uint8_t v = lv[j];
+    return v == kSep ? -1 : (int)v;
+}
+
+// parent of every non-root node, owner of every particle, octant occupancy
+__global__ void k_link(int64_t n, int64_t m, int64_t B, const uint64_t *__restrict__ skey,
                        const uint8_t *__restrict__ lv, const uint32_t *__restrict__ sid,
-                       const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ nbeg,
-                       const uint32_t *__restrict__ nend, int32_t *npar, uint32_t *owner,
-                       uint32_t *occ, uint32_t *nnc, uint32_t *status) {
+                       const uint32_t *__restrict__ sseg, const uint8_t *__restrict__ nlev,
+                       const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
+                       int32_t *npar, uint32_t *owner, uint32_t *occ, uint32_t *nnc,
+                       uint32_t *status) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) {
         const int64_t p = t;
-        int dl = p > 0 ? lv[p - 1] : -1;
-        int dr = p < n - 1 ? lv[p] : -1;
+        const int dl = split_at(lv, p - 1, n), dr = split_at(lv, p, n);
         uint32_t own;
-        if (dl < 0 && dr < 0) own = 0;
+        if (dl < 0 && dr < 0) own = sseg[p];  // alone in its box: hangs from the root
         else own = sid[dl >= dr ? p - 1 : p];
         if (own >= (uint32_t)m) {
             atomicOr(status, ST_INTERNAL);
-            own = 0;
+            own = sseg[p];
         }
         owner[p] = own;
         int lo = nlev[own];
         if (lo < kLevels) atomicOr(&occ[own], 1u << digit_at(skey[p], lo + 1));
-    } else if (t < n + m - 1) {
-        const int64_t id = t - n + 1;
+    } else if (t < n + (m - B)) {
+        const int64_t id = B + (t - n);
         const int64_t b = nbeg[id], e = nend[id];
-        int dl = b > 0 ? lv[b - 1] : -1;
-        int dr = e < n ? lv[e - 1] : -1;
+        const int dl = split_at(lv, b - 1, n), dr = split_at(lv, e - 1, n);
         uint32_t par;
-        if (dl < 0 && dr < 0) par = 0;
+        if (dl < 0 && dr < 0) par = sseg[b];  // the whole box: child of its root
         else par = sid[dl >= dr ? b - 1 : e - 1];
         npar[id] = (int32_t)par;
         if (par >= (uint32_t)m || nlev[par] >= nlev[id] || nlev[par] >= kLevels) {
@@ -220,8 +280,8 @@ __global__ void k_link(int64_t n, int64_t m, const uint64_t *__restrict__ skey,
         }
         atomicOr(&occ[par], 1u << digit_at(skey[b], nlev[par] + 1));
         atomicAdd(&nnc[par], 1u);
-    } else if (t == n + m - 1) {
-        npar[0] = -1;
+    } else if (t < n + m) {
+        npar[t - n - (m - B)] = -1;  // roots
     }
 }
 
@@ -233,7 +293,7 @@ __global__ void k_ccnt(int64_t m, const uint8_t *__restrict__ nlev,
     nccnt[id] = nlev[id] == kLevels ? nend[id] - nbeg[id] : (uint32_t)__popc(occ[id]);
 }
 
-__global__ void k_place(int64_t n, int64_t m, const uint64_t *__restrict__ skey,
+__global__ void k_place(int64_t n, int64_t m, int64_t B, const uint64_t *__restrict__ skey,
                         const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ nbeg,
                         const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
                         const int32_t *__restrict__ npar, const uint32_t *__restrict__ owner,
@@ -252,8 +312,8 @@ __global__ void k_place(int64_t n, int64_t m, const uint64_t *__restrict__ skey,
         }
         if (slot >= (uint64_t)nchild) { atomicOr(status, ST_INTERNAL); return; }
         child[slot] = (uint32_t)p;
-    } else if (t < n + m - 1) {
-        const int64_t id = t - n + 1;
+    } else if (t < n + m - B) {
+        const int64_t id = B + (t - n);
         uint32_t par = (uint32_t)npar[id];
         int d = digit_at(skey[nbeg[id]], nlev[par] + 1);
         uint32_t slot = ncbeg[par] + __popc(occ[par] & ((1u << d) - 1u));
@@ -263,7 +323,8 @@ __global__ void k_place(int64_t n, int64_t m, const uint64_t *__restrict__ skey,
     }
 }
 
-__global__ void k_threading(int64_t n, int64_t m, int64_t nchild, const uint32_t *__restrict__ child,
+__global__ void k_threading(int64_t n, int64_t m, int64_t B, int64_t nchild,
+                            const uint32_t *__restrict__ child,
                             const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ nccnt,
                             const int32_t *__restrict__ npar, const uint32_t *__restrict__ npos,
                             const uint32_t *__restrict__ owner, int32_t *nnext, int32_t *nsib,
@@ -271,7 +332,7 @@ __global__ void k_threading(int64_t n, int64_t m, int64_t nchild, const uint32_t
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c < m) {
         nnext[c] = (int32_t)child[ncbeg[c]];
-        if (c == 0) nsib[0] = -1;
+        if (c < B) nsib[c] = -1;  // a root ends its box's threading
     }
     if (c >= nchild) return;
     const uint32_t item = child[c];
@@ -281,7 +342,7 @@ __global__ void k_threading(int64_t n, int64_t m, int64_t nchild, const uint32_t
     for (int guard = 0;; ++guard) {
         if (guard > 2 * kLevels + 2 || par < 0 || par >= m) { atomicOr(status, ST_INTERNAL); break; }
         if (cc + 1 < (int64_t)ncbeg[par] + nccnt[par]) { after = (int32_t)child[cc + 1]; break; }
-        if (par == 0) { after = -1; break; }
+        if (par < B) { after = -1; break; }
         cc = npos[par];
         par = npar[par];
     }
@@ -424,16 +485,17 @@ __global__ void __launch_bounds__(kT) k_moments_level(
 }
 
 // frontier node of p: the deepest node with more than G particles containing
-// p (or the root); unit: the child of the frontier node that contains p
+// p (or its box's root); unit: the child of the frontier node that contains p
 // (its first particle), or p itself when p hangs directly from it
-__global__ void k_frontier(int64_t n, int G, const uint32_t *__restrict__ owner,
+__global__ void k_frontier(int64_t n, int64_t B, int G, const uint32_t *__restrict__ owner,
                            const int32_t *__restrict__ npar, const uint32_t *__restrict__ nbeg,
                            const uint32_t *__restrict__ nend, uint32_t *fp, uint32_t *unit) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     uint32_t node = owner[p];
     int64_t prev = -1;
-    for (int guard = 0; node != 0 && nend[node] - nbeg[node] <= (uint32_t)G && guard <= kLevels + 2;
+    for (int guard = 0; node >= (uint64_t)B && nend[node] - nbeg[node] <= (uint32_t)G &&
+                        guard <= kLevels + 2;
          ++guard) {
         prev = node;
         node = (uint32_t)npar[node];
@@ -473,10 +535,11 @@ __global__ void k_group_init(int64_t n, const uint32_t *__restrict__ gs,
 __global__ void k_group_fin(int64_t n, int64_t ng, const uint32_t *__restrict__ gbeg,
                             uint32_t *gend, const uint32_t *__restrict__ px,
                             const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
-                            uint32_t *gbox) {
+                            const uint32_t *__restrict__ sseg, uint32_t *gbox, uint32_t *gseg) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng) return;
     uint32_t b = gbeg[g];
+    gseg[g] = sseg[b];
     uint32_t e = (g + 1 < ng) ? gbeg[g + 1] : (uint32_t)n;
     gend[g] = e;
     uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
@@ -543,31 +606,31 @@ struct Bump {
 
 }  // namespace
 
-// Bytes of the persistent arrays of a tree with n particles.
-static size_t tree_bytes(int64_t n, bool alloc) {
-    (void)alloc;
-    int64_t m = n;            // nodes <= n
-    int64_t c = n + m;        // children = (n - 1) + nodes <= 2n
+// Bytes of the persistent arrays of a forest with n particles in B boxes.
+static size_t tree_bytes(int64_t n, int64_t B) {
+    int64_t m = n + B;        // nodes: B roots + at most n - B split nodes
+    int64_t c = n + m;        // children = n + (m - B)
     size_t b = 0;
     auto add = [&](size_t sz, int64_t cnt) { b += ((size_t)(cnt > 0 ? cnt : 1) * sz + 255) & ~(size_t)255; };
-    add(8, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n); add(8, n);    // particles
+    add(8, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n); add(8, n); add(4, n);  // particles
     add(1, m); add(4, m); add(4, m); add(4, m); add(4, m); add(4, m);               // nlev..npos
     add(4, m); add(4, m); add(4, m); add(8, m); add(8, 3 * m); add(4, 3 * m);       // npar.. ncom
     add(4, n); add(4, n);                                                           // pnext, owner
     add(4, c); add(32, c);                                                          // child, crec
-    add(4, n); add(4, n); add(4, 6 * n); add(4, n); add(4, n);                      // groups
+    add(4, n); add(4, n); add(4, 6 * n); add(4, n); add(4, n); add(4, n);           // groups
     add(4, 3 * n); add(4, 3 * n); add(4, n); add(4, n);                             // force arrays
+    add(4, B + 1); add(sizeof(SegGeom), B); add(sizeof(WalkParams), 2 * B);         // boxes
     return b + 4096;
 }
 
 og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     cudaStream_t s = t->ctx->stream;
     const int64_t n = t->n;
-    const og_params &p = t->prm;
+    const int64_t B = t->nseg;
     cudaError_t err;
 
     // ---- persistent arrays
-    size_t tb = tree_bytes(n, true);
+    size_t tb = tree_bytes(n, B);
     if ((err = cudaMallocAsync(&t->arena, tb, s)) != cudaSuccess) {
         t->arena = nullptr;
         return err == cudaErrorMemoryAllocation ? (set_error("device allocation of %zu bytes failed", tb), OG_ERR_OOM)
@@ -575,7 +638,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     }
     t->arena_bytes = tb;
     Bump A(t->arena, tb);
-    const int64_t mcap = n, ccap = 2 * n;
+    const int64_t mcap = n + B, ccap = n + mcap;
     t->skey = A.take<uint64_t>(n);
     t->perm = A.take<uint32_t>(n);
     t->px = A.take<uint32_t>(n);
@@ -583,6 +646,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     t->pz = A.take<uint32_t>(n);
     t->pm32 = A.take<float>(n);
     t->pm64 = A.take<double>(n);
+    t->sseg = A.take<uint32_t>(n);
     t->nlev = A.take<uint8_t>(mcap);
     t->nbeg = A.take<uint32_t>(mcap);
     t->nend = A.take<uint32_t>(mcap);
@@ -604,46 +668,67 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     t->gbox = A.take<uint32_t>(6 * n);
     t->gcost = A.take<uint32_t>(n);
     t->gorder = A.take<uint32_t>(n);
+    t->gseg = A.take<uint32_t>(n);
     t->a_sorted = A.take<float>(3 * n);
     t->a_old_sorted = A.take<float>(3 * n);
     t->npp_sorted = A.take<uint32_t>(n);
     t->npn_sorted = A.take<uint32_t>(n);
+    t->seg_off = A.take<uint32_t>(B + 1);
+    t->geom = A.take<SegGeom>(B);
+    t->segp = A.take<WalkParams>(2 * B);
     if (A.off > tb) { set_error("internal: arena overflow"); return OG_ERR_STATE; }
+
+    // ---- box table
+    {
+        std::vector<SegGeom> hg((size_t)B);
+        for (int64_t b = 0; b < B; ++b) {
+            int e2 = 0;
+            hg[b].box = t->seg_prm[b].box;
+            hg[b].inv_box = 1.0 / t->seg_prm[b].box;
+            hg[b].pow2 = std::frexp(t->seg_prm[b].box, &e2) == 0.5 ? 1 : 0;
+        }
+        cudaMemcpyAsync(t->seg_off, t->h_seg_off.data(), (B + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(t->geom, hg.data(), B * sizeof(SegGeom), cudaMemcpyHostToDevice, s);
+        // the host vector must outlive the copy
+        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "build (boxes)");
+    }
 
     // ---- scratch
     size_t sb_bytes = 0;
     {
         auto add = [&](size_t sz, int64_t cnt) { sb_bytes += ((size_t)(cnt > 0 ? cnt : 1) * sz + 255) & ~(size_t)255; };
-        add(4, n); add(4, n); add(4, n);        // qx qy qz
-        add(8, n); add(4, n); add(8, n); add(4, n);  // keys, idx, alt
+        add(4, n); add(4, n); add(4, n);                        // qx qy qz
+        add(8, n); add(4, n); add(8, n); add(4, n); add(8, n); add(4, n);  // keys, idx, alt, key copy, pseg
         add(1, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // lv sb se first nid sid
-        add(4, n); add(4, n); add(4, n); add(4, n); add(4, 3 * 24);  // occ nnc arrive lnodes levels
+        add(4, n + B); add(4, n + B); add(4, n + B); add(4, 3 * 24);  // occ nnc lnodes levels
         add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs gid unit
-        sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + 8) + 4096;
+        sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + B + 8) + 4096;
     }
     void *scratch = nullptr;
     if ((err = cudaMallocAsync(&scratch, sb_bytes, s)) != cudaSuccess)
         return err == cudaErrorMemoryAllocation ? (set_error("device allocation of %zu bytes failed", sb_bytes), OG_ERR_OOM)
                                                 : cuda_fail(err, "cudaMallocAsync");
-    Bump B(scratch, sb_bytes);
-    uint32_t *qx = B.take<uint32_t>(n), *qy = B.take<uint32_t>(n), *qz = B.take<uint32_t>(n);
-    uint64_t *keys = B.take<uint64_t>(n);
-    uint32_t *idx = B.take<uint32_t>(n);
-    uint64_t *keys_alt = B.take<uint64_t>(n);
-    uint32_t *idx_alt = B.take<uint32_t>(n);
-    uint8_t *lv = B.take<uint8_t>(n);
-    uint32_t *sbeg = B.take<uint32_t>(n), *send = B.take<uint32_t>(n);
-    uint32_t *first = B.take<uint32_t>(n), *nid = B.take<uint32_t>(n), *sid = B.take<uint32_t>(n);
-    uint32_t *occ = B.take<uint32_t>(n), *nnc = B.take<uint32_t>(n), *arrive = B.take<uint32_t>(n);
-    uint32_t *lnodes = B.take<uint32_t>(n);
-    uint32_t *lcount = B.take<uint32_t>(3 * (kLevels + 2));
+    Bump W(scratch, sb_bytes);
+    uint32_t *qx = W.take<uint32_t>(n), *qy = W.take<uint32_t>(n), *qz = W.take<uint32_t>(n);
+    uint64_t *keys = W.take<uint64_t>(n);
+    uint32_t *idx = W.take<uint32_t>(n);
+    uint64_t *keys_alt = W.take<uint64_t>(n);
+    uint32_t *idx_alt = W.take<uint32_t>(n);
+    uint64_t *key0 = W.take<uint64_t>(n);
+    uint32_t *pseg = W.take<uint32_t>(n);
+    uint8_t *lv = W.take<uint8_t>(n);
+    uint32_t *sbeg = W.take<uint32_t>(n), *send = W.take<uint32_t>(n);
+    uint32_t *first = W.take<uint32_t>(n), *nid = W.take<uint32_t>(n), *sid = W.take<uint32_t>(n);
+    uint32_t *occ = W.take<uint32_t>(n + B), *nnc = W.take<uint32_t>(n + B);
+    uint32_t *lnodes = W.take<uint32_t>(n + B);
+    uint32_t *lcount = W.take<uint32_t>(3 * (kLevels + 2));
     uint32_t *loff = lcount + (kLevels + 2), *lcursor = lcount + 2 * (kLevels + 2);
-    uint32_t *fp = B.take<uint32_t>(n), *rs = B.take<uint32_t>(n), *gs = B.take<uint32_t>(n);
-    uint32_t *gid = B.take<uint32_t>(n);
-    uint32_t *unit = B.take<uint32_t>(n);
-    void *sort_scratch = B.take<char>((int64_t)radix_sort_scratch_bytes(n));
-    void *scan_scratch = B.take<char>((int64_t)scan_scratch_bytes(2 * n + 8));
-    uint32_t *d_tot = B.take<uint32_t>(4);
+    uint32_t *fp = W.take<uint32_t>(n), *rs = W.take<uint32_t>(n), *gs = W.take<uint32_t>(n);
+    uint32_t *gid = W.take<uint32_t>(n);
+    uint32_t *unit = W.take<uint32_t>(n);
+    void *sort_scratch = W.take<char>((int64_t)radix_sort_scratch_bytes(n));
+    void *scan_scratch = W.take<char>((int64_t)scan_scratch_bytes(2 * n + B + 8));
+    uint32_t *d_tot = W.take<uint32_t>(4);
     uint32_t *status = t->ctx->d_status;
 
     cudaEvent_t e0, e1;
@@ -652,25 +737,43 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     cudaEventRecord(e0, s);
 
     // a1, a2
-    int box_exp = 0;
-    const bool box_pow2 = std::frexp(p.box, &box_exp) == 0.5;
-    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, d_mass, n, p.box, 1.0 / p.box, box_pow2, qx, qy, qz,
-                                           keys, idx, status); note_launch();
-    // a3
+    if (B > 1) {
+        k_fill_seg<<<nblk(n), kT, 0, s>>>(n, B, t->seg_off, pseg); note_launch();
+    }
+    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, d_mass, n, B > 1 ? pseg : nullptr, t->geom, qx, qy,
+                                           qz, keys, B > 1 ? key0 : nullptr, idx, status); note_launch();
+    // a3: by key, then (several boxes) stably by box
     bool in_alt = false;
     radix_sort_pairs(keys, idx, keys_alt, idx_alt, n, 63, sort_scratch, s, &in_alt);
-    const uint64_t *skey_src = in_alt ? keys_alt : keys;
-    const uint32_t *perm_src = in_alt ? idx_alt : idx;
-    cudaMemcpyAsync(t->skey, skey_src, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    if (B > 1) {
+        uint32_t *perm1 = in_alt ? idx_alt : idx;
+        uint64_t *segkey = in_alt ? keys : keys_alt;      // the free key buffer
+        uint64_t *segkey_alt = in_alt ? keys_alt : keys;
+        uint32_t *perm1_alt = in_alt ? idx : idx_alt;
+        k_seg_keys<<<nblk(n), kT, 0, s>>>(n, perm1, pseg, segkey); note_launch();
+        int bits = 1;
+        while ((1ll << bits) < B) ++bits;
+        bool alt2 = false;
+        radix_sort_pairs(segkey, perm1, segkey_alt, perm1_alt, n, bits, sort_scratch, s, &alt2);
+        const uint32_t *perm_src = alt2 ? perm1_alt : perm1;
+        cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        k_gather_keys<<<nblk(n), kT, 0, s>>>(n, t->perm, key0, pseg, t->skey, t->sseg); note_launch();
+    } else {
+        const uint64_t *skey_src = in_alt ? keys_alt : keys;
+        const uint32_t *perm_src = in_alt ? idx_alt : idx;
+        cudaMemcpyAsync(t->skey, skey_src, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(t->sseg, 0, n * sizeof(uint32_t), s);
+    }
     k_permute<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, d_mass, t->px, t->py, t->pz, t->pm32,
                                      t->pm64); note_launch();
     // a4: nodes from splits
     uint32_t h_tot[4] = {0, 0, 0, 0};
     int64_t nsplit = n - 1;
     if (nsplit > 0) {
-        k_split_levels<<<nblk(nsplit), kT, 0, s>>>(t->skey, n, lv); note_launch();
-        k_split_nodes<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, n, sbeg, send, first); note_launch();
+        k_split_levels<<<nblk(nsplit), kT, 0, s>>>(t->skey, t->sseg, n, lv); note_launch();
+        k_split_nodes<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, t->sseg, t->seg_off, n, sbeg, send,
+                                                  first); note_launch();
         scan_exclusive_u32(first, nid, nsplit, d_tot, scan_scratch, s);
         cudaMemcpyAsync(h_tot, d_tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if ((err = cudaStreamSynchronize(s)) != cudaSuccess) {
@@ -678,24 +781,24 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
             return cuda_fail(err, "build (sort)");
         }
     }
-    const int64_t m = 1 + (int64_t)h_tot[0];
+    const int64_t m = B + (int64_t)h_tot[0];
     t->nnodes = m;
-    k_node_init<<<nblk(nsplit > 0 ? nsplit : 1), kT, 0, s>>>(n, first, nid, lv, sbeg, send, t->nlev,
-                                                             t->nbeg, t->nend); note_launch();
-    if (nsplit > 0)
-        k_split_node_id<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, sbeg, first, nid, n, sid); note_launch();
+    k_node_init<<<nblk(nsplit > B ? nsplit : B), kT, 0, s>>>(n, B, t->seg_off, first, nid, lv, sbeg,
+                                                            send, t->nlev, t->nbeg, t->nend); note_launch();
+    if (nsplit > 0) {
+        k_split_node_id<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, sbeg, first, nid, t->sseg, n, B, sid); note_launch();
+    }
     cudaMemsetAsync(occ, 0, m * sizeof(uint32_t), s);
     cudaMemsetAsync(nnc, 0, m * sizeof(uint32_t), s);
-    cudaMemsetAsync(arrive, 0, m * sizeof(uint32_t), s);
-    k_link<<<nblk(n + m), kT, 0, s>>>(n, m, t->skey, lv, sid, t->nlev, t->nbeg, t->nend, t->npar,
-                                      t->owner, occ, nnc, status); note_launch();
+    k_link<<<nblk(n + m), kT, 0, s>>>(n, m, B, t->skey, lv, sid, t->sseg, t->nlev, t->nbeg, t->nend,
+                                      t->npar, t->owner, occ, nnc, status); note_launch();
     k_ccnt<<<nblk(m), kT, 0, s>>>(m, t->nlev, t->nbeg, t->nend, occ, t->nccnt); note_launch();
     scan_exclusive_u32(t->nccnt, t->ncbeg, m, d_tot + 1, scan_scratch, s);
-    const int64_t nchild = (n - 1) + m;
+    const int64_t nchild = n + (m - B);
     t->nchild = nchild;
-    k_place<<<nblk(n + m), kT, 0, s>>>(n, m, t->skey, t->nlev, t->nbeg, t->ncbeg, occ, t->npar,
+    k_place<<<nblk(n + m), kT, 0, s>>>(n, m, B, t->skey, t->nlev, t->nbeg, t->ncbeg, occ, t->npar,
                                        t->owner, t->child, t->npos, nchild, status); note_launch();
-    k_threading<<<nblk(nchild), kT, 0, s>>>(n, m, nchild, t->child, t->ncbeg, t->nccnt, t->npar,
+    k_threading<<<nblk(nchild), kT, 0, s>>>(n, m, B, nchild, t->child, t->ncbeg, t->nccnt, t->npar,
                                             t->npos, t->owner, t->nnext, t->nsib, t->pnext, status); note_launch();
     // a5 (part 1): node ids by level
     cudaMemsetAsync(lcount, 0, (kLevels + 2) * sizeof(uint32_t), s);
@@ -703,9 +806,9 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     k_level_hist<<<lv_blocks, kT, 0, s>>>(m, t->nlev, lcount); note_launch();
     k_level_offsets<<<1, 32, 0, s>>>(lcount, loff, lcursor); note_launch();
     k_level_scatter<<<lv_blocks, kT, 0, s>>>(m, t->nlev, loff, lcursor, lnodes); note_launch();
-    // a6: groups
-    const int G = p.group_max;
-    k_frontier<<<nblk(n), kT, 0, s>>>(n, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit); note_launch();
+    // a6: groups (one group size for the whole forest)
+    const int G = t->prm.group_max;
+    k_frontier<<<nblk(n), kT, 0, s>>>(n, B, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit); note_launch();
     k_runmark<<<nblk(n), kT, 0, s>>>(n, fp, rs); note_launch();
     scan_inclusive_max_u32(rs, rs, n, scan_scratch, s);
     k_groupmark<<<nblk(n), kT, 0, s>>>(n, G, rs, fp, unit, t->nbeg, t->nend, gs); note_launch();
@@ -741,7 +844,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         }
     }
     k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
-                                                t->pz, t->gbox); note_launch();
+                                                t->pz, t->sseg, t->gbox, t->gseg); note_launch();
     k_records<<<nblk(nchild), kT, 0, s>>>(n, nchild, t->child, t->px, t->py, t->pz, t->pm32,
                                           t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nM, t->ncom,
                                           t->crec); note_launch();

@@ -200,6 +200,9 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
     t->prm = *p;
     if (t->prm.group_max == 0) t->prm.group_max = 32;
     t->n = n;
+    t->nseg = 1;
+    t->seg_prm.assign(1, t->prm);
+    t->h_seg_off = {0u, (uint32_t)n};
     cudaStream_t s = c->stream;
     const double *d_pos = pos, *d_mass = mass;
     void *staging = nullptr;
@@ -227,6 +230,52 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
     return OG_OK;
 }
 
+}  // extern "C"
+
+namespace og {
+
+// Both passes of the force on a built tree (sorted order, device results in
+// t->a_sorted, t->npp_sorted, t->npn_sorted).  d_aold: previous accelerations
+// in input order on the device, or null.
+og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out) {
+    cudaStream_t s = t->ctx->stream;
+    const int64_t n = t->n;
+    cudaError_t e;
+    float ms_walk = 0, ms = 0;
+    t->interactions = 0;
+    if (t->prm.flags & OG_DEBUG_DUMP_LISTS) {
+        if (!t->lists) {
+            t->list_cap = (int64_t)1 << 28;
+            if ((e = cudaMalloc(&t->lists, (size_t)t->list_cap * 2 * sizeof(uint32_t))) != cudaSuccess) {
+                t->lists = nullptr;
+                return cuda_fail(e, "cudaMalloc (lists)");
+            }
+        }
+        t->list_len = 0;
+    }
+    const float *a_old_sorted = nullptr;
+    if (t->prm.opening == OG_OPEN_REL) {
+        if (d_aold) {
+            k_gather_aold<<<nblk(n), kT, 0, s>>>(n, t->perm, d_aold, t->a_old_sorted); note_launch();
+        } else {
+            // first pass: Barnes-Hut with theta_first_pass
+            og_status st = walk_pass(t, OG_OPEN_BH, true, nullptr, t->a_old_sorted, &ms, false);
+            if (st) return st;
+            ms_walk += ms;
+        }
+        a_old_sorted = t->a_old_sorted;
+    }
+    og_status st = walk_pass(t, t->prm.opening, false, a_old_sorted, t->a_sorted, &ms, true);
+    if (st) return st;
+    ms_walk += ms;
+    if (ms_walk_out) *ms_walk_out = ms_walk;
+    return OG_OK;
+}
+
+}  // namespace og
+
+extern "C" {
+
 og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_pp,
                         uint32_t *n_pn) {
     if (!t || !acc) { set_error("NULL argument"); return OG_ERR_ARG; }
@@ -240,50 +289,21 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    t->interactions = 0;
-    float ms_walk = 0, ms;
-
-    // debug lists
-    if (t->prm.flags & OG_DEBUG_DUMP_LISTS) {
-        if (!t->lists) {
-            t->list_cap = (int64_t)1 << 28;
-            if ((e = cudaMalloc(&t->lists, (size_t)t->list_cap * 2 * sizeof(uint32_t))) != cudaSuccess) {
-                t->lists = nullptr;
-                return cuda_fail(e, "cudaMalloc (lists)");
-            }
-        }
-        t->list_len = 0;
-    }
-    // previous accelerations
-    const float *a_old_sorted = nullptr;
+    float ms_walk = 0, ms = 0;
     void *tmp = nullptr;
-    if (t->prm.opening == OG_OPEN_REL) {
-        if (a_old) {
-            const float *d_aold = a_old;
-            if (!dev) {
-                if ((e = cudaMallocAsync(&tmp, (size_t)n * 3 * sizeof(float), s)) != cudaSuccess)
-                    return cuda_fail(e, "cudaMallocAsync (a_old)");
-                cudaMemcpyAsync(tmp, a_old, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
-                d_aold = static_cast<const float *>(tmp);
-            }
-            k_gather_aold<<<nblk(n), kT, 0, s>>>(n, t->perm, d_aold, t->a_old_sorted); note_launch();
-        } else {
-            // first pass: Barnes-Hut with theta_first_pass
-            WalkParams w1 = make_walk_params(t->prm, OG_OPEN_BH, t->prm.theta_first_pass);
-            w1.dump = false;
-            og_status st = walk_pass(t, w1, nullptr, t->a_old_sorted, &ms, false);
-            if (st) return st;
-            ms_walk += ms;
+    const float *d_aold = nullptr;
+    if (t->prm.opening == OG_OPEN_REL && a_old) {
+        d_aold = a_old;
+        if (!dev) {
+            if ((e = cudaMallocAsync(&tmp, (size_t)n * 3 * sizeof(float), s)) != cudaSuccess)
+                return cuda_fail(e, "cudaMallocAsync (a_old)");
+            cudaMemcpyAsync(tmp, a_old, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+            d_aold = static_cast<const float *>(tmp);
         }
-        a_old_sorted = t->a_old_sorted;
     }
-    WalkParams w = make_walk_params(t->prm, t->prm.opening, t->prm.theta);
-    int64_t inter_before = t->interactions;
-    og_status st = walk_pass(t, w, a_old_sorted, t->a_sorted, &ms, true);
+    og_status st = force_sorted(t, d_aold, &ms_walk);
     if (tmp) cudaFreeAsync(tmp, s);
     if (st) return st;
-    (void)inter_before;
-    ms_walk += ms;
     // back to caller order
     float *d_acc = acc;
     uint32_t *d_npp = n_pp, *d_npn = n_pn;
@@ -311,6 +331,109 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
     t->ms_force = ms;
     t->ms_walk = ms_walk;
     return check_status(c);
+}
+
+og_status og_batch_force(og_ctx *c, int64_t nbox, const og_box *boxes, og_batch_info *info) {
+    if (!c || !boxes || nbox < 1) { set_error("og_batch_force: NULL argument or no boxes"); return OG_ERR_ARG; }
+    const og_params &p0 = boxes[0].params;
+    int64_t total = 0;
+    for (int64_t b = 0; b < nbox; ++b) {
+        const og_box &x = boxes[b];
+        if (!x.pos || !x.mass || !x.acc) { set_error("og_batch_force: box %lld has a NULL pointer", (long long)b); return OG_ERR_ARG; }
+        og_status st = validate(&x.params, x.n);
+        if (st) return st;
+        if (x.params.opening != p0.opening || (x.params.r_s > 0.0) != (p0.r_s > 0.0) ||
+            x.params.group_max != p0.group_max || x.params.flags != p0.flags ||
+            (x.a_old != nullptr) != (boxes[0].a_old != nullptr)) {
+            set_error("og_batch_force: opening, split on/off, group_max, flags and a_old presence must agree across boxes");
+            return OG_ERR_ARG;
+        }
+        total += x.n;
+    }
+    if (total > kMaxN) { set_error("og_batch_force: %lld particles in total exceed %lld", (long long)total, (long long)kMaxN); return OG_ERR_ARG; }
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const bool dev = (p0.flags & OG_DEVICE_PTRS) != 0;
+    const cudaMemcpyKind in_kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind out_kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    og_tree *t = new (std::nothrow) og_tree();
+    if (!t) { set_error("host allocation failed"); return OG_ERR_OOM; }
+    t->ctx = c;
+    t->prm = p0;
+    if (t->prm.group_max == 0) t->prm.group_max = 32;
+    t->n = total;
+    t->nseg = nbox;
+    t->seg_prm.resize((size_t)nbox);
+    t->h_seg_off.resize((size_t)nbox + 1);
+    uint32_t off = 0;
+    for (int64_t b = 0; b < nbox; ++b) {
+        t->seg_prm[b] = boxes[b].params;
+        t->h_seg_off[b] = off;
+        off += (uint32_t)boxes[b].n;
+    }
+    t->h_seg_off[nbox] = off;
+    // inputs, concatenated: positions, masses, previous accelerations
+    const bool have_aold = p0.opening == OG_OPEN_REL && boxes[0].a_old != nullptr;
+    size_t in_bytes = (size_t)total * 4 * sizeof(double) + (have_aold ? (size_t)total * 3 * sizeof(float) : 0) + 512;
+    void *in = nullptr;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&in, in_bytes, s)) != cudaSuccess) { delete t; return cuda_fail(e, "cudaMallocAsync (batch inputs)"); }
+    double *d_pos = static_cast<double *>(in);
+    double *d_mass = d_pos + 3 * total;
+    float *d_aold = have_aold ? reinterpret_cast<float *>(d_mass + total) : nullptr;
+    for (int64_t b = 0; b < nbox; ++b) {
+        const int64_t o = t->h_seg_off[b], nb = boxes[b].n;
+        cudaMemcpyAsync(d_pos + 3 * o, boxes[b].pos, (size_t)nb * 3 * sizeof(double), in_kind, s);
+        cudaMemcpyAsync(d_mass + o, boxes[b].mass, (size_t)nb * sizeof(double), in_kind, s);
+        if (have_aold) cudaMemcpyAsync(d_aold + 3 * o, boxes[b].a_old, (size_t)nb * 3 * sizeof(float), in_kind, s);
+    }
+    og_status st = build_tree(t, d_pos, d_mass);
+    if (st == OG_OK) st = check_status(c);
+    float ms_walk = 0;
+    if (st == OG_OK) st = force_sorted(t, d_aold, &ms_walk);
+    cudaFreeAsync(in, s);
+    if (st != OG_OK) {
+        og_tree_free(t);
+        return st;
+    }
+    // results back to every box in its own order
+    void *out = nullptr;
+    size_t out_bytes = (size_t)total * (3 * sizeof(float) + 2 * sizeof(uint32_t)) + 512;
+    if ((e = cudaMallocAsync(&out, out_bytes, s)) != cudaSuccess) { og_tree_free(t); return cuda_fail(e, "cudaMallocAsync (batch outputs)"); }
+    float *o_acc = static_cast<float *>(out);
+    uint32_t *o_pp = reinterpret_cast<uint32_t *>(o_acc + 3 * total);
+    uint32_t *o_pn = o_pp + total;
+    k_unpermute<<<nblk(total), kT, 0, s>>>(total, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+                                           o_acc, o_pp, o_pn); note_launch();
+    for (int64_t b = 0; b < nbox; ++b) {
+        const int64_t o = t->h_seg_off[b], nb = boxes[b].n;
+        cudaMemcpyAsync(boxes[b].acc, o_acc + 3 * o, (size_t)nb * 3 * sizeof(float), out_kind, s);
+        if (boxes[b].n_pp) cudaMemcpyAsync(boxes[b].n_pp, o_pp + o, (size_t)nb * sizeof(uint32_t), out_kind, s);
+        if (boxes[b].n_pn) cudaMemcpyAsync(boxes[b].n_pn, o_pn + o, (size_t)nb * sizeof(uint32_t), out_kind, s);
+    }
+    cudaFreeAsync(out, s);
+    cudaEventRecord(e1, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { og_tree_free(t); return cuda_fail(e, "batch"); }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (info) {
+        info->boxes = nbox;
+        info->particles = total;
+        info->groups = t->ngroups;
+        info->interactions = t->interactions;
+        info->ms_total = ms;
+        info->ms_build = t->ms_build;
+        info->ms_walk = ms_walk;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st = check_status(c);
+    og_tree_free(t);
+    return st;
 }
 
 og_status og_tree_info_get(const og_tree *t, og_tree_info *info) {

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "og.h"
 
@@ -38,7 +39,14 @@ struct __align__(16) CRec {
 };
 static_assert(sizeof(CRec) == 32, "CRec must be 32 bytes");
 
-struct Alloc;  // stream-ordered device allocator of a context
+// geometry of one box (segment) of a forest
+struct SegGeom {
+    double box, inv_box;
+    int pow2;        // box is a power of two: x / box == x * inv_box exactly
+    int pad;
+};
+
+struct WalkParams;
 
 }  // namespace og
 
@@ -54,8 +62,17 @@ struct og_ctx {
 
 struct og_tree {
     og_ctx *ctx = nullptr;
-    og_params prm{};
+    og_params prm{};                  // parameters shared by all boxes (flags, group size)
     int64_t n = 0, nnodes = 0, nchild = 0, ngroups = 0;
+    // boxes (segments) of the forest; a single system has nseg = 1
+    int64_t nseg = 1;
+    std::vector<og_params> seg_prm;   // per-box parameters
+    std::vector<uint32_t> h_seg_off;  // first particle of each box, plus n
+    uint32_t *seg_off = nullptr;      // device copy
+    og::SegGeom *geom = nullptr;
+    og::WalkParams *segp = nullptr;   // per-box walk parameters of the current pass
+    uint32_t *sseg = nullptr;         // box of each sorted particle
+    uint32_t *gseg = nullptr;         // box of each group
     // sorted particles
     uint64_t *skey = nullptr;
     uint32_t *perm = nullptr;
@@ -143,9 +160,11 @@ struct WalkParams {
     float kexp;        // -log2(e) / (4 r_s^2), grid units
     float out_scale;   // G (2^32/L)^2
 };
-// One walk launch over all groups.  use_order: take the groups longest list
-// first, by the list lengths of the previous pass on this tree (if any).
-og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted,
+// One walk launch over all groups of all boxes.  first_pass: the Barnes-Hut
+// pass that supplies a_old for the relative criterion (each box's
+// theta_first_pass).  use_order: take the groups longest list first, by the
+// list lengths of the previous pass on this tree (if any).
+og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
                     float *acc_sorted, float *ms_out, bool use_order);
 WalkParams make_walk_params(const og_params &p, int opening, double theta);
 

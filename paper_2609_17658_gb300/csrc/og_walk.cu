@@ -34,6 +34,8 @@
 // Work distribution: persistent blocks; warps take groups from a global
 // atomic counter, in decreasing order of the previous pass's list length
 // when that is known (longest first shortens the tail of the launch).
+#include <vector>
+
 #include "og_internal.h"
 
 namespace og {
@@ -63,7 +65,9 @@ struct WalkArgs {
     uint32_t *gcost;              // out: list length per group
     const CRec *crec;
     int64_t nchild, max_rounds;
-    uint32_t root_cbeg, root_ccnt;
+    const uint32_t *gseg;         // box of each group
+    const uint32_t *ncbeg, *nccnt;  // child range of each node (the roots are nodes 0..B-1)
+    const WalkParams *segp;       // per-box parameters
     const uint32_t *px, *py, *pz;
     const float *a_old;           // [3][n] sorted, relative criterion only
     float *acc;                   // [3][n] sorted, out
@@ -74,7 +78,6 @@ struct WalkArgs {
     unsigned long long *work;     // group counter
     unsigned long long *inter;    // interactions evaluated
     uint32_t *status;
-    WalkParams p;
 };
 
 // multi-function-unit approximations (PTX .approx with flush-to-zero); the
@@ -218,7 +221,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
     uint4 *chn = chf + kChunk;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
-    const WalkParams &p = a.p;
 
     while (true) {
         unsigned long long gq = 0;
@@ -226,6 +228,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         gq = __shfl_sync(FULL, gq, 0);
         if (gq >= (unsigned long long)a.ngroups) break;
         const int64_t g = a.gorder ? (int64_t)a.gorder[gq] : (int64_t)gq;
+        const uint32_t seg = a.gseg[g];
+        const WalkParams &p = a.segp[seg];
         const uint32_t gb = a.gbeg[g], ge = a.gend[g];
         const uint32_t gsize = ge - gb;
         uint32_t lo[3], hi[3];
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             arelf = __double2float_rn(arel);
         }
 
-        if (lane == 0) stk[0] = make_uint2(a.root_cbeg, a.root_ccnt);
+        if (lane == 0) stk[0] = make_uint2(a.ncbeg[seg], a.nccnt[seg]);
         __syncwarp();
         int sp = 1, cf = 0, cn = 0;
         int64_t rounds = 0;
@@ -520,9 +524,19 @@ WalkParams make_walk_params(const og_params &p, int opening, double theta) {
     return w;
 }
 
-og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted, float *acc_sorted,
-                    float *ms_out, bool use_order) {
+og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
+                    float *acc_sorted, float *ms_out, bool use_order) {
     cudaStream_t s = t->ctx->stream;
+    const int64_t B = t->nseg;
+    // per-box parameters of this pass: the first pass of the relative
+    // criterion is Barnes-Hut with each box's theta_first_pass
+    std::vector<WalkParams> hp((size_t)B);
+    for (int64_t b = 0; b < B; ++b) {
+        const og_params &q = t->seg_prm[b];
+        hp[b] = make_walk_params(q, opening, first_pass ? q.theta_first_pass : q.theta);
+        hp[b].dump = first_pass ? false : hp[b].dump;
+    }
+    const WalkParams &wp = hp[0];
     WalkArgs a{};
     a.n = t->n;
     a.ngroups = t->ngroups;
@@ -534,13 +548,13 @@ og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted,
     a.crec = t->crec;
     a.nchild = t->nchild;
     a.max_rounds = t->nchild + 2;
-    uint32_t root[2];
-    cudaMemcpyAsync(root, t->ncbeg, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(root + 1, t->nccnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-    cudaError_t err = cudaStreamSynchronize(s);
+    a.gseg = t->gseg;
+    a.ncbeg = t->ncbeg;
+    a.nccnt = t->nccnt;
+    WalkParams *dp = t->segp + (first_pass ? 0 : B);
+    cudaError_t err = cudaMemcpyAsync(dp, hp.data(), B * sizeof(WalkParams), cudaMemcpyHostToDevice, s);
     if (err != cudaSuccess) return cuda_fail(err, "walk setup");
-    a.root_cbeg = root[0];
-    a.root_ccnt = root[1];
+    a.segp = dp;
     void *sort_tmp = nullptr;
     if (use_order && t->have_cost && t->ngroups > 1) {
         // longest list first, from the costs of the previous pass on this tree
@@ -573,7 +587,6 @@ og_status walk_pass(og_tree *t, const WalkParams &wp, const float *a_old_sorted,
     a.inter = t->ctx->d_counters + 1;
     a.list_cursor = t->ctx->d_counters + 2;
     a.status = t->ctx->d_status;
-    a.p = wp;
     cudaMemsetAsync(t->ctx->d_counters, 0, 3 * sizeof(unsigned long long), s);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

@@ -59,6 +59,18 @@ class og_tree_info(C.Structure):
                 ("ms_build", C.c_double), ("ms_force", C.c_double), ("ms_walk", C.c_double)]
 
 
+class og_box(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("mass", C.c_void_p), ("n", C.c_int64),
+                ("params", og_params), ("a_old", C.c_void_p), ("acc", C.c_void_p),
+                ("n_pp", C.c_void_p), ("n_pn", C.c_void_p)]
+
+
+class og_batch_info(C.Structure):
+    _fields_ = [("boxes", C.c_int64), ("particles", C.c_int64), ("groups", C.c_int64),
+                ("interactions", C.c_int64), ("ms_total", C.c_double), ("ms_build", C.c_double),
+                ("ms_walk", C.c_double)]
+
+
 _lib = None
 
 
@@ -88,6 +100,8 @@ def lib():
         L.og_last_error.restype = C.c_char_p
         L.og_kernel_launches.restype = C.c_int64
         L.og_sort_keys_noalloc.argtypes = [P, P, P, i64, P]
+        L.og_batch_force.argtypes = [P, i64, C.POINTER(og_box), C.POINTER(og_batch_info)]
+        L.og_batch_force.restype = C.c_int
         L.og_sort_keys_noalloc.restype = C.c_int
         for name in ("og_create", "og_destroy", "og_set_stream", "og_params_default",
                      "og_tree_build", "og_tree_refit", "og_tree_force", "og_tree_info_get",
@@ -223,6 +237,40 @@ def og_tree_export(tree, field: int) -> np.ndarray:
         out = np.zeros((cnt,) + tuple(tail), dtype=dt)
     _check(lib().og_tree_export(tree, int(field), out.ctypes.data_as(C.c_void_p), out.nbytes))
     return out
+
+
+def og_batch_force(ctx, boxes) -> dict:
+    """Many independent boxes in one call.  ``boxes``: sequence of dicts with
+    keys pos (float64 [n,3]), mass (float64 [n]), params (dict), acc (float32
+    [n,3] out) and optionally a_old (float32 [n,3]), n_pp, n_pn (uint32 [n]
+    out); numpy host arrays or torch CUDA tensors (all boxes alike)."""
+    nb = len(boxes)
+    arr = (og_box * nb)()
+    dev = _is_torch_cuda(boxes[0]["pos"])
+    for k, b in enumerate(boxes):
+        x = arr[k]
+        if dev:
+            x.pos = _dev_ptr(b["pos"], "float64").value
+            x.mass = _dev_ptr(b["mass"], "float64").value
+            x.acc = _dev_ptr(b["acc"], "float32").value
+            x.a_old = _dev_ptr(b["a_old"], "float32").value if b.get("a_old") is not None else None
+            x.n_pp = _dev_ptr(b["n_pp"], "int32").value if b.get("n_pp") is not None else None
+            x.n_pn = _dev_ptr(b["n_pn"], "int32").value if b.get("n_pn") is not None else None
+        else:
+            x.pos = _host_ptr(b["pos"], np.float64, (3,)).value
+            x.mass = _host_ptr(b["mass"], np.float64).value
+            x.acc = _host_ptr(b["acc"], np.float32, (3,)).value
+            x.a_old = _host_ptr(b["a_old"], np.float32, (3,)).value if b.get("a_old") is not None else None
+            x.n_pp = _host_ptr(b["n_pp"], np.uint32).value if b.get("n_pp") is not None else None
+            x.n_pn = _host_ptr(b["n_pn"], np.uint32).value if b.get("n_pn") is not None else None
+        x.n = int(b["pos"].shape[0])
+        prm = params_from_dict(b["params"], OG_DEVICE_PTRS if dev else 0)
+        if not dev:
+            prm.flags = int(prm.flags) & ~OG_DEVICE_PTRS
+        x.params = prm
+    info = og_batch_info()
+    _check(lib().og_batch_force(ctx, nb, arr, C.byref(info)))
+    return {k: getattr(info, k) for k, _ in og_batch_info._fields_}
 
 
 OG_NOALLOC_MAX_N = 1048576
