@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="clustered-2m")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-boxes", type=int, default=512)
     return ap.parse_args()
 
 
@@ -145,6 +147,62 @@ def cpu_baseline(pos, mass, prm, budget_s=20.0):
             "sample": f"full FP64 tree build of all {n} particles ({t_build:.2f} s) + both walk "
                       f"passes for {targets} targets in {done_groups} random groups "
                       f"({t_force:.2f} s), force time scaled to all {n} targets"}
+
+
+def batched_bench(og, ctx, torch, dev, stream, nboxes, steps):
+    """Many independent boxes: one og_batch_force call (one forest, one walk
+    launch per pass) against one og_tree_build + og_tree_force call per box,
+    inputs resident on the device, same GPU, same results."""
+    boxes = gi.batch_boxes(nboxes)
+    descs = []
+    for b in boxes:
+        n = len(b.mass)
+        descs.append(dict(pos=torch.from_numpy(b.pos).to(dev), mass=torch.from_numpy(b.mass).to(dev),
+                          params=b.params,
+                          acc=torch.empty((n, 3), dtype=torch.float32, device=dev),
+                          n_pp=torch.empty(n, dtype=torch.int32, device=dev),
+                          n_pn=torch.empty(n, dtype=torch.int32, device=dev)))
+    total = sum(len(b.mass) for b in boxes)
+
+    def one_batch():
+        return og.og_batch_force(ctx.h, descs)
+
+    def per_box():
+        inter = 0
+        for d in descs:
+            h = og.og_tree_build(ctx.h, d["pos"], d["mass"], d["params"])
+            og.og_tree_force(h, d["acc"], None, d["n_pp"], d["n_pn"])
+            inter += og.og_tree_info_get(h)["interactions"]
+            og.og_tree_free(h)
+        return inter
+
+    info = one_batch()
+    per_box()
+    torch.cuda.synchronize()
+    tb, tp = [], []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = one_batch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb.append(e0.elapsed_time(e1))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inter_pb = per_box()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp.append(e0.elapsed_time(e1))
+    mb, mp = statistics.median(tb), statistics.median(tp)
+    return {"workload": f"{nboxes} boxes, N log-uniform [4096, 262144], uniform or halo-clustered "
+                        f"(coin flip), eps=1/(50 N^(1/3)), r_s=1.25/(2 N^(1/3)), BH theta 0.5",
+            "particles": total, "groups": info["groups"], "interactions": info["interactions"],
+            "batched_ms": mb, "per_box_ms": mp,
+            "batched_particles_per_s": total / (mb * 1e-3),
+            "per_box_particles_per_s": total / (mp * 1e-3),
+            "batched_speedup": mp / mb,
+            "batched_walk_ms": info["ms_walk"], "batched_build_ms": info["ms_build"],
+            "same_interactions": int(inter_pb) == int(info["interactions"])}
 
 
 def run_reference(args):
@@ -287,6 +345,10 @@ def main():
                                                    clocks["sm_mhz"] * 1e6 / 1e12)
                                        if clocks.get("sm_mhz") else None)}
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_bench(og, ctx, torch, dev, stream, args.batched_boxes, max(1, min(args.steps, 3)))
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(pos, mass, prm)
@@ -306,7 +368,7 @@ def main():
                "build_ms_per_step": float(np.mean(ms_build)),
                "walk_interactions_per_s": inter_step / (walk_ms * 1e-3),
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-               "roofline": roof, "cpu_baseline": cpu}
+               "roofline": roof, "cpu_baseline": cpu, "batched": batched}
         print(json.dumps(out), flush=True)
     ctx.close()
     if ws > 1:

@@ -119,8 +119,14 @@ og_status og_params_default(og_params *p);
 og_status og_tree_build(og_ctx *ctx, const double *pos, const double *mass, int64_t n,
                         const og_params *p, og_tree **out);
 
-/* Recompute moments for drifted positions of the same N particles with the
- * topology kept; node extents grow to cover the drifted members. */
+/* Refit for drifted positions of the same N particles (caller order, same
+ * pointer convention as the build): the topology, groups and octant slots
+ * of the build are kept; masses, centres of mass, group boxes and node
+ * extents are recomputed.  A node's extent is its cell joined with its
+ * drifted members (per axis an interval on the periodic circle); the walk's
+ * prune, boundary and opening tests then use the extent and its largest
+ * side instead of the cell, so the lists stay correct for any drift.  The
+ * cost grows with the drift (extents widen); rebuild when it is large. */
 og_status og_tree_refit(og_tree *t, const double *pos);
 
 /* Short-range accelerations (Sect. 4.1.2, 4.1.3, 4.2).
@@ -183,11 +189,13 @@ og_status og_batch_force(og_ctx *ctx, int64_t nbox, const og_box *boxes, og_batc
  *   OG_F_GEND     uint32[groups] one past the last
  *   OG_F_GBOX     uint32[groups][6] integer bounding box lo xyz, hi xyz
  *   OG_F_LISTS    uint32[list_entries][2] (group, unified ref) pairs of the
- *                 last OG_DEBUG_DUMP_LISTS force call, in no particular order */
+ *                 last OG_DEBUG_DUMP_LISTS force call, in no particular order
+ *   OG_F_EXTENT   uint32[2][nodes][3] after a refit: extent start per axis, then
+ *                 extent length per axis (intervals on the circle of 2^32 units) */
 enum {
     OG_F_SKEY = 0, OG_F_PERM, OG_F_SPOS, OG_F_LEVEL, OG_F_NBEG, OG_F_NEND, OG_F_PARENT,
     OG_F_CBEG, OG_F_CCNT, OG_F_CHILD, OG_F_MASS, OG_F_COM, OG_F_NEXTNODE, OG_F_SIBLING,
-    OG_F_PNEXT, OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS
+    OG_F_PNEXT, OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS, OG_F_EXTENT
 };
 og_status og_tree_export(const og_tree *t, int field, void *host_dst, size_t bytes);
 

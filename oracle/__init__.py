@@ -39,7 +39,8 @@ OPEN_REL = 1
 
 (N, NODES, CHILDREN, GROUPS, LIST_LEN) = range(5)
 (F_X, F_Y, F_Z, F_KEY, F_PERM, F_LEVEL, F_BEG, F_END, F_PARENT, F_CBEG, F_CCNT, F_CHILD,
- F_MASS, F_COM, F_MSUM, F_NEXTNODE, F_SIBLING, F_PNEXT, F_GBEG, F_GEND, F_GLO, F_GHI) = range(22)
+ F_MASS, F_COM, F_MSUM, F_NEXTNODE, F_SIBLING, F_PNEXT, F_GBEG, F_GEND, F_GLO, F_GHI,
+ F_EXT_S, F_EXT_L) = range(24)
 
 
 class Params(C.Structure):
@@ -84,6 +85,7 @@ def lib():
             L.ora_split_s.restype = C.c_double
             L.ora_tree_build.argtypes = [P, P, i64, C.POINTER(Params), C.POINTER(P)]
             L.ora_tree_free.argtypes = [P]
+            L.ora_tree_refit.argtypes = [P, P]
             L.ora_tree_free.restype = None
             L.ora_tree_count.argtypes = [P, C.c_int]
             L.ora_tree_count.restype = i64
@@ -176,12 +178,23 @@ class Tree:
             F_MASS: (m, np.float64), F_COM: ((m, 3), np.uint32), F_MSUM: ((m, 3), np.float64),
             F_NEXTNODE: (m, np.int64), F_SIBLING: (m, np.int64), F_PNEXT: (n, np.int64),
             F_GBEG: (g, np.int64), F_GEND: (g, np.int64), F_GLO: ((g, 3), np.uint32),
-            F_GHI: ((g, 3), np.uint32)}[field]
+            F_GHI: ((g, 3), np.uint32), F_EXT_S: ((m, 3), np.uint32),
+            F_EXT_L: ((m, 3), np.uint32)}[field]
         out = np.zeros(shape, dtype=dt)
         rc = lib().ora_tree_get(self._h, field, _ptr(out))
         if rc:
             raise ValueError("bad field")
         return out
+
+    def refit(self, pos):
+        """Drifted positions of the same particles (input order): same
+        topology and groups, new moments, node extents and group boxes."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        if pos.shape[0] != self.n:
+            raise ValueError("refit needs the same number of particles")
+        rc = lib().ora_tree_refit(self._h, _ptr(pos))
+        if rc:
+            raise ValueError(f"oracle refit failed ({rc})")
 
     def force(self, opening=None, theta=None, alpha=None, a_old=None, groups=None,
               keep_lists=False, nthreads=0):

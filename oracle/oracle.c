@@ -172,6 +172,9 @@ struct ora_tree {
     double *M, *Sx, *Sy, *Sz;
     uint32_t *cx, *cy, *cz;
     int64_t *nextnode, *sibling, *pnext;
+    uint32_t *ox, *oy, *oz; /* cell origin of each node (fixed by the build) */
+    uint32_t *es, *el;      /* after a refit: extent start and length, 3 per node */
+    int refit;
     /* groups */
     int64_t *gbeg, *gend;
     uint32_t *glo, *ghi;    /* 3 per group */
@@ -194,7 +197,7 @@ void ora_tree_free(ora_tree *t)
                     t->sm, t->level, t->beg, t->end, t->parent, t->cbeg, t->ccnt,
                     t->child, t->M, t->Sx, t->Sy, t->Sz, t->cx, t->cy, t->cz,
                     t->nextnode, t->sibling, t->pnext, t->gbeg, t->gend, t->glo,
-                    t->ghi, t->list_off, t->list};
+                    t->ghi, t->list_off, t->list, t->ox, t->oy, t->oz, t->es, t->el};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(t);
 }
@@ -225,6 +228,13 @@ static int64_t build_node(ora_tree *t, int level, int64_t b, int64_t e, int64_t 
     t->beg[id] = b;
     t->end[id] = e;
     t->parent[id] = parent;
+    {
+        /* the cell: the top `level` bits of every coordinate of its particles */
+        uint32_t mask = level == 0 ? 0u : (uint32_t)~(((uint64_t)1 << (32 - level)) - 1);
+        t->ox[id] = t->sx[b] & mask;
+        t->oy[id] = t->sy[b] & mask;
+        t->oz[id] = t->sz[b] & mask;
+    }
     t->cbeg[id] = t->nchild;
     int64_t pend_pos[8], pend_b[8], pend_e[8];
     int npend = 0;
@@ -383,6 +393,27 @@ static void make_groups(ora_tree *t, int64_t id)
     if (rb >= 0) emit_run(t, rb, re);
 }
 
+/* integer bounding box of every group, per axis an interval on the circle:
+ * the member offsets from the first member, min to max (a drifted group may
+ * wrap through 0) */
+static void group_boxes(ora_tree *t)
+{
+    for (int64_t g = 0; g < t->ngroups; ++g) {
+        const uint32_t *xs[3] = {t->sx, t->sy, t->sz};
+        for (int a = 0; a < 3; ++a) {
+            uint32_t ref = xs[a][t->gbeg[g]];
+            int64_t lo = 0, hi = 0;
+            for (int64_t q = t->gbeg[g]; q < t->gend[g]; ++q) {
+                int64_t d = (int64_t)(int32_t)(uint32_t)(xs[a][q] - ref);
+                if (d < lo) lo = d;
+                if (d > hi) hi = d;
+            }
+            t->glo[3 * g + a] = (uint32_t)(ref + (uint32_t)lo);
+            t->ghi[3 * g + a] = (uint32_t)(ref + (uint32_t)hi);
+        }
+    }
+}
+
 int ora_tree_build(const double *pos, const double *mass, int64_t n, const ora_params *p,
                    ora_tree **out)
 {
@@ -407,13 +438,15 @@ int ora_tree_build(const double *pos, const double *mass, int64_t n, const ora_p
     t->Sz = xcalloc(mcap, 8);
     t->cx = xcalloc(mcap, 4); t->cy = xcalloc(mcap, 4); t->cz = xcalloc(mcap, 4);
     t->nextnode = xcalloc(mcap, 8); t->sibling = xcalloc(mcap, 8); t->pnext = xcalloc(n, 8);
+    t->ox = xcalloc(mcap, 4); t->oy = xcalloc(mcap, 4); t->oz = xcalloc(mcap, 4);
+    t->es = xcalloc(3 * mcap, 4); t->el = xcalloc(3 * mcap, 4);
     t->gbeg = xcalloc(n, 8); t->gend = xcalloc(n, 8);
     t->glo = xcalloc(3 * n, 4); t->ghi = xcalloc(3 * n, 4);
     if (!t->x || !t->y || !t->z || !t->key || !t->perm || !t->skey || !t->sx || !t->sy ||
         !t->sz || !t->sm || !t->level || !t->beg || !t->end || !t->parent || !t->cbeg ||
         !t->ccnt || !t->child || !t->M || !t->Sx || !t->Sy || !t->Sz || !t->cx || !t->cy ||
         !t->cz || !t->nextnode || !t->sibling || !t->pnext || !t->gbeg || !t->gend ||
-        !t->glo || !t->ghi) {
+        !t->glo || !t->ghi || !t->ox || !t->oy || !t->oz || !t->es || !t->el) {
         ora_tree_free(t);
         return ORA_ERR_OOM;
     }
@@ -449,20 +482,7 @@ int ora_tree_build(const double *pos, const double *mass, int64_t n, const ora_p
     thread_node(t, 0, -1);
     /* a6 */
     make_groups(t, 0);
-    for (int64_t g = 0; g < t->ngroups; ++g) {
-        uint32_t lo[3] = {UINT32_MAX, UINT32_MAX, UINT32_MAX}, hi[3] = {0, 0, 0};
-        for (int64_t q = t->gbeg[g]; q < t->gend[g]; ++q) {
-            uint32_t v[3] = {t->sx[q], t->sy[q], t->sz[q]};
-            for (int a = 0; a < 3; ++a) {
-                if (v[a] < lo[a]) lo[a] = v[a];
-                if (v[a] > hi[a]) hi[a] = v[a];
-            }
-        }
-        for (int a = 0; a < 3; ++a) {
-            t->glo[3 * g + a] = lo[a];
-            t->ghi[3 * g + a] = hi[a];
-        }
-    }
+    group_boxes(t);
     *out = t;
     return ORA_OK;
 }
@@ -471,18 +491,23 @@ int ora_tree_build(const double *pos, const double *mass, int64_t n, const ora_p
 /* geometry on the circle of 2^32 grid units                                 */
 /* ------------------------------------------------------------------------ */
 
+/* Intervals on the circle of 2^32 grid units are [lo, hi] with length
+ * hi - lo (mod 2^32); an interval may wrap through 0 (a drifted box). */
+
 /* distance from point c to the interval [lo, hi] (0 inside) */
 static uint64_t circ_point_gap(uint32_t c, uint32_t lo, uint32_t hi)
 {
-    if (c >= lo && c <= hi) return 0;
-    uint32_t a = lo - c, b = c - hi; /* wrap-around differences */
-    return a < b ? a : b;
+    uint32_t len = hi - lo, d = c - lo;
+    if (d <= len) return 0;
+    uint32_t fwd = d - len, back = (uint32_t)(0u - d);
+    return fwd < back ? fwd : back;
 }
 
 /* distance between the intervals [alo, ahi] and [blo, bhi] (0 if they meet) */
 static uint64_t circ_box_gap(uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi)
 {
-    if (alo <= bhi && blo <= ahi) return 0;
+    uint32_t la = ahi - alo, lb = bhi - blo;
+    if ((uint32_t)(blo - alo) <= la || (uint32_t)(alo - blo) <= lb) return 0;
     uint32_t a = blo - ahi, b = alo - bhi;
     return a < b ? a : b;
 }
@@ -494,6 +519,68 @@ static int64_t min_image(uint32_t xj, uint32_t xi)
     if (d >= ((int64_t)1 << 31)) d -= ((int64_t)1 << 32);
     else if (d < -((int64_t)1 << 31)) d += ((int64_t)1 << 32);
     return d;
+}
+
+/* ------------------------------------------------------------------------ */
+/* refit: drifted positions, the same topology                              */
+/* ------------------------------------------------------------------------ */
+
+/* Refit for drifted positions of the same particles (input order): the
+ * topology, the groups and the octant slots of the build stay; masses, sums
+ * and centres of mass are recomputed in the same slot order; every node gets
+ * an extent, its cell joined with the members' positions (offsets from the
+ * cell origin as 32-bit differences, so drift across the periodic boundary
+ * stays local); group boxes are recomputed. */
+int ora_tree_refit(ora_tree *t, const double *pos)
+{
+    const int64_t n = t->n;
+    for (int64_t i = 0; i < n; ++i) {
+        if (ora_quantize1(pos[3 * i + 0], t->p.box, &t->x[i]) ||
+            ora_quantize1(pos[3 * i + 1], t->p.box, &t->y[i]) ||
+            ora_quantize1(pos[3 * i + 2], t->p.box, &t->z[i]))
+            return ORA_ERR_ARG;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t j = t->perm[i];
+        t->sx[i] = t->x[j];
+        t->sy[i] = t->y[j];
+        t->sz[i] = t->z[j];
+    }
+    for (int64_t id = t->nnodes - 1; id >= 0; --id) {
+        node_moments(t, id);
+        const uint32_t o[3] = {t->ox[id], t->oy[id], t->oz[id]};
+        const int lev = t->level[id];
+        const int64_t side = (int64_t)1 << (32 - lev);
+        int64_t lo[3] = {0, 0, 0}, hi[3] = {side - 1, side - 1, side - 1};
+        for (int64_t k = 0; k < t->ccnt[id]; ++k) {
+            int64_t c = t->child[t->cbeg[id] + k];
+            for (int a = 0; a < 3; ++a) {
+                int64_t clo, chi;
+                if (c < n) {
+                    const uint32_t *xs = a == 0 ? t->sx : a == 1 ? t->sy : t->sz;
+                    clo = chi = (int64_t)(int32_t)(uint32_t)(xs[c] - o[a]);
+                } else {
+                    int64_t j = c - n;
+                    clo = (int64_t)(int32_t)(uint32_t)(t->es[3 * j + a] - o[a]);
+                    chi = clo + (int64_t)t->el[3 * j + a];
+                }
+                if (clo < lo[a]) lo[a] = clo;
+                if (chi > hi[a]) hi[a] = chi;
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
+            if (hi[a] - lo[a] >= (int64_t)0xffffffff) {
+                t->es[3 * id + a] = 0; /* the whole circle */
+                t->el[3 * id + a] = 0xffffffffu;
+            } else {
+                t->es[3 * id + a] = (uint32_t)(o[a] + (uint32_t)lo[a]);
+                t->el[3 * id + a] = (uint32_t)(hi[a] - lo[a]);
+            }
+        }
+    }
+    group_boxes(t);
+    t->refit = 1;
+    return ORA_OK;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -603,25 +690,49 @@ typedef struct {
     int err;
 } walk_state;
 
+/* The node's extent on every axis: the cell [o, o + side - 1] of a built
+ * tree, or, after a refit, the cell joined with its drifted members.  ell is
+ * the largest side of the extent. */
+static void node_extent(const ora_tree *t, int64_t j, uint32_t s[3], uint32_t len[3], uint64_t *ell)
+{
+    if (t->refit) {
+        uint64_t m = 0;
+        for (int a = 0; a < 3; ++a) {
+            s[a] = t->es[3 * j + a];
+            len[a] = t->el[3 * j + a];
+            if ((uint64_t)len[a] + 1 > m) m = (uint64_t)len[a] + 1;
+        }
+        *ell = m;
+        return;
+    }
+    uint64_t side = (uint64_t)1 << (32 - t->level[j]);
+    s[0] = t->ox[j];
+    s[1] = t->oy[j];
+    s[2] = t->oz[j];
+    for (int a = 0; a < 3; ++a) len[a] = (uint32_t)(side - 1);
+    *ell = side;
+}
+
 static int must_open(walk_state *w, int64_t j)
 {
     const ora_tree *t = w->t;
-    int lev = t->level[j];
-    uint64_t side = (uint64_t)1 << (32 - lev);
+    uint32_t s[3], len[3];
+    uint64_t ell;
+    node_extent(t, j, s, len, &ell);
     uint32_t com[3] = {t->cx[j], t->cy[j], t->cz[j]};
-    /* boundary check: the group box meets the cell enlarged to 0.6 side */
+    /* boundary check: the group box meets the cube of side 1.2 ell centred
+       on the extent (the cell enlarged by 10 % on every side) */
     int near = 1;
     for (int a = 0; a < 3; ++a) {
-        uint32_t origin = (lev == 0) ? 0u : (uint32_t)(com[a] & ~(uint32_t)(side - 1));
-        uint32_t centre = (uint32_t)((uint64_t)origin + side / 2);
+        uint32_t centre = (uint32_t)(s[a] + (uint32_t)(((uint64_t)len[a] + 1) / 2));
         uint64_t dc = circ_point_gap(centre, w->lo[a], w->hi[a]);
-        if (10 * dc > 6 * side) near = 0;
+        if (10 * dc > 6 * ell) near = 0;
     }
     if (near) return 1;
     double d[3];
     for (int a = 0; a < 3; ++a) d[a] = (double)circ_point_gap(com[a], w->lo[a], w->hi[a]);
     double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-    double l2 = (double)side * (double)side;
+    double l2 = (double)ell * (double)ell;
     if (w->opening == ORA_OPEN_BH) return l2 > w->c->th2 * d2;
     double lhs = (w->c->G * t->M[j]) * l2;
     double rhs = w->arel * (d2 * d2);
@@ -646,14 +757,12 @@ static void walk_node(walk_state *w, int64_t id)
         } else {
             int64_t j = c - n;
             if (w->c->cut) {
-                int lev = t->level[j];
-                uint64_t side = (uint64_t)1 << (32 - lev);
-                uint32_t com[3] = {t->cx[j], t->cy[j], t->cz[j]};
+                uint32_t s[3], len[3];
+                uint64_t ell;
+                node_extent(t, j, s, len, &ell);
                 uint64_t g2 = 0;
                 for (int a = 0; a < 3; ++a) {
-                    uint32_t origin = (uint32_t)(com[a] & ~(uint32_t)(side - 1));
-                    uint32_t last = (uint32_t)((uint64_t)origin + side - 1);
-                    uint64_t g = circ_box_gap(w->lo[a], w->hi[a], origin, last);
+                    uint64_t g = circ_box_gap(w->lo[a], w->hi[a], s[a], (uint32_t)(s[a] + len[a]));
                     g2 += g * g;
                 }
                 if (g2 > w->c->rprune) continue;
@@ -1015,6 +1124,8 @@ int ora_tree_get(const ora_tree *t, int what, void *dst)
     case ORA_F_GEND: memcpy(dst, t->gend, (size_t)g * 8); break;
     case ORA_F_GLO: memcpy(dst, t->glo, (size_t)(3 * g) * 4); break;
     case ORA_F_GHI: memcpy(dst, t->ghi, (size_t)(3 * g) * 4); break;
+    case ORA_F_EXT_S: memcpy(dst, t->es, (size_t)(3 * m) * 4); break;
+    case ORA_F_EXT_L: memcpy(dst, t->el, (size_t)(3 * m) * 4); break;
     default: return ORA_ERR_ARG;
     }
     return ORA_OK;

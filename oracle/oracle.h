@@ -39,7 +39,7 @@ enum {
     ORA_F_X = 0, ORA_F_Y, ORA_F_Z, ORA_F_KEY, ORA_F_PERM,
     ORA_F_LEVEL, ORA_F_BEG, ORA_F_END, ORA_F_PARENT, ORA_F_CBEG, ORA_F_CCNT, ORA_F_CHILD,
     ORA_F_MASS, ORA_F_COM, ORA_F_MSUM, ORA_F_NEXTNODE, ORA_F_SIBLING, ORA_F_PNEXT,
-    ORA_F_GBEG, ORA_F_GEND, ORA_F_GLO, ORA_F_GHI
+    ORA_F_GBEG, ORA_F_GEND, ORA_F_GLO, ORA_F_GHI, ORA_F_EXT_S, ORA_F_EXT_L
 };
 
 int ora_quantize1(double v, double box, uint32_t *out);
@@ -50,6 +50,7 @@ double ora_split_s(double r, double rs);
 int ora_tree_build(const double *pos, const double *mass, int64_t n, const ora_params *p,
                    ora_tree **out);
 void ora_tree_free(ora_tree *t);
+int ora_tree_refit(ora_tree *t, const double *pos);
 int64_t ora_tree_count(const ora_tree *t, int what);
 int ora_tree_get(const ora_tree *t, int what, void *dst);
 int ora_tree_force(ora_tree *t, const float *a_old, int opening, double theta, double alpha,

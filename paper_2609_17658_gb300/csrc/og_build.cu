@@ -100,8 +100,10 @@ __global__ void k_quantize_keys(const double *__restrict__ pos, const double *__
     uint32_t x = quantize(pos[3 * i + 0], box, inv_box, pow2, status);
     uint32_t y = quantize(pos[3 * i + 1], box, inv_box, pow2, status);
     uint32_t z = quantize(pos[3 * i + 2], box, inv_box, pow2, status);
-    double m = mass[i];
-    if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
+    if (mass) {  // a refit passes no masses (they do not change)
+        const double m = mass[i];
+        if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
+    }
     qx[i] = x;
     qy[i] = y;
     qz[i] = z;
@@ -203,19 +205,28 @@ __global__ void k_split_nodes(const uint64_t *__restrict__ skey, const uint8_t *
 __global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ seg_off,
                             const uint32_t *__restrict__ first, const uint32_t *__restrict__ nid,
                             const uint8_t *__restrict__ lv, const uint32_t *__restrict__ sb,
-                            const uint32_t *__restrict__ se, uint8_t *nlev, uint32_t *nbeg,
-                            uint32_t *nend) {
+                            const uint32_t *__restrict__ se, const uint32_t *__restrict__ px,
+                            const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
+                            uint8_t *nlev, uint32_t *nbeg, uint32_t *nend, uint32_t *norg) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < B) {  // the root of box i covers the whole box
         nlev[i] = 0;
         nbeg[i] = seg_off[i];
         nend[i] = seg_off[i + 1];
+        norg[3 * i + 0] = norg[3 * i + 1] = norg[3 * i + 2] = 0u;
     }
     if (i >= n - 1 || !first[i]) return;
-    uint32_t id = (uint32_t)B + nid[i];
-    nlev[id] = lv[i];
+    const uint32_t id = (uint32_t)B + nid[i];
+    const int L = lv[i];
+    nlev[id] = (uint8_t)L;
     nbeg[id] = sb[i];
     nend[id] = se[i];
+    // the cell: the top L bits of every coordinate of its particles
+    const uint32_t mask = ~(uint32_t)((1ull << (32 - L)) - 1ull);
+    const uint32_t q = sb[i];
+    norg[3 * id + 0] = px[q] & mask;
+    norg[3 * id + 1] = py[q] & mask;
+    norg[3 * id + 2] = pz[q] & mask;
 }
 
 __global__ void k_split_node_id(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ lv,
@@ -422,13 +433,60 @@ __global__ void __launch_bounds__(kT) k_moments_level(
     const uint32_t *__restrict__ child, const uint32_t *__restrict__ px,
     const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
     const double *__restrict__ pm64, double *nM, double *nS, uint32_t *ncom, int64_t nchild,
-    uint32_t *status) {
+    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cnt) return;
     const uint32_t node = lnodes[k];
     if (node >= (uint64_t)m) {
         atomicOr(status, ST_INTERNAL);
         return;
+    }
+    if (ext_s) {
+        // refit: the extent is the cell joined with the members' positions,
+        // as 32-bit offsets from the cell origin (drift stays local across
+        // the periodic boundary)
+        const uint32_t o[3] = {norg[3 * node + 0], norg[3 * node + 1], norg[3 * node + 2]};
+        const int64_t side = (int64_t)1 << (32 - level);
+        int64_t lo[3] = {0, 0, 0}, hi[3] = {side - 1, side - 1, side - 1};
+        auto add_point = [&](uint32_t x, uint32_t y, uint32_t z) {
+            const int64_t d[3] = {(int64_t)(int32_t)(x - o[0]), (int64_t)(int32_t)(y - o[1]),
+                                  (int64_t)(int32_t)(z - o[2])};
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = d[a] < lo[a] ? d[a] : lo[a];
+                hi[a] = d[a] > hi[a] ? d[a] : hi[a];
+            }
+        };
+        if (level == kLevels) {
+            for (uint32_t q = nbeg[node]; q < nend[node]; ++q) add_point(px[q], py[q], pz[q]);
+        } else {
+            const uint32_t oc = occ[node];
+            const uint32_t cb = ncbeg[node];
+            for (int sidx = 0; sidx < 8; ++sidx) {
+                const uint32_t slot = cb + __popc(oc & ((1u << sidx) - 1u));
+                if (!((oc >> sidx) & 1u) || slot >= (uint64_t)nchild) continue;
+                const uint32_t item = child[slot];
+                if (item < n) {
+                    add_point(px[item], py[item], pz[item]);
+                } else {
+                    const int64_t j = item - n;
+                    for (int a = 0; a < 3; ++a) {
+                        const int64_t clo = (int64_t)(int32_t)(ext_s[3 * j + a] - o[a]);
+                        const int64_t chi = clo + (int64_t)ext_l[3 * j + a];
+                        lo[a] = clo < lo[a] ? clo : lo[a];
+                        hi[a] = chi > hi[a] ? chi : hi[a];
+                    }
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
+            if (hi[a] - lo[a] >= (int64_t)0xffffffffll) {
+                ext_s[3 * node + a] = 0u;  // the whole circle
+                ext_l[3 * node + a] = 0xffffffffu;
+            } else {
+                ext_s[3 * node + a] = o[a] + (uint32_t)lo[a];
+                ext_l[3 * node + a] = (uint32_t)(hi[a] - lo[a]);
+            }
+        }
     }
     Slot tot = {0.0, 0.0, 0.0, 0.0};
     if (level == kLevels) {
@@ -542,18 +600,49 @@ __global__ void k_group_fin(int64_t n, int64_t ng, const uint32_t *__restrict__ 
     gseg[g] = sseg[b];
     uint32_t e = (g + 1 < ng) ? gbeg[g + 1] : (uint32_t)n;
     gend[g] = e;
-    uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
+    // per axis an interval on the circle: member offsets from the first
+    // member, min to max (a drifted group may wrap through 0)
+    const uint32_t ref[3] = {px[b], py[b], pz[b]};
+    int32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     for (uint32_t q = b; q < e; ++q) {
-        uint32_t v[3] = {px[q], py[q], pz[q]};
+        const uint32_t v[3] = {px[q], py[q], pz[q]};
         for (int a = 0; a < 3; ++a) {
-            lo[a] = min(lo[a], v[a]);
-            hi[a] = max(hi[a], v[a]);
+            const int32_t d = (int32_t)(v[a] - ref[a]);
+            lo[a] = min(lo[a], d);
+            hi[a] = max(hi[a], d);
         }
     }
     for (int a = 0; a < 3; ++a) {
-        gbox[6 * g + a] = lo[a];
-        gbox[6 * g + 3 + a] = hi[a];
+        gbox[6 * g + a] = ref[a] + (uint32_t)lo[a];
+        gbox[6 * g + 3 + a] = ref[a] + (uint32_t)hi[a];
     }
+}
+
+__global__ void k_ext_records(int64_t n, int64_t nchild, const uint32_t *__restrict__ child,
+                              const uint32_t *__restrict__ ext_s, const uint32_t *__restrict__ ext_l,
+                              CExt *cext) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchild) return;
+    const uint32_t item = child[c];
+    CExt x = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (item >= n) {
+        const int64_t j = item - n;
+        x = {ext_s[3 * j], ext_s[3 * j + 1], ext_s[3 * j + 2], 0u,
+             ext_l[3 * j], ext_l[3 * j + 1], ext_l[3 * j + 2], 0u};
+    }
+    cext[c] = x;
+}
+
+// refit: drifted fixed-point positions into sorted order (masses unchanged)
+__global__ void k_repos(int64_t n, const uint32_t *__restrict__ perm, const uint32_t *__restrict__ qx,
+                        const uint32_t *__restrict__ qy, const uint32_t *__restrict__ qz,
+                        uint32_t *px, uint32_t *py, uint32_t *pz) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    px[i] = qx[j];
+    py[i] = qy[j];
+    pz[i] = qz[j];
 }
 
 __global__ void k_records(int64_t n, int64_t nchild, const uint32_t *__restrict__ child,
@@ -620,7 +709,84 @@ static size_t tree_bytes(int64_t n, int64_t B) {
     add(4, n); add(4, n); add(4, 6 * n); add(4, n); add(4, n); add(4, n);           // groups
     add(4, 3 * n); add(4, 3 * n); add(4, n); add(4, n);                             // force arrays
     add(4, B + 1); add(sizeof(SegGeom), B); add(sizeof(WalkParams), 2 * B);         // boxes
+    add(4, 3 * m); add(4, m); add(4, m);                                            // norg nocc lnodes
     return b + 4096;
+}
+
+// Moments (and, for a refit, extents) level by level from the deepest level
+// up; each launch reads only nodes of deeper levels, finished by the previous
+// launches.
+static void moments_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
+    cudaStream_t s = t->ctx->stream;
+    const int64_t n = t->n, m = t->nnodes;
+    uint32_t off = 0;
+    uint32_t offs[kLevels + 1];
+    for (int l = 0; l <= kLevels; ++l) {
+        offs[l] = off;
+        off += t->h_lcount[l];
+    }
+    for (int l = kLevels; l >= 0; --l) {
+        const uint32_t cnt = t->h_lcount[l];
+        if (cnt == 0) continue;
+        k_moments_level<<<nblk(cnt), kT, 0, s>>>(
+            n, m, l, t->lnodes + offs[l], cnt, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child,
+            t->px, t->py, t->pz, t->pm64, t->nM, t->nS, t->ncom, t->nchild, t->ctx->d_status,
+            t->norg, ext_s, ext_l); note_launch();
+    }
+}
+
+og_status refit_tree(og_tree *t, const double *d_pos) {
+    cudaStream_t s = t->ctx->stream;
+    const int64_t n = t->n, B = t->nseg, m = t->nnodes;
+    cudaError_t err;
+    if (!t->cext) {
+        // extents live in their own allocation, made on the first refit
+        size_t bytes = (size_t)m * 6 * sizeof(uint32_t) + (size_t)t->nchild * sizeof(CExt) + 1024;
+        void *p = nullptr;
+        if ((err = cudaMallocAsync(&p, bytes, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (extents)");
+        t->ext_arena = p;
+        t->next_s = static_cast<uint32_t *>(p);
+        t->next_l = t->next_s + 3 * m;
+        t->cext = reinterpret_cast<CExt *>(reinterpret_cast<char *>(p) +
+                                           (((size_t)m * 6 * sizeof(uint32_t) + 255) & ~(size_t)255));
+    }
+    size_t sb = (size_t)n * (3 * 4 + 8 + 4 + 4) + 4096;
+    void *scratch = nullptr;
+    if ((err = cudaMallocAsync(&scratch, sb, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (refit)");
+    Bump W(scratch, sb);
+    uint32_t *qx = W.take<uint32_t>(n), *qy = W.take<uint32_t>(n), *qz = W.take<uint32_t>(n);
+    uint64_t *keys = W.take<uint64_t>(n);
+    uint32_t *idx = W.take<uint32_t>(n);
+    uint32_t *pseg = W.take<uint32_t>(n);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    if (B > 1) {
+        k_fill_seg<<<nblk(n), kT, 0, s>>>(n, B, t->seg_off, pseg); note_launch();
+    }
+    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, nullptr, n, B > 1 ? pseg : nullptr, t->geom, qx,
+                                           qy, qz, keys, nullptr, idx, t->ctx->d_status); note_launch();
+    k_repos<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, t->px, t->py, t->pz); note_launch();
+    moments_bottom_up(t, t->next_s, t->next_l);
+    k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
+                                                t->pz, t->sseg, t->gbox, t->gseg); note_launch();
+    k_records<<<nblk(t->nchild), kT, 0, s>>>(n, t->nchild, t->child, t->px, t->py, t->pz, t->pm32,
+                                             t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nM, t->ncom,
+                                             t->crec); note_launch();
+    k_ext_records<<<nblk(t->nchild), kT, 0, s>>>(n, t->nchild, t->child, t->next_s, t->next_l,
+                                                 t->cext); note_launch();
+    cudaEventRecord(e1, s);
+    cudaFreeAsync(scratch, s);
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "refit");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    t->ms_refit = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t->refit = true;
+    (void)m;
+    return OG_OK;
 }
 
 og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
@@ -676,6 +842,9 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     t->seg_off = A.take<uint32_t>(B + 1);
     t->geom = A.take<SegGeom>(B);
     t->segp = A.take<WalkParams>(2 * B);
+    t->norg = A.take<uint32_t>(3 * mcap);
+    t->nocc = A.take<uint32_t>(mcap);
+    t->lnodes = A.take<uint32_t>(mcap);
     if (A.off > tb) { set_error("internal: arena overflow"); return OG_ERR_STATE; }
 
     // ---- box table
@@ -700,7 +869,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         add(4, n); add(4, n); add(4, n);                        // qx qy qz
         add(8, n); add(4, n); add(8, n); add(4, n); add(8, n); add(4, n);  // keys, idx, alt, key copy, pseg
         add(1, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // lv sb se first nid sid
-        add(4, n + B); add(4, n + B); add(4, n + B); add(4, 3 * 24);  // occ nnc lnodes levels
+        add(4, n + B); add(4, 3 * 24);  // nnc levels
         add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs gid unit
         sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + B + 8) + 4096;
     }
@@ -719,8 +888,8 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     uint8_t *lv = W.take<uint8_t>(n);
     uint32_t *sbeg = W.take<uint32_t>(n), *send = W.take<uint32_t>(n);
     uint32_t *first = W.take<uint32_t>(n), *nid = W.take<uint32_t>(n), *sid = W.take<uint32_t>(n);
-    uint32_t *occ = W.take<uint32_t>(n + B), *nnc = W.take<uint32_t>(n + B);
-    uint32_t *lnodes = W.take<uint32_t>(n + B);
+    uint32_t *occ = t->nocc, *nnc = W.take<uint32_t>(n + B);
+    uint32_t *lnodes = t->lnodes;
     uint32_t *lcount = W.take<uint32_t>(3 * (kLevels + 2));
     uint32_t *loff = lcount + (kLevels + 2), *lcursor = lcount + 2 * (kLevels + 2);
     uint32_t *fp = W.take<uint32_t>(n), *rs = W.take<uint32_t>(n), *gs = W.take<uint32_t>(n);
@@ -784,7 +953,8 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     const int64_t m = B + (int64_t)h_tot[0];
     t->nnodes = m;
     k_node_init<<<nblk(nsplit > B ? nsplit : B), kT, 0, s>>>(n, B, t->seg_off, first, nid, lv, sbeg,
-                                                            send, t->nlev, t->nbeg, t->nend); note_launch();
+                                                            send, t->px, t->py, t->pz, t->nlev,
+                                                            t->nbeg, t->nend, t->norg); note_launch();
     if (nsplit > 0) {
         k_split_node_id<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, sbeg, first, nid, t->sseg, n, B, sid); note_launch();
     }
@@ -827,22 +997,9 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         return OG_ERR_STATE;
     }
     t->ngroups = h_tot[2];
-    // a5 (part 2): moments from the deepest level up; each launch reads only
-    // nodes of deeper levels, finished by the previous launches
-    {
-        uint32_t off = 0;
-        uint32_t offs[kLevels + 1];
-        for (int l = 0; l <= kLevels; ++l) {
-            offs[l] = off;
-            off += h_lcount[l];
-        }
-        for (int l = kLevels; l >= 0; --l) {
-            if (h_lcount[l] == 0) continue;
-            k_moments_level<<<nblk(h_lcount[l]), kT, 0, s>>>(
-                n, m, l, lnodes + offs[l], h_lcount[l], t->nbeg, t->nend, t->ncbeg, occ, t->child,
-                t->px, t->py, t->pz, t->pm64, t->nM, t->nS, t->ncom, nchild, status); note_launch();
-        }
-    }
+    t->h_lcount.assign(h_lcount, h_lcount + kLevels + 1);
+    // a5 (part 2): moments from the deepest level up
+    moments_bottom_up(t, nullptr, nullptr);
     k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
                                                 t->pz, t->sseg, t->gbox, t->gseg); note_launch();
     k_records<<<nblk(nchild), kT, 0, s>>>(n, nchild, t->child, t->px, t->py, t->pz, t->pm32,

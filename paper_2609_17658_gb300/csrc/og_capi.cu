@@ -476,13 +476,21 @@ og_status og_tree_export(const og_tree *t, int field, void *dst, size_t bytes) {
     case OG_F_GEND: src = t->gend; need = g * 4; break;
     case OG_F_GBOX: src = t->gbox; need = 6 * g * 4; break;
     case OG_F_LISTS: src = t->lists; need = t->list_len * 8; break;
+    case OG_F_EXTENT:
+        if (!t->refit) { set_error("no extents before a refit"); return OG_ERR_STATE; }
+        need = 6 * m * 4;
+        break;
     default: set_error("unknown field %d", field); return OG_ERR_ARG;
     }
     if (bytes != need) { set_error("field %d needs %zu bytes, got %zu", field, need, bytes); return OG_ERR_ARG; }
     if (need == 0) return OG_OK;
     cudaSetDevice(t->ctx->device);
     cudaStream_t s = t->ctx->stream;
-    if (field == OG_F_SPOS) {
+    if (field == OG_F_EXTENT) {
+        char *d = static_cast<char *>(dst);
+        cudaMemcpyAsync(d, t->next_s, 3 * m * 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(d + 3 * m * 4, t->next_l, 3 * m * 4, cudaMemcpyDeviceToHost, s);
+    } else if (field == OG_F_SPOS) {
         char *d = static_cast<char *>(dst);
         cudaMemcpyAsync(d, t->px, n * 4, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(d + n * 4, t->py, n * 4, cudaMemcpyDeviceToHost, s);
@@ -499,6 +507,7 @@ og_status og_tree_free(og_tree *t) {
     if (!t) return OG_OK;
     cudaSetDevice(t->ctx->device);
     if (t->arena) cudaFreeAsync(t->arena, t->ctx->stream);
+    if (t->ext_arena) cudaFreeAsync(t->ext_arena, t->ctx->stream);
     if (t->lists) {
         cudaStreamSynchronize(t->ctx->stream);
         cudaFree(t->lists);
@@ -508,10 +517,24 @@ og_status og_tree_free(og_tree *t) {
 }
 
 og_status og_tree_refit(og_tree *t, const double *pos) {
-    (void)pos;
-    if (!t) { set_error("NULL argument"); return OG_ERR_ARG; }
-    set_error("og_tree_refit: not available in this build");
-    return OG_ERR_STATE;
+    if (!t || !pos) { set_error("NULL argument"); return OG_ERR_ARG; }
+    og_ctx *c = t->ctx;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int64_t n = t->n;
+    const double *d_pos = pos;
+    void *tmp = nullptr;
+    cudaError_t e;
+    if (!(t->prm.flags & OG_DEVICE_PTRS)) {
+        if ((e = cudaMallocAsync(&tmp, (size_t)n * 3 * sizeof(double), s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMallocAsync (refit)");
+        cudaMemcpyAsync(tmp, pos, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
+        d_pos = static_cast<const double *>(tmp);
+    }
+    og_status st = refit_tree(t, d_pos);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (st == OG_OK) st = check_status(c);
+    return st;
 }
 
 }  // extern "C"

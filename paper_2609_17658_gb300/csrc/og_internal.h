@@ -39,6 +39,14 @@ struct __align__(16) CRec {
 };
 static_assert(sizeof(CRec) == 32, "CRec must be 32 bytes");
 
+// extent of a node after a refit (per child slot): start and length per axis
+// on the circle of 2^32 grid units; a built tree uses the node's cell instead
+struct __align__(16) CExt {
+    uint32_t sx, sy, sz, pad0;
+    uint32_t lx, ly, lz, pad1;
+};
+static_assert(sizeof(CExt) == 32, "CExt must be 32 bytes");
+
 // geometry of one box (segment) of a forest
 struct SegGeom {
     double box, inv_box;
@@ -88,6 +96,15 @@ struct og_tree {
     uint32_t *ncom = nullptr;
     int32_t *pnext = nullptr;
     uint32_t *owner = nullptr;        // node a particle hangs from
+    uint32_t *norg = nullptr;         // cell origin of each node (3 per node, fixed by the build)
+    uint32_t *nocc = nullptr;         // octant occupancy of each node
+    uint32_t *lnodes = nullptr;       // node ids by level (for the bottom-up passes)
+    std::vector<uint32_t> h_lcount;   // nodes per level
+    uint32_t *next_s = nullptr, *next_l = nullptr;  // extents after a refit (3 per node)
+    og::CExt *cext = nullptr;         // extents per child slot (null until a refit)
+    void *ext_arena = nullptr;        // allocation holding next_s, next_l, cext
+    bool refit = false;
+    double ms_refit = 0;
     uint32_t *child = nullptr;
     og::CRec *crec = nullptr;
     // groups
@@ -139,6 +156,8 @@ void radix_sort_pairs_every_pass(uint64_t *keys, uint32_t *vals, uint64_t *keys_
 
 // build stages (og_build.cu)
 og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass);
+// refit for drifted positions (input order, device): same topology and groups
+og_status refit_tree(og_tree *t, const double *d_pos);
 
 // force (og_walk.cu)
 struct WalkParams {

@@ -64,6 +64,7 @@ struct WalkArgs {
     const uint32_t *gorder;       // processing order of the groups, or null (key order)
     uint32_t *gcost;              // out: list length per group
     const CRec *crec;
+    const CExt *cext;             // node extents after a refit, or null (cells)
     int64_t nchild, max_rounds;
     const uint32_t *gseg;         // box of each group
     const uint32_t *ncbeg, *nccnt;  // child range of each node (the roots are nodes 0..B-1)
@@ -98,15 +99,20 @@ __device__ __forceinline__ float ex2_ftz(float x) {
     return y;
 }
 
-__device__ __forceinline__ uint32_t point_gap(uint32_t c, uint32_t lo, uint32_t hi) {
-    if (c >= lo && c <= hi) return 0u;
-    uint32_t a = lo - c, b = c - hi;
-    return a < b ? a : b;
+// Intervals on the circle of 2^32 grid units are [lo, hi] with length
+// hi - lo (mod 2^32); a drifted interval may wrap through 0.
+// point c to the interval [lo, lo + len]
+__device__ __forceinline__ uint32_t point_gap(uint32_t c, uint32_t lo, uint32_t len) {
+    const uint32_t d = c - lo;
+    if (d <= len) return 0u;
+    const uint32_t fwd = d - len, back = 0u - d;
+    return fwd < back ? fwd : back;
 }
 
-__device__ __forceinline__ uint32_t box_gap(uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi) {
-    if (alo <= bhi && blo <= ahi) return 0u;
-    uint32_t a = blo - ahi, b = alo - bhi;
+// interval [alo, alo + la] to interval [blo, blo + lb]
+__device__ __forceinline__ uint32_t box_gap(uint32_t alo, uint32_t la, uint32_t blo, uint32_t lb) {
+    if (blo - alo <= la || alo - blo <= lb) return 0u;
+    const uint32_t a = blo - (alo + la), b = alo - (blo + lb);
     return a < b ? a : b;
 }
 
@@ -211,7 +217,7 @@ __device__ __forceinline__ bool open_rel(uint32_t gx, uint32_t gy, uint32_t gz, 
     return __dmul_rn(__dmul_rn(p.G, M), l2) > __dmul_rn(arel, __dmul_rn(d2, d2));
 }
 
-template <int kOpen, bool kSplit, bool kDump>
+template <int kOpen, bool kSplit, bool kDump, bool kRefit>
 __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -232,11 +238,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         const WalkParams &p = a.segp[seg];
         const uint32_t gb = a.gbeg[g], ge = a.gend[g];
         const uint32_t gsize = ge - gb;
-        uint32_t lo[3], hi[3];
+        uint32_t lo[3], gl[3];  // the group box: [lo, lo + gl] per axis
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             lo[k] = a.gbox[6 * g + k];
-            hi[k] = a.gbox[6 * g + 3 + k];
+            gl[k] = a.gbox[6 * g + 3 + k] - lo[k];
         }
         // lane -> (target, replica): P lanes per replica, R = 32 / P replicas
         const int P = gsize > 16u ? 32 : gsize > 8u ? 16 : gsize > 4u ? 8 : gsize > 2u ? 4 : gsize > 1u ? 2 : 1;
@@ -318,37 +324,60 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
                 const CRec r = a.crec[ci];
                 ent = make_uint4(r.x, r.y, r.z, __float_as_uint(r.m));
                 isnode = (r.info >> 31) != 0u;
-                const uint32_t gx = point_gap(r.x, lo[0], hi[0]);
-                const uint32_t gy = point_gap(r.y, lo[1], hi[1]);
-                const uint32_t gz = point_gap(r.z, lo[2], hi[2]);
+                const uint32_t gx = point_gap(r.x, lo[0], gl[0]);
+                const uint32_t gy = point_gap(r.y, lo[1], gl[1]);
+                const uint32_t gz = point_gap(r.z, lo[2], gl[2]);
                 const unsigned long long pg2 = sq64(gx) + sq64(gy) + sq64(gz);
                 near = pg2 < p.hnear2;
                 if (!isnode) {
                     emit = !kSplit || pg2 <= p.rprune;
                 } else {
-                    const uint32_t lev = (r.info >> 26) & 31u;
-                    const uint32_t side = 1u << (32u - lev);
-                    const uint32_t msk = ~(side - 1u);
-                    const uint32_t ox = r.x & msk, oy = r.y & msk, oz = r.z & msk;
-                    bool pruned = false;
-                    if (kSplit) {
-                        const unsigned long long g2 = sq64(box_gap(lo[0], hi[0], ox, ox + (side - 1u))) +
-                                                      sq64(box_gap(lo[1], hi[1], oy, oy + (side - 1u))) +
-                                                      sq64(box_gap(lo[2], hi[2], oz, oz + (side - 1u)));
-                        pruned = g2 > p.rprune;
-                    }
-                    if (!pruned) {
+                    bool pruned = false, bnear;
+                    float l2f;
+                    double l2;
+                    if (kRefit) {
+                        // the node's extent: its cell joined with its drifted members
+                        const CExt e = a.cext[ci];
+                        const unsigned long long ell =
+                            (unsigned long long)max(e.lx, max(e.ly, e.lz)) + 1ull;
+                        l2 = (double)ell * (double)ell;
+                        l2f = (float)l2;
+                        if (kSplit) {
+                            const unsigned long long g2 = sq64(box_gap(lo[0], gl[0], e.sx, e.lx)) +
+                                                          sq64(box_gap(lo[1], gl[1], e.sy, e.ly)) +
+                                                          sq64(box_gap(lo[2], gl[2], e.sz, e.lz));
+                            pruned = g2 > p.rprune;
+                        }
+                        // boundary check: the box meets the cube of side 1.2 ell
+                        // centred on the extent
+                        const unsigned long long lim = 6ull * ell;
+                        bnear = 10ull * point_gap(e.sx + (uint32_t)(((unsigned long long)e.lx + 1ull) >> 1), lo[0], gl[0]) <= lim &&
+                                10ull * point_gap(e.sy + (uint32_t)(((unsigned long long)e.ly + 1ull) >> 1), lo[1], gl[1]) <= lim &&
+                                10ull * point_gap(e.sz + (uint32_t)(((unsigned long long)e.lz + 1ull) >> 1), lo[2], gl[2]) <= lim;
+                    } else {
+                        // the node's cell, from its level and centre of mass
+                        const uint32_t lev = (r.info >> 26) & 31u;
+                        const uint32_t side = 1u << (32u - lev);
+                        const uint32_t msk = ~(side - 1u);
+                        const uint32_t ox = r.x & msk, oy = r.y & msk, oz = r.z & msk;
+                        l2f = __uint_as_float((uint32_t)(127 + 64 - 2 * lev) << 23);
+                        l2 = __longlong_as_double((long long)(1023 + 64 - 2 * lev) << 52);
+                        if (kSplit) {
+                            const unsigned long long g2 = sq64(box_gap(lo[0], gl[0], ox, side - 1u)) +
+                                                          sq64(box_gap(lo[1], gl[1], oy, side - 1u)) +
+                                                          sq64(box_gap(lo[2], gl[2], oz, side - 1u));
+                            pruned = g2 > p.rprune;
+                        }
                         // boundary check: the box meets the cell enlarged to 0.6 side
                         const unsigned long long lim = 6ull * (unsigned long long)side;
-                        const bool bnear =
-                            10ull * point_gap(ox + (side >> 1), lo[0], hi[0]) <= lim &&
-                            10ull * point_gap(oy + (side >> 1), lo[1], hi[1]) <= lim &&
-                            10ull * point_gap(oz + (side >> 1), lo[2], hi[2]) <= lim;
+                        bnear = 10ull * point_gap(ox + (side >> 1), lo[0], gl[0]) <= lim &&
+                                10ull * point_gap(oy + (side >> 1), lo[1], gl[1]) <= lim &&
+                                10ull * point_gap(oz + (side >> 1), lo[2], gl[2]) <= lim;
+                    }
+                    if (!pruned) {
                         if (bnear) {
                             open = true;
                         } else {
-                            const float l2f = __uint_as_float((uint32_t)(127 + 64 - 2 * lev) << 23);
-                            const double l2 = __longlong_as_double((long long)(1023 + 64 - 2 * lev) << 52);
                             if (kOpen == OG_OPEN_BH) open = open_bh(gx, gy, gz, l2f, l2, p);
                             else open = open_rel(gx, gy, gz, l2f, l2, r.m, r.M, arelf, arel, p);
                         }
@@ -456,15 +485,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
     }
 }
 
-template <int kOpen, bool kSplit, bool kDump>
-void launch_walk(const WalkArgs &a, cudaStream_t s, int sms) {
+template <int kOpen, bool kSplit, bool kDump, bool kRefit>
+void launch_walk_t(const WalkArgs &a, cudaStream_t s, int sms) {
     const size_t smem = kWarps * (kStackCap * sizeof(uint2) + (kChunk + kNearChunk) * sizeof(uint4));
     static bool attr = false;
     static int per_sm = 1;
     if (!attr) {
-        cudaFuncSetAttribute(k_walk<kOpen, kSplit, kDump>,
+        cudaFuncSetAttribute(k_walk<kOpen, kSplit, kDump, kRefit>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<kOpen, kSplit, kDump>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<kOpen, kSplit, kDump, kRefit>,
                                                       kWarps * 32, smem);
         if (per_sm < 1) per_sm = 1;
         attr = true;
@@ -473,7 +502,13 @@ void launch_walk(const WalkArgs &a, cudaStream_t s, int sms) {
     int64_t grid = (int64_t)sms * per_sm;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    k_walk<kOpen, kSplit, kDump><<<(unsigned)grid, kWarps * 32, smem, s>>>(a); note_launch();
+    k_walk<kOpen, kSplit, kDump, kRefit><<<(unsigned)grid, kWarps * 32, smem, s>>>(a); note_launch();
+}
+
+template <int kOpen, bool kSplit, bool kDump>
+void launch_walk(const WalkArgs &a, cudaStream_t s, int sms) {
+    if (a.cext) launch_walk_t<kOpen, kSplit, kDump, true>(a, s, sms);
+    else launch_walk_t<kOpen, kSplit, kDump, false>(a, s, sms);
 }
 
 __global__ void k_cost_keys(int64_t ng, const uint32_t *__restrict__ gcost, uint64_t *keys,
@@ -546,6 +581,7 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
     a.gcost = t->gcost;
     a.gorder = nullptr;
     a.crec = t->crec;
+    a.cext = t->refit ? t->cext : nullptr;
     a.nchild = t->nchild;
     a.max_rounds = t->nchild + 2;
     a.gseg = t->gseg;

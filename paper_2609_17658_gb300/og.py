@@ -35,7 +35,7 @@ OG_DEBUG_DUMP_LISTS = 2
 
 (OG_F_SKEY, OG_F_PERM, OG_F_SPOS, OG_F_LEVEL, OG_F_NBEG, OG_F_NEND, OG_F_PARENT, OG_F_CBEG,
  OG_F_CCNT, OG_F_CHILD, OG_F_MASS, OG_F_COM, OG_F_NEXTNODE, OG_F_SIBLING, OG_F_PNEXT,
- OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS) = range(19)
+ OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS, OG_F_EXTENT) = range(20)
 
 
 class OGError(RuntimeError):
@@ -224,6 +224,7 @@ _FIELD_SPEC = {
     OG_F_PNEXT: ("n", np.int32, ()), OG_F_GBEG: ("groups", np.uint32, ()),
     OG_F_GEND: ("groups", np.uint32, ()), OG_F_GBOX: ("groups", np.uint32, (6,)),
     OG_F_LISTS: ("list_entries", np.uint32, (2,)),
+    OG_F_EXTENT: ("nodes", np.uint32, "2x3"),
 }
 
 
@@ -233,6 +234,8 @@ def og_tree_export(tree, field: int) -> np.ndarray:
     cnt = int(info[key])
     if tail == "3n":
         out = np.zeros((3, cnt), dtype=dt)
+    elif tail == "2x3":
+        out = np.zeros((2, cnt, 3), dtype=dt)
     else:
         out = np.zeros((cnt,) + tuple(tail), dtype=dt)
     _check(lib().og_tree_export(tree, int(field), out.ctypes.data_as(C.c_void_p), out.nbytes))
@@ -337,6 +340,9 @@ class Tree:
         ao = None if a_old is None else np.ascontiguousarray(a_old, dtype=np.float32)
         og_tree_force(self.h, acc, ao, npp, npn)
         return acc, npp, npn
+
+    def refit(self, pos) -> None:
+        og_tree_refit(self.h, np.ascontiguousarray(pos, dtype=np.float64) if not _is_torch_cuda(pos) else pos)
 
     def info(self) -> dict:
         return og_tree_info_get(self.h)

@@ -418,3 +418,72 @@ def test_list_partition_invariant(opening):
         assert np.all(cover[near] == 1)                      # every neighbour once
         # the group's own members are always PP entries
         assert set(range(gb[g], ge[g])) <= set(entries[entries < n].tolist())
+
+
+# ---------------------------------------------------------------------------
+# refit: same topology, drifted positions
+# ---------------------------------------------------------------------------
+
+def _drift(pos, seed, scale):
+    r = np.random.default_rng(seed)
+    return np.mod(pos + r.normal(0.0, scale, size=pos.shape), 1.0)
+
+
+def test_refit_without_drift_is_the_built_tree():
+    pos, mass, prm = gi.config("clustered-2m", n=6000)
+    prm["r_s"] = 0.02
+    t = oracle.Tree(pos, mass, prm)
+    a0, p0, n0 = t.force(keep_lists=True)
+    off0, l0 = t.lists()
+    t.refit(pos)
+    a1, p1, n1 = t.force(keep_lists=True)
+    off1, l1 = t.lists()
+    assert np.array_equal(a0, a1) and np.array_equal(p0, p1) and np.array_equal(n0, n1)
+    assert np.array_equal(off0, off1) and np.array_equal(l0, l1)
+
+
+def test_refit_extents_contain_members_and_partition_holds():
+    pos, mass, prm = gi.config("clustered-2m", n=3000)
+    prm["r_s"] = 0.02
+    pos[:50, 0] = 0.999                       # these drift across the periodic boundary
+    t = oracle.Tree(pos, mass, prm)
+    new = _drift(pos, 3, 2e-3)
+    t.refit(new)
+    n = t.n
+    perm = t.get(oracle.F_PERM)
+    q = np.stack([t.get(f)[perm] for f in (oracle.F_X, oracle.F_Y, oracle.F_Z)], 1).astype(np.int64)
+    es, el = t.get(oracle.F_EXT_S).astype(np.int64), t.get(oracle.F_EXT_L).astype(np.int64)
+    beg, end = t.get(oracle.F_BEG), t.get(oracle.F_END)
+    for j in range(t.nnodes):
+        off = (q[beg[j]:end[j]] - es[j]) % (1 << 32)
+        assert np.all(off <= el[j])            # every member inside the extent
+    gb, ge = t.get(oracle.F_GBEG), t.get(oracle.F_GEND)
+    glo, ghi = t.get(oracle.F_GLO).astype(np.int64), t.get(oracle.F_GHI).astype(np.int64)
+    for g in range(t.ngroups):
+        off = (q[gb[g]:ge[g]] - glo[g]) % (1 << 32)
+        assert np.all(off <= (ghi[g] - glo[g]) % (1 << 32))
+    t.force(theta=0.6, keep_lists=True)
+    offl, lst = t.lists()
+    rcg2 = (4.5 * prm["r_s"] * 2.0 ** 32) ** 2
+    for g in range(t.ngroups):
+        entries = lst[offl[g]:offl[g + 1]]
+        cover = np.zeros(n, dtype=np.int64)
+        for e in entries:
+            if e < n:
+                cover[e] += 1
+            else:
+                cover[beg[e - n]:end[e - n]] += 1
+        assert cover.max() <= 1
+        d = brute.min_image_int(q[None, :, :] - q[gb[g]:ge[g]][:, None, :]).astype(np.float64)
+        near = ((d ** 2).sum(-1) < rcg2).any(0)
+        assert np.all(cover[near] == 1)
+
+
+def test_refit_theta_zero_equals_direct_sum():
+    pos, mass, prm = gi.config("uniform-32k", n=3000)
+    t = oracle.Tree(pos, mass, prm)
+    new = _drift(pos, 4, 5e-3)
+    t.refit(new)
+    acc, _, _ = t.force(theta=0.0)
+    d = oracle.direct(new, mass, prm)
+    assert np.abs(acc - d).max() <= 1e-12 * np.abs(d).max()
