@@ -204,6 +204,52 @@ og_status og_tree_free(og_tree *t);
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *og_last_error(void);
 
+/* ---- serving: continuous batching of requests --------------------------- */
+
+/* One served request: a system integrated for nsteps steps of
+ *   a = short-range acceleration at x;  v += a dt_kick;  x += v dt_drift
+ * (positions wrapped into the box).  All arrays are host memory; the input
+ * arrays are copied by og_serve_submit.  acc_out / pos_out (caller-owned, may
+ * be NULL) receive the accelerations of the last force evaluation and the
+ * final positions; they must stay valid until og_serve_poll returns OG_OK. */
+typedef struct {
+    int64_t n;
+    const double *pos;       /* double[n][3] */
+    const double *vel;       /* double[n][3], box lengths per unit drift time */
+    const double *mass;      /* double[n] */
+    og_params params;        /* Barnes-Hut opening; host pointers */
+    int32_t nsteps;          /* >= 1 */
+    double dt_kick, dt_drift;
+    float *acc_out;          /* float[n][3] or NULL */
+    double *pos_out;         /* double[n][3] or NULL */
+} og_request;
+
+typedef struct {
+    int64_t n, steps, rebuilds, refits;
+    double t_submit, t_start, t_done;   /* seconds on a steady clock */
+} og_result;
+
+/* Queue a request (non-blocking).  The context's engine thread admits
+ * requests in arrival order while the estimated device memory of the active
+ * systems stays within the context's hbm_budget_bytes (0: no bound) and at
+ * most 256 are active; it keeps each admitted system's tree, positions,
+ * velocities and accelerations on the device, walks all active systems in
+ * one launch per step, and refits a tree after a step unless the drift since
+ * its build exceeds a quarter of its mean group box side (or four refits
+ * have passed), in which case it rebuilds.  OG_ERR_BUDGET if the system
+ * alone exceeds the budget.  Thread safe. */
+og_status og_serve_submit(og_ctx *ctx, const og_request *req, uint64_t *ticket);
+
+/* Device memory the admission control charges for a request of n particles
+ * against hbm_budget_bytes. */
+size_t og_serve_request_bytes(int64_t n);
+
+/* Wait up to timeout_ms (0: do not wait, < 0: wait as long as needed) for a
+ * ticket.  OG_OK and *out filled when done (a ticket can be collected once),
+ * OG_PENDING if not done yet, a negative status if the request failed.
+ * Thread safe. */
+og_status og_serve_poll(og_ctx *ctx, uint64_t ticket, og_result *out, int timeout_ms);
+
 /* ---- sort without device allocation ------------------------------------ */
 
 /* Largest n accepted by og_sort_keys_noalloc. */

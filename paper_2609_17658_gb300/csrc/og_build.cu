@@ -633,6 +633,18 @@ __global__ void k_ext_records(int64_t n, int64_t nchild, const uint32_t *__restr
     cext[c] = x;
 }
 
+// a built tree's node extents: its cells
+__global__ void k_cell_ext(int64_t m, const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ norg,
+                           uint32_t *ext_s, uint32_t *ext_l) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int L = nlev[j];
+    for (int a = 0; a < 3; ++a) {
+        ext_s[3 * j + a] = norg[3 * j + a];
+        ext_l[3 * j + a] = (uint32_t)((1ull << (32 - L)) - 1ull);
+    }
+}
+
 // refit: drifted fixed-point positions into sorted order (masses unchanged)
 __global__ void k_repos(int64_t n, const uint32_t *__restrict__ perm, const uint32_t *__restrict__ qx,
                         const uint32_t *__restrict__ qy, const uint32_t *__restrict__ qz,
@@ -735,20 +747,40 @@ static void moments_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
     }
 }
 
+static og_status alloc_extents(og_tree *t) {
+    if (t->cext) return OG_OK;
+    cudaStream_t s = t->ctx->stream;
+    const int64_t m = t->nnodes;
+    cudaError_t err;
+    size_t bytes = (size_t)m * 6 * sizeof(uint32_t) + (size_t)t->nchild * sizeof(CExt) + 1024;
+    void *p = nullptr;
+    if ((err = cudaMallocAsync(&p, bytes, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (extents)");
+    t->ext_arena = p;
+    t->next_s = static_cast<uint32_t *>(p);
+    t->next_l = t->next_s + 3 * m;
+    t->cext = reinterpret_cast<CExt *>(reinterpret_cast<char *>(p) +
+                                       (((size_t)m * 6 * sizeof(uint32_t) + 255) & ~(size_t)255));
+    return OG_OK;
+}
+
+og_status cell_extents(og_tree *t) {
+    og_status st = alloc_extents(t);
+    if (st) return st;
+    cudaStream_t s = t->ctx->stream;
+    k_cell_ext<<<nblk(t->nnodes), kT, 0, s>>>(t->nnodes, t->nlev, t->norg, t->next_s, t->next_l); note_launch();
+    k_ext_records<<<nblk(t->nchild), kT, 0, s>>>(t->n, t->nchild, t->child, t->next_s, t->next_l,
+                                                 t->cext); note_launch();
+    return OG_OK;
+}
+
 og_status refit_tree(og_tree *t, const double *d_pos) {
     cudaStream_t s = t->ctx->stream;
     const int64_t n = t->n, B = t->nseg, m = t->nnodes;
     cudaError_t err;
     if (!t->cext) {
         // extents live in their own allocation, made on the first refit
-        size_t bytes = (size_t)m * 6 * sizeof(uint32_t) + (size_t)t->nchild * sizeof(CExt) + 1024;
-        void *p = nullptr;
-        if ((err = cudaMallocAsync(&p, bytes, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (extents)");
-        t->ext_arena = p;
-        t->next_s = static_cast<uint32_t *>(p);
-        t->next_l = t->next_s + 3 * m;
-        t->cext = reinterpret_cast<CExt *>(reinterpret_cast<char *>(p) +
-                                           (((size_t)m * 6 * sizeof(uint32_t) + 255) & ~(size_t)255));
+        og_status st = alloc_extents(t);
+        if (st) return st;
     }
     size_t sb = (size_t)n * (3 * 4 + 8 + 4 + 4) + 4096;
     void *scratch = nullptr;

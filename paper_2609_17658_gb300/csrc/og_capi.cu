@@ -172,6 +172,7 @@ og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
 
 og_status og_destroy(og_ctx *c) {
     if (!c) return OG_OK;
+    serve_shutdown(c);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     cudaFree(c->d_status);

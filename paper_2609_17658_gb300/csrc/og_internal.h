@@ -75,6 +75,7 @@ struct og_tree {
     // boxes (segments) of the forest; a single system has nseg = 1
     int64_t nseg = 1;
     std::vector<og_params> seg_prm;   // per-box parameters
+    std::vector<og::WalkParams> h_wp; // host staging of the per-box walk parameters
     std::vector<uint32_t> h_seg_off;  // first particle of each box, plus n
     uint32_t *seg_off = nullptr;      // device copy
     og::SegGeom *geom = nullptr;
@@ -131,6 +132,8 @@ namespace og {
 
 // thread-local last error
 void set_error(const char *fmt, ...);
+// stop the serving engine of a context (og_serve.cu)
+void serve_shutdown(og_ctx *c);
 // count of kernels launched by this library in this process
 void note_launch();
 og_status cuda_fail(cudaError_t e, const char *what);
@@ -185,6 +188,14 @@ struct WalkParams {
 // list lengths of the previous pass on this tree (if any).
 og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
                     float *acc_sorted, float *ms_out, bool use_order);
+// One walk launch over the groups of several trees (the serving loop), in
+// decreasing order of their previous list lengths.  Every tree's per-box
+// parameters must agree on split on/off.
+og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int opening,
+                     const float *const *a_old_sorted, float *const *acc_sorted, float *ms_out,
+                     int64_t *interactions);
+// cell extents for a built tree (so that it can join a walk of refitted trees)
+og_status cell_extents(og_tree *t);
 WalkParams make_walk_params(const og_params &p, int opening, double theta);
 
 }  // namespace og

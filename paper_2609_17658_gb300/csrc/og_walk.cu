@@ -58,13 +58,14 @@ constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 constexpr float kFilterHi = 1.0f + 1.0f / 65536.0f;
 constexpr float kFilterLo = 1.0f - 1.0f / 65536.0f;
 
-struct WalkArgs {
+// One tree as the walk sees it (a forest counts as one tree).
+struct TreeView {
     int64_t n, ngroups;
     const uint32_t *gbeg, *gend, *gbox;
     const uint32_t *gorder;       // processing order of the groups, or null (key order)
     uint32_t *gcost;              // out: list length per group
     const CRec *crec;
-    const CExt *cext;             // node extents after a refit, or null (cells)
+    const CExt *cext;             // node extents after a refit (kRefit), else unused
     int64_t nchild, max_rounds;
     const uint32_t *gseg;         // box of each group
     const uint32_t *ncbeg, *nccnt;  // child range of each node (the roots are nodes 0..B-1)
@@ -73,10 +74,19 @@ struct WalkArgs {
     const float *a_old;           // [3][n] sorted, relative criterion only
     float *acc;                   // [3][n] sorted, out
     uint32_t *npp, *npn;          // [n] sorted, out
+    int has_cost;                 // gcost holds the list lengths of a previous pass
+};
+
+struct WalkArgs {
+    TreeView tree0;               // the tree of a single-tree launch
+    const TreeView *trees;        // several trees: descriptors in device memory
+    const uint64_t *goff;         // several trees: first item of each tree, plus the total
+    const uint32_t *items;        // several trees: item order (longest list first), or null
+    int64_t ntrees, nitems;
     uint32_t *lists;              // debug dump: (group, child slot) pairs
     unsigned long long *list_cursor;
     int64_t list_cap;
-    unsigned long long *work;     // group counter
+    unsigned long long *work;     // item counter
     unsigned long long *inter;    // interactions evaluated
     uint32_t *status;
 };
@@ -217,7 +227,7 @@ __device__ __forceinline__ bool open_rel(uint32_t gx, uint32_t gy, uint32_t gz, 
     return __dmul_rn(__dmul_rn(p.G, M), l2) > __dmul_rn(arel, __dmul_rn(d2, d2));
 }
 
-template <int kOpen, bool kSplit, bool kDump, bool kRefit>
+template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti>
 __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -232,17 +242,32 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         unsigned long long gq = 0;
         if (lane == 0) gq = atomicAdd(a.work, 1ull);
         gq = __shfl_sync(FULL, gq, 0);
-        if (gq >= (unsigned long long)a.ngroups) break;
-        const int64_t g = a.gorder ? (int64_t)a.gorder[gq] : (int64_t)gq;
-        const uint32_t seg = a.gseg[g];
-        const WalkParams &p = a.segp[seg];
-        const uint32_t gb = a.gbeg[g], ge = a.gend[g];
+        int64_t g;
+        int64_t ti = 0;
+        if (kMulti) {
+            if (gq >= (unsigned long long)a.nitems) break;
+            const uint64_t item = a.items ? a.items[gq] : gq;
+            int64_t lo_t = 0, hi_t = a.ntrees;  // goff[lo_t] <= item < goff[hi_t]
+            while (hi_t - lo_t > 1) {
+                const int64_t mid = (lo_t + hi_t) >> 1;
+                if (a.goff[mid] <= item) lo_t = mid; else hi_t = mid;
+            }
+            ti = lo_t;
+            g = (int64_t)(item - a.goff[ti]);
+        } else {
+            if (gq >= (unsigned long long)a.tree0.ngroups) break;
+            g = a.tree0.gorder ? (int64_t)a.tree0.gorder[gq] : (int64_t)gq;
+        }
+        const TreeView &T = kMulti ? a.trees[ti] : a.tree0;
+        const uint32_t seg = T.gseg[g];
+        const WalkParams &p = T.segp[seg];
+        const uint32_t gb = T.gbeg[g], ge = T.gend[g];
         const uint32_t gsize = ge - gb;
         uint32_t lo[3], gl[3];  // the group box: [lo, lo + gl] per axis
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            lo[k] = a.gbox[6 * g + k];
-            gl[k] = a.gbox[6 * g + 3 + k] - lo[k];
+            lo[k] = T.gbox[6 * g + k];
+            gl[k] = T.gbox[6 * g + 3 + k] - lo[k];
         }
         // lane -> (target, replica): P lanes per replica, R = 32 / P replicas
         const int P = gsize > 16u ? 32 : gsize > 8u ? 16 : gsize > 4u ? 8 : gsize > 2u ? 4 : gsize > 1u ? 2 : 1;
@@ -250,9 +275,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         const int tl = lane & (P - 1), rep = lane / P;
         const uint32_t i = gb + tl;
         const bool active = (uint32_t)tl < gsize;
-        const uint32_t xi = active ? a.px[i] : 0u;
-        const uint32_t yi = active ? a.py[i] : 0u;
-        const uint32_t zi = active ? a.pz[i] : 0u;
+        const uint32_t xi = active ? T.px[i] : 0u;
+        const uint32_t yi = active ? T.py[i] : 0u;
+        const uint32_t zi = active ? T.pz[i] : 0u;
         // relative criterion: arel = (alpha * a_min) * s^2, a_min = min over the group
         // of |a_old| in FP64 of the single-precision components
         double arel = 0.0;
@@ -260,7 +285,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         if (kOpen == OG_OPEN_REL) {
             double an = __longlong_as_double(0x7ff0000000000000ll);  // +inf
             if (active) {
-                double ax0 = a.a_old[i], ay0 = a.a_old[a.n + i], az0 = a.a_old[2 * a.n + i];
+                double ax0 = T.a_old[i], ay0 = T.a_old[T.n + i], az0 = T.a_old[2 * T.n + i];
                 an = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ax0, ax0), __dmul_rn(ay0, ay0)),
                                           __dmul_rn(az0, az0)));
             }
@@ -270,7 +295,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             arelf = __double2float_rn(arel);
         }
 
-        if (lane == 0) stk[0] = make_uint2(a.ncbeg[seg], a.nccnt[seg]);
+        if (lane == 0) stk[0] = make_uint2(T.ncbeg[seg], T.nccnt[seg]);
         __syncwarp();
         int sp = 1, cf = 0, cn = 0;
         int64_t rounds = 0;
@@ -281,7 +306,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         while (sp > 0) {
             // every round consumes at least one child record and a record is
             // visited at most once per walk: more rounds than records is a bug
-            if (++rounds > a.max_rounds) {
+            if (++rounds > T.max_rounds) {
                 overflow = true;
                 if (lane == 0) atomicOr(a.status, ST_INTERNAL);
                 break;
@@ -320,8 +345,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             bool emit = false, open = false, isnode = false, near = false;
             uint4 ent = make_uint4(0u, 0u, 0u, 0u);
             uint32_t push_ref = 0u, push_cnt = 0u;
-            if (has && ci < a.nchild) {
-                const CRec r = a.crec[ci];
+            if (has && ci < T.nchild) {
+                const CRec r = T.crec[ci];
                 ent = make_uint4(r.x, r.y, r.z, __float_as_uint(r.m));
                 isnode = (r.info >> 31) != 0u;
                 const uint32_t gx = point_gap(r.x, lo[0], gl[0]);
@@ -337,7 +362,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
                     double l2;
                     if (kRefit) {
                         // the node's extent: its cell joined with its drifted members
-                        const CExt e = a.cext[ci];
+                        const CExt e = T.cext[ci];
                         const unsigned long long ell =
                             (unsigned long long)max(e.lx, max(e.ly, e.lz)) + 1ull;
                         l2 = (double)ell * (double)ell;
@@ -397,7 +422,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             if (open) {
                 // a node always has children; a zero count would stall the walk
                 stk[sp_new + __popc(bo & lt)] = make_uint2(push_ref, push_cnt > 0u ? push_cnt : 1u);
-                if (push_cnt == 0u || (uint64_t)push_ref + push_cnt > (uint64_t)a.nchild)
+                if (push_cnt == 0u || (uint64_t)push_ref + push_cnt > (uint64_t)T.nchild)
                     atomicOr(a.status, ST_INTERNAL);
             }
             sp = sp_new + npush;
@@ -472,43 +497,52 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             vz = __fadd_rn(vz, __shfl_xor_sync(FULL, vz, o));
         }
         if (active && rep == 0) {
-            a.acc[i] = vx * p.out_scale;
-            a.acc[a.n + i] = vy * p.out_scale;
-            a.acc[2 * a.n + i] = vz * p.out_scale;
-            a.npp[i] = cnt_pp - 1u;
-            a.npn[i] = cnt_pn;
+            T.acc[i] = vx * p.out_scale;
+            T.acc[T.n + i] = vy * p.out_scale;
+            T.acc[2 * T.n + i] = vz * p.out_scale;
+            T.npp[i] = cnt_pp - 1u;
+            T.npn[i] = cnt_pn;
         }
         if (lane == 0) {
-            a.gcost[g] = cnt_pp + cnt_pn;
+            T.gcost[g] = cnt_pp + cnt_pn;
             atomicAdd(a.inter, (unsigned long long)gsize * (unsigned long long)(cnt_pp - 1u + cnt_pn));
         }
     }
 }
 
-template <int kOpen, bool kSplit, bool kDump, bool kRefit>
-void launch_walk_t(const WalkArgs &a, cudaStream_t s, int sms) {
+template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti>
+void launch_walk_t(const WalkArgs &a, int64_t nitems, cudaStream_t s, int sms) {
     const size_t smem = kWarps * (kStackCap * sizeof(uint2) + (kChunk + kNearChunk) * sizeof(uint4));
     static bool attr = false;
     static int per_sm = 1;
     if (!attr) {
-        cudaFuncSetAttribute(k_walk<kOpen, kSplit, kDump, kRefit>,
+        cudaFuncSetAttribute(k_walk<kOpen, kSplit, kDump, kRefit, kMulti>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<kOpen, kSplit, kDump, kRefit>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<kOpen, kSplit, kDump, kRefit, kMulti>,
                                                       kWarps * 32, smem);
         if (per_sm < 1) per_sm = 1;
         attr = true;
     }
-    int64_t want = (a.ngroups + kWarps - 1) / kWarps;
+    int64_t want = (nitems + kWarps - 1) / kWarps;
     int64_t grid = (int64_t)sms * per_sm;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    k_walk<kOpen, kSplit, kDump, kRefit><<<(unsigned)grid, kWarps * 32, smem, s>>>(a); note_launch();
+    k_walk<kOpen, kSplit, kDump, kRefit, kMulti><<<(unsigned)grid, kWarps * 32, smem, s>>>(a); note_launch();
 }
 
-template <int kOpen, bool kSplit, bool kDump>
-void launch_walk(const WalkArgs &a, cudaStream_t s, int sms) {
-    if (a.cext) launch_walk_t<kOpen, kSplit, kDump, true>(a, s, sms);
-    else launch_walk_t<kOpen, kSplit, kDump, false>(a, s, sms);
+template <int kOpen, bool kSplit>
+void launch_walk(const WalkArgs &a, bool dump, bool refit, bool multi, int64_t nitems,
+                 cudaStream_t s, int sms) {
+    if (multi) {
+        if (refit) launch_walk_t<kOpen, kSplit, false, true, true>(a, nitems, s, sms);
+        else launch_walk_t<kOpen, kSplit, false, false, true>(a, nitems, s, sms);
+    } else if (dump) {
+        if (refit) launch_walk_t<kOpen, kSplit, true, true, false>(a, nitems, s, sms);
+        else launch_walk_t<kOpen, kSplit, true, false, false>(a, nitems, s, sms);
+    } else {
+        if (refit) launch_walk_t<kOpen, kSplit, false, true, false>(a, nitems, s, sms);
+        else launch_walk_t<kOpen, kSplit, false, false, false>(a, nitems, s, sms);
+    }
 }
 
 __global__ void k_cost_keys(int64_t ng, const uint32_t *__restrict__ gcost, uint64_t *keys,
@@ -517,6 +551,91 @@ __global__ void k_cost_keys(int64_t ng, const uint32_t *__restrict__ gcost, uint
     if (g >= ng) return;
     keys[g] = (uint64_t)(0xffffffffu - gcost[g]);  // decreasing cost, ties in key order
     vals[g] = (uint32_t)g;
+}
+
+// several trees: sort keys of every (tree, group) item, longest list first
+__global__ void k_item_keys(int64_t nitems, int64_t ntrees, const uint64_t *__restrict__ goff,
+                            const TreeView *__restrict__ trees, uint64_t *keys, uint32_t *vals) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nitems) return;
+    int64_t lo = 0, hi = ntrees;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (goff[mid] <= (uint64_t)q) lo = mid; else hi = mid;
+    }
+    const TreeView &T = trees[lo];
+    const uint32_t cost = T.has_cost ? T.gcost[q - goff[lo]] : 0u;
+    keys[q] = (uint64_t)(0xffffffffu - cost);
+    vals[q] = (uint32_t)q;
+}
+
+template <int kOpen>
+void dispatch(const WalkArgs &a, bool split, bool dump, bool refit, bool multi, int64_t nitems,
+              cudaStream_t s, int sms) {
+    if (split) launch_walk<kOpen, true>(a, dump, refit, multi, nitems, s, sms);
+    else launch_walk<kOpen, false>(a, dump, refit, multi, nitems, s, sms);
+}
+
+void launch(const WalkArgs &a, int opening, bool split, bool dump, bool refit, bool multi,
+            int64_t nitems, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (opening == OG_OPEN_BH) dispatch<OG_OPEN_BH>(a, split, dump, refit, multi, nitems, s, sms);
+    else dispatch<OG_OPEN_REL>(a, split, dump, refit, multi, nitems, s, sms);
+}
+
+// Per-box parameters of a pass (uploaded) and the tree's view.  The first
+// pass of the relative criterion is Barnes-Hut with theta_first_pass.
+og_status prepare_view(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
+                       float *acc_sorted, TreeView *v, WalkParams *wp0) {
+    cudaStream_t s = t->ctx->stream;
+    const int64_t B = t->nseg;
+    t->h_wp.resize((size_t)B);
+    for (int64_t b = 0; b < B; ++b) {
+        const og_params &q = t->seg_prm[b];
+        t->h_wp[b] = make_walk_params(q, opening, first_pass ? q.theta_first_pass : q.theta);
+        if (first_pass) t->h_wp[b].dump = false;
+    }
+    *wp0 = t->h_wp[0];
+    WalkParams *dp = t->segp + (first_pass ? 0 : B);
+    cudaError_t err = cudaMemcpyAsync(dp, t->h_wp.data(), B * sizeof(WalkParams), cudaMemcpyHostToDevice, s);
+    if (err != cudaSuccess) return cuda_fail(err, "walk setup");
+    TreeView &w = *v;
+    w = TreeView{};
+    w.n = t->n;
+    w.ngroups = t->ngroups;
+    w.gbeg = t->gbeg;
+    w.gend = t->gend;
+    w.gbox = t->gbox;
+    w.gcost = t->gcost;
+    w.gorder = nullptr;
+    w.crec = t->crec;
+    w.cext = t->cext;
+    w.nchild = t->nchild;
+    w.max_rounds = t->nchild + 2;
+    w.gseg = t->gseg;
+    w.ncbeg = t->ncbeg;
+    w.nccnt = t->nccnt;
+    w.segp = dp;
+    w.px = t->px;
+    w.py = t->py;
+    w.pz = t->pz;
+    w.a_old = a_old_sorted;
+    w.acc = acc_sorted;
+    w.npp = t->npp_sorted;
+    w.npn = t->npn_sorted;
+    w.has_cost = t->have_cost ? 1 : 0;
+    return OG_OK;
+}
+
+void fill_common(WalkArgs &a, og_ctx *c, og_tree *t) {
+    a.lists = t ? t->lists : nullptr;
+    a.list_cap = t ? t->list_cap : 0;
+    a.work = c->d_counters;
+    a.inter = c->d_counters + 1;
+    a.list_cursor = c->d_counters + 2;
+    a.status = c->d_status;
 }
 
 }  // namespace
@@ -559,38 +678,30 @@ WalkParams make_walk_params(const og_params &p, int opening, double theta) {
     return w;
 }
 
+static og_status finish_pass(og_ctx *c, cudaEvent_t e0, cudaEvent_t e1, float *ms_out,
+                             unsigned long long h[3]) {
+    cudaStream_t s = c->stream;
+    cudaMemcpyAsync(h, c->d_counters, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    cudaError_t err = cudaStreamSynchronize(s);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "walk");
+    if ((err = cudaGetLastError()) != cudaSuccess) return cuda_fail(err, "walk launch");
+    if (ms_out) *ms_out = ms;
+    return OG_OK;
+}
+
 og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
                     float *acc_sorted, float *ms_out, bool use_order) {
     cudaStream_t s = t->ctx->stream;
-    const int64_t B = t->nseg;
-    // per-box parameters of this pass: the first pass of the relative
-    // criterion is Barnes-Hut with each box's theta_first_pass
-    std::vector<WalkParams> hp((size_t)B);
-    for (int64_t b = 0; b < B; ++b) {
-        const og_params &q = t->seg_prm[b];
-        hp[b] = make_walk_params(q, opening, first_pass ? q.theta_first_pass : q.theta);
-        hp[b].dump = first_pass ? false : hp[b].dump;
-    }
-    const WalkParams &wp = hp[0];
     WalkArgs a{};
-    a.n = t->n;
-    a.ngroups = t->ngroups;
-    a.gbeg = t->gbeg;
-    a.gend = t->gend;
-    a.gbox = t->gbox;
-    a.gcost = t->gcost;
-    a.gorder = nullptr;
-    a.crec = t->crec;
-    a.cext = t->refit ? t->cext : nullptr;
-    a.nchild = t->nchild;
-    a.max_rounds = t->nchild + 2;
-    a.gseg = t->gseg;
-    a.ncbeg = t->ncbeg;
-    a.nccnt = t->nccnt;
-    WalkParams *dp = t->segp + (first_pass ? 0 : B);
-    cudaError_t err = cudaMemcpyAsync(dp, hp.data(), B * sizeof(WalkParams), cudaMemcpyHostToDevice, s);
-    if (err != cudaSuccess) return cuda_fail(err, "walk setup");
-    a.segp = dp;
+    WalkParams wp;
+    og_status st = prepare_view(t, opening, first_pass, a_old_sorted, acc_sorted, &a.tree0, &wp);
+    if (st) return st;
+    fill_common(a, t->ctx, t);
+    cudaError_t err;
     void *sort_tmp = nullptr;
     if (use_order && t->have_cost && t->ngroups > 1) {
         // longest list first, from the costs of the previous pass on this tree
@@ -608,62 +719,101 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
         bool alt = false;
         radix_sort_pairs(k0, v0, k1, v1, ng, 32, scr, s, &alt);
         cudaMemcpyAsync(t->gorder, alt ? v1 : v0, ng * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
-        a.gorder = t->gorder;
+        a.tree0.gorder = t->gorder;
     }
-    a.px = t->px;
-    a.py = t->py;
-    a.pz = t->pz;
-    a.a_old = a_old_sorted;
-    a.acc = acc_sorted;
-    a.npp = t->npp_sorted;
-    a.npn = t->npn_sorted;
-    a.lists = t->lists;
-    a.list_cap = t->list_cap;
-    a.work = t->ctx->d_counters;
-    a.inter = t->ctx->d_counters + 1;
-    a.list_cursor = t->ctx->d_counters + 2;
-    a.status = t->ctx->d_status;
     cudaMemsetAsync(t->ctx->d_counters, 0, 3 * sizeof(unsigned long long), s);
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    if (wp.opening == OG_OPEN_BH) {
-        if (wp.split) {
-            if (wp.dump) launch_walk<OG_OPEN_BH, true, true>(a, s, sms);
-            else launch_walk<OG_OPEN_BH, true, false>(a, s, sms);
-        } else {
-            if (wp.dump) launch_walk<OG_OPEN_BH, false, true>(a, s, sms);
-            else launch_walk<OG_OPEN_BH, false, false>(a, s, sms);
-        }
-    } else {
-        if (wp.split) {
-            if (wp.dump) launch_walk<OG_OPEN_REL, true, true>(a, s, sms);
-            else launch_walk<OG_OPEN_REL, true, false>(a, s, sms);
-        } else {
-            if (wp.dump) launch_walk<OG_OPEN_REL, false, true>(a, s, sms);
-            else launch_walk<OG_OPEN_REL, false, false>(a, s, sms);
-        }
-    }
+    launch(a, opening, wp.split, wp.dump, t->refit, false, t->ngroups, s);
     cudaEventRecord(e1, s);
     if (sort_tmp) cudaFreeAsync(sort_tmp, s);
     unsigned long long h[3] = {0, 0, 0};
-    cudaMemcpyAsync(h, t->ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost, s);
-    err = cudaStreamSynchronize(s);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (err != cudaSuccess) return cuda_fail(err, "walk");
-    if ((err = cudaGetLastError()) != cudaSuccess) return cuda_fail(err, "walk launch");
-    if (ms_out) *ms_out = ms;
+    st = finish_pass(t->ctx, e0, e1, ms_out, h);
+    if (st) return st;
     t->have_cost = true;
     t->interactions_last = (int64_t)h[1];
     t->interactions += (int64_t)h[1];
     if (wp.dump) t->list_len = (int64_t)(h[2] < (unsigned long long)t->list_cap ? h[2] : t->list_cap);
+    return OG_OK;
+}
+
+og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int opening,
+                     const float *const *a_old_sorted, float *const *acc_sorted, float *ms_out,
+                     int64_t *interactions) {
+    cudaStream_t s = c->stream;
+    if (ntrees < 1) return OG_OK;
+    std::vector<TreeView> hv((size_t)ntrees);
+    std::vector<uint64_t> hoff((size_t)ntrees + 1);
+    bool split = false, refit = false;
+    uint64_t total = 0;
+    for (int64_t k = 0; k < ntrees; ++k) {
+        WalkParams wp;
+        og_status st = prepare_view(trees[k], opening, false, a_old_sorted ? a_old_sorted[k] : nullptr,
+                                    acc_sorted[k], &hv[k], &wp);
+        if (st) return st;
+        if (k == 0) split = wp.split;
+        else if (wp.split != split) {
+            set_error("walk over several trees: split on/off must agree");
+            return OG_ERR_ARG;
+        }
+        refit = refit || trees[k]->refit;
+        hoff[k] = total;
+        total += (uint64_t)trees[k]->ngroups;
+    }
+    hoff[ntrees] = total;
+    if (refit) {
+        // one instantiation for all trees: built trees read their cells as extents
+        for (int64_t k = 0; k < ntrees; ++k) {
+            if (!trees[k]->cext) {
+                og_status st = cell_extents(trees[k]);
+                if (st) return st;
+            }
+            hv[k].cext = trees[k]->cext;
+        }
+    }
+    const int64_t nitems = (int64_t)total;
+    size_t bytes = (size_t)ntrees * sizeof(TreeView) + (size_t)(ntrees + 1) * 8 + (size_t)nitems * 24 +
+                   radix_sort_scratch_bytes(nitems) + 4096;
+    void *tmp = nullptr;
+    cudaError_t err;
+    if ((err = cudaMallocAsync(&tmp, bytes, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (walk items)");
+    char *q = static_cast<char *>(tmp);
+    TreeView *dv = reinterpret_cast<TreeView *>(q);
+    q += ((size_t)ntrees * sizeof(TreeView) + 255) & ~(size_t)255;
+    uint64_t *doff = reinterpret_cast<uint64_t *>(q);
+    q += ((size_t)(ntrees + 1) * 8 + 255) & ~(size_t)255;
+    uint64_t *k0 = reinterpret_cast<uint64_t *>(q);
+    uint64_t *k1 = k0 + nitems;
+    uint32_t *v0 = reinterpret_cast<uint32_t *>(k1 + nitems);
+    uint32_t *v1 = v0 + nitems;
+    void *scr = v1 + nitems + 64;
+    cudaMemcpyAsync(dv, hv.data(), ntrees * sizeof(TreeView), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(doff, hoff.data(), (ntrees + 1) * 8, cudaMemcpyHostToDevice, s);
+    k_item_keys<<<(unsigned)((nitems + 255) / 256), 256, 0, s>>>(nitems, ntrees, doff, dv, k0, v0); note_launch();
+    bool alt = false;
+    radix_sort_pairs(k0, v0, k1, v1, nitems, 32, scr, s, &alt);
+    WalkArgs a{};
+    fill_common(a, c, nullptr);
+    a.trees = dv;
+    a.goff = doff;
+    a.items = alt ? v1 : v0;
+    a.ntrees = ntrees;
+    a.nitems = nitems;
+    cudaMemsetAsync(c->d_counters, 0, 3 * sizeof(unsigned long long), s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    launch(a, opening, split, false, refit, true, nitems, s);
+    cudaEventRecord(e1, s);
+    cudaFreeAsync(tmp, s);
+    unsigned long long h[3] = {0, 0, 0};
+    og_status st = finish_pass(c, e0, e1, ms_out, h);
+    if (st) return st;
+    for (int64_t k = 0; k < ntrees; ++k) trees[k]->have_cost = true;
+    if (interactions) *interactions = (int64_t)h[1];
     return OG_OK;
 }
 

@@ -71,6 +71,18 @@ class og_batch_info(C.Structure):
                 ("ms_walk", C.c_double)]
 
 
+class og_request(C.Structure):
+    _fields_ = [("n", C.c_int64), ("pos", C.c_void_p), ("vel", C.c_void_p), ("mass", C.c_void_p),
+                ("params", og_params), ("nsteps", C.c_int32), ("dt_kick", C.c_double),
+                ("dt_drift", C.c_double), ("acc_out", C.c_void_p), ("pos_out", C.c_void_p)]
+
+
+class og_result(C.Structure):
+    _fields_ = [("n", C.c_int64), ("steps", C.c_int64), ("rebuilds", C.c_int64),
+                ("refits", C.c_int64), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double)]
+
+
 _lib = None
 
 
@@ -102,6 +114,12 @@ def lib():
         L.og_sort_keys_noalloc.argtypes = [P, P, P, i64, P]
         L.og_batch_force.argtypes = [P, i64, C.POINTER(og_box), C.POINTER(og_batch_info)]
         L.og_batch_force.restype = C.c_int
+        L.og_serve_submit.argtypes = [P, C.POINTER(og_request), C.POINTER(C.c_uint64)]
+        L.og_serve_submit.restype = C.c_int
+        L.og_serve_poll.argtypes = [P, C.c_uint64, C.POINTER(og_result), C.c_int]
+        L.og_serve_poll.restype = C.c_int
+        L.og_serve_request_bytes.argtypes = [i64]
+        L.og_serve_request_bytes.restype = C.c_size_t
         L.og_sort_keys_noalloc.restype = C.c_int
         for name in ("og_create", "og_destroy", "og_set_stream", "og_params_default",
                      "og_tree_build", "og_tree_refit", "og_tree_force", "og_tree_info_get",
@@ -274,6 +292,43 @@ def og_batch_force(ctx, boxes) -> dict:
     info = og_batch_info()
     _check(lib().og_batch_force(ctx, nb, arr, C.byref(info)))
     return {k: getattr(info, k) for k, _ in og_batch_info._fields_}
+
+
+def og_serve_submit(ctx, pos, vel, mass, params: dict, nsteps: int = 8, dt_kick: float = 1e-5,
+                    dt_drift: float = 1.0, acc_out=None, pos_out=None) -> int:
+    """Queue a served request (host numpy arrays; acc_out float32 [n,3] and
+    pos_out float64 [n,3] are filled when the request completes and must stay
+    alive until og_serve_poll returns it).  Returns the ticket."""
+    r = og_request()
+    r.n = int(pos.shape[0])
+    r.pos = _host_ptr(pos, np.float64, (3,)).value
+    r.vel = _host_ptr(vel, np.float64, (3,)).value
+    r.mass = _host_ptr(mass, np.float64).value
+    prm = params_from_dict(params)
+    prm.flags = int(prm.flags) & ~OG_DEVICE_PTRS
+    r.params = prm
+    r.nsteps = int(nsteps)
+    r.dt_kick = float(dt_kick)
+    r.dt_drift = float(dt_drift)
+    r.acc_out = _host_ptr(acc_out, np.float32, (3,)).value if acc_out is not None else None
+    r.pos_out = _host_ptr(pos_out, np.float64, (3,)).value if pos_out is not None else None
+    t = C.c_uint64()
+    _check(lib().og_serve_submit(ctx, C.byref(r), C.byref(t)))
+    return int(t.value)
+
+
+def og_serve_request_bytes(n: int) -> int:
+    return int(lib().og_serve_request_bytes(int(n)))
+
+
+def og_serve_poll(ctx, ticket: int, timeout_ms: int = -1):
+    """(status, result dict or None): OG_OK with the result, or OG_PENDING."""
+    res = og_result()
+    st = lib().og_serve_poll(ctx, C.c_uint64(ticket), C.byref(res), int(timeout_ms))
+    if st == OG_PENDING:
+        return st, None
+    _check(st)
+    return st, {k: getattr(res, k) for k, _ in og_result._fields_}
 
 
 OG_NOALLOC_MAX_N = 1048576

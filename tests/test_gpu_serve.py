@@ -1,0 +1,108 @@
+"""Served stream: og_serve_submit / og_serve_poll.
+
+Every system of a request is computed independently of the other systems in
+the engine's launches (its own tree, lists, summation order, kick, drift and
+refit-or-rebuild decisions), so each request's final accelerations and
+positions must be bitwise identical whether it is served alone or in a mix of
+concurrent requests.  Admission respects the HBM budget.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import og_inputs as gi
+from paper_2609_17658_gb300 import build as B
+from paper_2609_17658_gb300 import og
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(count=12, seed=3):
+    reqs = gi.request_stream(1000.0, 10.0, seed=seed, n_lo=2000, n_hi=60000, max_requests=count)
+    return reqs
+
+
+def _serve(ctx, reqs, wait_each=False):
+    outs, tickets = [], []
+    for r in reqs:
+        n = len(r.mass)
+        acc = np.zeros((n, 3), np.float32)
+        pos = np.zeros((n, 3), np.float64)
+        t = og.og_serve_submit(ctx.h, r.pos, r.vel, r.mass, r.params, r.nsteps, r.dt_kick,
+                               r.dt_drift, acc, pos)
+        outs.append((acc, pos))
+        tickets.append(t)
+        if wait_each:
+            st, res = og.og_serve_poll(ctx.h, t, -1)
+            assert st == og.OG_OK
+            outs[-1] = (acc, pos, res)
+    results = []
+    for k, t in enumerate(tickets):
+        if wait_each:
+            results.append(outs[k][2])
+            continue
+        st, res = og.og_serve_poll(ctx.h, t, -1)
+        assert st == og.OG_OK
+        results.append(res)
+    return [(o[0], o[1]) for o in outs], results
+
+
+def test_each_result_same_alone_and_in_the_mix():
+    B.build()
+    reqs = _requests()
+    with og.Context(0) as ctx:
+        mixed, res_m = _serve(ctx, reqs)
+    with og.Context(0) as ctx:
+        alone, res_a = _serve(ctx, reqs, wait_each=True)
+    for (am, pm), (aa, pa), r, q in zip(mixed, alone, res_m, reqs):
+        assert r["steps"] == q.nsteps and r["n"] == len(q.mass)
+        assert np.isfinite(am).all() and np.abs(am).max() > 0
+        assert np.array_equal(am, aa)
+        assert np.array_equal(pm, pa)
+        assert r["rebuilds"] >= 1 and r["rebuilds"] + r["refits"] == q.nsteps
+        assert r["t_submit"] <= r["t_start"] <= r["t_done"]
+
+
+def test_positions_follow_kick_and_drift():
+    B.build()
+    r = _requests(count=1, seed=8)[0]
+    n = len(r.mass)
+    acc = np.zeros((n, 3), np.float32)
+    pos = np.zeros((n, 3), np.float64)
+    with og.Context(0) as ctx:
+        t = og.og_serve_submit(ctx.h, r.pos, r.vel, r.mass, r.params, 1, r.dt_kick, r.dt_drift, acc, pos)
+        st, res = og.og_serve_poll(ctx.h, t, -1)
+        assert st == og.OG_OK
+        a0, _, _ = og.Tree(ctx, r.pos, r.mass, r.params).force(counts=False)
+    assert np.array_equal(acc, a0)                        # one step: the force at the start
+    expect = np.mod(r.pos + (r.vel + a0.astype(np.float64) * r.dt_kick) * r.dt_drift, 1.0)
+    d = np.abs(pos - expect)
+    d = np.minimum(d, 1.0 - d)
+    assert d.max() < 1e-12
+
+
+def test_budget_admission_and_errors():
+    B.build()
+    n = 20000
+    reqs = []
+    for k in range(4):
+        pos, mass = gi.halo_mix(n, 40 + k, n_halo=10)
+        vel = np.random.default_rng(k).normal(0.0, 1e-3, size=(n, 3))
+        prm = gi.default_params(eps=1 / (50 * n ** (1 / 3)), r_s=1.25 / (2 * n ** (1 / 3)))
+        reqs.append(gi.Request(0.0, pos, vel, mass, prm))
+    budget = int(1.5 * og.og_serve_request_bytes(n))   # one system at a time
+    with og.Context(0, hbm_budget_bytes=budget) as ctx:
+        _, res = _serve(ctx, reqs)
+        spans = sorted((r["t_start"], r["t_done"]) for r in res)
+        for (s0, d0), (s1, d1) in zip(spans, spans[1:]):
+            assert s1 >= d0                              # never two admitted at once
+        big = gi.uniform(4 * n, 1)
+        with pytest.raises(og.OGError) as e:
+            og.og_serve_submit(ctx.h, big[0], np.zeros_like(big[0]), big[1], gi.default_params(r_s=0.01))
+        assert e.value.status == og.OG_ERR_BUDGET
+        with pytest.raises(og.OGError):
+            og.og_serve_poll(ctx.h, 10 ** 9, 0)
+        with pytest.raises(og.OGError):
+            og.og_serve_submit(ctx.h, reqs[0].pos, reqs[0].vel, reqs[0].mass,
+                               dict(reqs[0].params, opening=gi.OPEN_REL))
