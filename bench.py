@@ -40,6 +40,39 @@ FLOPS_PER_INTERACTION = 38
 FP32_LANES_PER_SM = 128
 
 
+WALK_SOURCES = ("paper_2609_17658_gb300/csrc/og_walk.cu", "paper_2609_17658_gb300/csrc/og_internal.h")
+
+
+def walk_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in WALK_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload):
+    """DRAM bytes (read + write) of the walk's launches in one step, from the
+    committed ncu summary of this workload; None when there is none or when
+    the walk's source changed after the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"k_walk_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+    if fields.get("walk source sha256") != walk_source_hash():
+        return None
+    try:
+        return int(fields["dram bytes per step"])
+    except (KeyError, ValueError):
+        return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -50,6 +83,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-seconds", type=float, default=6.0)
     ap.add_argument("--batched-boxes", type=int, default=512)
     return ap.parse_args()
 
@@ -205,6 +240,76 @@ def batched_bench(og, ctx, torch, dev, stream, nboxes, steps):
             "same_interactions": int(inter_pb) == int(info["interactions"])}
 
 
+def served_bench(og, torch, dev, rates=(10.0, 30.0, 100.0), seconds=6.0, pool_size=16):
+    """Served stream: Poisson arrivals of systems with N log-uniform in
+    [1e4, 2e6] (halo-clustered, 8 kick-drift steps each, HBM budget 40 GB)
+    against the plain per-box path (build + force per step, then kick and
+    drift, one request after another), both on this GPU from host arrays,
+    results left on the device."""
+    pool = gi.request_stream(1e9, 1e9, seed=12349, max_requests=pool_size)
+    # plain path
+    ctx = og.Context(dev.index or 0)
+    stream = torch.cuda.current_stream(dev)
+    og.og_set_stream(ctx.h, stream.cuda_stream)
+    plain_req = pool[:6]
+    work = sum(len(r.mass) * r.nsteps for r in plain_req)
+
+    def plain_run(reqs):
+        for r in reqs:
+            pos = torch.from_numpy(r.pos).to(dev)
+            vel = torch.from_numpy(r.vel).to(dev)
+            mass = torch.from_numpy(r.mass).to(dev)
+            acc = torch.empty((len(r.mass), 3), dtype=torch.float32, device=dev)
+            for _ in range(r.nsteps):
+                h = og.og_tree_build(ctx.h, pos, mass, r.params)
+                og.og_tree_force(h, acc)
+                og.og_tree_free(h)
+                vel += acc.double() * r.dt_kick
+                pos = torch.remainder(pos + vel * r.dt_drift, 1.0)
+
+    plain_run(pool[:2])          # warm-up: first use of every kernel, torch's included
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_run(plain_req)
+    torch.cuda.synchronize()
+    plain = work / (time.perf_counter() - t0)
+    ctx.close()
+    out = {"workload": "Poisson arrivals, N log-uniform [1e4, 2e6], halo-clustered, 8 kick-drift "
+                       "steps, v Gaussian sigma 1e-3 box/step, BH theta 0.5, budget 40 GB",
+           "plain_particle_steps_per_s": plain, "rates": []}
+    for rate in rates:
+        r = np.random.default_rng(int(rate))
+        arrivals = np.cumsum(r.exponential(1.0 / rate, size=int(rate * seconds * 3) + 8))
+        arrivals = arrivals[arrivals < seconds]
+        ctx = og.Context(dev.index or 0, hbm_budget_bytes=40 << 30)
+        tickets = []
+        t_base = time.perf_counter()
+        for k, ta in enumerate(arrivals):
+            q = pool[k % pool_size]
+            delay = t_base + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append((og.og_serve_submit(ctx.h, q.pos, q.vel, q.mass, q.params, q.nsteps,
+                                               q.dt_kick, q.dt_drift), len(q.mass) * q.nsteps))
+        res = []
+        for t, w in tickets:
+            st, x = og.og_serve_poll(ctx.h, t, -1)
+            res.append((x, w))
+        ctx.close()
+        lat = np.array([x["t_done"] - x["t_submit"] for x, _ in res])
+        span = max(x["t_done"] for x, _ in res) - min(x["t_submit"] for x, _ in res)
+        work = sum(w for _, w in res)
+        out["rates"].append({"rate_per_s": rate, "requests": len(res),
+                             "particle_steps_per_s": work / span,
+                             "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
+                             "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
+                             "refits": int(sum(x["refits"] for x, _ in res)),
+                             "rebuilds": int(sum(x["rebuilds"] for x, _ in res))})
+    best = max(x["particle_steps_per_s"] for x in out["rates"])
+    out["served_over_plain"] = best / plain
+    return out
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle (the paper's method as the CPU program
     of this repository) timed on the host cores, each step a bounded sample."""
@@ -227,6 +332,20 @@ def run_reference(args):
                             "sample": cb["sample"]},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def describe(name, prm):
+    """One-line recipe of a named workload, from its parameters."""
+    side = round(1.0 / (50 * prm["eps"]))
+    if name.startswith("clustered"):
+        nh = 2000 if name == "clustered-2m" else 16000
+        head = f"70% in {nh} NFW haloes + 30% uniform"
+    else:
+        head = "Poisson-uniform"
+    crit = (f"relative alpha={prm['alpha']:g} after BH theta={prm['theta_first_pass']:g}"
+            if prm["opening"] == gi.OPEN_REL else f"BH theta={prm['theta']:g}")
+    return (f"{head}, eps=1/{50 * side}, r_s=1.25/{2 * side}, "
+            f"cutoff {prm['rcut_over_rs']:g} r_s, {crit}")
 
 
 def main():
@@ -338,7 +457,8 @@ def main():
     peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     achieved = inter_step * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
+            "traffic_unit": "bytes per step (both walk launches)",
             "kernel": "k_walk (both passes)",
             "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
             "frac_at_observed_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 *
@@ -349,6 +469,10 @@ def main():
     if not args.no_batched:
         batched = batched_bench(og, ctx, torch, dev, stream, args.batched_boxes, max(1, min(args.steps, 3)))
 
+    served = None
+    if not args.no_served and rank == 0:
+        served = served_bench(og, torch, dev, seconds=args.served_seconds)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(pos, mass, prm)
@@ -358,9 +482,7 @@ def main():
                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                "data": "synthetic",
-               "config": {"workload": f"{args.workload}: N={n} per GPU, 70% in 2000 NFW haloes "
-                                      f"+ 30% uniform, eps=1/6400, r_s=1.25/256, cutoff 4.5 r_s, "
-                                      f"relative alpha=0.005 after BH theta=0.5",
+               "config": {"workload": f"{args.workload}: N={n} per GPU, " + describe(args.workload, prm),
                           "l2": "flushed between steps (256 MB write)"},
                "interactions_per_s": ws * inter_step / (ms_per_step * 1e-3),
                "interactions_per_step": inter_step,
@@ -368,7 +490,7 @@ def main():
                "build_ms_per_step": float(np.mean(ms_build)),
                "walk_interactions_per_s": inter_step / (walk_ms * 1e-3),
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-               "roofline": roof, "cpu_baseline": cpu, "batched": batched}
+               "roofline": roof, "cpu_baseline": cpu, "batched": batched, "served": served}
         print(json.dumps(out), flush=True)
     ctx.close()
     if ws > 1:

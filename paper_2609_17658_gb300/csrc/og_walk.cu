@@ -180,6 +180,87 @@ __device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, in
     }
 }
 
+// Far entries: every target of the group is at least h away (the entry lies
+// outside the group box by more than h, and by at least one grid unit), so
+// no softening applies and r^2 >= 1 needs no guard.  Two entries of this
+// lane's share, e and e + R, go through the arithmetic together as FP32
+// pairs (the f32x2 multiply and fused multiply-add of sm_100 and later:
+// each half is the same IEEE operation as the scalar one, so the cutoff
+// decision is unchanged); an odd last entry goes alone.
+template <bool kSplit>
+__device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int R, uint32_t xi,
+                                         uint32_t yi, uint32_t zi, const WalkParams &p,
+                                         float &ax, float &ay, float &az) {
+    const float rc2 = p.rc2;
+    const float2 c_inv2rs = make_float2(p.inv_2rs, p.inv_2rs);
+    const float2 c_kexp = make_float2(p.kexp, p.kexp);
+    const float2 c_p = make_float2(kAsP, kAsP), c_one = make_float2(1.0f, 1.0f);
+    const float2 c5 = make_float2(kAs5, kAs5), c4 = make_float2(kAs4, kAs4);
+    const float2 c3 = make_float2(kAs3, kAs3), c2 = make_float2(kAs2, kAs2);
+    const float2 c1 = make_float2(kAs1, kAs1);
+    const float2 c_tsp = make_float2(kTwoOverSqrtPi, kTwoOverSqrtPi);
+    float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx;
+    int e = rep;
+#pragma unroll 2
+    for (; e + R < cnt; e += 2 * R) {
+        const uint4 s0 = ch[e], s1 = ch[e + R];
+        const float2 fx = make_float2((float)(int)(s0.x - xi), (float)(int)(s1.x - xi));
+        const float2 fy = make_float2((float)(int)(s0.y - yi), (float)(int)(s1.y - yi));
+        const float2 fz = make_float2((float)(int)(s0.z - zi), (float)(int)(s1.z - zi));
+        const float2 r2 = __ffma2_rn(fx, fx, __ffma2_rn(fy, fy, __fmul2_rn(fz, fz)));
+        float2 m = make_float2(__uint_as_float(s0.w), __uint_as_float(s1.w));
+        if (kSplit) {
+            m.x = (r2.x < rc2) ? m.x : 0.0f;
+            m.y = (r2.y < rc2) ? m.y : 0.0f;
+        }
+        const float2 rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+        float2 mS = m;
+        if (kSplit) {
+            const float2 us = __fmul2_rn(__fmul2_rn(r2, rinv), c_inv2rs);
+            const float2 den = __ffma2_rn(c_p, us, c_one);
+            const float2 t = make_float2(rcp_ftz(den.x), rcp_ftz(den.y));
+            float2 q = __ffma2_rn(t, c5, c4);
+            q = __ffma2_rn(t, q, c3);
+            q = __ffma2_rn(t, q, c2);
+            q = __ffma2_rn(t, q, c1);
+            const float2 poly = __fmul2_rn(t, q);
+            const float2 arg = __fmul2_rn(r2, c_kexp);
+            const float2 ex = make_float2(ex2_ftz(arg.x), ex2_ftz(arg.y));
+            mS = __fmul2_rn(m, __fmul2_rn(ex, __ffma2_rn(c_tsp, us, poly)));
+        }
+        const float2 f = __fmul2_rn(mS, __fmul2_rn(rinv, __fmul2_rn(rinv, rinv)));
+        sx = __ffma2_rn(f, fx, sx);
+        sy = __ffma2_rn(f, fy, sy);
+        sz = __ffma2_rn(f, fz, sz);
+    }
+    float tx = __fadd_rn(sx.x, sx.y), ty = __fadd_rn(sy.x, sy.y), tz = __fadd_rn(sz.x, sz.y);
+    if (e < cnt) {
+        const uint4 s = ch[e];
+        const float fx = (float)(int)(s.x - xi);
+        const float fy = (float)(int)(s.y - yi);
+        const float fz = (float)(int)(s.z - zi);
+        const float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, __fmul_rn(fz, fz)));
+        float m = __uint_as_float(s.w);
+        if (kSplit) m = (r2 < rc2) ? m : 0.0f;
+        const float rinv = rsqrt_ftz(r2);
+        float mS = m;
+        if (kSplit) {
+            const float us = (r2 * rinv) * p.inv_2rs;
+            const float t = rcp_ftz(fmaf(kAsP, us, 1.0f));
+            const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, kAs5, kAs4), kAs3), kAs2), kAs1);
+            const float ex = ex2_ftz(r2 * p.kexp);
+            mS = m * (ex * fmaf(kTwoOverSqrtPi, us, poly));
+        }
+        const float f = mS * (rinv * (rinv * rinv));
+        tx = fmaf(f, fx, tx);
+        ty = fmaf(f, fy, ty);
+        tz = fmaf(f, fz, tz);
+    }
+    ax = tx;
+    ay = ty;
+    az = tz;
+}
+
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
     const float y = __fsub_rn(v, comp);
     const float t = __fadd_rn(sum, y);
@@ -437,7 +518,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             if (cf + nfar > kChunk) {
                 __syncwarp();
                 float tx = 0.f, ty = 0.f, tz = 0.f;
-                eval_chunk<kSplit, false>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz);
+                eval_far<kSplit>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz);
                 acc.add(tx, ty, tz);
                 cf = 0;
                 __syncwarp();
@@ -481,7 +562,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         __syncwarp();
         {
             float tx = 0.f, ty = 0.f, tz = 0.f;
-            eval_chunk<kSplit, false>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz);
+            eval_far<kSplit>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz);
             acc.add(tx, ty, tz);
             tx = ty = tz = 0.f;
             eval_chunk<kSplit, true>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz);
@@ -671,9 +752,11 @@ WalkParams make_walk_params(const og_params &p, int opening, double theta) {
     w.h = (float)hg;
     w.inv_h = hg > 0.0 ? (float)(1.0 / hg) : 0.0f;
     // an entry is "near" when its integer distance to the group box is below
-    // h (with a generous rounding margin); only near entries may need softening
+    // h (with a generous rounding margin); only near entries may need
+    // softening.  An entry inside the group box (a member itself) is always
+    // near, so a far entry is at r^2 >= 1 from every target.
     const double hn = hg * (1.0 + 1.0 / 256.0) + 2.0;
-    w.hnear2 = hg > 0.0 ? (unsigned long long)(hn * hn) : 0ull;
+    w.hnear2 = hg > 0.0 ? (unsigned long long)(hn * hn) : 1ull;
     w.out_scale = (float)(p.G * (two32 / p.box) * (two32 / p.box));
     return w;
 }
@@ -690,6 +773,30 @@ static og_status finish_pass(og_ctx *c, cudaEvent_t e0, cudaEvent_t e1, float *m
     if (err != cudaSuccess) return cuda_fail(err, "walk");
     if ((err = cudaGetLastError()) != cudaSuccess) return cuda_fail(err, "walk launch");
     if (ms_out) *ms_out = ms;
+    return OG_OK;
+}
+
+// Replace the debug list buffer by one of at least `need` entries and clear
+// the overflow bit the short buffer left in the status word.
+static og_status grow_lists(og_tree *t, int64_t need) {
+    cudaStream_t s = t->ctx->stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "list buffer");
+    cudaFree(t->lists);
+    t->lists = nullptr;
+    t->list_cap = 0;
+    const int64_t cap = need + need / 8 + 1024;
+    if ((e = cudaMalloc(&t->lists, (size_t)cap * 2 * sizeof(uint32_t))) != cudaSuccess) {
+        t->lists = nullptr;
+        return cuda_fail(e, "cudaMalloc (lists)");
+    }
+    t->list_cap = cap;
+    uint32_t st = 0;
+    if ((e = cudaMemcpy(&st, t->ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    st &= ~(uint32_t)ST_LIST_OVF;
+    if ((e = cudaMemcpy(t->ctx->d_status, &st, sizeof(st), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "status write");
     return OG_OK;
 }
 
@@ -721,16 +828,26 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
         cudaMemcpyAsync(t->gorder, alt ? v1 : v0, ng * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         a.tree0.gorder = t->gorder;
     }
-    cudaMemsetAsync(t->ctx->d_counters, 0, 3 * sizeof(unsigned long long), s);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-    launch(a, opening, wp.split, wp.dump, t->refit, false, t->ngroups, s);
-    cudaEventRecord(e1, s);
-    if (sort_tmp) cudaFreeAsync(sort_tmp, s);
     unsigned long long h[3] = {0, 0, 0};
-    st = finish_pass(t->ctx, e0, e1, ms_out, h);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        cudaMemsetAsync(t->ctx->d_counters, 0, 3 * sizeof(unsigned long long), s);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, s);
+        launch(a, opening, wp.split, wp.dump, t->refit, false, t->ngroups, s);
+        cudaEventRecord(e1, s);
+        st = finish_pass(t->ctx, e0, e1, ms_out, h);
+        if (st) break;
+        if (!wp.dump || h[2] <= (unsigned long long)t->list_cap) break;
+        // debug lists only: the pass counted every entry it could not keep;
+        // give the buffer that size and walk again (the pass is deterministic)
+        st = grow_lists(t, (int64_t)h[2]);
+        if (st) break;
+        a.lists = t->lists;
+        a.list_cap = t->list_cap;
+    }
+    if (sort_tmp) cudaFreeAsync(sort_tmp, s);
     if (st) return st;
     t->have_cost = true;
     t->interactions_last = (int64_t)h[1];

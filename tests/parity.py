@@ -88,9 +88,15 @@ def compare_build(gt: og.Tree, ot: oracle.Tree):
     return gmap
 
 
-def gpu_lists(gt: og.Tree, gmap):
-    """Dumped (group, child slot) pairs -> {group: sorted unified refs (oracle ids)}."""
-    pairs = gt.export(og.OG_F_LISTS).astype(np.int64)
+def gpu_lists(gt: og.Tree, gmap, groups=None):
+    """Dumped (group, child slot) pairs -> {group: sorted unified refs (oracle ids)},
+    for every group or only for ``groups``."""
+    pairs = gt.export(og.OG_F_LISTS)
+    if groups is not None:
+        want = np.zeros(gt.info()["groups"], dtype=bool)
+        want[np.asarray(groups, dtype=np.int64)] = True
+        pairs = pairs[want[pairs[:, 0]]]
+    pairs = pairs.astype(np.int64)
     child = gt.export(og.OG_F_CHILD).astype(np.int64)
     n = gt.n
     refs = map_unified(child[pairs[:, 1]], n, gmap)

@@ -190,11 +190,13 @@ def _sample_groups(ngroups, k, seed):
     return np.sort(r.choice(ngroups, size=min(k, ngroups), replace=False))
 
 
-def test_fullsize_clustered_2m_sampled(ctx):
-    """The benchmark workload at full size: tree bit-exact everywhere, lists and
-    accelerations of sampled groups against the oracle (relative criterion with
-    the library's own first-pass accelerations fed to both sides)."""
-    pos, mass, prm = gi.config("clustered-2m")
+@pytest.mark.parametrize("name,nsample", [("clustered-2m", 400), ("clustered-16m", 150)])
+def test_fullsize_clustered_sampled(ctx, name, nsample):
+    """The clustered workloads at full size (2,097,152 and 16,777,216
+    particles): tree bit-exact everywhere, lists and accelerations of sampled
+    groups against the oracle (relative criterion with the library's own
+    first-pass accelerations fed to both sides)."""
+    pos, mass, prm = gi.config(name)
     bh = dict(prm, opening=gi.OPEN_BH, theta=prm["theta_first_pass"])
     a1, _, _ = og.Tree(ctx, pos, mass, bh).force(counts=False)
     rel = dict(prm, opening=gi.OPEN_REL, flags=og.OG_DEBUG_DUMP_LISTS)
@@ -202,10 +204,10 @@ def test_fullsize_clustered_2m_sampled(ctx):
     ot = oracle.Tree(pos, mass, rel)
     gmap = parity.compare_build(gt, ot)
     acc, npp, npn = gt.force(a_old=a1)
-    sel = _sample_groups(ot.ngroups, 400, 5)
+    sel = _sample_groups(ot.ngroups, nsample, 5)
     ref, rpp, rpn = ot.force(a_old=a1, groups=sel, keep_lists=True)
     off, lst = ot.lists()
-    parity.compare_lists(parity.gpu_lists(gt, gmap), off, lst, sel)
+    parity.compare_lists(parity.gpu_lists(gt, gmap, sel), off, lst, sel)
     perm = ot.get(oracle.F_PERM)
     gb, ge = ot.get(oracle.F_GBEG), ot.get(oracle.F_GEND)
     tgt = np.concatenate([perm[gb[g]:ge[g]] for g in sel])
