@@ -77,7 +77,8 @@ typedef struct {
     double theta_first_pass; /* OG_OPEN_REL without a_old: BH angle of the first pass */
     int32_t opening;         /* og_open */
     int32_t leaf_max;        /* particles per leaf cell; 1 = one particle per leaf (Sect. 4.1) */
-    int32_t group_max;       /* targets per group, 1..32 (0 = 32) */
+    int32_t group_max;       /* targets per group, 1..32; 0 = measured per kind of input
+                                (og_tune_group_max) */
     int32_t flags;           /* OG_DEVICE_PTRS | OG_DEBUG_DUMP_LISTS */
 } og_params;
 
@@ -96,6 +97,9 @@ typedef struct {
     double  ms_build;        /* device time of the last build (ms) */
     double  ms_force;        /* device time of the last force call, all passes (ms) */
     double  ms_walk;         /* device time of the walk kernels of the last force call (ms) */
+    int32_t group_max;       /* the group size the tree was built with (the measured
+                                choice when og_params.group_max was 0) */
+    int32_t pad;
 } og_tree_info;
 
 /* ---- context ----------------------------------------------------------- */
@@ -249,6 +253,32 @@ size_t og_serve_request_bytes(int64_t n);
  * OG_PENDING if not done yet, a negative status if the request failed.
  * Thread safe. */
 og_status og_serve_poll(og_ctx *ctx, uint64_t ticket, og_result *out, int timeout_ms);
+
+/* ---- group size: measured choice ---------------------------------------- */
+
+/* The group size G (targets sharing one interaction list, Sect. 3.4 and
+ * 19.2: one walk per group of nearby particles) trades list building against
+ * evaluation; the paper fixes no value.  og_tune_group_max returns the G in
+ * {8, 16, 24, 32} with the shortest walk for inputs of this kind: the key is
+ * (floor(log2 n), opening criterion, split on/off).  The first call for a key
+ * builds and walks this input once per candidate (both force passes for
+ * OG_OPEN_REL), times the walk kernels with CUDA events on the context's
+ * stream, and keeps the result in the context; later calls return it at once.
+ * og_tree_build with params.group_max = 0 calls it.  pos/mass as in
+ * og_tree_build (host or, with OG_DEVICE_PTRS, device); p->group_max is
+ * ignored.  Errors as og_tree_build. */
+og_status og_tune_group_max(og_ctx *ctx, const double *pos, const double *mass, int64_t n,
+                            const og_params *p, int32_t *group_max);
+
+/* Write the context's measured group sizes to `path`, one JSON object per
+ * line: {"n_log2": .., "opening": .., "split": .., "group_max": ..,
+ * "walk_ms": [t8, t16, t24, t32]}.  OG_ERR_ARG if the file cannot be written. */
+og_status og_tune_save(og_ctx *ctx, const char *path);
+
+/* Add the records of a file written by og_tune_save to the context (a record
+ * replaces one with the same key).  OG_ERR_ARG, and nothing added, if a line
+ * is not such a record or the file cannot be read. */
+og_status og_tune_load(og_ctx *ctx, const char *path);
 
 /* ---- sort without device allocation ------------------------------------ */
 

@@ -663,7 +663,7 @@ __global__ void k_records(int64_t n, int64_t nchild, const uint32_t *__restrict_
                           const double *__restrict__ pm64, const uint8_t *__restrict__ nlev,
                           const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ nccnt,
                           const double *__restrict__ nM, const uint32_t *__restrict__ ncom,
-                          CRec *crec) {
+                          CRec *crec, uint32_t *status) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nchild) return;
     uint32_t item = child[c];
@@ -685,6 +685,11 @@ __global__ void k_records(int64_t n, int64_t nchild, const uint32_t *__restrict_
         r.m = __double2float_rn(r.M);
         r.info = (1u << 31) | ((uint32_t)nlev[j] << 26) | (nccnt[j] & 0x3ffffffu);
         r.ref = ncbeg[j];
+        // the walk pushes (ref, count) unchecked: a node has children, inside
+        // the child array, and is never a root
+        if (nccnt[j] == 0u || nccnt[j] > 0x3ffffffu || nlev[j] == 0u || nlev[j] > kLevels ||
+            (uint64_t)ncbeg[j] + nccnt[j] > (uint64_t)nchild)
+            atomicOr(status, ST_INTERNAL);
     }
     crec[c] = r;
 }
@@ -805,7 +810,7 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
                                                 t->pz, t->sseg, t->gbox, t->gseg); note_launch();
     k_records<<<nblk(t->nchild), kT, 0, s>>>(n, t->nchild, t->child, t->px, t->py, t->pz, t->pm32,
                                              t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nM, t->ncom,
-                                             t->crec); note_launch();
+                                             t->crec, t->ctx->d_status); note_launch();
     k_ext_records<<<nblk(t->nchild), kT, 0, s>>>(n, t->nchild, t->child, t->next_s, t->next_l,
                                                  t->cext); note_launch();
     cudaEventRecord(e1, s);
@@ -1036,7 +1041,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
                                                 t->pz, t->sseg, t->gbox, t->gseg); note_launch();
     k_records<<<nblk(nchild), kT, 0, s>>>(n, nchild, t->child, t->px, t->py, t->pz, t->pm32,
                                           t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nM, t->ncom,
-                                          t->crec); note_launch();
+                                          t->crec, t->ctx->d_status); note_launch();
     cudaEventRecord(e1, s);
     cudaFreeAsync(scratch, s);
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "build");

@@ -63,6 +63,8 @@ __global__ void k_unpermute(int64_t n, const uint32_t *__restrict__ perm,
     if (npn) npn[j] = npn_s[i];
 }
 
+}  // namespace
+
 og_status check_status(og_ctx *c) {
     uint32_t st = 0;
     cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
@@ -106,7 +108,6 @@ og_status validate(const og_params *p, int64_t n) {
     return OG_OK;
 }
 
-}  // namespace
 }  // namespace og
 
 using namespace og;
@@ -173,6 +174,7 @@ og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
 og_status og_destroy(og_ctx *c) {
     if (!c) return OG_OK;
     serve_shutdown(c);
+    og::tune_free(c);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     cudaFree(c->d_status);
@@ -199,10 +201,8 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
     if (!t) { set_error("host allocation failed"); return OG_ERR_OOM; }
     t->ctx = c;
     t->prm = *p;
-    if (t->prm.group_max == 0) t->prm.group_max = 32;
     t->n = n;
     t->nseg = 1;
-    t->seg_prm.assign(1, t->prm);
     t->h_seg_off = {0u, (uint32_t)n};
     cudaStream_t s = c->stream;
     const double *d_pos = pos, *d_mass = mass;
@@ -220,6 +220,18 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
         d_pos = dp;
         d_mass = dp + 3 * n;
     }
+    if (t->prm.group_max == 0) {
+        // measured choice of the group size for this kind of input (og_tune.cu)
+        int G = 32;
+        st = tuned_group_max(c, d_pos, d_mass, n, t->prm, &G);
+        if (st) {
+            if (staging) cudaFreeAsync(staging, s);
+            delete t;
+            return st;
+        }
+        t->prm.group_max = G;
+    }
+    t->seg_prm.assign(1, t->prm);
     st = build_tree(t, d_pos, d_mass);
     if (staging) cudaFreeAsync(staging, s);
     if (st == OG_OK) st = check_status(c);
@@ -449,6 +461,8 @@ og_status og_tree_info_get(const og_tree *t, og_tree_info *info) {
     info->ms_build = t->ms_build;
     info->ms_force = t->ms_force;
     info->ms_walk = t->ms_walk;
+    info->group_max = t->prm.group_max;
+    info->pad = 0;
     return OG_OK;
 }
 

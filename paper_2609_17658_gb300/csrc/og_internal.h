@@ -66,6 +66,7 @@ struct og_ctx {
     uint32_t *d_status = nullptr;     // device status word
     unsigned long long *d_counters = nullptr;  // scratch counters (work queues, totals)
     void *serve = nullptr;            // serving state (og_serve.cu)
+    void *tune = nullptr;             // measured group sizes (og_tune.cu)
 };
 
 struct og_tree {
@@ -134,6 +135,15 @@ namespace og {
 void set_error(const char *fmt, ...);
 // stop the serving engine of a context (og_serve.cu)
 void serve_shutdown(og_ctx *c);
+// argument checks and the device status word (og_capi.cu)
+og_status validate(const og_params *p, int64_t n);
+og_status check_status(og_ctx *c);
+// both force passes on a built tree, results in sorted order (og_capi.cu)
+og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out);
+// group size for group_max = 0: measured once per kind of input (og_tune.cu)
+og_status tuned_group_max(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
+                          const og_params &p, int *group_max);
+void tune_free(og_ctx *c);
 // count of kernels launched by this library in this process
 void note_launch();
 og_status cuda_fail(cudaError_t e, const char *what);

@@ -56,7 +56,8 @@ class og_tree_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nodes", C.c_int64), ("children", C.c_int64),
                 ("groups", C.c_int64), ("list_entries", C.c_int64),
                 ("interactions", C.c_int64), ("interactions_last_pass", C.c_int64),
-                ("ms_build", C.c_double), ("ms_force", C.c_double), ("ms_walk", C.c_double)]
+                ("ms_build", C.c_double), ("ms_force", C.c_double), ("ms_walk", C.c_double),
+                ("group_max", C.c_int32), ("pad", C.c_int32)]
 
 
 class og_box(C.Structure):
@@ -121,6 +122,11 @@ def lib():
         L.og_serve_request_bytes.argtypes = [i64]
         L.og_serve_request_bytes.restype = C.c_size_t
         L.og_sort_keys_noalloc.restype = C.c_int
+        L.og_tune_group_max.argtypes = [P, P, P, i64, C.POINTER(og_params), C.POINTER(C.c_int32)]
+        L.og_tune_save.argtypes = [P, C.c_char_p]
+        L.og_tune_load.argtypes = [P, C.c_char_p]
+        for name in ("og_tune_group_max", "og_tune_save", "og_tune_load"):
+            getattr(L, name).restype = C.c_int
         for name in ("og_create", "og_destroy", "og_set_stream", "og_params_default",
                      "og_tree_build", "og_tree_refit", "og_tree_force", "og_tree_info_get",
                      "og_tree_export", "og_tree_free"):
@@ -191,23 +197,43 @@ def og_set_stream(ctx, stream_handle: int | None) -> None:
     _check(lib().og_set_stream(ctx, C.c_void_p(stream_handle) if stream_handle else None))
 
 
-def og_tree_build(ctx, pos, mass, params: dict) -> C.c_void_p:
-    """pos: float64 [N,3], mass: float64 [N] (numpy host or torch CUDA)."""
+def _inputs(pos, mass, params: dict):
     dev = _is_torch_cuda(pos)
     if dev:
         pp, mp = _dev_ptr(pos, "float64"), _dev_ptr(mass, "float64")
-        n = int(pos.shape[0])
     else:
         pp, mp = _host_ptr(pos, np.float64, (3,)), _host_ptr(mass, np.float64)
-        n = int(pos.shape[0])
+    n = int(pos.shape[0])
     if int(mass.shape[0]) != n:
         raise ValueError("mass and pos lengths differ")
     prm = params_from_dict(params, OG_DEVICE_PTRS if dev else 0)
     if not dev:
         prm.flags = int(prm.flags) & ~OG_DEVICE_PTRS
+    return pp, mp, n, prm
+
+
+def og_tree_build(ctx, pos, mass, params: dict) -> C.c_void_p:
+    """pos: float64 [N,3], mass: float64 [N] (numpy host or torch CUDA)."""
+    pp, mp, n, prm = _inputs(pos, mass, params)
     h = C.c_void_p()
     _check(lib().og_tree_build(ctx, pp, mp, n, C.byref(prm), C.byref(h)))
     return h
+
+
+def og_tune_group_max(ctx, pos, mass, params: dict) -> int:
+    """The measured group size for inputs of this kind (see include/og.h)."""
+    pp, mp, n, prm = _inputs(pos, mass, params)
+    g = C.c_int32()
+    _check(lib().og_tune_group_max(ctx, pp, mp, n, C.byref(prm), C.byref(g)))
+    return int(g.value)
+
+
+def og_tune_save(ctx, path: str) -> None:
+    _check(lib().og_tune_save(ctx, os.fsencode(path)))
+
+
+def og_tune_load(ctx, path: str) -> None:
+    _check(lib().og_tune_load(ctx, os.fsencode(path)))
 
 
 def og_tree_force(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
