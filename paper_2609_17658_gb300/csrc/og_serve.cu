@@ -34,6 +34,10 @@ constexpr int kT = 256;
 inline unsigned nblk(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
 constexpr int kMaxActive = 256;
 constexpr int kMaxRefits = 4;
+// systems are built on this many private streams at once: a small build is
+// bound by launch and synchronisation latency, so builds of several systems
+// overlap on the device
+constexpr int kBuildWorkers = 4;
 
 double now_s() {
     using namespace std::chrono;
@@ -106,9 +110,16 @@ struct System {
     og_result res{};
 };
 
+// a build stream: its own context (stream, status word, counters)
+struct Worker {
+    og_ctx *ctx = nullptr;
+    unsigned long long *d_side = nullptr;
+};
+
 struct Server {
     og_ctx *owner = nullptr;
     og_ctx *ctx = nullptr;  // private context of the engine
+    std::vector<Worker> workers;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<System *> pending;
@@ -138,15 +149,18 @@ og_status free_system(Server *S, System *sy) {
     return OG_OK;
 }
 
-og_status build_system(Server *S, System *sy) {
-    cudaStream_t s = S->ctx->stream;
+// Build (or rebuild) a system's tree on a worker's stream.  Returns once the
+// tree is complete on the device; the tree then belongs to the engine's
+// context (refits, walks and frees are ordered on the engine's stream).
+og_status build_system(Server *S, System *sy, const Worker &w) {
+    cudaStream_t s = w.ctx->stream;
     if (sy->tree) {
         og_tree_free(sy->tree);
         sy->tree = nullptr;
     }
     og_tree *t = new (std::nothrow) og_tree();
     if (!t) { set_error("host allocation failed"); return OG_ERR_OOM; }
-    t->ctx = S->ctx;
+    t->ctx = w.ctx;
     t->prm = sy->prm;
     if (t->prm.group_max == 0) t->prm.group_max = 32;
     t->n = sy->n;
@@ -162,20 +176,23 @@ og_status build_system(Server *S, System *sy) {
     sy->refits_since_build = 0;
     cudaMemcpyAsync(sy->d_xbuild, sy->d_pos, (size_t)sy->n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
     // rebuild threshold: a quarter of the mean group box side
-    cudaMemsetAsync(S->d_side, 0, sizeof(unsigned long long), s);
-    k_group_side_sum<<<nblk(t->ngroups), kT, 0, s>>>(t->ngroups, t->gbox, S->d_side); note_launch();
+    cudaMemsetAsync(w.d_side, 0, sizeof(unsigned long long), s);
+    k_group_side_sum<<<nblk(t->ngroups), kT, 0, s>>>(t->ngroups, t->gbox, w.d_side); note_launch();
     unsigned long long side = 0;
-    cudaMemcpyAsync(&side, S->d_side, sizeof(side), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&side, w.d_side, sizeof(side), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
+    t->ctx = S->ctx;
     if (e != cudaSuccess) return cuda_fail(e, "serve build");
+    st = check_status(w.ctx);
+    if (st) return st;
     const double mean_side = t->ngroups ? (double)side / (double)t->ngroups : 0.0;
     sy->rebuild_thr = 0.25 * mean_side * (sy->prm.box / 4294967296.0);
     sy->res.rebuilds++;
     return OG_OK;
 }
 
-og_status admit_system(Server *S, System *sy) {
-    cudaStream_t s = S->ctx->stream;
+og_status admit_system(Server *S, System *sy, const Worker &w) {
+    cudaStream_t s = w.ctx->stream;
     const int64_t n = sy->n;
     size_t bytes = (size_t)n * (3 * 8 * 3 + 8 + 3 * 4) + 4096;
     cudaError_t e;
@@ -189,9 +206,37 @@ og_status admit_system(Server *S, System *sy) {
     cudaMemcpyAsync(sy->d_pos, sy->h_pos.data(), (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(sy->d_vel, sy->h_vel.data(), (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(sy->d_mass, sy->h_mass.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s);
-    og_status st = build_system(S, sy);
-    if (st) return st;
-    return OG_OK;
+    return build_system(S, sy, w);
+}
+
+// fn(system, worker) for every system; the systems, largest first, are dealt
+// round-robin to the build workers, one host thread per worker
+template <class F>
+std::vector<og_status> on_workers(Server *S, std::vector<System *> v, F fn, std::vector<System *> *order) {
+    std::stable_sort(v.begin(), v.end(), [](const System *a, const System *b) { return a->n > b->n; });
+    *order = v;
+    std::vector<og_status> st(v.size(), OG_OK);
+    const int W = (int)std::min(S->workers.size(), v.size());
+    // a worker's stream is drained after every system, whatever the outcome, so
+    // nothing of a failed build is still in flight when its memory is freed
+    if (W <= 1) {
+        for (size_t k = 0; k < v.size(); ++k) {
+            st[k] = fn(v[k], S->workers[0]);
+            cudaStreamSynchronize(S->workers[0].ctx->stream);
+        }
+        return st;
+    }
+    std::vector<std::thread> th;
+    for (int w = 0; w < W; ++w)
+        th.emplace_back([&, w] {
+            cudaSetDevice(S->ctx->device);
+            for (size_t k = (size_t)w; k < v.size(); k += (size_t)W) {
+                st[k] = fn(v[k], S->workers[w]);
+                cudaStreamSynchronize(S->workers[w].ctx->stream);
+            }
+        });
+    for (auto &x : th) x.join();
+    return st;
 }
 
 void finish(Server *S, System *sy, og_status st) {
@@ -248,7 +293,7 @@ void engine_step(Server *S) {
     std::vector<unsigned int> drift(act.size(), 0u);
     cudaMemcpyAsync(drift.data(), S->d_drift, act.size() * sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    std::vector<System *> keep;
+    std::vector<System *> keep, rebuild;
     for (size_t k = 0; k < act.size(); ++k) {
         System *sy = act[k];
         sy->step++;
@@ -268,14 +313,13 @@ void engine_step(Server *S) {
             delete sy;
             continue;
         }
-        og_status st2;
         if ((double)dmax > sy->rebuild_thr || sy->refits_since_build >= kMaxRefits) {
-            st2 = build_system(S, sy);
-        } else {
-            st2 = refit_tree(sy->tree, sy->d_pos);
-            sy->refits_since_build++;
-            sy->res.refits++;
+            rebuild.push_back(sy);
+            continue;
         }
+        og_status st2 = refit_tree(sy->tree, sy->d_pos);
+        sy->refits_since_build++;
+        sy->res.refits++;
         if (st2 != OG_OK) {
             free_system(S, sy);
             finish(S, sy, st2);
@@ -283,6 +327,20 @@ void engine_step(Server *S) {
             continue;
         }
         keep.push_back(sy);
+    }
+    if (!rebuild.empty()) {
+        std::vector<System *> order;
+        std::vector<og_status> st2 = on_workers(
+            S, rebuild, [S](System *sy, const Worker &w) { return build_system(S, sy, w); }, &order);
+        for (size_t k = 0; k < order.size(); ++k) {
+            if (st2[k] != OG_OK) {
+                free_system(S, order[k]);
+                finish(S, order[k], st2[k]);
+                delete order[k];
+            } else {
+                keep.push_back(order[k]);
+            }
+        }
     }
     act.swap(keep);
     S->interactions += inter;
@@ -308,16 +366,21 @@ void engine_main(Server *S) {
                 admit.push_back(sy);
             }
         }
-        for (System *sy : admit) {
-            sy->res.t_start = now_s();
-            og_status st = admit_system(S, sy);
-            if (st != OG_OK) {
-                free_system(S, sy);
-                finish(S, sy, st);
-                delete sy;
-                continue;
+        if (!admit.empty()) {
+            const double t0 = now_s();
+            for (System *sy : admit) sy->res.t_start = t0;
+            std::vector<System *> order;
+            std::vector<og_status> st = on_workers(
+                S, admit, [S](System *sy, const Worker &w) { return admit_system(S, sy, w); }, &order);
+            for (size_t k = 0; k < order.size(); ++k) {
+                if (st[k] != OG_OK) {
+                    free_system(S, order[k]);
+                    finish(S, order[k], st[k]);
+                    delete order[k];
+                } else {
+                    S->active.push_back(order[k]);
+                }
             }
-            S->active.push_back(sy);
         }
         if (S->active.empty()) continue;
         engine_step(S);
@@ -351,6 +414,23 @@ og_status ensure_server(og_ctx *c, Server **out) {
         return cuda_fail(e, "serve setup");
     }
     S->d_side = reinterpret_cast<unsigned long long *>(S->d_drift + kMaxActive);
+    for (int w = 0; w < kBuildWorkers; ++w) {
+        Worker W;
+        st = og_create(&W.ctx, c->device, 0);
+        if (st == OG_OK && (e = cudaMalloc(&W.d_side, 64)) != cudaSuccess) st = cuda_fail(e, "serve setup");
+        if (st != OG_OK) {
+            if (W.ctx) og_destroy(W.ctx);
+            for (Worker &x : S->workers) {
+                cudaFree(x.d_side);
+                og_destroy(x.ctx);
+            }
+            cudaFree(S->d_drift);
+            og_destroy(S->ctx);
+            delete S;
+            return st;
+        }
+        S->workers.push_back(W);
+    }
     S->budget = c->hbm_budget;
     S->engine = std::thread(engine_main, S);
     c->serve = S;
@@ -376,6 +456,10 @@ void serve_shutdown(og_ctx *c) {
     if (S->engine.joinable()) S->engine.join();
     cudaSetDevice(S->ctx->device);
     cudaFree(S->d_drift);
+    for (Worker &w : S->workers) {
+        cudaFree(w.d_side);
+        og_destroy(w.ctx);
+    }
     og_destroy(S->ctx);
     delete S;
     c->serve = nullptr;
