@@ -89,6 +89,28 @@ def parse():
     return ap.parse_args()
 
 
+def seed_for_rank(rank: int) -> int:
+    """Each rank times its own independent system (weak scaling, no data-path
+    collective); rank 0 runs the single-GPU workload itself."""
+    return 12346 + 1000 * rank
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The slowest rank's value (the job's time), via one all-reduce."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_per_rank: int, ws: int, ms_per_step: float) -> float:
+    """Whole-job particles/s: every rank's particles over the slowest rank's step."""
+    return ws * n_per_rank / (ms_per_step * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,7 +349,8 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": len(mass) / v * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": f"{args.workload}: N={len(mass)}", "l2": "n/a (CPU)"},
+           "config": {"workload": f"{args.workload}: N={len(mass)} per GPU, " + describe(args.workload, prm),
+                      "l2": "n/a (CPU)"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                             "sample": cb["sample"]},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -367,7 +390,7 @@ def main():
         dist.barrier()
     from paper_2609_17658_gb300 import og
 
-    pos, mass, prm = gi.config(args.workload, seed=12346 + 1000 * rank)
+    pos, mass, prm = gi.config(args.workload, seed=seed_for_rank(rank))
     n = len(mass)
     dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream(dev)
@@ -414,14 +437,11 @@ def main():
     launches = og.og_kernel_launches() - launches0
     clocks = sampler.stop()
     torch.cuda.synchronize()
-    total_ms = float(sum(ms_steps))
+    total_ms = max_over_ranks(float(sum(ms_steps)), ws, dev)
     if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = ws * n / (ms_per_step * 1e-3)
+    value = job_value(n, ws, ms_per_step)
     inter_step = float(np.mean(inter))
     walk_ms = float(np.mean(ms_walk))
 
