@@ -205,6 +205,20 @@ og_status og_tree_export(const og_tree *t, int field, void *host_dst, size_t byt
 
 og_status og_tree_free(og_tree *t);
 
+/* Forces on the active particles only: the individual time steps of Sect.
+ * 3.2 need new accelerations only for the particles whose time bin is
+ * active.  active: uint8_t[n] in the caller's order, nonzero = active (host,
+ * or device with OG_DEVICE_PTRS).  Every group holding at least one active
+ * particle is walked exactly as og_tree_force walks it (the same list for all
+ * its members, the same arithmetic), so an active particle's acceleration and
+ * counts equal those of og_tree_force on the same tree; the entries of acc,
+ * n_pp, n_pn of inactive particles are left as they were.  OG_OPEN_REL:
+ * a_old as in og_tree_force, else a Barnes-Hut first pass over the same
+ * groups.  *groups_walked (may be NULL) receives the number of groups walked;
+ * with no active particle nothing is walked and the outputs are untouched. */
+og_status og_tree_force_active(og_tree *t, const uint8_t *active, const float *a_old, float *acc,
+                               uint32_t *n_pp, uint32_t *n_pn, int64_t *groups_walked);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *og_last_error(void);
 

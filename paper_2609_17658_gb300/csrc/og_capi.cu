@@ -63,6 +63,43 @@ __global__ void k_unpermute(int64_t n, const uint32_t *__restrict__ perm,
     if (npn) npn[j] = npn_s[i];
 }
 
+// 1 for a group holding at least one active particle (active: caller order)
+__global__ void k_group_active(int64_t ng, const uint32_t *__restrict__ gbeg,
+                               const uint32_t *__restrict__ gend, const uint32_t *__restrict__ perm,
+                               const uint8_t *__restrict__ active, int64_t n, uint32_t *flag) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    uint32_t f = 0;
+    const uint32_t e = gend[g] < (uint64_t)n ? gend[g] : (uint32_t)n;
+    for (uint32_t i = gbeg[g]; i < e && !f; ++i) f = active[perm[i]] != 0;
+    flag[g] = f;
+}
+
+// the flagged groups' ids, in key order, at their exclusive-scan positions
+__global__ void k_group_compact(int64_t ng, const uint32_t *__restrict__ flag,
+                                const uint32_t *__restrict__ pos, uint32_t *out) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng && flag[g]) out[pos[g]] = (uint32_t)g;
+}
+
+// k_unpermute for the active particles only
+__global__ void k_unpermute_active(int64_t n, const uint32_t *__restrict__ perm,
+                                   const uint8_t *__restrict__ active,
+                                   const float *__restrict__ acc_sorted,
+                                   const uint32_t *__restrict__ npp_s,
+                                   const uint32_t *__restrict__ npn_s, float *acc, uint32_t *npp,
+                                   uint32_t *npn) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = perm[i];
+    if (!active[j]) return;
+    acc[3ull * j + 0] = acc_sorted[i];
+    acc[3ull * j + 1] = acc_sorted[n + i];
+    acc[3ull * j + 2] = acc_sorted[2 * n + i];
+    if (npp) npp[j] = npp_s[i];
+    if (npn) npn[j] = npn_s[i];
+}
+
 }  // namespace
 
 og_status check_status(og_ctx *c) {
@@ -250,7 +287,8 @@ namespace og {
 // Both passes of the force on a built tree (sorted order, device results in
 // t->a_sorted, t->npp_sorted, t->npn_sorted).  d_aold: previous accelerations
 // in input order on the device, or null.
-og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out) {
+og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out, const uint32_t *subset,
+                       int64_t nsubset) {
     cudaStream_t s = t->ctx->stream;
     const int64_t n = t->n;
     cudaError_t e;
@@ -272,13 +310,15 @@ og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out) {
             k_gather_aold<<<nblk(n), kT, 0, s>>>(n, t->perm, d_aold, t->a_old_sorted); note_launch();
         } else {
             // first pass: Barnes-Hut with theta_first_pass
-            og_status st = walk_pass(t, OG_OPEN_BH, true, nullptr, t->a_old_sorted, &ms, false);
+            og_status st = walk_pass(t, OG_OPEN_BH, true, nullptr, t->a_old_sorted, &ms, false,
+                                     subset, nsubset);
             if (st) return st;
             ms_walk += ms;
         }
         a_old_sorted = t->a_old_sorted;
     }
-    og_status st = walk_pass(t, t->prm.opening, false, a_old_sorted, t->a_sorted, &ms, true);
+    og_status st = walk_pass(t, t->prm.opening, false, a_old_sorted, t->a_sorted, &ms, true,
+                             subset, nsubset);
     if (st) return st;
     ms_walk += ms;
     if (ms_walk_out) *ms_walk_out = ms_walk;
@@ -343,6 +383,100 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
     cudaEventDestroy(e1);
     t->ms_force = ms;
     t->ms_walk = ms_walk;
+    return check_status(c);
+}
+
+og_status og_tree_force_active(og_tree *t, const uint8_t *active, const float *a_old, float *acc,
+                               uint32_t *n_pp, uint32_t *n_pn, int64_t *groups_walked) {
+    if (!t || !active || !acc) { set_error("NULL argument"); return OG_ERR_ARG; }
+    og_ctx *c = t->ctx;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int64_t n = t->n, ng = t->ngroups;
+    const bool dev = (t->prm.flags & OG_DEVICE_PTRS) != 0;
+    cudaError_t e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    // scratch: active mask (host input), group flags, scan positions, group list,
+    // count, scan scratch, and for host outputs a staging copy of the outputs
+    const size_t al = 256;
+    auto up = [&](size_t b) { return (b + al - 1) & ~(al - 1); };
+    const size_t b_mask = dev ? 0 : up((size_t)n);
+    const size_t b_g = up((size_t)ng * sizeof(uint32_t));
+    const size_t b_scan = up(scan_scratch_bytes(ng));
+    const size_t b_out = dev ? 0 : up((size_t)n * 3 * sizeof(float)) + 2 * up((size_t)n * sizeof(uint32_t));
+    const size_t b_aold = (!dev && a_old && t->prm.opening == OG_OPEN_REL) ? up((size_t)n * 3 * sizeof(float)) : 0;
+    void *tmp = nullptr;
+    if ((e = cudaMallocAsync(&tmp, b_mask + 3 * b_g + al + b_scan + b_out + b_aold, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync (active set)");
+    char *q = static_cast<char *>(tmp);
+    const uint8_t *d_active = active;
+    if (!dev) {
+        cudaMemcpyAsync(q, active, (size_t)n, cudaMemcpyHostToDevice, s);
+        d_active = reinterpret_cast<const uint8_t *>(q);
+        q += b_mask;
+    }
+    uint32_t *flag = reinterpret_cast<uint32_t *>(q); q += b_g;
+    uint32_t *pos = reinterpret_cast<uint32_t *>(q); q += b_g;
+    uint32_t *list = reinterpret_cast<uint32_t *>(q); q += b_g;
+    uint32_t *d_total = reinterpret_cast<uint32_t *>(q); q += al;
+    void *scan_scr = q; q += b_scan;
+    float *d_acc = acc;
+    uint32_t *d_npp = n_pp, *d_npn = n_pn;
+    if (!dev) {
+        d_acc = reinterpret_cast<float *>(q); q += up((size_t)n * 3 * sizeof(float));
+        d_npp = n_pp ? reinterpret_cast<uint32_t *>(q) : nullptr; q += up((size_t)n * sizeof(uint32_t));
+        d_npn = n_pn ? reinterpret_cast<uint32_t *>(q) : nullptr; q += up((size_t)n * sizeof(uint32_t));
+    }
+    const float *d_aold = nullptr;
+    if (t->prm.opening == OG_OPEN_REL && a_old) {
+        d_aold = a_old;
+        if (!dev) {
+            cudaMemcpyAsync(q, a_old, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+            d_aold = reinterpret_cast<const float *>(q);
+        }
+    }
+    k_group_active<<<nblk(ng), kT, 0, s>>>(ng, t->gbeg, t->gend, t->perm, d_active, n, flag); note_launch();
+    scan_exclusive_u32(flag, pos, ng, d_total, scan_scr, s);
+    k_group_compact<<<nblk(ng), kT, 0, s>>>(ng, flag, pos, list); note_launch();
+    uint32_t nact = 0;
+    cudaMemcpyAsync(&nact, d_total, sizeof(nact), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        cudaFreeAsync(tmp, s);
+        return cuda_fail(e, "active set");
+    }
+    float ms_walk = 0;
+    og_status st = OG_OK;
+    t->interactions = 0;
+    if (nact > 0) st = force_sorted(t, d_aold, &ms_walk, list, (int64_t)nact);
+    if (st == OG_OK && nact > 0) {
+        if (!dev) {
+            // the inactive entries of the caller's outputs stay as they are
+            cudaMemcpyAsync(d_acc, acc, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+            if (n_pp) cudaMemcpyAsync(d_npp, n_pp, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+            if (n_pn) cudaMemcpyAsync(d_npn, n_pn, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+        }
+        k_unpermute_active<<<nblk(n), kT, 0, s>>>(n, t->perm, d_active, t->a_sorted, t->npp_sorted,
+                                                  t->npn_sorted, d_acc, d_npp, d_npn); note_launch();
+        if (!dev) {
+            cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
+            if (n_pp) cudaMemcpyAsync(n_pp, d_npp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+            if (n_pn) cudaMemcpyAsync(n_pn, d_npn, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        }
+    }
+    cudaFreeAsync(tmp, s);
+    if (st) return st;
+    cudaEventRecord(e1, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "active force");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t->ms_force = ms;
+    t->ms_walk = ms_walk;
+    if (groups_walked) *groups_walked = (int64_t)nact;
     return check_status(c);
 }
 

@@ -138,8 +138,10 @@ void serve_shutdown(og_ctx *c);
 // argument checks and the device status word (og_capi.cu)
 og_status validate(const og_params *p, int64_t n);
 og_status check_status(og_ctx *c);
-// both force passes on a built tree, results in sorted order (og_capi.cu)
-og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out);
+// both force passes on a built tree, results in sorted order (og_capi.cu);
+// subset: only these groups (device array of nsubset group ids)
+og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out,
+                       const uint32_t *subset = nullptr, int64_t nsubset = 0);
 // group size for group_max = 0: measured once per kind of input (og_tune.cu)
 og_status tuned_group_max(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
                           const og_params &p, int *group_max);
@@ -195,9 +197,11 @@ struct WalkParams {
 // One walk launch over all groups of all boxes.  first_pass: the Barnes-Hut
 // pass that supplies a_old for the relative criterion (each box's
 // theta_first_pass).  use_order: take the groups longest list first, by the
-// list lengths of the previous pass on this tree (if any).
+// list lengths of the previous pass on this tree (if any).  subset: walk only
+// these nsubset groups, in this order (device array), instead of all groups.
 og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
-                    float *acc_sorted, float *ms_out, bool use_order);
+                    float *acc_sorted, float *ms_out, bool use_order,
+                    const uint32_t *subset = nullptr, int64_t nsubset = 0);
 // One walk launch over the groups of several trees (the serving loop), in
 // decreasing order of their previous list lengths.  Every tree's per-box
 // parameters must agree on split on/off.

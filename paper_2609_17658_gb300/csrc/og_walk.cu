@@ -801,7 +801,8 @@ static og_status grow_lists(og_tree *t, int64_t need) {
 }
 
 og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
-                    float *acc_sorted, float *ms_out, bool use_order) {
+                    float *acc_sorted, float *ms_out, bool use_order, const uint32_t *subset,
+                    int64_t nsubset) {
     cudaStream_t s = t->ctx->stream;
     WalkArgs a{};
     WalkParams wp;
@@ -810,7 +811,11 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
     fill_common(a, t->ctx, t);
     cudaError_t err;
     void *sort_tmp = nullptr;
-    if (use_order && t->have_cost && t->ngroups > 1) {
+    if (subset) {
+        // only these groups, in this order (the walk takes them from gorder)
+        a.tree0.gorder = subset;
+        a.tree0.ngroups = nsubset;
+    } else if (use_order && t->have_cost && t->ngroups > 1) {
         // longest list first, from the costs of the previous pass on this tree
         const int64_t ng = t->ngroups;
         size_t bytes = (size_t)ng * 24 + radix_sort_scratch_bytes(ng) + 1024;
@@ -835,7 +840,7 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, s);
-        launch(a, opening, wp.split, wp.dump, t->refit, false, t->ngroups, s);
+        launch(a, opening, wp.split, wp.dump, t->refit, false, a.tree0.ngroups, s);
         cudaEventRecord(e1, s);
         st = finish_pass(t->ctx, e0, e1, ms_out, h);
         if (st) break;

@@ -122,6 +122,8 @@ def lib():
         L.og_serve_request_bytes.argtypes = [i64]
         L.og_serve_request_bytes.restype = C.c_size_t
         L.og_sort_keys_noalloc.restype = C.c_int
+        L.og_tree_force_active.argtypes = [P, P, P, P, P, P, C.POINTER(C.c_int64)]
+        L.og_tree_force_active.restype = C.c_int
         L.og_tune_group_max.argtypes = [P, P, P, i64, C.POINTER(og_params), C.POINTER(C.c_int32)]
         L.og_tune_save.argtypes = [P, C.c_char_p]
         L.og_tune_load.argtypes = [P, C.c_char_p]
@@ -249,6 +251,27 @@ def og_tree_force(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
         pp = None if n_pp is None else _host_ptr(n_pp, np.uint32)
         np_ = None if n_pn is None else _host_ptr(n_pn, np.uint32)
     _check(lib().og_tree_force(tree, op, ap, pp, np_))
+
+
+def og_tree_force_active(tree, active, acc, a_old=None, n_pp=None, n_pn=None) -> int:
+    """Forces on the active particles only (active: uint8 [N], nonzero = active);
+    the other entries of acc / n_pp / n_pn are left as they were.  Returns the
+    number of groups walked."""
+    g = C.c_int64(0)
+    if _is_torch_cuda(acc):
+        act = _dev_ptr(active, "uint8")
+        ap = _dev_ptr(acc, "float32")
+        op = None if a_old is None else _dev_ptr(a_old, "float32")
+        pp = None if n_pp is None else _dev_ptr(n_pp, "int32")
+        np_ = None if n_pn is None else _dev_ptr(n_pn, "int32")
+    else:
+        act = _host_ptr(active, np.uint8)
+        ap = _host_ptr(acc, np.float32, (3,))
+        op = None if a_old is None else _host_ptr(a_old, np.float32, (3,))
+        pp = None if n_pp is None else _host_ptr(n_pp, np.uint32)
+        np_ = None if n_pn is None else _host_ptr(n_pn, np.uint32)
+    _check(lib().og_tree_force_active(tree, act, op, ap, pp, np_, C.byref(g)))
+    return int(g.value)
 
 
 def og_tree_info_get(tree) -> dict:
