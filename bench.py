@@ -84,6 +84,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-kdk", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=6.0)
     ap.add_argument("--batched-boxes", type=int, default=512)
     return ap.parse_args()
@@ -260,6 +261,37 @@ def batched_bench(og, ctx, torch, dev, stream, nboxes, steps):
             "batched_speedup": mp / mb,
             "batched_walk_ms": info["ms_walk"], "batched_build_ms": info["ms_build"],
             "same_interactions": int(inter_pb) == int(info["interactions"])}
+
+
+def kdk_bench(og, ctx, n=262144, max_bin=6, dt_max=0.02):
+    """Individual power-of-two time steps against global stepping.  A
+    halo-clustered system (the 2.1M generator at n particles, velocities
+    Gaussian 1e-3 box per unit time) is integrated over one maximum step with
+    bins chosen by the acceleration criterion (eta 0.05), and again with every
+    particle at the finest step the first run used.  Host arrays in and out,
+    the tree rebuilt every 4 ticks and refitted in between."""
+    pos, mass, prm = gi.config("clustered-2m", n=n, seed=12350)
+    prm = dict(prm, opening=gi.OPEN_BH, theta=0.5)
+    vel = np.random.default_rng(12350).normal(0.0, 1e-3, size=pos.shape)
+    p1, v1 = pos.copy(), vel.copy()
+    t0 = time.perf_counter()
+    _, bins, st = og.og_kdk_run(ctx.h, p1, v1, mass, prm, dt_max=dt_max, eta=0.05,
+                                max_bin=max_bin, nsteps=1, rebuild_every=4)
+    t_ind = time.perf_counter() - t0
+    bmax = int(bins.max())
+    p2, v2 = pos.copy(), vel.copy()
+    t0 = time.perf_counter()
+    _, _, sg = og.og_kdk_run(ctx.h, p2, v2, mass, prm, dt_max=dt_max / (1 << bmax), eta=0.05,
+                             max_bin=0, nsteps=1 << bmax, rebuild_every=4)
+    t_glob = time.perf_counter() - t0
+    return {"workload": f"{n} particles, halo-clustered, one maximum step dt_max={dt_max}, "
+                        f"max_bin={max_bin}, BH theta 0.5, rebuild every 4 ticks",
+            "bins_used": sorted(int(b) for b in np.unique(bins)),
+            "individual": {"ticks": st["ticks"], "forces": st["forces"], "seconds": t_ind,
+                           "forces_per_s": st["forces"] / t_ind, "device_ms": st["ms"]},
+            "global_finest": {"ticks": sg["ticks"], "forces": sg["forces"], "seconds": t_glob,
+                              "forces_per_s": sg["forces"] / t_glob},
+            "force_ratio": sg["forces"] / st["forces"], "speedup": t_glob / t_ind}
 
 
 def served_bench(og, torch, dev, rates=(10.0, 30.0, 100.0), seconds=6.0, pool_size=16):
@@ -493,6 +525,10 @@ def main():
     if not args.no_served and rank == 0:
         served = served_bench(og, torch, dev, seconds=args.served_seconds)
 
+    kdk = None
+    if not args.no_kdk and rank == 0:
+        kdk = kdk_bench(og, ctx)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(pos, mass, prm)
@@ -510,7 +546,8 @@ def main():
                "build_ms_per_step": float(np.mean(ms_build)),
                "walk_interactions_per_s": inter_step / (walk_ms * 1e-3),
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-               "roofline": roof, "cpu_baseline": cpu, "batched": batched, "served": served}
+               "roofline": roof, "cpu_baseline": cpu, "batched": batched, "served": served,
+               "individual_steps": kdk}
         print(json.dumps(out), flush=True)
     ctx.close()
     if ws > 1:

@@ -268,6 +268,47 @@ size_t og_serve_request_bytes(int64_t n);
  * Thread safe. */
 og_status og_serve_poll(og_ctx *ctx, uint64_t ticket, og_result *out, int timeout_ms);
 
+/* ---- time integration: individual power-of-two time steps -------------- */
+
+/* Kick-drift-kick leapfrog with individual time steps (Sect. 3.2).  One
+ * maximum step dt_max is 2^max_bin ticks; a particle in bin b steps by
+ * dt_max / 2^b and is active at the ticks that are multiples of 2^(max_bin - b).
+ * Its bin is the smallest b with dt_max / 2^b <= sqrt(2 eta eps / |a|) (the
+ * acceleration criterion of Sect. 3.2, eps = og_params.eps), at most max_bin;
+ * a particle only enters a bin whose period divides the current tick.  Per
+ * tick every particle drifts by v dt_max / 2^max_bin (wrapped into the box),
+ * the active particles get new accelerations (og_tree_force_active on the tree
+ * of the drifted positions: rebuilt every rebuild_every ticks, refitted in
+ * between), their closing half kick with the old bin, and, except at the last
+ * tick, a new bin and the opening half kick.  FP64 positions and velocities. */
+typedef struct {
+    double dt_max;           /* the longest step (bin 0), > 0 */
+    double eta;              /* integration tolerance of the criterion (paper default 0.05) */
+    int32_t max_bin;         /* finest bin, 0..30 */
+    int32_t nsteps;          /* maximum steps to integrate, >= 1 */
+    int32_t rebuild_every;   /* >= 1; 1 = a new tree every tick */
+    int32_t pad;
+} og_kdk_params;
+
+typedef struct {
+    int64_t ticks;           /* last tick index (nsteps * 2^max_bin) */
+    int64_t forces;          /* accelerations computed, summed over ticks */
+    int64_t groups_walked;   /* groups walked, summed over ticks */
+    int64_t interactions;    /* PP + PN entries evaluated, summed over ticks */
+    int64_t rebuilds, refits;
+    double ms;               /* device time of the whole call */
+} og_kdk_stats;
+
+/* Integrate n particles (pos, vel: double[n][3] in/out, mass: double[n]; host
+ * arrays, or device arrays with OG_DEVICE_PTRS in p->flags) for kp->nsteps
+ * maximum steps.  acc_out (float[n][3]) and bins_out (int32[n]) receive the
+ * last accelerations and bins (either may be NULL).  p as for og_tree_build
+ * (eps > 0 required).  OG_ERR_ARG for invalid parameters; errors of the tree
+ * calls are passed on. */
+og_status og_kdk_run(og_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass,
+                     const og_params *p, const og_kdk_params *kp, float *acc_out,
+                     int32_t *bins_out, og_kdk_stats *stats);
+
 /* ---- group size: measured choice ---------------------------------------- */
 
 /* The group size G (targets sharing one interaction list, Sect. 3.4 and

@@ -122,6 +122,9 @@ def lib():
         L.og_serve_request_bytes.argtypes = [i64]
         L.og_serve_request_bytes.restype = C.c_size_t
         L.og_sort_keys_noalloc.restype = C.c_int
+        L.og_kdk_run.argtypes = [P, i64, P, P, P, C.POINTER(og_params), C.POINTER(og_kdk_params), P, P,
+                                 C.POINTER(og_kdk_stats)]
+        L.og_kdk_run.restype = C.c_int
         L.og_tree_force_active.argtypes = [P, P, P, P, P, P, C.POINTER(C.c_int64)]
         L.og_tree_force_active.restype = C.c_int
         L.og_tune_group_max.argtypes = [P, P, P, i64, C.POINTER(og_params), C.POINTER(C.c_int32)]
@@ -272,6 +275,38 @@ def og_tree_force_active(tree, active, acc, a_old=None, n_pp=None, n_pn=None) ->
         np_ = None if n_pn is None else _host_ptr(n_pn, np.uint32)
     _check(lib().og_tree_force_active(tree, act, op, ap, pp, np_, C.byref(g)))
     return int(g.value)
+
+
+class og_kdk_params(C.Structure):
+    _fields_ = [("dt_max", C.c_double), ("eta", C.c_double), ("max_bin", C.c_int32),
+                ("nsteps", C.c_int32), ("rebuild_every", C.c_int32), ("pad", C.c_int32)]
+
+
+class og_kdk_stats(C.Structure):
+    _fields_ = [("ticks", C.c_int64), ("forces", C.c_int64), ("groups_walked", C.c_int64),
+                ("interactions", C.c_int64), ("rebuilds", C.c_int64), ("refits", C.c_int64),
+                ("ms", C.c_double)]
+
+
+def og_kdk_run(ctx, pos, vel, mass, params: dict, dt_max: float, eta: float = 0.05,
+               max_bin: int = 6, nsteps: int = 1, rebuild_every: int = 1):
+    """Integrate (host numpy arrays; pos and vel are updated in place).
+    Returns (acc float32 [N,3], bins int32 [N], stats dict)."""
+    n = int(pos.shape[0])
+    pp = _host_ptr(pos, np.float64, (3,))
+    vp = _host_ptr(vel, np.float64, (3,))
+    mp = _host_ptr(mass, np.float64)
+    prm = params_from_dict(params, 0)
+    prm.flags = int(prm.flags) & ~OG_DEVICE_PTRS
+    kp = og_kdk_params(dt_max=float(dt_max), eta=float(eta), max_bin=int(max_bin),
+                       nsteps=int(nsteps), rebuild_every=int(rebuild_every))
+    acc = np.zeros((n, 3), np.float32)
+    bins = np.zeros(n, np.int32)
+    st = og_kdk_stats()
+    _check(lib().og_kdk_run(ctx, n, pp, vp, mp, C.byref(prm), C.byref(kp),
+                            acc.ctypes.data_as(C.c_void_p), bins.ctypes.data_as(C.c_void_p),
+                            C.byref(st)))
+    return acc, bins, {k: getattr(st, k) for k, _ in og_kdk_stats._fields_}
 
 
 def og_tree_info_get(tree) -> dict:
