@@ -83,6 +83,13 @@ def lib():
             L.ora_soft_g.restype = C.c_double
             L.ora_split_s.argtypes = [C.c_double, C.c_double]
             L.ora_split_s.restype = C.c_double
+            L.ora_soft_psi.argtypes = [C.c_double, C.c_double]
+            L.ora_soft_psi.restype = C.c_double
+            L.ora_split_p.argtypes = [C.c_double, C.c_double]
+            L.ora_split_p.restype = C.c_double
+            L.ora_tree_force_pot.argtypes = [P, P, C.c_int, C.c_double, C.c_double, P, i64, P, P,
+                                             P, P, C.c_int, C.c_int]
+            L.ora_direct_pot.argtypes = [P, P, i64, C.POINTER(Params), P, i64, P, P, C.c_int]
             L.ora_tree_build.argtypes = [P, P, i64, C.POINTER(Params), C.POINTER(P)]
             L.ora_tree_free.argtypes = [P]
             L.ora_tree_refit.argtypes = [P, P]
@@ -130,6 +137,14 @@ def soft_g(r: float, h: float) -> float:
 
 def split_s(r: float, rs: float) -> float:
     return float(lib().ora_split_s(float(r), float(rs)))
+
+
+def soft_psi(r: float, h: float) -> float:
+    return float(lib().ora_soft_psi(float(r), float(h)))
+
+
+def split_p(r: float, rs: float) -> float:
+    return float(lib().ora_split_p(float(r), float(rs)))
 
 
 def num_threads() -> int:
@@ -197,7 +212,7 @@ class Tree:
             raise ValueError(f"oracle refit failed ({rc})")
 
     def force(self, opening=None, theta=None, alpha=None, a_old=None, groups=None,
-              keep_lists=False, nthreads=0):
+              keep_lists=False, nthreads=0, want_pot=False):
         """a7-a9.  Returns (acc[N,3] f64, n_pp[N], n_pn[N]) in input order; with
         ``groups`` only the targets of those groups are filled (others NaN).
         ``a_old`` (input order, float32 [N,3]) feeds the relative criterion;
@@ -212,13 +227,19 @@ class Tree:
         ao = None if a_old is None else np.ascontiguousarray(a_old, dtype=np.float32).reshape(-1, 3)
         sel = None if groups is None else np.ascontiguousarray(groups, dtype=np.int64)
         nsel = 0 if sel is None else sel.shape[0]
-        rc = lib().ora_tree_force(self._h, _ptr(ao), int(opening), float(theta), float(alpha),
-                                  _ptr(sel), nsel, _ptr(acc), _ptr(npp), _ptr(npn),
-                                  int(bool(keep_lists)), int(nthreads))
+        pot = np.full(self.n, np.nan) if want_pot else None
+        rc = lib().ora_tree_force_pot(self._h, _ptr(ao), int(opening), float(theta), float(alpha),
+                                      _ptr(sel), nsel, _ptr(acc), _ptr(npp), _ptr(npn), _ptr(pot),
+                                      int(bool(keep_lists)), int(nthreads))
         if rc:
             raise ValueError(f"oracle force failed ({rc})")
         self._nsel = self.ngroups if sel is None else nsel
-        return acc, npp, npn
+        return (acc, npp, npn, pot) if want_pot else (acc, npp, npn)
+
+    def force_pot(self, **kw):
+        """force() plus the short-range potential per target (input order):
+        returns (acc, n_pp, n_pn, pot)."""
+        return self.force(want_pot=True, **kw)
 
     def lists(self):
         """Per selected group of the last force call: sorted unified refs
@@ -246,6 +267,22 @@ def direct(pos, mass, params: dict, targets=None, nthreads=0) -> np.ndarray:
     if rc:
         raise ValueError(f"direct failed ({rc})")
     return acc
+
+
+def direct_pot(pos, mass, params: dict, targets=None, nthreads=0):
+    """direct() plus the short-range potential: returns (acc, pot)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    t = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = pos.shape[0] if t is None else t.shape[0]
+    acc = np.zeros((nt, 3))
+    pot = np.zeros(nt)
+    prm = make_params(params)
+    rc = lib().ora_direct_pot(_ptr(pos), _ptr(mass), pos.shape[0], C.byref(prm), _ptr(t),
+                              0 if t is None else nt, _ptr(acc), _ptr(pot), int(nthreads))
+    if rc:
+        raise ValueError(f"direct failed ({rc})")
+    return acc, pot
 
 
 def cell_exact(pos, mass, params: dict, targets=None, nthreads=0) -> np.ndarray:

@@ -598,6 +598,30 @@ double ora_soft_g(double r, double h)
                  1.0 / (15.0 * u * u * u));
 }
 
+/* potential kernel of the same spline mass distribution: psi(r) = integral
+ * from r to infinity of g(s) s ds, so that -d psi / dr = r g(r); psi = 1/r for
+ * r >= h and psi(0) = 14 / (5 h) = 1 / eps (h = 2.8 eps).  With u = r/h:
+ *   u < 1/2      : psi = h^-1 (14/5 - 16/3 u^2 + 48/5 u^4 - 32/5 u^5)
+ *   1/2 <= u < 1 : psi = h^-1 (16/5 - 1/(15 u) - 32/3 u^2 + 16 u^3
+ *                              - 48/5 u^4 + 32/15 u^5)                      */
+double ora_soft_psi(double r, double h)
+{
+    if (!(h > 0.0) || r >= h) return 1.0 / r;
+    double u = r / h;
+    double u2 = u * u;
+    if (u < 0.5)
+        return (14.0 / 5.0 - 16.0 / 3.0 * u2 + 48.0 / 5.0 * u2 * u2 - 32.0 / 5.0 * u2 * u2 * u) / h;
+    return (16.0 / 5.0 - 1.0 / (15.0 * u) - 32.0 / 3.0 * u2 + 16.0 * u2 * u - 48.0 / 5.0 * u2 * u2 +
+            32.0 / 15.0 * u2 * u2 * u) / h;
+}
+
+/* short-range potential factor erfc(r / 2 r_s) (Sect. 4.2); 1 without split */
+double ora_split_p(double r, double rs)
+{
+    if (!(rs > 0.0)) return 1.0;
+    return erfc(r / (2.0 * rs));
+}
+
 /* short-range factor S(r) = -r^2 d/dr[erfc(r/2r_s)/r] */
 double ora_split_s(double r, double rs)
 {
@@ -644,9 +668,11 @@ static int pair_active(int64_t dx, int64_t dy, int64_t dz, float rc2f)
     return r2 > 0.0f && r2 < rc2f;
 }
 
-/* FP64 contribution of a mass m at (xj, yj, zj) to the target at (xi, yi, zi) */
+/* FP64 contribution of a mass m at (xj, yj, zj) to the target at (xi, yi, zi):
+ * acceleration, and (phi != NULL) the short-range potential
+ * -G m psi(r) erfc(r / 2 r_s) (the reading of the potential output) */
 static void add_pair(const force_ctx *c, uint32_t xi, uint32_t yi, uint32_t zi, uint32_t xj,
-                     uint32_t yj, uint32_t zj, double m, double acc[3])
+                     uint32_t yj, uint32_t zj, double m, double acc[3], double *phi)
 {
     int64_t ix = min_image(xj, xi), iy = min_image(yj, yi), iz = min_image(zj, zi);
     if (!pair_active(ix, iy, iz, c->rc2f)) return;
@@ -656,6 +682,7 @@ static void add_pair(const force_ctx *c, uint32_t xi, uint32_t yi, uint32_t zi, 
     acc[0] += f * dx;
     acc[1] += f * dy;
     acc[2] += f * dz;
+    if (phi) *phi -= c->G * m * ora_soft_psi(r, c->h) * ora_split_p(r, c->rs);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -782,7 +809,8 @@ static int cmp_i64(const void *a, const void *b)
 /* one force pass over the selected groups; acc, npp, npn in input order */
 static int force_pass(ora_tree *t, const force_ctx *c, int opening, const float *a_old,
                       const int64_t *sel, int64_t nsel, double *acc, uint32_t *npp,
-                      uint32_t *npn, int keep_lists, int64_t **glist, int64_t *glen)
+                      uint32_t *npn, int keep_lists, int64_t **glist, int64_t *glen,
+                      double *pot)
 {
     const int64_t n = t->n;
     int err = 0;
@@ -820,17 +848,19 @@ static int force_pass(ora_tree *t, const force_ctx *c, int opening, const float 
                 continue;
             }
             for (int64_t q = t->gbeg[g]; q < t->gend[g]; ++q) {
-                double a3[3] = {0.0, 0.0, 0.0};
+                double a3[3] = {0.0, 0.0, 0.0}, ph = 0.0;
+                double *php = pot ? &ph : NULL;
                 uint32_t xi = t->sx[q], yi = t->sy[q], zi = t->sz[q];
                 for (int64_t k = 0; k < w.pp.len; ++k) {
                     int64_t j = w.pp.v[k];
-                    add_pair(c, xi, yi, zi, t->sx[j], t->sy[j], t->sz[j], t->sm[j], a3);
+                    add_pair(c, xi, yi, zi, t->sx[j], t->sy[j], t->sz[j], t->sm[j], a3, php);
                 }
                 for (int64_t k = 0; k < w.pn.len; ++k) {
                     int64_t j = w.pn.v[k];
-                    add_pair(c, xi, yi, zi, t->cx[j], t->cy[j], t->cz[j], t->M[j], a3);
+                    add_pair(c, xi, yi, zi, t->cx[j], t->cy[j], t->cz[j], t->M[j], a3, php);
                 }
                 int64_t o = t->perm[q];
+                if (pot) pot[o] = ph;
                 acc[3 * o + 0] = a3[0];
                 acc[3 * o + 1] = a3[1];
                 acc[3 * o + 2] = a3[2];
@@ -862,6 +892,14 @@ int ora_tree_force(ora_tree *t, const float *a_old, int opening, double theta, d
                    const int64_t *sel, int64_t nsel, double *acc, uint32_t *npp,
                    uint32_t *npn, int keep_lists, int nthreads)
 {
+    return ora_tree_force_pot(t, a_old, opening, theta, alpha, sel, nsel, acc, npp, npn, NULL,
+                              keep_lists, nthreads);
+}
+
+int ora_tree_force_pot(ora_tree *t, const float *a_old, int opening, double theta, double alpha,
+                       const int64_t *sel, int64_t nsel, double *acc, uint32_t *npp,
+                       uint32_t *npn, double *pot, int keep_lists, int nthreads)
+{
     if (!t || !acc) return ORA_ERR_ARG;
     if (opening != ORA_OPEN_BH && opening != ORA_OPEN_REL) return ORA_ERR_ARG;
 #ifdef _OPENMP
@@ -892,7 +930,7 @@ int ora_tree_force(ora_tree *t, const float *a_old, int opening, double theta, d
             return ORA_ERR_OOM;
         }
         rc = force_pass(t, &c, ORA_OPEN_BH, NULL, NULL, t->ngroups, a1, NULL, NULL, 0, NULL,
-                        NULL);
+                        NULL, NULL);
         for (int64_t i = 0; i < 3 * t->n; ++i) aprev[i] = (float)a1[i];
         free(a1);
         if (rc) {
@@ -913,7 +951,7 @@ int ora_tree_force(ora_tree *t, const float *a_old, int opening, double theta, d
             return ORA_ERR_OOM;
         }
     }
-    rc = force_pass(t, &c, opening, a_old, sel, nsel, acc, npp, npn, keep_lists, glist, glen);
+    rc = force_pass(t, &c, opening, a_old, sel, nsel, acc, npp, npn, keep_lists, glist, glen, pot);
     free(aprev);
     if (keep_lists) {
         free(t->list_off);
@@ -954,6 +992,13 @@ static int quantize_all(const double *pos, int64_t n, double box, uint32_t *q)
 int ora_direct(const double *pos, const double *mass, int64_t n, const ora_params *p,
                const int64_t *targets, int64_t ntargets, double *acc, int nthreads)
 {
+    return ora_direct_pot(pos, mass, n, p, targets, ntargets, acc, NULL, nthreads);
+}
+
+int ora_direct_pot(const double *pos, const double *mass, int64_t n, const ora_params *p,
+                   const int64_t *targets, int64_t ntargets, double *acc, double *pot,
+                   int nthreads)
+{
     if (n < 1 || !p || !(p->box > 0.0)) return ORA_ERR_ARG;
     if (p->r_s > 0.0 && !(p->rcut_over_rs * p->r_s < 0.5 * p->box)) return ORA_ERR_ARG;
 #ifdef _OPENMP
@@ -973,12 +1018,13 @@ int ora_direct(const double *pos, const double *mass, int64_t n, const ora_param
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t s = 0; s < nt; ++s) {
         int64_t i = targets ? targets[s] : s;
-        double a3[3] = {0.0, 0.0, 0.0};
+        double a3[3] = {0.0, 0.0, 0.0}, ph = 0.0;
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             add_pair(&c, q[3 * i], q[3 * i + 1], q[3 * i + 2], q[3 * j], q[3 * j + 1],
-                     q[3 * j + 2], mass[j], a3);
+                     q[3 * j + 2], mass[j], a3, pot ? &ph : NULL);
         }
+        if (pot) pot[s] = ph;
         acc[3 * s + 0] = a3[0];
         acc[3 * s + 1] = a3[1];
         acc[3 * s + 2] = a3[2];
@@ -1055,7 +1101,7 @@ int ora_cell_exact(const double *pos, const double *mass, int64_t n, const ora_p
                         int64_t j = order[k];
                         if (j == i) continue;
                         add_pair(&c, q[3 * i], q[3 * i + 1], q[3 * i + 2], q[3 * j],
-                                 q[3 * j + 1], q[3 * j + 2], mass[j], a3);
+                                 q[3 * j + 1], q[3 * j + 2], mass[j], a3, NULL);
                     }
                 }
         acc[3 * s + 0] = a3[0];

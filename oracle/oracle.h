@@ -46,6 +46,8 @@ int ora_quantize1(double v, double box, uint32_t *out);
 uint64_t ora_morton(uint32_t x, uint32_t y, uint32_t z);
 double ora_soft_g(double r, double h);
 double ora_split_s(double r, double rs);
+double ora_soft_psi(double r, double h);
+double ora_split_p(double r, double rs);
 
 int ora_tree_build(const double *pos, const double *mass, int64_t n, const ora_params *p,
                    ora_tree **out);
@@ -56,9 +58,15 @@ int ora_tree_get(const ora_tree *t, int what, void *dst);
 int ora_tree_force(ora_tree *t, const float *a_old, int opening, double theta, double alpha,
                    const int64_t *sel, int64_t nsel, double *acc, uint32_t *npp,
                    uint32_t *npn, int keep_lists, int nthreads);
+int ora_tree_force_pot(ora_tree *t, const float *a_old, int opening, double theta, double alpha,
+                       const int64_t *sel, int64_t nsel, double *acc, uint32_t *npp,
+                       uint32_t *npn, double *pot, int keep_lists, int nthreads);
 int ora_tree_get_lists(const ora_tree *t, int64_t nsel, int64_t *off, int64_t *list);
 int ora_direct(const double *pos, const double *mass, int64_t n, const ora_params *p,
                const int64_t *targets, int64_t ntargets, double *acc, int nthreads);
+int ora_direct_pot(const double *pos, const double *mass, int64_t n, const ora_params *p,
+                   const int64_t *targets, int64_t ntargets, double *acc, double *pot,
+                   int nthreads);
 int ora_cell_exact(const double *pos, const double *mass, int64_t n, const ora_params *p,
                    const int64_t *targets, int64_t ntargets, double *acc, int nthreads);
 int ora_num_threads(void);

@@ -487,3 +487,64 @@ def test_refit_theta_zero_equals_direct_sum():
     acc, _, _ = t.force(theta=0.0)
     d = oracle.direct(new, mass, prm)
     assert np.abs(acc - d).max() <= 1e-12 * np.abs(d).max()
+
+
+# ---------------------------------------------------------------------------
+# short-range potential (the potential output of the force call)
+# ---------------------------------------------------------------------------
+
+def test_spline_potential_is_the_integral_of_the_force_kernel():
+    # psi(r) = integral_r^inf g(s) s ds with the quadrature-pinned force kernel g
+    h = 0.8
+    for r in [1e-6, 0.05, 0.2, 0.3999, 0.4, 0.4001, 0.55, 0.79, 0.8, 1.1]:
+        tail, _ = integrate.quad(lambda s: oracle.soft_g(s, h) * s, r, h, epsabs=1e-13,
+                                 epsrel=1e-13, limit=200) if r < h else (0.0, 0.0)
+        expect = tail + 1.0 / max(r, h)
+        assert abs(oracle.soft_psi(r, h) - expect) <= 1e-11 * expect, r
+    eps = h / 2.8
+    assert abs(oracle.soft_psi(0.0, h) - 1.0 / eps) <= 1e-14 / eps      # Plummer-equivalent
+    for r0 in (h / 2, h):                                                # continuous
+        assert abs(oracle.soft_psi(r0 * (1 - 1e-12), h) - oracle.soft_psi(r0 * (1 + 1e-12), h)) < 1e-9
+
+
+def test_potential_derivative_gives_the_split_force():
+    # -d/dr [erfc(r/2r_s) / r] = S(r) / r^2 outside the softening (r >= h)
+    rs, h = 0.02, 1e-4
+    for r in [0.001, 0.01, 0.03, 0.06, 0.09]:
+        f = lambda x: oracle.soft_psi(x, h) * oracle.split_p(x, rs)
+        dr = r * 1e-5
+        deriv = (f(r + dr) - f(r - dr)) / (2 * dr)
+        expect = -oracle.split_s(r, rs) / r ** 2
+        assert abs(deriv - expect) <= 1e-7 * abs(expect), r
+    assert oracle.split_p(0.5, 0.0) == 1.0                                # no split
+    assert abs(oracle.split_p(0.04, 0.01) - special.erfc(2.0)) < 1e-15
+
+
+def test_two_body_potential_closed_form():
+    prm = gi.default_params(eps=1e-3, r_s=0.02, opening=gi.OPEN_BH, theta=0.5)
+    h, rcut = 2.8e-3, 4.5 * 0.02
+    for r in (0.5 * h, 2 * h, 0.03, 0.08, rcut * 1.01):
+        pos = np.array([[0.3, 0.4, 0.5], [0.3 + r, 0.4, 0.5]])
+        mass = np.array([2e-3, 3e-3])
+        _, pot = oracle.direct_pot(pos, mass, prm)
+        d = (oracle.quantize1(0.3 + r) - oracle.quantize1(0.3)) / 2 ** 32   # exact grid separation
+        if d < rcut:
+            psi = oracle.soft_psi(d, h) * special.erfc(d / (2 * 0.02))
+            assert abs(pot[0] + 3e-3 * psi) <= 1e-12 * 3e-3 * psi
+            assert abs(pot[1] + 2e-3 * psi) <= 1e-12 * 2e-3 * psi
+        else:
+            assert pot[0] == 0.0 and pot[1] == 0.0                         # beyond the cutoff
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_tree_potential_theta_zero_equals_direct(kind):
+    if kind == "uniform":
+        pos, mass, prm = gi.config("uniform-32k", n=3000)
+    else:
+        pos, mass, prm = gi.config("clustered-2m", n=3000)
+        prm["opening"] = gi.OPEN_BH
+    t = oracle.Tree(pos, mass, prm)
+    acc, _, _, pot = t.force_pot(theta=0.0)
+    d_acc, d_pot = oracle.direct_pot(pos, mass, prm)
+    assert np.abs(pot - d_pot).max() <= 1e-12 * np.abs(d_pot).max()
+    assert np.abs(acc - d_acc).max() <= 1e-12 * np.abs(d_acc).max()
