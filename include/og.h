@@ -107,6 +107,8 @@ typedef struct {
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device
  * memory the serving loop may admit (0 = no bound).  Owns a CUDA stream. */
 og_status og_create(og_ctx **ctx, int device, size_t hbm_budget_bytes);
+/* Stops the context's serving engine and frees the trees of og_tree_build
+ * that were not freed; afterwards no tree of the context may be used. */
 og_status og_destroy(og_ctx *ctx);
 /* Order all further work of the context on `stream` (a cudaStream_t of the
  * context's device; NULL restores the context's own stream). */
@@ -204,6 +206,16 @@ enum {
 og_status og_tree_export(const og_tree *t, int field, void *host_dst, size_t bytes);
 
 og_status og_tree_free(og_tree *t);
+
+/* og_tree_force plus the short-range potential of every particle (pot:
+ * float[n], caller order, host or device like acc), from the same lists in the
+ * same pass: phi_i = -G sum_j m_j psi(r) erfc(r / 2 r_s) (Sect. 4.2, phi_s =
+ * -G m erfc(u) / r), psi the potential of the spline mass distribution used by
+ * the force (psi = 1/r for r >= h, 1/eps at r = 0); the particle itself and
+ * entries beyond the cutoff contribute nothing.  Accelerations and counts are
+ * those of og_tree_force.  OG_DEBUG_DUMP_LISTS does not apply to this call. */
+og_status og_tree_force_pot(og_tree *t, const float *a_old, float *acc, float *pot,
+                            uint32_t *n_pp, uint32_t *n_pn);
 
 /* Forces on the active particles only: the individual time steps of Sect.
  * 3.2 need new accelerations only for the particles whose time bin is

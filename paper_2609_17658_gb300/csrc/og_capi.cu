@@ -11,7 +11,9 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <mutex>
 #include <new>
+#include <unordered_set>
 
 #include "og_internal.h"
 
@@ -63,6 +65,13 @@ __global__ void k_unpermute(int64_t n, const uint32_t *__restrict__ perm,
     if (npn) npn[j] = npn_s[i];
 }
 
+__global__ void k_unpermute_pot(int64_t n, const uint32_t *__restrict__ perm,
+                                const float *__restrict__ pot_sorted, float *pot) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pot[perm[i]] = pot_sorted[i];
+}
+
 // 1 for a group holding at least one active particle (active: caller order)
 __global__ void k_group_active(int64_t ng, const uint32_t *__restrict__ gbeg,
                                const uint32_t *__restrict__ gend, const uint32_t *__restrict__ perm,
@@ -101,6 +110,28 @@ __global__ void k_unpermute_active(int64_t n, const uint32_t *__restrict__ perm,
 }
 
 }  // namespace
+
+// trees handed out by og_tree_build, so that og_destroy can free the ones the
+// caller did not
+struct LiveTrees {
+    std::mutex mu;
+    std::unordered_set<og_tree *> set;
+};
+
+void live_add(og_ctx *c, og_tree *t) {
+    if (!c->live) c->live = new (std::nothrow) LiveTrees();
+    LiveTrees *L = static_cast<LiveTrees *>(c->live);
+    if (!L) return;
+    std::lock_guard<std::mutex> lk(L->mu);
+    L->set.insert(t);
+}
+
+void live_remove(og_tree *t) {
+    LiveTrees *L = t->ctx ? static_cast<LiveTrees *>(t->ctx->live) : nullptr;
+    if (!L) return;
+    std::lock_guard<std::mutex> lk(L->mu);
+    L->set.erase(t);
+}
 
 og_status check_status(og_ctx *c) {
     uint32_t st = 0;
@@ -212,6 +243,18 @@ og_status og_destroy(og_ctx *c) {
     if (!c) return OG_OK;
     serve_shutdown(c);
     og::tune_free(c);
+    if (c->live) {
+        // trees the caller did not free
+        LiveTrees *L = static_cast<LiveTrees *>(c->live);
+        std::vector<og_tree *> left;
+        {
+            std::lock_guard<std::mutex> lk(L->mu);
+            left.assign(L->set.begin(), L->set.end());
+        }
+        for (og_tree *t : left) og_tree_free(t);
+        delete L;
+        c->live = nullptr;
+    }
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     cudaFree(c->d_status);
@@ -276,6 +319,7 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
         og_tree_free(t);
         return st;
     }
+    live_add(c, t);
     *out = t;
     return OG_OK;
 }
@@ -288,7 +332,7 @@ namespace og {
 // t->a_sorted, t->npp_sorted, t->npn_sorted).  d_aold: previous accelerations
 // in input order on the device, or null.
 og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out, const uint32_t *subset,
-                       int64_t nsubset) {
+                       int64_t nsubset, float *pot_sorted) {
     cudaStream_t s = t->ctx->stream;
     const int64_t n = t->n;
     cudaError_t e;
@@ -318,7 +362,7 @@ og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out, cons
         a_old_sorted = t->a_old_sorted;
     }
     og_status st = walk_pass(t, t->prm.opening, false, a_old_sorted, t->a_sorted, &ms, true,
-                             subset, nsubset);
+                             subset, nsubset, pot_sorted);
     if (st) return st;
     ms_walk += ms;
     if (ms_walk_out) *ms_walk_out = ms_walk;
@@ -354,7 +398,7 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
             d_aold = static_cast<const float *>(tmp);
         }
     }
-    og_status st = force_sorted(t, d_aold, &ms_walk);
+    og_status st = force_sorted(t, d_aold, &ms_walk, nullptr, 0, t->pot_next);
     if (tmp) cudaFreeAsync(tmp, s);
     if (st) return st;
     // back to caller order
@@ -384,6 +428,33 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
     t->ms_force = ms;
     t->ms_walk = ms_walk;
     return check_status(c);
+}
+
+og_status og_tree_force_pot(og_tree *t, const float *a_old, float *acc, float *pot,
+                            uint32_t *n_pp, uint32_t *n_pn) {
+    if (!t || !acc || !pot) { set_error("NULL argument"); return OG_ERR_ARG; }
+    og_ctx *c = t->ctx;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int64_t n = t->n;
+    const bool dev = (t->prm.flags & OG_DEVICE_PTRS) != 0;
+    cudaError_t e;
+    void *tmp = nullptr;
+    if ((e = cudaMallocAsync(&tmp, (size_t)n * 2 * sizeof(float) + 512, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync (potential)");
+    float *pot_sorted = static_cast<float *>(tmp);
+    float *d_pot = dev ? pot : pot_sorted + ((n + 63) & ~(int64_t)63);
+    // the force call with the potential output of its last pass
+    t->pot_next = pot_sorted;
+    og_status st = og_tree_force(t, a_old, acc, n_pp, n_pn);
+    t->pot_next = nullptr;
+    if (st == OG_OK) {
+        k_unpermute_pot<<<nblk(n), kT, 0, s>>>(n, t->perm, pot_sorted, d_pot); note_launch();
+        if (!dev) cudaMemcpyAsync(pot, d_pot, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "potential");
+    }
+    cudaFreeAsync(tmp, s);
+    return st;
 }
 
 og_status og_tree_force_active(og_tree *t, const uint8_t *active, const float *a_old, float *acc,
@@ -654,6 +725,7 @@ og_status og_tree_export(const og_tree *t, int field, void *dst, size_t bytes) {
 
 og_status og_tree_free(og_tree *t) {
     if (!t) return OG_OK;
+    live_remove(t);
     cudaSetDevice(t->ctx->device);
     if (t->arena) cudaFreeAsync(t->arena, t->ctx->stream);
     if (t->ext_arena) cudaFreeAsync(t->ext_arena, t->ctx->stream);

@@ -67,6 +67,7 @@ struct og_ctx {
     unsigned long long *d_counters = nullptr;  // scratch counters (work queues, totals)
     void *serve = nullptr;            // serving state (og_serve.cu)
     void *tune = nullptr;             // measured group sizes (og_tune.cu)
+    void *live = nullptr;             // trees of og_tree_build not yet freed (og_capi.cu)
 };
 
 struct og_tree {
@@ -124,6 +125,7 @@ struct og_tree {
     // stats
     int64_t interactions = 0, interactions_last = 0;
     double ms_build = 0, ms_force = 0, ms_walk = 0;
+    float *pot_next = nullptr;        // potential output of the next force call (sorted order)
     // one allocation holds every array above
     void *arena = nullptr;
     size_t arena_bytes = 0;
@@ -141,7 +143,8 @@ og_status check_status(og_ctx *c);
 // both force passes on a built tree, results in sorted order (og_capi.cu);
 // subset: only these groups (device array of nsubset group ids)
 og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out,
-                       const uint32_t *subset = nullptr, int64_t nsubset = 0);
+                       const uint32_t *subset = nullptr, int64_t nsubset = 0,
+                       float *pot_sorted = nullptr);
 // group size for group_max = 0: measured once per kind of input (og_tune.cu)
 og_status tuned_group_max(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
                           const og_params &p, int *group_max);
@@ -193,6 +196,7 @@ struct WalkParams {
     float inv_2rs;     // 1 / (2 r_s), grid units
     float kexp;        // -log2(e) / (4 r_s^2), grid units
     float out_scale;   // G (2^32/L)^2
+    float pot_scale;   // G 2^32/L (potential from grid units)
 };
 // One walk launch over all groups of all boxes.  first_pass: the Barnes-Hut
 // pass that supplies a_old for the relative criterion (each box's
@@ -201,7 +205,8 @@ struct WalkParams {
 // these nsubset groups, in this order (device array), instead of all groups.
 og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
                     float *acc_sorted, float *ms_out, bool use_order,
-                    const uint32_t *subset = nullptr, int64_t nsubset = 0);
+                    const uint32_t *subset = nullptr, int64_t nsubset = 0,
+                    float *pot_sorted = nullptr);
 // One walk launch over the groups of several trees (the serving loop), in
 // decreasing order of their previous list lengths.  Every tree's per-box
 // parameters must agree on split on/off.

@@ -73,6 +73,7 @@ struct TreeView {
     const uint32_t *px, *py, *pz;
     const float *a_old;           // [3][n] sorted, relative criterion only
     float *acc;                   // [3][n] sorted, out
+    float *pot;                   // [n] sorted, out (potential launches only)
     uint32_t *npp, *npn;          // [n] sorted, out
     int has_cost;                 // gcost holds the list lengths of a previous pass
 };
@@ -134,10 +135,13 @@ __device__ __forceinline__ unsigned long long sq64(uint32_t g) {
 // are this lane's share.  r^2 is guarded from below by 1 (a nonzero integer
 // separation has r^2 >= 1 in grid units); a zero separation then contributes
 // f * 0 = 0 exactly, the self term included.
-template <bool kSplit, bool kNear>
+// kPot: also the short-range potential sum of m erfc(r / 2 r_s) psi(r), psi the
+// potential kernel of the spline (1/r beyond h); the self term (r = 0) is left
+// out explicitly, it has no force to vanish with.
+template <bool kSplit, bool kNear, bool kPot = false>
 __device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, int R, uint32_t xi,
                                            uint32_t yi, uint32_t zi, const WalkParams &p,
-                                           float &ax, float &ay, float &az) {
+                                           float &ax, float &ay, float &az, float &ap) {
     const float rc2 = p.rc2, inv_2rs = p.inv_2rs, kexp = p.kexp;
     const float h = p.h, inv_h = p.inv_h;
     const float hinv3 = inv_h * inv_h * inv_h;
@@ -154,6 +158,7 @@ __device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, in
         const float rinv = rsqrt_ftz(r2c);
         float mS = m;
         float r = 0.0f;
+        float erfcv = 1.0f;
         if (kSplit || kNear) r = r2c * rinv;
         if (kSplit) {
             const float us = r * inv_2rs;
@@ -161,6 +166,22 @@ __device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, in
             const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, kAs5, kAs4), kAs3), kAs2), kAs1);
             const float ex = ex2_ftz(r2c * kexp);
             mS = m * (ex * fmaf(kTwoOverSqrtPi, us, poly));
+            if (kPot) erfcv = ex * poly;
+        }
+        if (kPot) {
+            float psi = rinv;
+            if (kNear) {
+                const float u = r * inv_h;
+                const float u2 = u * u;
+                const float pin = fmaf(u2, fmaf(u2, fmaf(-32.0f / 5.0f, u, 48.0f / 5.0f), -16.0f / 3.0f),
+                                       14.0f / 5.0f);
+                const float pout = fmaf(u2, fmaf(u, fmaf(u, fmaf(32.0f / 15.0f, u, -48.0f / 5.0f), 16.0f),
+                                                 -32.0f / 3.0f),
+                                        16.0f / 5.0f) -
+                                   (1.0f / 15.0f) * rcp_ftz(u);
+                psi = (r < h) ? inv_h * ((u < 0.5f) ? pin : pout) : psi;
+            }
+            ap = fmaf((r2 > 0.0f ? m : 0.0f) * erfcv, psi, ap);
         }
         float g = rinv * rinv * rinv;
         if (kNear) {
@@ -187,10 +208,10 @@ __device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, in
 // pairs (the f32x2 multiply and fused multiply-add of sm_100 and later:
 // each half is the same IEEE operation as the scalar one, so the cutoff
 // decision is unchanged); an odd last entry goes alone.
-template <bool kSplit>
+template <bool kSplit, bool kPot = false>
 __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int R, uint32_t xi,
                                          uint32_t yi, uint32_t zi, const WalkParams &p,
-                                         float &ax, float &ay, float &az) {
+                                         float &ax, float &ay, float &az, float &ap) {
     const float rc2 = p.rc2;
     const float2 c_inv2rs = make_float2(p.inv_2rs, p.inv_2rs);
     const float2 c_kexp = make_float2(p.kexp, p.kexp);
@@ -199,7 +220,7 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
     const float2 c3 = make_float2(kAs3, kAs3), c2 = make_float2(kAs2, kAs2);
     const float2 c1 = make_float2(kAs1, kAs1);
     const float2 c_tsp = make_float2(kTwoOverSqrtPi, kTwoOverSqrtPi);
-    float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx;
+    float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
     int e = rep;
 #pragma unroll 2
     for (; e + R < cnt; e += 2 * R) {
@@ -215,6 +236,7 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
         }
         const float2 rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
         float2 mS = m;
+        float2 mP = m;
         if (kSplit) {
             const float2 us = __fmul2_rn(__fmul2_rn(r2, rinv), c_inv2rs);
             const float2 den = __ffma2_rn(c_p, us, c_one);
@@ -227,13 +249,16 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
             const float2 arg = __fmul2_rn(r2, c_kexp);
             const float2 ex = make_float2(ex2_ftz(arg.x), ex2_ftz(arg.y));
             mS = __fmul2_rn(m, __fmul2_rn(ex, __ffma2_rn(c_tsp, us, poly)));
+            if (kPot) mP = __fmul2_rn(m, __fmul2_rn(ex, poly));
         }
+        if (kPot) sp = __ffma2_rn(mP, rinv, sp);
         const float2 f = __fmul2_rn(mS, __fmul2_rn(rinv, __fmul2_rn(rinv, rinv)));
         sx = __ffma2_rn(f, fx, sx);
         sy = __ffma2_rn(f, fy, sy);
         sz = __ffma2_rn(f, fz, sz);
     }
     float tx = __fadd_rn(sx.x, sx.y), ty = __fadd_rn(sy.x, sy.y), tz = __fadd_rn(sz.x, sz.y);
+    float tp = kPot ? __fadd_rn(sp.x, sp.y) : 0.0f;
     if (e < cnt) {
         const uint4 s = ch[e];
         const float fx = (float)(int)(s.x - xi);
@@ -244,13 +269,16 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
         if (kSplit) m = (r2 < rc2) ? m : 0.0f;
         const float rinv = rsqrt_ftz(r2);
         float mS = m;
+        float mP = m;
         if (kSplit) {
             const float us = (r2 * rinv) * p.inv_2rs;
             const float t = rcp_ftz(fmaf(kAsP, us, 1.0f));
             const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, kAs5, kAs4), kAs3), kAs2), kAs1);
             const float ex = ex2_ftz(r2 * p.kexp);
             mS = m * (ex * fmaf(kTwoOverSqrtPi, us, poly));
+            if (kPot) mP = m * (ex * poly);
         }
+        if (kPot) tp = fmaf(mP, rinv, tp);
         const float f = mS * (rinv * (rinv * rinv));
         tx = fmaf(f, fx, tx);
         ty = fmaf(f, fy, ty);
@@ -259,6 +287,7 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
     ax = tx;
     ay = ty;
     az = tz;
+    if (kPot) ap = tp;
 }
 
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
@@ -308,7 +337,7 @@ __device__ __forceinline__ bool open_rel(uint32_t gx, uint32_t gy, uint32_t gz, 
     return __dmul_rn(__dmul_rn(p.G, M), l2) > __dmul_rn(arel, __dmul_rn(d2, d2));
 }
 
-template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti>
+template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot = false>
 __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -382,6 +411,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         int64_t rounds = 0;
         uint32_t cnt_pp = 0, cnt_pn = 0;
         Acc acc;
+        float psum = 0.f, pcomp = 0.f;   // potential total (kPot), compensated
         bool overflow = false;
 
         while (sp > 0) {
@@ -517,17 +547,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             const int nfar = __popc(bfar), nnear = __popc(bnear);
             if (cf + nfar > kChunk) {
                 __syncwarp();
-                float tx = 0.f, ty = 0.f, tz = 0.f;
-                eval_far<kSplit>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz);
+                float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+                eval_far<kSplit, kPot>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
                 acc.add(tx, ty, tz);
+                if (kPot) kahan_add(psum, pcomp, tp);
                 cf = 0;
                 __syncwarp();
             }
             if (cn + nnear > kNearChunk) {
                 __syncwarp();
-                float tx = 0.f, ty = 0.f, tz = 0.f;
-                eval_chunk<kSplit, true>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz);
+                float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+                eval_chunk<kSplit, true, kPot>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
                 acc.add(tx, ty, tz);
+                if (kPot) kahan_add(psum, pcomp, tp);
                 cn = 0;
                 __syncwarp();
             }
@@ -561,21 +593,25 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
         }
         __syncwarp();
         {
-            float tx = 0.f, ty = 0.f, tz = 0.f;
-            eval_far<kSplit>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz);
+            float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+            eval_far<kSplit, kPot>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
             acc.add(tx, ty, tz);
-            tx = ty = tz = 0.f;
-            eval_chunk<kSplit, true>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz);
+            if (kPot) kahan_add(psum, pcomp, tp);
+            tx = ty = tz = tp = 0.f;
+            eval_chunk<kSplit, true, kPot>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
             acc.add(tx, ty, tz);
+            if (kPot) kahan_add(psum, pcomp, tp);
         }
         __syncwarp();
         float vx = __fsub_rn(acc.sx, acc.kx), vy = __fsub_rn(acc.sy, acc.ky),
               vz = __fsub_rn(acc.sz, acc.kz);
+        float vp = kPot ? __fsub_rn(psum, pcomp) : 0.f;
         // replicas of a target: fixed-order pairwise sums
         for (int o = P; o < 32; o <<= 1) {
             vx = __fadd_rn(vx, __shfl_xor_sync(FULL, vx, o));
             vy = __fadd_rn(vy, __shfl_xor_sync(FULL, vy, o));
             vz = __fadd_rn(vz, __shfl_xor_sync(FULL, vz, o));
+            if (kPot) vp = __fadd_rn(vp, __shfl_xor_sync(FULL, vp, o));
         }
         if (active && rep == 0) {
             T.acc[i] = vx * p.out_scale;
@@ -583,6 +619,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             T.acc[2 * T.n + i] = vz * p.out_scale;
             T.npp[i] = cnt_pp - 1u;
             T.npn[i] = cnt_pn;
+            if (kPot) T.pot[i] = -vp * p.pot_scale;
         }
         if (lane == 0) {
             T.gcost[g] = cnt_pp + cnt_pn;
@@ -591,15 +628,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
     }
 }
 
-template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti>
+template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot = false>
 void launch_walk_t(const WalkArgs &a, int64_t nitems, cudaStream_t s, int sms) {
     const size_t smem = kWarps * (kStackCap * sizeof(uint2) + (kChunk + kNearChunk) * sizeof(uint4));
     static bool attr = false;
     static int per_sm = 1;
     if (!attr) {
-        cudaFuncSetAttribute(k_walk<kOpen, kSplit, kDump, kRefit, kMulti>,
+        cudaFuncSetAttribute(k_walk<kOpen, kSplit, kDump, kRefit, kMulti, kPot>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<kOpen, kSplit, kDump, kRefit, kMulti>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<kOpen, kSplit, kDump, kRefit, kMulti, kPot>,
                                                       kWarps * 32, smem);
         if (per_sm < 1) per_sm = 1;
         attr = true;
@@ -608,13 +645,17 @@ void launch_walk_t(const WalkArgs &a, int64_t nitems, cudaStream_t s, int sms) {
     int64_t grid = (int64_t)sms * per_sm;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    k_walk<kOpen, kSplit, kDump, kRefit, kMulti><<<(unsigned)grid, kWarps * 32, smem, s>>>(a); note_launch();
+    k_walk<kOpen, kSplit, kDump, kRefit, kMulti, kPot><<<(unsigned)grid, kWarps * 32, smem, s>>>(a); note_launch();
 }
 
 template <int kOpen, bool kSplit>
-void launch_walk(const WalkArgs &a, bool dump, bool refit, bool multi, int64_t nitems,
+void launch_walk(const WalkArgs &a, bool dump, bool refit, bool multi, bool pot, int64_t nitems,
                  cudaStream_t s, int sms) {
-    if (multi) {
+    if (pot) {
+        // the potential is computed on single trees without list dumps
+        if (refit) launch_walk_t<kOpen, kSplit, false, true, false, true>(a, nitems, s, sms);
+        else launch_walk_t<kOpen, kSplit, false, false, false, true>(a, nitems, s, sms);
+    } else if (multi) {
         if (refit) launch_walk_t<kOpen, kSplit, false, true, true>(a, nitems, s, sms);
         else launch_walk_t<kOpen, kSplit, false, false, true>(a, nitems, s, sms);
     } else if (dump) {
@@ -651,19 +692,19 @@ __global__ void k_item_keys(int64_t nitems, int64_t ntrees, const uint64_t *__re
 }
 
 template <int kOpen>
-void dispatch(const WalkArgs &a, bool split, bool dump, bool refit, bool multi, int64_t nitems,
-              cudaStream_t s, int sms) {
-    if (split) launch_walk<kOpen, true>(a, dump, refit, multi, nitems, s, sms);
-    else launch_walk<kOpen, false>(a, dump, refit, multi, nitems, s, sms);
+void dispatch(const WalkArgs &a, bool split, bool dump, bool refit, bool multi, bool pot,
+              int64_t nitems, cudaStream_t s, int sms) {
+    if (split) launch_walk<kOpen, true>(a, dump, refit, multi, pot, nitems, s, sms);
+    else launch_walk<kOpen, false>(a, dump, refit, multi, pot, nitems, s, sms);
 }
 
 void launch(const WalkArgs &a, int opening, bool split, bool dump, bool refit, bool multi,
-            int64_t nitems, cudaStream_t s) {
+            int64_t nitems, cudaStream_t s, bool pot = false) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (opening == OG_OPEN_BH) dispatch<OG_OPEN_BH>(a, split, dump, refit, multi, nitems, s, sms);
-    else dispatch<OG_OPEN_REL>(a, split, dump, refit, multi, nitems, s, sms);
+    if (opening == OG_OPEN_BH) dispatch<OG_OPEN_BH>(a, split, dump, refit, multi, pot, nitems, s, sms);
+    else dispatch<OG_OPEN_REL>(a, split, dump, refit, multi, pot, nitems, s, sms);
 }
 
 // Per-box parameters of a pass (uploaded) and the tree's view.  The first
@@ -758,6 +799,7 @@ WalkParams make_walk_params(const og_params &p, int opening, double theta) {
     const double hn = hg * (1.0 + 1.0 / 256.0) + 2.0;
     w.hnear2 = hg > 0.0 ? (unsigned long long)(hn * hn) : 1ull;
     w.out_scale = (float)(p.G * (two32 / p.box) * (two32 / p.box));
+    w.pot_scale = (float)(p.G * (two32 / p.box));
     return w;
 }
 
@@ -802,7 +844,7 @@ static og_status grow_lists(og_tree *t, int64_t need) {
 
 og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
                     float *acc_sorted, float *ms_out, bool use_order, const uint32_t *subset,
-                    int64_t nsubset) {
+                    int64_t nsubset, float *pot_sorted) {
     cudaStream_t s = t->ctx->stream;
     WalkArgs a{};
     WalkParams wp;
@@ -840,7 +882,9 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, s);
-        launch(a, opening, wp.split, wp.dump, t->refit, false, a.tree0.ngroups, s);
+        a.tree0.pot = pot_sorted;
+        launch(a, opening, wp.split, wp.dump && !pot_sorted, t->refit, false, a.tree0.ngroups, s,
+               pot_sorted != nullptr);
         cudaEventRecord(e1, s);
         st = finish_pass(t->ctx, e0, e1, ms_out, h);
         if (st) break;

@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -122,6 +123,8 @@ def lib():
         L.og_serve_request_bytes.argtypes = [i64]
         L.og_serve_request_bytes.restype = C.c_size_t
         L.og_sort_keys_noalloc.restype = C.c_int
+        L.og_tree_force_pot.argtypes = [P, P, P, P, P, P]
+        L.og_tree_force_pot.restype = C.c_int
         L.og_kdk_run.argtypes = [P, i64, P, P, P, C.POINTER(og_params), C.POINTER(og_kdk_params), P, P,
                                  C.POINTER(og_kdk_stats)]
         L.og_kdk_run.restype = C.c_int
@@ -254,6 +257,21 @@ def og_tree_force(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
         pp = None if n_pp is None else _host_ptr(n_pp, np.uint32)
         np_ = None if n_pn is None else _host_ptr(n_pn, np.uint32)
     _check(lib().og_tree_force(tree, op, ap, pp, np_))
+
+
+def og_tree_force_pot(tree, acc, pot, a_old=None, n_pp=None, n_pn=None) -> None:
+    """og_tree_force plus the short-range potential (pot: float32 [N])."""
+    if _is_torch_cuda(acc):
+        ap, pp_ = _dev_ptr(acc, "float32"), _dev_ptr(pot, "float32")
+        op = None if a_old is None else _dev_ptr(a_old, "float32")
+        cp = None if n_pp is None else _dev_ptr(n_pp, "int32")
+        np_ = None if n_pn is None else _dev_ptr(n_pn, "int32")
+    else:
+        ap, pp_ = _host_ptr(acc, np.float32, (3,)), _host_ptr(pot, np.float32)
+        op = None if a_old is None else _host_ptr(a_old, np.float32, (3,))
+        cp = None if n_pp is None else _host_ptr(n_pp, np.uint32)
+        np_ = None if n_pn is None else _host_ptr(n_pn, np.uint32)
+    _check(lib().og_tree_force_pot(tree, op, ap, pp_, cp, np_))
 
 
 def og_tree_force_active(tree, active, acc, a_old=None, n_pp=None, n_pn=None) -> int:
@@ -445,9 +463,12 @@ def og_tree_refit(tree, pos) -> None:
 class Context:
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
         self.h = og_create(device, hbm_budget_bytes)
+        self._trees = weakref.WeakSet()
 
     def close(self):
         if self.h is not None:
+            for t in list(self._trees):      # a tree must not outlive its context
+                t.free()
             og_destroy(self.h)
             self.h = None
 
@@ -471,6 +492,7 @@ class Tree:
         self.ctx = ctx
         self.n = int(pos.shape[0])
         self.h = og_tree_build(ctx.h, pos, mass, params)
+        ctx._trees.add(self)
 
     def force(self, a_old=None, counts: bool = True):
         acc = np.zeros((self.n, 3), dtype=np.float32)
@@ -479,6 +501,16 @@ class Tree:
         ao = None if a_old is None else np.ascontiguousarray(a_old, dtype=np.float32)
         og_tree_force(self.h, acc, ao, npp, npn)
         return acc, npp, npn
+
+    def force_pot(self, a_old=None):
+        """(acc, n_pp, n_pn, pot) of one force call with the potential output."""
+        acc = np.zeros((self.n, 3), dtype=np.float32)
+        pot = np.zeros(self.n, dtype=np.float32)
+        npp = np.zeros(self.n, dtype=np.uint32)
+        npn = np.zeros(self.n, dtype=np.uint32)
+        ao = None if a_old is None else np.ascontiguousarray(a_old, dtype=np.float32)
+        og_tree_force_pot(self.h, acc, pot, ao, npp, npn)
+        return acc, npp, npn, pot
 
     def refit(self, pos) -> None:
         og_tree_refit(self.h, np.ascontiguousarray(pos, dtype=np.float64) if not _is_torch_cuda(pos) else pos)
@@ -491,7 +523,8 @@ class Tree:
 
     def free(self):
         if self.h is not None:
-            og_tree_free(self.h)
+            if self.ctx.h is not None:       # else og_destroy has freed it already
+                og_tree_free(self.h)
             self.h = None
 
     def __del__(self):
