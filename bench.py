@@ -263,7 +263,7 @@ def batched_bench(og, ctx, torch, dev, stream, nboxes, steps):
             "same_interactions": int(inter_pb) == int(info["interactions"])}
 
 
-def kdk_bench(og, ctx, n=262144, max_bin=6, dt_max=0.02):
+def kdk_bench(og, ctx, n=2097152, max_bin=6, dt_max=0.02, rebuild_every=8):
     """Individual power-of-two time steps against global stepping.  A
     halo-clustered system (the 2.1M generator at n particles, velocities
     Gaussian 1e-3 box per unit time) is integrated over one maximum step with
@@ -276,22 +276,26 @@ def kdk_bench(og, ctx, n=262144, max_bin=6, dt_max=0.02):
     p1, v1 = pos.copy(), vel.copy()
     t0 = time.perf_counter()
     _, bins, st = og.og_kdk_run(ctx.h, p1, v1, mass, prm, dt_max=dt_max, eta=0.05,
-                                max_bin=max_bin, nsteps=1, rebuild_every=4)
+                                max_bin=max_bin, nsteps=1, rebuild_every=rebuild_every)
     t_ind = time.perf_counter() - t0
     bmax = int(bins.max())
     p2, v2 = pos.copy(), vel.copy()
     t0 = time.perf_counter()
     _, _, sg = og.og_kdk_run(ctx.h, p2, v2, mass, prm, dt_max=dt_max / (1 << bmax), eta=0.05,
-                             max_bin=0, nsteps=1 << bmax, rebuild_every=4)
+                             max_bin=0, nsteps=1 << bmax, rebuild_every=rebuild_every)
     t_glob = time.perf_counter() - t0
     return {"workload": f"{n} particles, halo-clustered, one maximum step dt_max={dt_max}, "
-                        f"max_bin={max_bin}, BH theta 0.5, rebuild every 4 ticks",
+                        f"max_bin={max_bin}, BH theta 0.5, rebuild every {rebuild_every} ticks",
             "bins_used": sorted(int(b) for b in np.unique(bins)),
-            "individual": {"ticks": st["ticks"], "forces": st["forces"], "seconds": t_ind,
+            "individual": {"ticks": st["ticks"], "forces": st["forces"],
+                           "interactions": st["interactions"], "seconds": t_ind,
                            "forces_per_s": st["forces"] / t_ind, "device_ms": st["ms"]},
-            "global_finest": {"ticks": sg["ticks"], "forces": sg["forces"], "seconds": t_glob,
-                              "forces_per_s": sg["forces"] / t_glob},
-            "force_ratio": sg["forces"] / st["forces"], "speedup": t_glob / t_ind}
+            "global_finest": {"ticks": sg["ticks"], "forces": sg["forces"],
+                              "interactions": sg["interactions"], "seconds": t_glob,
+                              "forces_per_s": sg["forces"] / t_glob, "device_ms": sg["ms"]},
+            "force_ratio": sg["forces"] / st["forces"],
+            "interaction_ratio": sg["interactions"] / max(st["interactions"], 1),
+            "speedup": t_glob / t_ind}
 
 
 def served_bench(og, torch, dev, rates=(10.0, 30.0, 100.0), seconds=6.0, pool_size=16):
