@@ -40,15 +40,23 @@ FLOPS_PER_INTERACTION = 38
 FP32_LANES_PER_SM = 128
 
 
-WALK_SOURCES = ("paper_2609_17658_gb300/csrc/og_walk.cu", "paper_2609_17658_gb300/csrc/og_internal.h")
+WALK_SOURCE = "paper_2609_17658_gb300/csrc/og_walk.cu"
+WALK_TYPES = ("CRec", "CExt", "WalkParams")     # what the walk reads from og_internal.h
 
 
 def walk_source_hash():
+    """sha256 over the walk's source and the definitions of the structures it
+    reads (the rest of the internal header does not reach the kernel)."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    for f in WALK_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, WALK_SOURCE), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2609_17658_gb300/csrc/og_internal.h")) as fh:
+        hdr = fh.read()
+    for name in WALK_TYPES:
+        m = re.search(r"struct (?:__align__\(\d+\) )?%s \{.*?\n\};" % name, hdr, re.S)
+        h.update((m.group(0) if m else name).encode())
     return h.hexdigest()
 
 

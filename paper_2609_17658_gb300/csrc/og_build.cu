@@ -63,13 +63,48 @@ __device__ __forceinline__ int digit_at(uint64_t key, int lev) {
 // floor(t * 2^32) mod 2^32: t * 2^32 is an exact scaling and, for |t| < 2^31,
 // fits a signed 64-bit integer after the round-down conversion.  When L is a
 // power of two, x * (1/L) equals the correctly rounded quotient exactly.
+// floor(v * 2^s) mod 2^32 for a finite v, from the bits of v: |v| = M 2^e with
+// an integer mantissa M, so |v| 2^s = M 2^(e + s) is a shift of M.  Negative v:
+// floor(-a) = -(floor(a) + [a not an integer]).  Integer operations only (the
+// FP64 rate of the GPU is 1/64 of its FP32 rate), except for a negative v of
+// magnitude below one grid unit: there the FP64 quotient v / L the reading
+// starts from may underflow to -0 (then 0, else -1), so that product decides.
+__device__ __forceinline__ uint32_t fixed_shift(double v, int s, double inv_box) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7ffu);
+    unsigned long long M = b & 0xfffffffffffffull;
+    int e = -1074;                                   // subnormal
+    if (E != 0) {
+        M |= 1ull << 52;
+        e = E - 1075;
+    }
+    if (M == 0) return 0u;                           // +0 and -0
+    const int sh = e + s;
+    uint32_t mag = 0;
+    bool frac = false;
+    if (sh >= 32) {
+        mag = 0;                                     // a multiple of 2^32
+    } else if (sh >= 0) {
+        mag = (uint32_t)(M << sh);                   // the low 32 bits survive the wrap
+    } else if (sh > -64) {
+        mag = (uint32_t)(M >> -sh);
+        frac = (M & ((1ull << -sh) - 1ull)) != 0ull;
+    } else {
+        frac = true;                                 // 0 < a < 1
+    }
+    if (!(b >> 63)) return mag;
+    if (mag == 0u && frac) return (v * inv_box == 0.0) ? 0u : 0xffffffffu;
+    return 0u - (mag + (frac ? 1u : 0u));
+}
+
 __device__ __forceinline__ uint32_t quantize(double v, double box, double inv_box, bool pow2,
-                                             uint32_t *status) {
+                                             int shift, uint32_t *status) {
     if (!isfinite(v)) {
         atomicOr(status, ST_BAD_INPUT);
         return 0;
     }
-    const double t = pow2 ? v * inv_box : __ddiv_rn(v, box);
+    if (pow2) return fixed_shift(v, shift, inv_box);
+    const double t = __ddiv_rn(v, box);
     if (fabs(t) < 2147483648.0) return (uint32_t)(unsigned long long)__double2ll_rd(t * 4294967296.0);
     const double f = t - floor(t);  // exact for |t| >= 1
     return (uint32_t)floor(f * 4294967296.0);
@@ -97,9 +132,9 @@ __global__ void k_quantize_keys(const double *__restrict__ pos, const double *__
     const SegGeom g = geom[pseg ? pseg[i] : 0];
     const double box = g.box, inv_box = g.inv_box;
     const bool pow2 = g.pow2 != 0;
-    uint32_t x = quantize(pos[3 * i + 0], box, inv_box, pow2, status);
-    uint32_t y = quantize(pos[3 * i + 1], box, inv_box, pow2, status);
-    uint32_t z = quantize(pos[3 * i + 2], box, inv_box, pow2, status);
+    uint32_t x = quantize(pos[3 * i + 0], box, inv_box, pow2, g.shift, status);
+    uint32_t y = quantize(pos[3 * i + 1], box, inv_box, pow2, g.shift, status);
+    uint32_t z = quantize(pos[3 * i + 2], box, inv_box, pow2, g.shift, status);
     if (mass) {  // a refit passes no masses (they do not change)
         const double m = mass[i];
         if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
@@ -432,7 +467,7 @@ __global__ void __launch_bounds__(kT) k_moments_level(
     const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
     const uint32_t *__restrict__ child, const uint32_t *__restrict__ px,
     const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
-    const double *__restrict__ pm64, double *nM, double *nS, uint32_t *ncom, int64_t nchild,
+    const double *__restrict__ pm64, NodeMom *nmom, uint32_t *ncom, int64_t nchild,
     uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cnt) return;
@@ -514,17 +549,15 @@ __global__ void __launch_bounds__(kT) k_moments_level(
                                 __dmul_rn(mq, (double)pz[item])};
                 } else {
                     const int64_t j = item - n;
-                    sl[sidx] = {nM[j], nS[3 * j + 0], nS[3 * j + 1], nS[3 * j + 2]};
+                    const NodeMom q = nmom[j];
+                    sl[sidx] = {q.M, q.Sx, q.Sy, q.Sz};
                 }
             }
         }
         tot = slot_add(slot_add(slot_add(sl[0], sl[1]), slot_add(sl[2], sl[3])),
                        slot_add(slot_add(sl[4], sl[5]), slot_add(sl[6], sl[7])));
     }
-    nM[node] = tot.M;
-    nS[3 * node + 0] = tot.x;
-    nS[3 * node + 1] = tot.y;
-    nS[3 * node + 2] = tot.z;
+    nmom[node] = NodeMom{tot.M, tot.x, tot.y, tot.z};
     uint32_t c[3];
     if (tot.M > 0.0) {
         c[0] = (uint32_t)rint(__ddiv_rn(tot.x, tot.M));
@@ -662,7 +695,7 @@ __global__ void k_records(int64_t n, int64_t nchild, const uint32_t *__restrict_
                           const uint32_t *__restrict__ pz, const float *__restrict__ pm32,
                           const double *__restrict__ pm64, const uint8_t *__restrict__ nlev,
                           const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ nccnt,
-                          const double *__restrict__ nM, const uint32_t *__restrict__ ncom,
+                          const NodeMom *__restrict__ nmom, const uint32_t *__restrict__ ncom,
                           CRec *crec, uint32_t *status) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nchild) return;
@@ -681,7 +714,7 @@ __global__ void k_records(int64_t n, int64_t nchild, const uint32_t *__restrict_
         r.x = ncom[3 * j + 0];
         r.y = ncom[3 * j + 1];
         r.z = ncom[3 * j + 2];
-        r.M = nM[j];
+        r.M = nmom[j].M;
         r.m = __double2float_rn(r.M);
         r.info = (1u << 31) | ((uint32_t)nlev[j] << 26) | (nccnt[j] & 0x3ffffffu);
         r.ref = ncbeg[j];
@@ -720,7 +753,7 @@ static size_t tree_bytes(int64_t n, int64_t B) {
     auto add = [&](size_t sz, int64_t cnt) { b += ((size_t)(cnt > 0 ? cnt : 1) * sz + 255) & ~(size_t)255; };
     add(8, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n); add(8, n); add(4, n);  // particles
     add(1, m); add(4, m); add(4, m); add(4, m); add(4, m); add(4, m);               // nlev..npos
-    add(4, m); add(4, m); add(4, m); add(8, m); add(8, 3 * m); add(4, 3 * m);       // npar.. ncom
+    add(4, m); add(4, m); add(4, m); add(32, m); add(4, 3 * m);                     // npar.. ncom
     add(4, n); add(4, n);                                                           // pnext, owner
     add(4, c); add(32, c);                                                          // child, crec
     add(4, n); add(4, n); add(4, 6 * n); add(4, n); add(4, n); add(4, n);           // groups
@@ -747,7 +780,7 @@ static void moments_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
         if (cnt == 0) continue;
         k_moments_level<<<nblk(cnt), kT, 0, s>>>(
             n, m, l, t->lnodes + offs[l], cnt, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child,
-            t->px, t->py, t->pz, t->pm64, t->nM, t->nS, t->ncom, t->nchild, t->ctx->d_status,
+            t->px, t->py, t->pz, t->pm64, t->nmom, t->ncom, t->nchild, t->ctx->d_status,
             t->norg, ext_s, ext_l); note_launch();
     }
 }
@@ -809,7 +842,7 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
     k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
                                                 t->pz, t->sseg, t->gbox, t->gseg); note_launch();
     k_records<<<nblk(t->nchild), kT, 0, s>>>(n, t->nchild, t->child, t->px, t->py, t->pz, t->pm32,
-                                             t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nM, t->ncom,
+                                             t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nmom, t->ncom,
                                              t->crec, t->ctx->d_status); note_launch();
     k_ext_records<<<nblk(t->nchild), kT, 0, s>>>(n, t->nchild, t->child, t->next_s, t->next_l,
                                                  t->cext); note_launch();
@@ -859,8 +892,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     t->npar = A.take<int32_t>(mcap);
     t->nnext = A.take<int32_t>(mcap);
     t->nsib = A.take<int32_t>(mcap);
-    t->nM = A.take<double>(mcap);
-    t->nS = A.take<double>(3 * mcap);
+    t->nmom = A.take<NodeMom>(mcap);
     t->ncom = A.take<uint32_t>(3 * mcap);
     t->pnext = A.take<int32_t>(n);
     t->owner = A.take<uint32_t>(n);
@@ -892,6 +924,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
             hg[b].box = t->seg_prm[b].box;
             hg[b].inv_box = 1.0 / t->seg_prm[b].box;
             hg[b].pow2 = std::frexp(t->seg_prm[b].box, &e2) == 0.5 ? 1 : 0;
+            hg[b].shift = 33 - e2;   // box = 2^(e2 - 1): x / box * 2^32 = x * 2^(33 - e2)
         }
         cudaMemcpyAsync(t->seg_off, t->h_seg_off.data(), (B + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(t->geom, hg.data(), B * sizeof(SegGeom), cudaMemcpyHostToDevice, s);
@@ -1040,7 +1073,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
                                                 t->pz, t->sseg, t->gbox, t->gseg); note_launch();
     k_records<<<nblk(nchild), kT, 0, s>>>(n, nchild, t->child, t->px, t->py, t->pz, t->pm32,
-                                          t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nM, t->ncom,
+                                          t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nmom, t->ncom,
                                           t->crec, t->ctx->d_status); note_launch();
     cudaEventRecord(e1, s);
     cudaFreeAsync(scratch, s);

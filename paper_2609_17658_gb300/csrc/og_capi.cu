@@ -687,7 +687,7 @@ og_status og_tree_export(const og_tree *t, int field, void *dst, size_t bytes) {
     case OG_F_CBEG: src = t->ncbeg; need = m * 4; break;
     case OG_F_CCNT: src = t->nccnt; need = m * 4; break;
     case OG_F_CHILD: src = t->child; need = c * 4; break;
-    case OG_F_MASS: src = t->nM; need = m * 8; break;
+    case OG_F_MASS: src = t->nmom; need = m * 8; break;
     case OG_F_COM: src = t->ncom; need = 3 * m * 4; break;
     case OG_F_NEXTNODE: src = t->nnext; need = m * 4; break;
     case OG_F_SIBLING: src = t->nsib; need = m * 4; break;
@@ -710,6 +710,10 @@ og_status og_tree_export(const og_tree *t, int field, void *dst, size_t bytes) {
         char *d = static_cast<char *>(dst);
         cudaMemcpyAsync(d, t->next_s, 3 * m * 4, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(d + 3 * m * 4, t->next_l, 3 * m * 4, cudaMemcpyDeviceToHost, s);
+    } else if (field == OG_F_MASS) {
+        // the masses out of the nodes' 32-byte moment records
+        cudaMemcpy2DAsync(dst, sizeof(double), &t->nmom[0].M, sizeof(NodeMom), sizeof(double), m,
+                          cudaMemcpyDeviceToHost, s);
     } else if (field == OG_F_SPOS) {
         char *d = static_cast<char *>(dst);
         cudaMemcpyAsync(d, t->px, n * 4, cudaMemcpyDeviceToHost, s);

@@ -4,7 +4,8 @@
 //   skey[n] u64, perm[n] u32, px/py/pz[n] u32 fixed point, pm32[n] f32, pm64[n] f64
 //   nodes (id 0 = root; others in the order of their first split):
 //     nlev[m] u8, nbeg/nend[m] u32, npar[m] i32, ncbeg/nccnt[m] u32, npos[m] u32
-//     nM[m] f64, nS[3m] f64 (sum m x), ncom[3m] u32, nnext/nsib[m] i32
+//     nmom[m] {M, sum m x, sum m y, sum m z} f64 (one 32-byte record per node),
+//     ncom[3m] u32, nnext/nsib[m] i32
 //   child[c] u32 unified refs (particle < n, node + n), crec[c] 32-byte walk records
 //   groups: gbeg/gend[g] u32, gbox[6g] u32
 #pragma once
@@ -51,7 +52,13 @@ static_assert(sizeof(CExt) == 32, "CExt must be 32 bytes");
 struct SegGeom {
     double box, inv_box;
     int pow2;        // box is a power of two: x / box == x * inv_box exactly
-    int pad;
+    int shift;       // with pow2: x / box * 2^32 == x * 2^shift
+};
+
+// monopole moments of a node: one 32-byte record, so that a parent reading a
+// child node touches one sector
+struct __align__(32) NodeMom {
+    double M, Sx, Sy, Sz;
 };
 
 struct WalkParams;
@@ -95,7 +102,7 @@ struct og_tree {
     uint32_t *nbeg = nullptr, *nend = nullptr, *ncbeg = nullptr, *nccnt = nullptr;
     uint32_t *npos = nullptr;
     int32_t *npar = nullptr, *nnext = nullptr, *nsib = nullptr;
-    double *nM = nullptr, *nS = nullptr;
+    og::NodeMom *nmom = nullptr;      // mass and sum of m x per node
     uint32_t *ncom = nullptr;
     int32_t *pnext = nullptr;
     uint32_t *owner = nullptr;        // node a particle hangs from

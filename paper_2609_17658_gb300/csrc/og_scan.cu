@@ -1,4 +1,5 @@
-// og_scan.cu -- device-wide prefix scans (tile reduce, scan of tile totals, downsweep).
+// og_scan.cu -- device-wide prefix scans (tile reduce, then a downsweep in which
+// every tile adds up the totals of the tiles before it).
 //
 // Tiles of 4096 elements: 512 threads x 8 consecutive items, staged through
 // shared memory so that global loads and stores stay coalesced.  Used for
@@ -70,30 +71,19 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_reduce(const uint32_t *__
     if (threadIdx.x == 0) tile_tot[blockIdx.x] = tot;
 }
 
-// exclusive scan of the tile totals in one block, any number of tiles
-template <class Op>
-__global__ void __launch_bounds__(1024) k_tile_scan(uint32_t *tile_tot, int64_t ntiles,
-                                                    uint32_t *d_total) {
-    __shared__ uint32_t s_warp[32];
-    uint32_t carry = Op::id();
-    for (int64_t b = 0; b < ntiles; b += blockDim.x) {
-        int64_t i = b + threadIdx.x;
-        uint32_t v = i < ntiles ? tile_tot[i] : Op::id();
-        uint32_t tot;
-        uint32_t exc = block_exclusive<Op>(v, s_warp, &tot);
-        if (i < ntiles) tile_tot[i] = Op::op(carry, exc);
-        carry = Op::op(carry, tot);
-    }
-    if (threadIdx.x == 0 && d_total) *d_total = carry;
-}
-
 template <class Op, bool kExclusive>
 __global__ void __launch_bounds__(kScanThreads) k_tile_downsweep(const uint32_t *__restrict__ in,
                                                                   uint32_t *out, int64_t n,
-                                                                  const uint32_t *tile_pre) {
+                                                                  const uint32_t *tile_tot,
+                                                                  uint32_t *d_total) {
     __shared__ uint32_t s_items[kScanTile];
     __shared__ uint32_t s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t pre = Op::id();
+    for (int64_t t = threadIdx.x; t < (int64_t)blockIdx.x; t += kScanThreads)
+        pre = Op::op(pre, tile_tot[t]);
+    uint32_t tile_pre;
+    block_exclusive<Op>(pre, s_warp, &tile_pre);
     for (int k = 0; k < kScanItems; ++k) {
         int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
         s_items[k * kScanThreads + threadIdx.x] = i < n ? in[i] : Op::id();
@@ -107,7 +97,8 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_downsweep(const uint32_t 
         acc = Op::op(acc, v[k]);
     }
     uint32_t tot;
-    uint32_t r = Op::op(tile_pre[blockIdx.x], block_exclusive<Op>(acc, s_warp, &tot));
+    uint32_t r = Op::op(tile_pre, block_exclusive<Op>(acc, s_warp, &tot));
+    if (d_total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) *d_total = Op::op(tile_pre, tot);
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         if (kExclusive) {
@@ -134,9 +125,11 @@ void scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, 
     }
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     uint32_t *tile = static_cast<uint32_t *>(scratch);
-    k_tile_reduce<Op><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tile); note_launch();
-    k_tile_scan<Op><<<1, 1024, 0, s>>>(tile, ntiles, d_total); note_launch();
-    k_tile_downsweep<Op, kExclusive><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tile); note_launch();
+    if (ntiles > 1) {
+        k_tile_reduce<Op><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tile); note_launch();
+    }
+    k_tile_downsweep<Op, kExclusive><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tile,
+                                                                             d_total); note_launch();
 }
 
 }  // namespace

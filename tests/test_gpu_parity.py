@@ -213,3 +213,27 @@ def test_fullsize_clustered_sampled(ctx, name, nsample):
     tgt = np.concatenate([perm[gb[g]:ge[g]] for g in sel])
     assert np.array_equal(npp[tgt], rpp[tgt]) and np.array_equal(npn[tgt], rpn[tgt])
     parity.check_accel(acc[tgt], ref[tgt])
+
+
+@pytest.mark.parametrize("box", [1.0, 0.125, 1024.0, 3.0])
+def test_quantization_of_special_values(ctx, box):
+    """Fixed-point positions bit-exact with the oracle for negatives, subnormals,
+    values a rounding away from the box, and large multiples of the box
+    (power-of-two boxes take the integer path, 3.0 the division)."""
+    r = np.random.default_rng(12)
+    v = np.concatenate([
+        r.uniform(-3 * box, 3 * box, 3000),
+        r.standard_normal(1000) * box * 10.0 ** r.integers(-300, 12, 1000),
+        -np.abs(r.standard_normal(200)) * 10.0 ** r.integers(-324, -300, 200),
+        [0.0, -0.0, box, -box, box * (1 - 2 ** -53), -box * 2 ** -40, 5e-324, -5e-324,
+         box * 2 ** 31, -box * 2 ** 31.5, box * (2 ** 32 + 2 ** -33)]])
+    v = v[: (len(v) // 3) * 3]
+    pos = np.ascontiguousarray(v.reshape(-1, 3))
+    n = len(pos)
+    prm = gi.default_params(eps=box * 1e-3, r_s=box * 0.02, box=box)
+    gt = og.Tree(ctx, pos, np.full(n, 1.0 / n), prm)
+    spos = gt.export(og.OG_F_SPOS)
+    perm = gt.export(og.OG_F_PERM)
+    for a in range(3):
+        want = np.array([oracle.quantize1(float(x), box) for x in pos[perm, a]], dtype=np.uint32)
+        assert np.array_equal(spos[a], want)
