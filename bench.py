@@ -528,6 +528,11 @@ def main():
             "frac_at_observed_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 *
                                                    clocks["sm_mhz"] * 1e6 / 1e12)
                                        if clocks.get("sm_mhz") else None)}
+    # the FP32 rate this GPU sustains on independent FMA chains, measured after
+    # the timed region (not a denominator: the peak above is the unit count)
+    fp32 = og.og_measure_fp32_peak(ctx.h)
+    roof["fp32_measured_tflops"] = {"fma": fp32["fma"], "fma2": fp32["fma2"]}
+    roof["frac_of_measured_fma"] = achieved / fp32["fma"] if fp32["fma"] > 0 else None
 
     batched = None
     if not args.no_batched:

@@ -347,6 +347,17 @@ og_status og_tune_save(og_ctx *ctx, const char *path);
  * is not such a record or the file cannot be read. */
 og_status og_tune_load(og_ctx *ctx, const char *path);
 
+/* ---- measured FP32 throughput -------------------------------------------- */
+
+/* The walk is bound by the FP32 ALUs, not by a contraction, so its roofline
+ * is the FP32 fused multiply-add rate of this GPU.  og_measure_fp32_peak runs
+ * independent chains of FP32 FMAs (and of f32x2 FMAs) on every SM at full
+ * occupancy on the context's stream, times them with CUDA events (best of
+ * three after one warm-up round, about 0.1 s in all) and returns the rates in
+ * TFLOP/s (an FMA counts 2 flops, an f32x2 FMA 4).  The rates are at the
+ * clocks the GPU runs at during the call.  OG_ERR_ARG on NULL arguments. */
+og_status og_measure_fp32_peak(og_ctx *ctx, double *tflops_fma, double *tflops_fma2);
+
 /* ---- sort without device allocation ------------------------------------ */
 
 /* Largest n accepted by og_sort_keys_noalloc. */

@@ -133,7 +133,8 @@ def lib():
         L.og_tune_group_max.argtypes = [P, P, P, i64, C.POINTER(og_params), C.POINTER(C.c_int32)]
         L.og_tune_save.argtypes = [P, C.c_char_p]
         L.og_tune_load.argtypes = [P, C.c_char_p]
-        for name in ("og_tune_group_max", "og_tune_save", "og_tune_load"):
+        L.og_measure_fp32_peak.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        for name in ("og_tune_group_max", "og_tune_save", "og_tune_load", "og_measure_fp32_peak"):
             getattr(L, name).restype = C.c_int
         for name in ("og_create", "og_destroy", "og_set_stream", "og_params_default",
                      "og_tree_build", "og_tree_refit", "og_tree_force", "og_tree_info_get",
@@ -242,6 +243,13 @@ def og_tune_save(ctx, path: str) -> None:
 
 def og_tune_load(ctx, path: str) -> None:
     _check(lib().og_tune_load(ctx, os.fsencode(path)))
+
+
+def og_measure_fp32_peak(ctx) -> dict:
+    """Measured FP32 FMA and f32x2 FMA rates of the device, TFLOP/s."""
+    f1, f2 = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().og_measure_fp32_peak(ctx, C.byref(f1), C.byref(f2)))
+    return {"fma": f1.value, "fma2": f2.value}
 
 
 def og_tree_force(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
