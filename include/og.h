@@ -78,8 +78,12 @@ typedef struct {
     int32_t opening;         /* og_open */
     int32_t leaf_max;        /* particles per leaf cell; 1 = one particle per leaf (Sect. 4.1) */
     int32_t group_max;       /* targets per group, 1..32; 0 = measured per kind of input
-                                (og_tune_group_max) */
+                                together with the walk's launch shape (og_tune_walk) */
     int32_t flags;           /* OG_DEVICE_PTRS | OG_DEBUG_DUMP_LISTS */
+    int32_t walk_warps;      /* walk launch shape: warps (one group each) per block, 1..8;
+                                0 = the measured value when group_max = 0, else 4 */
+    int32_t walk_chunk;      /* entries of a warp's shared far-entry chunk, 32..1024;
+                                0 = the measured value when group_max = 0, else 256 */
 } og_params;
 
 typedef struct og_ctx og_ctx;
@@ -99,6 +103,8 @@ typedef struct {
     double  ms_walk;         /* device time of the walk kernels of the last force call (ms) */
     int32_t group_max;       /* the group size the tree was built with (the measured
                                 choice when og_params.group_max was 0) */
+    int32_t walk_warps;      /* the walk launch shape the tree's force calls use */
+    int32_t walk_chunk;
     int32_t pad;
 } og_tree_info;
 
@@ -325,21 +331,31 @@ og_status og_kdk_run(og_ctx *ctx, int64_t n, double *pos, double *vel, const dou
 
 /* The group size G (targets sharing one interaction list, Sect. 3.4 and
  * 19.2: one walk per group of nearby particles) trades list building against
- * evaluation; the paper fixes no value.  og_tune_group_max returns the G in
- * {8, 16, 24, 32} with the shortest walk for inputs of this kind: the key is
- * (floor(log2 n), opening criterion, split on/off).  The first call for a key
- * builds and walks this input once per candidate (both force passes for
- * OG_OPEN_REL), times the walk kernels with CUDA events on the context's
- * stream, and keeps the result in the context; later calls return it at once.
- * og_tree_build with params.group_max = 0 calls it.  pos/mass as in
- * og_tree_build (host or, with OG_DEVICE_PTRS, device); p->group_max is
- * ignored.  Errors as og_tree_build. */
+ * evaluation; the paper fixes no value, nor the walk's launch shape (warps
+ * per block, entries of the shared far-entry chunk).  og_tune_walk measures
+ * all three for inputs of this kind: the key is (floor(log2 n), opening
+ * criterion, split on/off).  The first call for a key builds and walks this
+ * input once per candidate (both force passes for OG_OPEN_REL) and times the
+ * walk kernels with CUDA events on the context's stream: G in {8, 16, 24, 32}
+ * with 4 warps and 256 entries, then 2 and 8 warps at the best G, then 128 and
+ * 512 entries at the best G and warps (coordinate descent, 8 trials).  The
+ * result stays in the context; later calls return it at once.  og_tree_build
+ * with params.group_max = 0 calls it (an explicit walk_warps or walk_chunk
+ * then replaces the measured one).  pos/mass as in og_tree_build (host or,
+ * with OG_DEVICE_PTRS, device); p->group_max, p->walk_warps and p->walk_chunk
+ * are ignored; any output pointer may be NULL.  Errors as og_tree_build. */
+og_status og_tune_walk(og_ctx *ctx, const double *pos, const double *mass, int64_t n,
+                       const og_params *p, int32_t *group_max, int32_t *walk_warps,
+                       int32_t *walk_chunk);
+
+/* og_tune_walk's group size alone. */
 og_status og_tune_group_max(og_ctx *ctx, const double *pos, const double *mass, int64_t n,
                             const og_params *p, int32_t *group_max);
 
-/* Write the context's measured group sizes to `path`, one JSON object per
- * line: {"n_log2": .., "opening": .., "split": .., "group_max": ..,
- * "walk_ms": [t8, t16, t24, t32]}.  OG_ERR_ARG if the file cannot be written. */
+/* Write the context's measured walk configurations to `path`, one JSON
+ * object per line: {"n_log2": .., "opening": .., "split": .., "group_max": ..,
+ * "walk_warps": .., "walk_chunk": .., "walk_ms": [8 trial times]}.
+ * OG_ERR_ARG if the file cannot be written. */
 og_status og_tune_save(og_ctx *ctx, const char *path);
 
 /* Add the records of a file written by og_tune_save to the context (a record

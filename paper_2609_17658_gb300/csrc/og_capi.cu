@@ -173,6 +173,11 @@ og_status validate(const og_params *p, int64_t n) {
     if (!(p->theta_first_pass >= 0.0)) { set_error("theta_first_pass must be >= 0"); return OG_ERR_ARG; }
     if (p->leaf_max != 1) { set_error("leaf_max must be 1 (one particle per leaf cell)"); return OG_ERR_ARG; }
     if (p->group_max < 0 || p->group_max > 32) { set_error("group_max must be in [0, 32]"); return OG_ERR_ARG; }
+    if (p->walk_warps < 0 || p->walk_warps > 8) { set_error("walk_warps must be in [0, 8]"); return OG_ERR_ARG; }
+    if (p->walk_chunk != 0 && (p->walk_chunk < 32 || p->walk_chunk > 1024)) {
+        set_error("walk_chunk must be 0 or in [32, 1024]");
+        return OG_ERR_ARG;
+    }
     return OG_OK;
 }
 
@@ -301,16 +306,21 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
         d_mass = dp + 3 * n;
     }
     if (t->prm.group_max == 0) {
-        // measured choice of the group size for this kind of input (og_tune.cu)
-        int G = 32;
-        st = tuned_group_max(c, d_pos, d_mass, n, t->prm, &G);
+        // measured group size and walk launch shape for this kind of input
+        // (og_tune.cu); explicit launch-shape fields stay as given
+        WalkConfig w{32, kDefaultWalkWarps, kDefaultWalkChunk};
+        st = tuned_walk(c, d_pos, d_mass, n, t->prm, &w);
         if (st) {
             if (staging) cudaFreeAsync(staging, s);
             delete t;
             return st;
         }
-        t->prm.group_max = G;
+        t->prm.group_max = w.group_max;
+        if (t->prm.walk_warps == 0) t->prm.walk_warps = w.warps;
+        if (t->prm.walk_chunk == 0) t->prm.walk_chunk = w.chunk;
     }
+    if (t->prm.walk_warps == 0) t->prm.walk_warps = kDefaultWalkWarps;
+    if (t->prm.walk_chunk == 0) t->prm.walk_chunk = kDefaultWalkChunk;
     t->seg_prm.assign(1, t->prm);
     st = build_tree(t, d_pos, d_mass);
     if (staging) cudaFreeAsync(staging, s);
@@ -562,8 +572,10 @@ og_status og_batch_force(og_ctx *c, int64_t nbox, const og_box *boxes, og_batch_
         if (st) return st;
         if (x.params.opening != p0.opening || (x.params.r_s > 0.0) != (p0.r_s > 0.0) ||
             x.params.group_max != p0.group_max || x.params.flags != p0.flags ||
+            x.params.walk_warps != p0.walk_warps || x.params.walk_chunk != p0.walk_chunk ||
             (x.a_old != nullptr) != (boxes[0].a_old != nullptr)) {
-            set_error("og_batch_force: opening, split on/off, group_max, flags and a_old presence must agree across boxes");
+            set_error("og_batch_force: opening, split on/off, group_max, walk_warps, walk_chunk, "
+                      "flags and a_old presence must agree across boxes");
             return OG_ERR_ARG;
         }
         total += x.n;
@@ -583,6 +595,8 @@ og_status og_batch_force(og_ctx *c, int64_t nbox, const og_box *boxes, og_batch_
     t->ctx = c;
     t->prm = p0;
     if (t->prm.group_max == 0) t->prm.group_max = 32;
+    if (t->prm.walk_warps == 0) t->prm.walk_warps = kDefaultWalkWarps;
+    if (t->prm.walk_chunk == 0) t->prm.walk_chunk = kDefaultWalkChunk;
     t->n = total;
     t->nseg = nbox;
     t->seg_prm.resize((size_t)nbox);
@@ -667,6 +681,8 @@ og_status og_tree_info_get(const og_tree *t, og_tree_info *info) {
     info->ms_force = t->ms_force;
     info->ms_walk = t->ms_walk;
     info->group_max = t->prm.group_max;
+    info->walk_warps = t->prm.walk_warps;
+    info->walk_chunk = t->prm.walk_chunk;
     info->pad = 0;
     return OG_OK;
 }

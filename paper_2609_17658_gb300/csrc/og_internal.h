@@ -152,9 +152,20 @@ og_status check_status(og_ctx *c);
 og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out,
                        const uint32_t *subset = nullptr, int64_t nsubset = 0,
                        float *pot_sorted = nullptr);
-// group size for group_max = 0: measured once per kind of input (og_tune.cu)
-og_status tuned_group_max(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
-                          const og_params &p, int *group_max);
+// default launch shape of the walk (og_params.walk_warps / walk_chunk = 0)
+constexpr int kDefaultWalkWarps = 4;
+constexpr int kDefaultWalkChunk = 256;
+// measured walk configuration for group_max = 0: the group size and the walk's
+// launch shape, once per kind of input (og_tune.cu)
+struct WalkConfig {
+    int group_max, warps, chunk;
+};
+og_status tuned_walk(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
+                     const og_params &p, WalkConfig *out);
+// a walk launch shape the kernel supports: 1..8 warps, 32..1024 chunk entries
+inline bool valid_walk_shape(int warps, int chunk) {
+    return warps >= 1 && warps <= 8 && chunk >= 32 && chunk <= 1024;
+}
 void tune_free(og_ctx *c);
 // count of kernels launched by this library in this process
 void note_launch();

@@ -163,6 +163,9 @@ og_status build_system(Server *S, System *sy, const Worker &w) {
     t->ctx = w.ctx;
     t->prm = sy->prm;
     if (t->prm.group_max == 0) t->prm.group_max = 32;
+    // the engine walks many trees in one launch of the default shape
+    t->prm.walk_warps = kDefaultWalkWarps;
+    t->prm.walk_chunk = kDefaultWalkChunk;
     t->n = sy->n;
     t->nseg = 1;
     t->seg_prm.assign(1, t->prm);

@@ -1,14 +1,19 @@
-// og_tune.cu -- choice of the group size G (targets per walk group).
+// og_tune.cu -- measured choice of the walk configuration: the group size G
+// (targets per walk group) and the walk's launch shape (warps per block,
+// entries of the shared far-entry chunk).
 //
 // The group size trades list building against evaluation: a larger group
 // shares one interaction list among more targets, but its bounding box is
-// larger, so the list is longer for every target.  Which G is fastest depends
-// on the clustering of the input and on N.  For og_params.group_max = 0 the
-// library measures it: the first call for a key (log2 N, opening criterion,
-// split on/off) builds and walks the caller's input once per candidate G,
-// times the walk kernels with CUDA events, and keeps the fastest G in the
-// context.  Later calls with the same key reuse it.  The table can be saved
-// to and loaded from a file of JSON lines, one key per line.
+// larger, so the list is longer for every target.  Warps per block and the
+// chunk length trade occupancy and shared memory against the cost of
+// flushing a chunk.  Which values are fastest depends on the clustering of
+// the input and on N.  For og_params.group_max = 0 the library measures them:
+// the first call for a key (log2 N, opening criterion, split on/off) builds
+// and walks the caller's input once per trial, times the walk kernels with
+// CUDA events, and keeps the fastest configuration in the context (a
+// coordinate descent: G first, then warps, then chunk).  Later calls with the
+// same key reuse it.  The table can be saved to and loaded from a file of
+// JSON lines, one key per line.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -21,7 +26,13 @@
 namespace og {
 namespace {
 
-constexpr int kCandidates[] = {8, 16, 24, 32};
+constexpr int kGroupCandidates[] = {8, 16, 24, 32};
+constexpr int kWarpCandidates[] = {2, 8};       // besides the default 4
+constexpr int kChunkCandidates[] = {128, 512};  // besides the default 256
+constexpr int kTrials = 4 + 2 + 2;   // the three stages of the descent
+static_assert(sizeof(kGroupCandidates) / sizeof(int) + sizeof(kWarpCandidates) / sizeof(int) +
+                      sizeof(kChunkCandidates) / sizeof(int) == kTrials,
+              "one time slot per trial");
 
 struct Key {
     int nlog2, opening, split;
@@ -33,8 +44,8 @@ struct Key {
 };
 
 struct Entry {
-    int group_max;
-    double ms[4];  // walk time per candidate, or 0 when loaded from a file
+    WalkConfig cfg;
+    double ms[kTrials];  // walk time per trial, or 0 when loaded from a file
 };
 
 struct Table {
@@ -53,14 +64,16 @@ Key key_of(int64_t n, const og_params &p) {
     return Key{l, p.opening, p.r_s > 0.0 ? 1 : 0};
 }
 
-// build + force of the caller's input with group size G; the walk time
+// build + force of the caller's input with one configuration; the walk time
 og_status trial(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
-                const og_params &p, int G, float *ms_walk) {
+                const og_params &p, const WalkConfig &w, float *ms_walk) {
     og_tree *t = new (std::nothrow) og_tree();
     if (!t) { set_error("host allocation failed"); return OG_ERR_OOM; }
     t->ctx = c;
     t->prm = p;
-    t->prm.group_max = G;
+    t->prm.group_max = w.group_max;
+    t->prm.walk_warps = w.warps;
+    t->prm.walk_chunk = w.chunk;
     t->prm.flags &= ~OG_DEBUG_DUMP_LISTS;
     t->n = n;
     t->nseg = 1;
@@ -78,8 +91,8 @@ og_status trial(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
 
 }  // namespace
 
-og_status tuned_group_max(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
-                          const og_params &p, int *group_max) {
+og_status tuned_walk(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
+                     const og_params &p, WalkConfig *out) {
     Table *tb = table(c);
     if (!tb) { set_error("host allocation failed"); return OG_ERR_OOM; }
     const Key k = key_of(n, p);
@@ -87,25 +100,36 @@ og_status tuned_group_max(og_ctx *c, const double *d_pos, const double *d_mass, 
         std::lock_guard<std::mutex> lk(tb->mu);
         auto it = tb->map.find(k);
         if (it != tb->map.end()) {
-            *group_max = it->second.group_max;
+            *out = it->second.cfg;
             return OG_OK;
         }
     }
-    Entry best{32, {0, 0, 0, 0}};
+    Entry best{{32, kDefaultWalkWarps, kDefaultWalkChunk}, {}};
     float best_ms = INFINITY;
-    for (int i = 0; i < 4; ++i) {
+    int k_trial = 0;
+    auto run = [&](const WalkConfig &w) -> og_status {
         float ms = 0.0f;
-        og_status st = trial(c, d_pos, d_mass, n, p, kCandidates[i], &ms);
+        og_status st = trial(c, d_pos, d_mass, n, p, w, &ms);
         if (st) return st;
-        best.ms[i] = ms;
+        if (k_trial < kTrials) best.ms[k_trial++] = ms;
         if (ms < best_ms) {
             best_ms = ms;
-            best.group_max = kCandidates[i];
+            best.cfg = w;
         }
-    }
+        return OG_OK;
+    };
+    og_status st = OG_OK;
+    for (int G : kGroupCandidates)
+        if ((st = run({G, kDefaultWalkWarps, kDefaultWalkChunk}))) return st;
+    const int G = best.cfg.group_max;
+    for (int W : kWarpCandidates)
+        if ((st = run({G, W, kDefaultWalkChunk}))) return st;
+    const int W = best.cfg.warps;
+    for (int C : kChunkCandidates)
+        if ((st = run({G, W, C}))) return st;
     std::lock_guard<std::mutex> lk(tb->mu);
     tb->map[k] = best;
-    *group_max = best.group_max;
+    *out = best.cfg;
     return OG_OK;
 }
 
@@ -118,11 +142,14 @@ void tune_free(og_ctx *c) {
 
 extern "C" {
 
-og_status og_tune_group_max(og_ctx *c, const double *pos, const double *mass, int64_t n,
-                            const og_params *p, int32_t *group_max) {
-    if (!c || !pos || !mass || !p || !group_max) { og::set_error("NULL argument"); return OG_ERR_ARG; }
+og_status og_tune_walk(og_ctx *c, const double *pos, const double *mass, int64_t n,
+                       const og_params *p, int32_t *group_max, int32_t *walk_warps,
+                       int32_t *walk_chunk) {
+    if (!c || !pos || !mass || !p) { og::set_error("NULL argument"); return OG_ERR_ARG; }
     og_params q = *p;
     q.group_max = 32;
+    q.walk_warps = 0;
+    q.walk_chunk = 0;
     og_status st = og::validate(&q, n);
     if (st) return st;
     cudaSetDevice(c->device);
@@ -139,12 +166,22 @@ og_status og_tune_group_max(og_ctx *c, const double *pos, const double *mass, in
         d_pos = dp;
         d_mass = dp + 3 * n;
     }
-    int G = 32;
-    st = og::tuned_group_max(c, d_pos, d_mass, n, q, &G);
+    og::WalkConfig w{32, og::kDefaultWalkWarps, og::kDefaultWalkChunk};
+    st = og::tuned_walk(c, d_pos, d_mass, n, q, &w);
     if (staging) cudaFreeAsync(staging, s);
     if (st == OG_OK) st = og::check_status(c);
-    if (st == OG_OK) *group_max = G;
+    if (st == OG_OK) {
+        if (group_max) *group_max = w.group_max;
+        if (walk_warps) *walk_warps = w.warps;
+        if (walk_chunk) *walk_chunk = w.chunk;
+    }
     return st;
+}
+
+og_status og_tune_group_max(og_ctx *c, const double *pos, const double *mass, int64_t n,
+                            const og_params *p, int32_t *group_max) {
+    if (!group_max) { og::set_error("NULL argument"); return OG_ERR_ARG; }
+    return og_tune_walk(c, pos, mass, n, p, group_max, nullptr, nullptr);
 }
 
 og_status og_tune_save(og_ctx *c, const char *path) {
@@ -158,9 +195,11 @@ og_status og_tune_save(og_ctx *c, const char *path) {
         const og::Entry &e = kv.second;
         std::fprintf(f,
                      "{\"n_log2\": %d, \"opening\": %d, \"split\": %d, \"group_max\": %d, "
-                     "\"walk_ms\": [%.6f, %.6f, %.6f, %.6f]}\n",
-                     kv.first.nlog2, kv.first.opening, kv.first.split, e.group_max, e.ms[0],
-                     e.ms[1], e.ms[2], e.ms[3]);
+                     "\"walk_warps\": %d, \"walk_chunk\": %d, "
+                     "\"walk_ms\": [%.6f, %.6f, %.6f, %.6f, %.6f, %.6f, %.6f, %.6f]}\n",
+                     kv.first.nlog2, kv.first.opening, kv.first.split, e.cfg.group_max,
+                     e.cfg.warps, e.cfg.chunk, e.ms[0], e.ms[1], e.ms[2], e.ms[3], e.ms[4],
+                     e.ms[5], e.ms[6], e.ms[7]);
     }
     const bool ok = std::fclose(f) == 0;
     if (!ok) { og::set_error("write to %s failed", path); return OG_ERR_ARG; }
@@ -181,15 +220,20 @@ og_status og_tune_load(og_ctx *c, const char *path) {
         ++lineno;
         if (line[0] == '\n' || line[0] == '\0') continue;
         og::Key k{};
-        og::Entry e{32, {0, 0, 0, 0}};
-        if (std::sscanf(line, " {\"n_log2\": %d, \"opening\": %d, \"split\": %d, \"group_max\": %d",
-                        &k.nlog2, &k.opening, &k.split, &e.group_max) != 4 ||
-            e.group_max < 1 || e.group_max > 32 || k.nlog2 < 0 || k.nlog2 > 62) {
+        og::Entry e{{32, og::kDefaultWalkWarps, og::kDefaultWalkChunk}, {}};
+        if (std::sscanf(line,
+                        " {\"n_log2\": %d, \"opening\": %d, \"split\": %d, \"group_max\": %d, "
+                        "\"walk_warps\": %d, \"walk_chunk\": %d",
+                        &k.nlog2, &k.opening, &k.split, &e.cfg.group_max, &e.cfg.warps,
+                        &e.cfg.chunk) != 6 ||
+            e.cfg.group_max < 1 || e.cfg.group_max > 32 || k.nlog2 < 0 || k.nlog2 > 62 ||
+            !og::valid_walk_shape(e.cfg.warps, e.cfg.chunk)) {
             og::set_error("%s:%d: not a tuning record", path, lineno);
             st = OG_ERR_ARG;
             break;
         }
-        std::sscanf(line, "%*[^[][%lf, %lf, %lf, %lf]", &e.ms[0], &e.ms[1], &e.ms[2], &e.ms[3]);
+        std::sscanf(line, "%*[^[][%lf, %lf, %lf, %lf, %lf, %lf, %lf, %lf]", &e.ms[0], &e.ms[1],
+                    &e.ms[2], &e.ms[3], &e.ms[4], &e.ms[5], &e.ms[6], &e.ms[7]);
         got[k] = e;
     }
     std::fclose(f);

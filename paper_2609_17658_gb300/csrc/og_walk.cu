@@ -34,6 +34,9 @@
 // Work distribution: persistent blocks; warps take groups from a global
 // atomic counter, in decreasing order of the previous pass's list length
 // when that is known (longest first shortens the tail of the launch).
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "og_internal.h"
@@ -41,10 +44,20 @@
 namespace og {
 namespace {
 
-constexpr int kWarps = 4;          // warps per block
+constexpr int kMaxWarps = 8;       // warps per block: 1..kMaxWarps, chosen at launch
 constexpr int kStackCap = 768;     // ranges per warp stack
-constexpr int kChunk = 256;        // far entries per shared chunk
 constexpr int kNearChunk = 64;     // near entries per shared chunk
+// The far chunk holds `chunk` entries (WalkArgs::chunk, chosen at launch,
+// kMinChunk..kMaxChunk): a round adds at most 32, so a flushed chunk always
+// has room for the next round.
+constexpr int kMinChunk = 32, kMaxChunk = 1024;
+
+// shared memory of one warp: its stack, near chunk and far chunk
+__host__ __device__ constexpr size_t warp_smem(int chunk) {
+    return kStackCap * sizeof(uint2) + ((size_t)chunk + kNearChunk) * sizeof(uint4);
+}
+constexpr size_t kMaxBlockSmem = kMaxWarps * warp_smem(kMaxChunk);
+static_assert(kMaxBlockSmem <= 227 * 1024, "walk block exceeds the shared memory of an SM");
 
 // Abramowitz & Stegun 7.1.26: erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
 // t = 1 / (1 + p x), |error| <= 1.5e-7 for x >= 0.
@@ -88,6 +101,7 @@ struct WalkArgs {
     unsigned long long *list_cursor;
     int64_t list_cap;
     unsigned long long *work;     // item counter
+    int warps, chunk;             // launch shape: warps per block, far-chunk entries
     unsigned long long *inter;    // interactions evaluated
     uint32_t *status;
 };
@@ -337,14 +351,23 @@ __device__ __forceinline__ bool open_rel(uint32_t gx, uint32_t gy, uint32_t gz, 
     return __dmul_rn(__dmul_rn(p.G, M), l2) > __dmul_rn(arel, __dmul_rn(d2, d2));
 }
 
+// Registers: at most 96 per thread (64 KB / (96 x 128) gives 5 blocks of 4
+// warps per SM, as many as their shared memory allows), 128 with the
+// potential output; a block of kMaxWarps warps fits either way.
 template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot = false>
-__global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
+__global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a);
+
+template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot>
+__global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    // layout: per warp, its stack, near chunk and far chunk (warp_smem bytes);
+    // blockDim.x = 32 * a.warps and the launch sizes smem to match
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint2 *stk = reinterpret_cast<uint2 *>(smem) + warp * kStackCap;
-    uint4 *chf = reinterpret_cast<uint4 *>(smem + kWarps * kStackCap * sizeof(uint2)) +
-                 warp * (kChunk + kNearChunk);
-    uint4 *chn = chf + kChunk;
+    const int chunk = a.chunk;
+    unsigned char *wbase = smem + (size_t)warp * warp_smem(chunk);
+    uint2 *stk = reinterpret_cast<uint2 *>(wbase);
+    uint4 *chn = reinterpret_cast<uint4 *>(wbase + kStackCap * sizeof(uint2));
+    uint4 *chf = chn + kNearChunk;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
 
@@ -545,7 +568,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
             cnt_pn += __popc(be & bn);
             cnt_pp += __popc(be & ~bn);
             const int nfar = __popc(bfar), nnear = __popc(bnear);
-            if (cf + nfar > kChunk) {
+            if (cf + nfar > chunk) {
                 __syncwarp();
                 float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
                 eval_far<kSplit, kPot>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
@@ -630,22 +653,29 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(WalkArgs a) {
 
 template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot = false>
 void launch_walk_t(const WalkArgs &a, int64_t nitems, cudaStream_t s, int sms) {
-    const size_t smem = kWarps * (kStackCap * sizeof(uint2) + (kChunk + kNearChunk) * sizeof(uint4));
-    static bool attr = false;
-    static int per_sm = 1;
-    if (!attr) {
-        cudaFuncSetAttribute(k_walk<kOpen, kSplit, kDump, kRefit, kMulti, kPot>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<kOpen, kSplit, kDump, kRefit, kMulti, kPot>,
-                                                      kWarps * 32, smem);
-        if (per_sm < 1) per_sm = 1;
-        attr = true;
+    const size_t smem = (size_t)a.warps * warp_smem(a.chunk);
+    auto kern = k_walk<kOpen, kSplit, kDump, kRefit, kMulti, kPot>;
+    // resident blocks per SM of each launch shape, queried once per shape
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> per_sm_of;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = per_sm_of.find({a.warps, a.chunk});
+        if (it != per_sm_of.end()) {
+            per_sm = it->second;
+        } else {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxBlockSmem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, a.warps * 32, smem);
+            if (per_sm < 1) per_sm = 1;
+            per_sm_of[{a.warps, a.chunk}] = per_sm;
+        }
     }
-    int64_t want = (nitems + kWarps - 1) / kWarps;
+    int64_t want = (nitems + a.warps - 1) / a.warps;
     int64_t grid = (int64_t)sms * per_sm;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    k_walk<kOpen, kSplit, kDump, kRefit, kMulti, kPot><<<(unsigned)grid, kWarps * 32, smem, s>>>(a); note_launch();
+    kern<<<(unsigned)grid, a.warps * 32, smem, s>>>(a); note_launch();
 }
 
 template <int kOpen, bool kSplit>
@@ -752,6 +782,9 @@ og_status prepare_view(og_tree *t, int opening, bool first_pass, const float *a_
 }
 
 void fill_common(WalkArgs &a, og_ctx *c, og_tree *t) {
+    // a tree's launch shape (zero fields take the defaults)
+    a.warps = t && t->prm.walk_warps > 0 ? t->prm.walk_warps : kDefaultWalkWarps;
+    a.chunk = t && t->prm.walk_chunk > 0 ? t->prm.walk_chunk : kDefaultWalkChunk;
     a.lists = t ? t->lists : nullptr;
     a.list_cap = t ? t->list_cap : 0;
     a.work = c->d_counters;

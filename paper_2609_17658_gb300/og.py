@@ -50,7 +50,7 @@ class og_params(C.Structure):
                 ("r_s", C.c_double), ("rcut_over_rs", C.c_double), ("theta", C.c_double),
                 ("alpha", C.c_double), ("theta_first_pass", C.c_double),
                 ("opening", C.c_int32), ("leaf_max", C.c_int32), ("group_max", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("walk_warps", C.c_int32), ("walk_chunk", C.c_int32)]
 
 
 class og_tree_info(C.Structure):
@@ -58,7 +58,8 @@ class og_tree_info(C.Structure):
                 ("groups", C.c_int64), ("list_entries", C.c_int64),
                 ("interactions", C.c_int64), ("interactions_last_pass", C.c_int64),
                 ("ms_build", C.c_double), ("ms_force", C.c_double), ("ms_walk", C.c_double),
-                ("group_max", C.c_int32), ("pad", C.c_int32)]
+                ("group_max", C.c_int32), ("walk_warps", C.c_int32), ("walk_chunk", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class og_box(C.Structure):
@@ -131,10 +132,13 @@ def lib():
         L.og_tree_force_active.argtypes = [P, P, P, P, P, P, C.POINTER(C.c_int64)]
         L.og_tree_force_active.restype = C.c_int
         L.og_tune_group_max.argtypes = [P, P, P, i64, C.POINTER(og_params), C.POINTER(C.c_int32)]
+        L.og_tune_walk.argtypes = [P, P, P, i64, C.POINTER(og_params), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.og_tune_save.argtypes = [P, C.c_char_p]
         L.og_tune_load.argtypes = [P, C.c_char_p]
         L.og_measure_fp32_peak.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
-        for name in ("og_tune_group_max", "og_tune_save", "og_tune_load", "og_measure_fp32_peak"):
+        for name in ("og_tune_group_max", "og_tune_walk", "og_tune_save", "og_tune_load",
+                     "og_measure_fp32_peak"):
             getattr(L, name).restype = C.c_int
         for name in ("og_create", "og_destroy", "og_set_stream", "og_params_default",
                      "og_tree_build", "og_tree_refit", "og_tree_force", "og_tree_info_get",
@@ -164,7 +168,7 @@ def params_from_dict(p: dict, flags: int = 0) -> og_params:
     for k in ("box", "G", "eps", "r_s", "rcut_over_rs", "theta", "alpha", "theta_first_pass"):
         if k in p:
             setattr(q, k, float(p[k]))
-    for k in ("opening", "leaf_max", "group_max", "flags"):
+    for k in ("opening", "leaf_max", "group_max", "flags", "walk_warps", "walk_chunk"):
         if k in p:
             setattr(q, k, int(p[k]))
     q.flags = int(q.flags) | int(flags)
@@ -235,6 +239,14 @@ def og_tune_group_max(ctx, pos, mass, params: dict) -> int:
     g = C.c_int32()
     _check(lib().og_tune_group_max(ctx, pp, mp, n, C.byref(prm), C.byref(g)))
     return int(g.value)
+
+
+def og_tune_walk(ctx, pos, mass, params: dict) -> dict:
+    """The measured group size and walk launch shape for inputs of this kind."""
+    pp, mp, n, prm = _inputs(pos, mass, params)
+    g, w, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().og_tune_walk(ctx, pp, mp, n, C.byref(prm), C.byref(g), C.byref(w), C.byref(c)))
+    return {"group_max": int(g.value), "walk_warps": int(w.value), "walk_chunk": int(c.value)}
 
 
 def og_tune_save(ctx, path: str) -> None:

@@ -1,10 +1,13 @@
-"""Measured group size (og_params.group_max = 0).
+"""Measured walk configuration (og_params.group_max = 0).
 
-The tuner picks G among 8, 16, 24, 32 by timing the walk on the caller's
-input, once per key (log2 N, criterion, split on/off).  A tree built with
-group_max = 0 must be the tree built with that G explicitly (bitwise), its
-lists and forces must match the oracle run with the same G, and a saved
-table must load into a fresh context without re-measuring.
+The tuner picks the group size G among 8, 16, 24, 32 and then the walk's
+launch shape (warps per block, far-chunk entries) by timing the walk on the
+caller's input, once per key (log2 N, criterion, split on/off).  A tree built
+with group_max = 0 must be the tree built with that configuration explicitly
+(bitwise), its lists and forces must match the oracle run with the same G, a
+saved table must load into a fresh context without re-measuring, and every
+launch shape must give the same lists (bitwise the same forces for the same
+chunk length, since warps per block do not change any arithmetic).
 """
 from __future__ import annotations
 
@@ -32,11 +35,15 @@ def ctx():
 def test_auto_group_size_is_the_explicit_build(ctx):
     pos, mass, prm = gi.config("clustered-2m", n=60000)
     auto = dict(prm, group_max=0)
-    G = og.og_tune_group_max(ctx.h, pos, mass, auto)
-    assert G in (8, 16, 24, 32)
+    cfg = og.og_tune_walk(ctx.h, pos, mass, auto)
+    G = cfg["group_max"]
+    assert G in (8, 16, 24, 32) and og.og_tune_group_max(ctx.h, pos, mass, auto) == G
+    assert cfg["walk_warps"] in (2, 4, 8) and cfg["walk_chunk"] in (128, 256, 512)
     ta = og.Tree(ctx, pos, mass, auto)
-    assert ta.info()["group_max"] == G
-    te = og.Tree(ctx, pos, mass, dict(prm, group_max=G))
+    info = ta.info()
+    assert (info["group_max"], info["walk_warps"], info["walk_chunk"]) == \
+        (G, cfg["walk_warps"], cfg["walk_chunk"])
+    te = og.Tree(ctx, pos, mass, dict(prm, **cfg))
     for f in (og.OG_F_GBEG, og.OG_F_GEND, og.OG_F_GBOX):
         assert np.array_equal(ta.export(f), te.export(f))
     a1, p1, n1 = ta.force()
@@ -64,6 +71,7 @@ def test_saved_table_loads_without_measuring(ctx, tmp_path):
     og.og_tune_save(ctx.h, path)
     text = open(path).read()
     assert '"group_max": %d' % G in text and '"n_log2": 14' in text
+    assert '"walk_warps": ' in text and '"walk_chunk": ' in text
     fresh = og.Context(0)
     try:
         og.og_tune_load(fresh.h, path)
@@ -76,9 +84,42 @@ def test_saved_table_loads_without_measuring(ctx, tmp_path):
 
 def test_load_rejects_other_files(ctx, tmp_path):
     bad = tmp_path / "bad.jsonl"
-    bad.write_text('{"n_log2": 14, "opening": 0, "split": 1, "group_max": 99}\n')
-    with pytest.raises(og.OGError) as e:
-        og.og_tune_load(ctx.h, str(bad))
-    assert e.value.status == og.OG_ERR_ARG
+    for line in ('{"n_log2": 14, "opening": 0, "split": 1, "group_max": 99, "walk_warps": 4, "walk_chunk": 256}',
+                 '{"n_log2": 14, "opening": 0, "split": 1, "group_max": 32, "walk_warps": 9, "walk_chunk": 256}',
+                 '{"n_log2": 14, "opening": 0, "split": 1, "group_max": 32, "walk_warps": 4, "walk_chunk": 16}',
+                 '{"n_log2": 14, "opening": 0, "split": 1, "group_max": 32}'):
+        bad.write_text(line + "\n")
+        with pytest.raises(og.OGError) as e:
+            og.og_tune_load(ctx.h, str(bad))
+        assert e.value.status == og.OG_ERR_ARG
     with pytest.raises(og.OGError):
         og.og_tune_load(ctx.h, str(tmp_path / "missing.jsonl"))
+
+
+@pytest.mark.parametrize("opening", [gi.OPEN_BH, gi.OPEN_REL])
+def test_launch_shapes(ctx, opening):
+    pos, mass, prm = gi.config("clustered-2m", n=40000)
+    prm = dict(prm, opening=opening, group_max=32)
+    ref = og.Tree(ctx, pos, mass, dict(prm, walk_warps=4, walk_chunk=256))
+    a0, p0, n0 = ref.force()
+    for w in (1, 2, 8):
+        t = og.Tree(ctx, pos, mass, dict(prm, walk_warps=w, walk_chunk=256))
+        a, p, n = t.force()
+        assert np.array_equal(a, a0) and np.array_equal(p, p0) and np.array_equal(n, n0), w
+    ot = oracle.Tree(pos, mass, prm)
+    a1, _, _ = og.Tree(ctx, pos, mass, dict(prm, opening=gi.OPEN_BH)).force(counts=False)
+    oref = ot.force(a_old=a1) if opening == gi.OPEN_REL else ot.force()
+    for w, c in ((2, 32), (8, 1024), (3, 100)):
+        t = og.Tree(ctx, pos, mass, dict(prm, walk_warps=w, walk_chunk=c))
+        a, p, n = t.force(a_old=a1) if opening == gi.OPEN_REL else t.force()
+        assert np.array_equal(p, p0) and np.array_equal(n, n0), (w, c)
+        assert np.array_equal(p, oref[1]) and np.array_equal(n, oref[2])
+        parity.check_accel(a, oref[0])
+
+
+def test_invalid_launch_shapes(ctx):
+    pos, mass, prm = gi.config("uniform-32k", n=1000)
+    for bad in (dict(walk_warps=9), dict(walk_warps=-1), dict(walk_chunk=31), dict(walk_chunk=1025)):
+        with pytest.raises(og.OGError) as e:
+            og.Tree(ctx, pos, mass, dict(prm, **bad))
+        assert e.value.status == og.OG_ERR_ARG
