@@ -461,21 +461,15 @@ __device__ __forceinline__ Slot slot_add(const Slot &a, const Slot &b) {
     return {__dadd_rn(a.M, b.M), __dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y), __dadd_rn(a.z, b.z)};
 }
 
-__global__ void __launch_bounds__(kT) k_moments_level(
-    int64_t n, int64_t m, int level, const uint32_t *__restrict__ lnodes, uint32_t cnt,
-    const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
+// moments (and, for a refit, the extent) of one node of this level; the
+// nodes of deeper levels are done
+__device__ __forceinline__ void moments_node(
+    int64_t n, int64_t m, const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
     const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
     const uint32_t *__restrict__ child, const uint32_t *__restrict__ px,
     const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
     const double *__restrict__ pm64, NodeMom *nmom, uint32_t *ncom, int64_t nchild,
-    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= cnt) return;
-    const uint32_t node = lnodes[k];
-    if (node >= (uint64_t)m) {
-        atomicOr(status, ST_INTERNAL);
-        return;
-    }
+    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l, uint32_t node, int level) {
     if (ext_s) {
         // refit: the extent is the cell joined with the members' positions,
         // as 32-bit offsets from the cell origin (drift stays local across
@@ -573,6 +567,58 @@ __global__ void __launch_bounds__(kT) k_moments_level(
     ncom[3 * node + 0] = c[0];
     ncom[3 * node + 1] = c[1];
     ncom[3 * node + 2] = c[2];
+}
+
+#define OG_MOMENT_ARGS n, m, nbeg, nend, ncbeg, occ, child, px, py, pz, pm64, nmom, ncom, nchild, \
+                       status, norg, ext_s, ext_l
+
+// one level with many nodes: a thread per node
+__global__ void __launch_bounds__(kT) k_moments_level(
+    int64_t n, int64_t m, const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
+    const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
+    const uint32_t *__restrict__ child, const uint32_t *__restrict__ px,
+    const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
+    const double *__restrict__ pm64, NodeMom *nmom, uint32_t *ncom, int64_t nchild,
+    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l, int level, const uint32_t *__restrict__ lnodes, uint32_t cnt) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    const uint32_t node = lnodes[k];
+    if (node >= (uint64_t)m) {
+        atomicOr(status, ST_INTERNAL);
+        return;
+    }
+    moments_node(OG_MOMENT_ARGS, node, level);
+}
+
+// consecutive levels with few nodes each, deepest first, in one block: a level
+// starts after the block barrier that ends the level below it (the block's
+// own global writes are visible to it after the barrier), which saves a
+// launch per level
+struct LevelRun {
+    int lo, hi;                                // levels hi, hi - 1, ..., lo
+    uint32_t off[kLevels + 1], cnt[kLevels + 1];
+};
+constexpr int kRunThreads = 512;
+constexpr uint32_t kRunMaxNodes = 1024;        // a level of at most 2 rounds of the block
+
+__global__ void __launch_bounds__(kRunThreads) k_moments_run(
+    int64_t n, int64_t m, const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
+    const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
+    const uint32_t *__restrict__ child, const uint32_t *__restrict__ px,
+    const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
+    const double *__restrict__ pm64, NodeMom *nmom, uint32_t *ncom, int64_t nchild,
+    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l, const uint32_t *__restrict__ lnodes, LevelRun run) {
+    for (int l = run.hi; l >= run.lo; --l) {
+        for (uint32_t k = threadIdx.x; k < run.cnt[l]; k += blockDim.x) {
+            const uint32_t node = lnodes[run.off[l] + k];
+            if (node >= (uint64_t)m) {
+                atomicOr(status, ST_INTERNAL);
+                continue;
+            }
+            moments_node(OG_MOMENT_ARGS, node, l);
+        }
+        __syncthreads();
+    }
 }
 
 // frontier node of p: the deepest node with more than G particles containing
@@ -775,14 +821,33 @@ static void moments_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
         offs[l] = off;
         off += t->h_lcount[l];
     }
+    // runs of small levels go to one block each; a large level to a grid
+    LevelRun run{};
+    run.hi = -1;
+    auto flush = [&]() {
+        if (run.hi < 0) return;
+        k_moments_run<<<1, kRunThreads, 0, s>>>(
+            n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child, t->px, t->py, t->pz, t->pm64,
+            t->nmom, t->ncom, t->nchild, t->ctx->d_status, t->norg, ext_s, ext_l, t->lnodes, run); note_launch();
+        run.hi = -1;
+    };
     for (int l = kLevels; l >= 0; --l) {
         const uint32_t cnt = t->h_lcount[l];
         if (cnt == 0) continue;
+        if (cnt <= kRunMaxNodes) {
+            if (run.hi < 0) run.hi = l;
+            run.lo = l;
+            run.off[l] = offs[l];
+            run.cnt[l] = cnt;
+            continue;
+        }
+        flush();
         k_moments_level<<<nblk(cnt), kT, 0, s>>>(
-            n, m, l, t->lnodes + offs[l], cnt, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child,
-            t->px, t->py, t->pz, t->pm64, t->nmom, t->ncom, t->nchild, t->ctx->d_status,
-            t->norg, ext_s, ext_l); note_launch();
+            n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child, t->px, t->py, t->pz, t->pm64,
+            t->nmom, t->ncom, t->nchild, t->ctx->d_status, t->norg, ext_s, ext_l, l,
+            t->lnodes + offs[l], cnt); note_launch();
     }
+    flush();
 }
 
 static og_status alloc_extents(og_tree *t) {

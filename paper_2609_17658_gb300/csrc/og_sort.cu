@@ -3,11 +3,11 @@
 // The paper inserts particles "sequentially following their Peano-Hilbert
 // ordering" (Sect. 4.1.1); here the order is a Morton order produced by a
 // least-significant-digit radix sort, 8 bits per pass.  Each pass is
-//   1. upsweep:   per 4096-key tile, a 256-bin digit histogram (shared-memory
+//   1. upsweep:   per 2048-key tile, a 256-bin digit histogram (shared-memory
 //                 atomics, one sub-histogram per warp), stored digit-major;
 //   2. scan:      exclusive scan over (digit, tile) -> global offsets;
 //   3. downsweep: stable in-tile ranking with __match_any_sync (each warp owns
-//                 512 consecutive keys, 16 rounds of 32), keys staged in shared
+//                 256 consecutive keys, 8 rounds of 32), keys staged in shared
 //                 memory in digit order, then written out so that runs of one
 //                 digit stay contiguous in global memory.
 // Passes whose digit is the same for every key (found from one histogram of
@@ -19,9 +19,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;        // 4096 keys per tile
-constexpr int kPerWarp = 32 * kItems;           // 512 consecutive keys per warp
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;        // 2048 keys per tile
+constexpr int kPerWarp = 32 * kItems;           // 256 consecutive keys per warp
 constexpr int kRadix = 256;
 
 __global__ void __launch_bounds__(kThreads) k_upsweep(const uint64_t *__restrict__ keys, int64_t n,
