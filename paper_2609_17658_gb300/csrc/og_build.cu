@@ -552,15 +552,27 @@ __device__ __forceinline__ void moments_node(
                        slot_add(slot_add(sl[4], sl[5]), slot_add(sl[6], sl[7])));
     }
     nmom[node] = NodeMom{tot.M, tot.x, tot.y, tot.z};
+}
+
+// centre of mass of every node on the grid, COM = round-half-even(S / M), once
+// all moments are done: the divisions stay off the level-by-level chain
+__global__ void k_com(int64_t m, const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ nbeg,
+                      const uint32_t *__restrict__ px, const uint32_t *__restrict__ py,
+                      const uint32_t *__restrict__ pz, const NodeMom *__restrict__ nmom,
+                      uint32_t *ncom) {
+    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= m) return;
+    const NodeMom q = nmom[node];
     uint32_t c[3];
-    if (tot.M > 0.0) {
-        c[0] = (uint32_t)rint(__ddiv_rn(tot.x, tot.M));
-        c[1] = (uint32_t)rint(__ddiv_rn(tot.y, tot.M));
-        c[2] = (uint32_t)rint(__ddiv_rn(tot.z, tot.M));
+    if (q.M > 0.0) {
+        c[0] = (uint32_t)rint(__ddiv_rn(q.Sx, q.M));
+        c[1] = (uint32_t)rint(__ddiv_rn(q.Sy, q.M));
+        c[2] = (uint32_t)rint(__ddiv_rn(q.Sz, q.M));
     } else {
         // massless node: the cell centre
-        const uint32_t q = nbeg[node];
-        const uint32_t pc[3] = {px[q], py[q], pz[q]};
+        const int level = nlev[node];
+        const uint32_t b = nbeg[node];
+        const uint32_t pc[3] = {px[b], py[b], pz[b]};
         const uint64_t mask = level == 0 ? 0ull : ~((1ull << (32 - level)) - 1ull);
         for (int a = 0; a < 3; ++a) c[a] = (uint32_t)(((uint64_t)pc[a] & mask) + (1ull << (31 - level)));
     }
@@ -848,6 +860,7 @@ static void moments_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
             t->lnodes + offs[l], cnt); note_launch();
     }
     flush();
+    k_com<<<nblk(m), kT, 0, s>>>(m, t->nlev, t->nbeg, t->px, t->py, t->pz, t->nmom, t->ncom); note_launch();
 }
 
 static og_status alloc_extents(og_tree *t) {

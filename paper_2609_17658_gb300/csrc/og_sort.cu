@@ -11,7 +11,10 @@
 //                 memory in digit order, then written out so that runs of one
 //                 digit stay contiguous in global memory.
 // Passes whose digit is the same for every key (found from one histogram of
-// all passes) are skipped.
+// all passes, read by the pass kernels themselves: no host round trip) only
+// copy their input.  With at most kFusedTiles tiles the downsweep forms its
+// global digit offsets from the tile counts itself, and the scan launches
+// are skipped (small sorts are bound by launch latency).
 #include "og_internal.h"
 
 namespace og {
@@ -23,12 +26,38 @@ constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;        // 2048 keys per tile
 constexpr int kPerWarp = 32 * kItems;           // 256 consecutive keys per warp
 constexpr int kRadix = 256;
+constexpr int64_t kFusedTiles = 64;
+static_assert(kThreads == kRadix, "one thread per digit in the pass kernels");
+
+// true in every thread of the block when all n keys share the digit of this
+// pass (hist8: the digit histograms of all passes)
+__device__ __forceinline__ bool trivial_pass(const uint32_t *hist8, int shift, int64_t n) {
+    return __syncthreads_or(hist8 && hist8[(shift / 8) * kRadix + threadIdx.x] == (uint64_t)n) != 0;
+}
+
+// exclusive scan of one value per thread over the block (kThreads values)
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t *warp_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += warp_tot[w];
+    __syncthreads();
+    return wpre + inc - v;
+}
 
 __global__ void __launch_bounds__(kThreads) k_upsweep(const uint64_t *__restrict__ keys, int64_t n,
                                                       int shift, uint32_t *counts,
-                                                      int64_t ntiles) {
+                                                      int64_t ntiles, const uint32_t *hist8) {
     __shared__ uint32_t hist[kWarps][kRadix];
     const int warp = threadIdx.x >> 5;
+    if (trivial_pass(hist8, shift, n)) return;
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&hist[0][0])[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kTile;
@@ -70,6 +99,7 @@ struct DownSmem {
     uint32_t dstart[kRadix];
     uint32_t gofs[kRadix];
     uint32_t warp_tot[kWarps];
+    uint32_t warp_tot2[kWarps];
 };
 
 __global__ void __launch_bounds__(kThreads) k_downsweep(const uint64_t *__restrict__ kin,
@@ -77,11 +107,22 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const uint64_t *__restri
                                                         uint64_t *__restrict__ kout,
                                                         uint32_t *__restrict__ vout, int64_t n,
                                                         int shift, const uint32_t *offsets,
-                                                        int64_t ntiles) {
+                                                        int64_t ntiles, const uint32_t *hist8,
+                                                        int fused) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DownSmem &S = *reinterpret_cast<DownSmem *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
+    if (trivial_pass(hist8, shift, n)) {
+        // every key has this digit: the stable order is the input order
+        const int64_t b0 = (int64_t)blockIdx.x * kTile;
+        const int64_t e0 = (n - b0) < kTile ? n : b0 + kTile;
+        for (int64_t i = b0 + threadIdx.x; i < e0; i += kThreads) {
+            kout[i] = kin[i];
+            vout[i] = vin[i];
+        }
+        return;
+    }
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&S.wcnt[0][0])[i] = 0;
     __syncthreads();
 
@@ -130,7 +171,19 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const uint64_t *__restri
     uint32_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += S.warp_tot[w];
     S.dstart[t] = wpre + inc - run;
-    S.gofs[t] = offsets[(int64_t)t * ntiles + blockIdx.x];
+    if (fused) {
+        // offsets = counts of the smaller digits in all tiles + counts of this
+        // digit in the tiles before this one (offsets holds the raw counts)
+        uint32_t before = 0, total = 0;
+        for (int64_t tt = 0; tt < ntiles; ++tt) {
+            const uint32_t c = offsets[(int64_t)t * ntiles + tt];
+            before += tt < (int64_t)blockIdx.x ? c : 0u;
+            total += c;
+        }
+        S.gofs[t] = block_exclusive(total, S.warp_tot2) + before;
+    } else {
+        S.gofs[t] = offsets[(int64_t)t * ntiles + blockIdx.x];
+    }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
@@ -174,14 +227,13 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     p += 8 * kRadix * sizeof(uint32_t);
     void *scan_scratch = p;
 
-    // which passes are trivial (all keys share the digit)?
+    // which passes are trivial (all keys share the digit)?  The pass kernels
+    // read the histograms.
     cudaMemsetAsync(hist8, 0, 8 * kRadix * sizeof(uint32_t), s);
     int grid = (int)((n + kThreads * 16 - 1) / (kThreads * 16));
     if (grid > 1184) grid = 1184;
     k_all_digits<<<grid, kThreads, 0, s>>>(keys, n, hist8); note_launch();
-    uint32_t h[8 * kRadix];
-    cudaMemcpyAsync(h, hist8, sizeof(h), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
+    const int fused = ntiles <= kFusedTiles ? 1 : 0;
 
     static bool attr_set = false;
     if (!attr_set) {
@@ -193,15 +245,12 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     uint32_t *vin = vals, *vout = vals_alt;
     int npasses = (bits + 7) / 8;
     for (int pass = 0; pass < npasses; ++pass) {
-        bool trivial = false;
-        for (int d = 0; d < kRadix; ++d)
-            if (h[pass * kRadix + d] == (uint32_t)n) trivial = true;
-        if (trivial) continue;
         int shift = 8 * pass;
-        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles); note_launch();
-        scan_exclusive_u32(counts, counts, (int64_t)kRadix * ntiles, nullptr, scan_scratch, s);
+        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles, hist8); note_launch();
+        if (!fused) scan_exclusive_u32(counts, counts, (int64_t)kRadix * ntiles, nullptr, scan_scratch, s);
         k_downsweep<<<(unsigned)ntiles, kThreads, sizeof(DownSmem), s>>>(kin, vin, kout, vout, n,
-                                                                         shift, counts, ntiles); note_launch();
+                                                                         shift, counts, ntiles, hist8,
+                                                                         fused); note_launch();
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
     }
@@ -225,10 +274,11 @@ void radix_sort_pairs_every_pass(uint64_t *keys, uint32_t *vals, uint64_t *keys_
     const int npasses = (bits + 7) / 8;
     for (int pass = 0; pass < npasses; ++pass) {
         const int shift = 8 * pass;
-        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles); note_launch();
+        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles, nullptr); note_launch();
         scan_exclusive_u32(counts, counts, (int64_t)kRadix * ntiles, nullptr, scan_scratch, s);
         k_downsweep<<<(unsigned)ntiles, kThreads, sizeof(DownSmem), s>>>(kin, vin, kout, vout, n,
-                                                                         shift, counts, ntiles); note_launch();
+                                                                         shift, counts, ntiles, nullptr,
+                                                                         0); note_launch();
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
     }
