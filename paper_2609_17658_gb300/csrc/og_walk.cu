@@ -508,11 +508,12 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
                             pruned = g2 > p.rprune;
                         }
                         // boundary check: the box meets the cube of side 1.2 ell
-                        // centred on the extent
-                        const unsigned long long lim = 6ull * ell;
-                        bnear = 10ull * point_gap(e.sx + (uint32_t)(((unsigned long long)e.lx + 1ull) >> 1), lo[0], gl[0]) <= lim &&
-                                10ull * point_gap(e.sy + (uint32_t)(((unsigned long long)e.ly + 1ull) >> 1), lo[1], gl[1]) <= lim &&
-                                10ull * point_gap(e.sz + (uint32_t)(((unsigned long long)e.lz + 1ull) >> 1), lo[2], gl[2]) <= lim;
+                        // centred on the extent: 10 g <= 6 ell, i.e. g <= floor(3 ell / 5)
+                        // (ell <= 2^32, so the limit fits in 32 bits)
+                        const uint32_t blim = (uint32_t)((3ull * ell) / 5ull);
+                        bnear = point_gap(e.sx + (uint32_t)(((unsigned long long)e.lx + 1ull) >> 1), lo[0], gl[0]) <= blim &&
+                                point_gap(e.sy + (uint32_t)(((unsigned long long)e.ly + 1ull) >> 1), lo[1], gl[1]) <= blim &&
+                                point_gap(e.sz + (uint32_t)(((unsigned long long)e.lz + 1ull) >> 1), lo[2], gl[2]) <= blim;
                     } else {
                         // the node's cell, from its level and centre of mass
                         const uint32_t lev = (r.info >> 26) & 31u;
@@ -527,11 +528,12 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
                                                           sq64(box_gap(lo[2], gl[2], oz, side - 1u));
                             pruned = g2 > p.rprune;
                         }
-                        // boundary check: the box meets the cell enlarged to 0.6 side
-                        const unsigned long long lim = 6ull * (unsigned long long)side;
-                        bnear = 10ull * point_gap(ox + (side >> 1), lo[0], gl[0]) <= lim &&
-                                10ull * point_gap(oy + (side >> 1), lo[1], gl[1]) <= lim &&
-                                10ull * point_gap(oz + (side >> 1), lo[2], gl[2]) <= lim;
+                        // boundary check: the box meets the cell enlarged to 0.6 side,
+                        // 10 g <= 6 side, i.e. g <= floor(3 side / 5) for an integer g
+                        const uint32_t blim = (uint32_t)((3ull << (32u - lev)) / 5ull);
+                        bnear = point_gap(ox + (side >> 1), lo[0], gl[0]) <= blim &&
+                                point_gap(oy + (side >> 1), lo[1], gl[1]) <= blim &&
+                                point_gap(oz + (side >> 1), lo[2], gl[2]) <= blim;
                     }
                     if (!pruned) {
                         if (bnear) {
