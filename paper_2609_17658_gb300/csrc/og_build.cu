@@ -19,10 +19,12 @@
 //                           octant-occupancy bits of every node
 //          k_place          child array in key order, grouped by parent
 //          k_threading      nextnode / sibling threading (unified index space)
-//   a5     k_moments        bottom-up FP64 mass and sum m x; 8 lanes per node hold
-//                           the 8 octant slots and combine them with warp
-//                           shuffles in the fixed order ((0+1)+(2+3))+((4+5)+(6+7));
-//                           the last child to finish climbs to the parent
+//   a5     k_level_hist .. k_level_scatter   node ids bucketed by tree level
+//          k_moments_level  bottom-up FP64 mass and sum m x, one thread per node and
+//                           one launch per large level, deepest first; the 8 octant
+//                           slots combine in the fixed order ((0+1)+(2+3))+((4+5)+(6+7))
+//          k_moments_run    a run of small levels in one block (a barrier per level)
+//          k_com            centre of mass of every node, round-half-even(S / M)
 //   a6     k_frontier .. k_group_fin   walk groups and their integer boxes
 //          k_records        32-byte child records read by the walk
 //
@@ -822,8 +824,9 @@ static size_t tree_bytes(int64_t n, int64_t B) {
 }
 
 // Moments (and, for a refit, extents) level by level from the deepest level
-// up; each launch reads only nodes of deeper levels, finished by the previous
-// launches.
+// up; each level reads only nodes of deeper levels, finished by the previous
+// launches (or, inside a run of small levels, before the block barrier); then
+// the centres of mass of all nodes.
 static void moments_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
     cudaStream_t s = t->ctx->stream;
     const int64_t n = t->n, m = t->nnodes;
