@@ -149,6 +149,15 @@ og_status og_tree_refit(og_tree *t, const double *pos);
 og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_pp,
                         uint32_t *n_pn);
 
+/* og_tree_force with double-precision output (the accelerations a caller in
+ * FP64 keeps): the same walk and the same FP32 sums, but the last pass
+ * leaves them in grid units and the conversion to G M / L^2 is one FP64
+ * multiplication by G (2^32 / L)^2, so the output carries no FP32 rounding
+ * of that scaling.  acc: double[N][3] out; other arguments as og_tree_force.
+ * Trees of og_tree_build only (one box); else OG_ERR_ARG. */
+og_status og_tree_force_f64(og_tree *t, const float *a_old, double *acc, uint32_t *n_pp,
+                            uint32_t *n_pn);
+
 og_status og_tree_info_get(const og_tree *t, og_tree_info *info);
 
 /* ---- many independent boxes in one launch ------------------------------ */

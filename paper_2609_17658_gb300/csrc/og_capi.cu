@@ -65,6 +65,21 @@ __global__ void k_unpermute(int64_t n, const uint32_t *__restrict__ perm,
     if (npn) npn[j] = npn_s[i];
 }
 
+// FP64 output: the walk's unscaled FP32 sums times G (2^32 / L)^2 in FP64
+__global__ void k_unpermute_f64(int64_t n, const uint32_t *__restrict__ perm,
+                                const float *__restrict__ acc_sorted,
+                                const uint32_t *__restrict__ npp_s, const uint32_t *__restrict__ npn_s,
+                                double scale, double *acc, uint32_t *npp, uint32_t *npn) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = perm[i];
+    acc[3ull * j + 0] = (double)acc_sorted[i] * scale;
+    acc[3ull * j + 1] = (double)acc_sorted[n + i] * scale;
+    acc[3ull * j + 2] = (double)acc_sorted[2 * n + i] * scale;
+    if (npp) npp[j] = npp_s[i];
+    if (npn) npn[j] = npn_s[i];
+}
+
 __global__ void k_unpermute_pot(int64_t n, const uint32_t *__restrict__ perm,
                                 const float *__restrict__ pot_sorted, float *pot) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -426,6 +441,67 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
                                        d_acc, d_npp, d_npn); note_launch();
     if (!dev) {
         cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (n_pp) cudaMemcpyAsync(n_pp, d_npp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (n_pn) cudaMemcpyAsync(n_pn, d_npn, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(out_tmp, s);
+    }
+    cudaEventRecord(e1, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "force");
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t->ms_force = ms;
+    t->ms_walk = ms_walk;
+    return check_status(c);
+}
+
+og_status og_tree_force_f64(og_tree *t, const float *a_old, double *acc, uint32_t *n_pp,
+                            uint32_t *n_pn) {
+    if (!t || !acc) { set_error("NULL argument"); return OG_ERR_ARG; }
+    if (t->nseg != 1) { set_error("og_tree_force_f64: a tree of one box only"); return OG_ERR_ARG; }
+    og_ctx *c = t->ctx;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int64_t n = t->n;
+    const bool dev = (t->prm.flags & OG_DEVICE_PTRS) != 0;
+    cudaError_t e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    float ms_walk = 0, ms = 0;
+    void *tmp = nullptr;
+    const float *d_aold = nullptr;
+    if (t->prm.opening == OG_OPEN_REL && a_old) {
+        d_aold = a_old;
+        if (!dev) {
+            if ((e = cudaMallocAsync(&tmp, (size_t)n * 3 * sizeof(float), s)) != cudaSuccess)
+                return cuda_fail(e, "cudaMallocAsync (a_old)");
+            cudaMemcpyAsync(tmp, a_old, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+            d_aold = static_cast<const float *>(tmp);
+        }
+    }
+    t->unscaled_out = true;
+    og_status st = force_sorted(t, d_aold, &ms_walk, nullptr, 0, nullptr);
+    t->unscaled_out = false;
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (st) return st;
+    const double g = 4294967296.0 / t->prm.box;
+    const double scale = t->prm.G * g * g;
+    double *d_acc = acc;
+    uint32_t *d_npp = n_pp, *d_npn = n_pn;
+    void *out_tmp = nullptr;
+    if (!dev) {
+        size_t bytes = (size_t)n * 3 * sizeof(double) + 2 * (size_t)n * sizeof(uint32_t) + 512;
+        if ((e = cudaMallocAsync(&out_tmp, bytes, s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (out)");
+        d_acc = static_cast<double *>(out_tmp);
+        d_npp = n_pp ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) : nullptr;
+        d_npn = n_pn ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) + n : nullptr;
+    }
+    k_unpermute_f64<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+                                           scale, d_acc, d_npp, d_npn); note_launch();
+    if (!dev) {
+        cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (n_pp) cudaMemcpyAsync(n_pp, d_npp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (n_pn) cudaMemcpyAsync(n_pn, d_npn, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         cudaFreeAsync(out_tmp, s);

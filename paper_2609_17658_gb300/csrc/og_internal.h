@@ -132,7 +132,8 @@ struct og_tree {
     // stats
     int64_t interactions = 0, interactions_last = 0;
     double ms_build = 0, ms_force = 0, ms_walk = 0;
-    float *pot_next = nullptr;        // potential output of the next force call (sorted order)
+    float *pot_next = nullptr;
+    bool unscaled_out = false;        // the last pass leaves accelerations in grid units        // potential output of the next force call (sorted order)
     // one allocation holds every array above
     void *arena = nullptr;
     size_t arena_bytes = 0;

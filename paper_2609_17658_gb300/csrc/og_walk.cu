@@ -750,6 +750,8 @@ og_status prepare_view(og_tree *t, int opening, bool first_pass, const float *a_
         const og_params &q = t->seg_prm[b];
         t->h_wp[b] = make_walk_params(q, opening, first_pass ? q.theta_first_pass : q.theta);
         if (first_pass) t->h_wp[b].dump = false;
+        // FP64 output: the last pass stores the unscaled sums, scaled in FP64 later
+        if (!first_pass && t->unscaled_out) t->h_wp[b].out_scale = 1.0f;
     }
     *wp0 = t->h_wp[0];
     WalkParams *dp = t->segp + (first_pass ? 0 : B);

@@ -125,6 +125,8 @@ def lib():
         L.og_serve_request_bytes.restype = C.c_size_t
         L.og_sort_keys_noalloc.restype = C.c_int
         L.og_tree_force_pot.argtypes = [P, P, P, P, P, P]
+        L.og_tree_force_f64.argtypes = [P, P, P, P, P]
+        L.og_tree_force_f64.restype = C.c_int
         L.og_tree_force_pot.restype = C.c_int
         L.og_kdk_run.argtypes = [P, i64, P, P, P, C.POINTER(og_params), C.POINTER(og_kdk_params), P, P,
                                  C.POINTER(og_kdk_stats)]
@@ -277,6 +279,21 @@ def og_tree_force(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
         pp = None if n_pp is None else _host_ptr(n_pp, np.uint32)
         np_ = None if n_pn is None else _host_ptr(n_pn, np.uint32)
     _check(lib().og_tree_force(tree, op, ap, pp, np_))
+
+
+def og_tree_force_f64(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
+    """og_tree_force with acc float64 [N,3] (scaled to G M / L^2 in FP64)."""
+    if _is_torch_cuda(acc):
+        ap = _dev_ptr(acc, "float64")
+        op = None if a_old is None else _dev_ptr(a_old, "float32")
+        pp = None if n_pp is None else _dev_ptr(n_pp, "int32")
+        np_ = None if n_pn is None else _dev_ptr(n_pn, "int32")
+    else:
+        ap = _host_ptr(acc, np.float64, (3,))
+        op = None if a_old is None else _host_ptr(a_old, np.float32, (3,))
+        pp = None if n_pp is None else _host_ptr(n_pp, np.uint32)
+        np_ = None if n_pn is None else _host_ptr(n_pn, np.uint32)
+    _check(lib().og_tree_force_f64(tree, op, ap, pp, np_))
 
 
 def og_tree_force_pot(tree, acc, pot, a_old=None, n_pp=None, n_pn=None) -> None:
