@@ -82,7 +82,7 @@ typedef struct {
     int32_t flags;           /* OG_DEVICE_PTRS | OG_DEBUG_DUMP_LISTS */
     int32_t walk_warps;      /* walk launch shape: warps (one group each) per block, 1..8;
                                 0 = the measured value when group_max = 0, else 4 */
-    int32_t walk_chunk;      /* entries of a warp's shared far-entry chunk, 32..1024;
+    int32_t walk_chunk;      /* entries of a warp's shared far-entry chunk, 64..1024;
                                 0 = the measured value when group_max = 0, else 256 */
 } og_params;
 

@@ -189,8 +189,8 @@ og_status validate(const og_params *p, int64_t n) {
     if (p->leaf_max != 1) { set_error("leaf_max must be 1 (one particle per leaf cell)"); return OG_ERR_ARG; }
     if (p->group_max < 0 || p->group_max > 32) { set_error("group_max must be in [0, 32]"); return OG_ERR_ARG; }
     if (p->walk_warps < 0 || p->walk_warps > 8) { set_error("walk_warps must be in [0, 8]"); return OG_ERR_ARG; }
-    if (p->walk_chunk != 0 && (p->walk_chunk < 32 || p->walk_chunk > 1024)) {
-        set_error("walk_chunk must be 0 or in [32, 1024]");
+    if (p->walk_chunk != 0 && (p->walk_chunk < 64 || p->walk_chunk > 1024)) {
+        set_error("walk_chunk must be 0 or in [64, 1024]");
         return OG_ERR_ARG;
     }
     return OG_OK;

@@ -163,9 +163,9 @@ struct WalkConfig {
 };
 og_status tuned_walk(og_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
                      const og_params &p, WalkConfig *out);
-// a walk launch shape the kernel supports: 1..8 warps, 32..1024 chunk entries
+// a walk launch shape the kernel supports: 1..8 warps, 64..1024 chunk entries
 inline bool valid_walk_shape(int warps, int chunk) {
-    return warps >= 1 && warps <= 8 && chunk >= 32 && chunk <= 1024;
+    return warps >= 1 && warps <= 8 && chunk >= 64 && chunk <= 1024;
 }
 void tune_free(og_ctx *c);
 // count of kernels launched by this library in this process

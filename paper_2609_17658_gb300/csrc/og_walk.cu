@@ -7,9 +7,10 @@
 //
 //   list building   the warp keeps a stack of child-array ranges of opened
 //                   nodes in shared memory.  Each round the 32 lanes take the
-//                   next 32 child records (32-byte records, coalesced loads),
-//                   and each lane classifies its record against the group's
-//                   integer bounding box:
+//                   next 64 child records (32-byte records, coalesced loads;
+//                   two independent records per lane), and each lane
+//                   classifies its records against the group's integer
+//                   bounding box:
 //                     particle -> PP entry unless beyond the prune distance;
 //                     node     -> pruned, opened (range pushed), or PN entry.
 //                   Prune and boundary tests are exact integer geometry.  The
@@ -46,11 +47,11 @@ namespace {
 
 constexpr int kMaxWarps = 8;       // warps per block: 1..kMaxWarps, chosen at launch
 constexpr int kStackCap = 768;     // ranges per warp stack
-constexpr int kNearChunk = 64;     // near entries per shared chunk
+constexpr int kNearChunk = 64;     // near entries per shared chunk (>= 64: see kMinChunk)
 // The far chunk holds `chunk` entries (WalkArgs::chunk, chosen at launch,
-// kMinChunk..kMaxChunk): a round adds at most 32, so a flushed chunk always
-// has room for the next round.
-constexpr int kMinChunk = 32, kMaxChunk = 1024;
+// kMinChunk..kMaxChunk): a round adds at most 64 entries to either chunk, so
+// a flushed chunk always has room for the next round.
+constexpr int kMinChunk = 64, kMaxChunk = 1024;
 
 // shared memory of one warp: its stack, near chunk and far chunk
 __host__ __device__ constexpr size_t warp_smem(int chunk) {
@@ -354,6 +355,93 @@ __device__ __forceinline__ bool open_rel(uint32_t gx, uint32_t gy, uint32_t gz, 
 // Registers: at most 96 per thread (64 KB / (96 x 128) gives 5 blocks of 4
 // warps per SM, as many as their shared memory allows), 128 with the
 // potential output; a block of kMaxWarps warps fits either way.
+// One child record against the group box: PP / PN entry, opened node (its
+// child range to push), or nothing (pruned, or no record in this slot).
+struct Cls {
+    bool emit, open, isnode, near;
+    uint4 ent;
+    uint32_t push_ref, push_cnt;
+};
+
+template <int kOpen, bool kSplit, bool kRefit>
+__device__ __forceinline__ Cls classify(const TreeView &T, uint32_t ci, bool has, const uint32_t *lo,
+                                        const uint32_t *gl, const WalkParams &p, float arelf,
+                                        double arel) {
+    bool emit = false, open = false, isnode = false, near = false;
+    uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t push_ref = 0u, push_cnt = 0u;
+    if (has && ci < T.nchild) {
+        const CRec r = T.crec[ci];
+        ent = make_uint4(r.x, r.y, r.z, __float_as_uint(r.m));
+        isnode = (r.info >> 31) != 0u;
+        const uint32_t gx = point_gap(r.x, lo[0], gl[0]);
+        const uint32_t gy = point_gap(r.y, lo[1], gl[1]);
+        const uint32_t gz = point_gap(r.z, lo[2], gl[2]);
+        const unsigned long long pg2 = sq64(gx) + sq64(gy) + sq64(gz);
+        near = pg2 < p.hnear2;
+        if (!isnode) {
+            emit = !kSplit || pg2 <= p.rprune;
+        } else {
+            bool pruned = false, bnear;
+            float l2f;
+            double l2;
+            if (kRefit) {
+                // the node's extent: its cell joined with its drifted members
+                const CExt e = T.cext[ci];
+                const unsigned long long ell =
+                    (unsigned long long)max(e.lx, max(e.ly, e.lz)) + 1ull;
+                l2 = (double)ell * (double)ell;
+                l2f = (float)l2;
+                if (kSplit) {
+                    const unsigned long long g2 = sq64(box_gap(lo[0], gl[0], e.sx, e.lx)) +
+                                                  sq64(box_gap(lo[1], gl[1], e.sy, e.ly)) +
+                                                  sq64(box_gap(lo[2], gl[2], e.sz, e.lz));
+                    pruned = g2 > p.rprune;
+                }
+                // boundary check: the box meets the cube of side 1.2 ell
+                // centred on the extent: 10 g <= 6 ell, i.e. g <= floor(3 ell / 5)
+                // (ell <= 2^32, so the limit fits in 32 bits)
+                const uint32_t blim = (uint32_t)((3ull * ell) / 5ull);
+                bnear = point_gap(e.sx + (uint32_t)(((unsigned long long)e.lx + 1ull) >> 1), lo[0], gl[0]) <= blim &&
+                        point_gap(e.sy + (uint32_t)(((unsigned long long)e.ly + 1ull) >> 1), lo[1], gl[1]) <= blim &&
+                        point_gap(e.sz + (uint32_t)(((unsigned long long)e.lz + 1ull) >> 1), lo[2], gl[2]) <= blim;
+            } else {
+                // the node's cell, from its level and centre of mass
+                const uint32_t lev = (r.info >> 26) & 31u;
+                const uint32_t side = 1u << (32u - lev);
+                const uint32_t msk = ~(side - 1u);
+                const uint32_t ox = r.x & msk, oy = r.y & msk, oz = r.z & msk;
+                l2f = __uint_as_float((uint32_t)(127 + 64 - 2 * lev) << 23);
+                l2 = __longlong_as_double((long long)(1023 + 64 - 2 * lev) << 52);
+                if (kSplit) {
+                    const unsigned long long g2 = sq64(box_gap(lo[0], gl[0], ox, side - 1u)) +
+                                                  sq64(box_gap(lo[1], gl[1], oy, side - 1u)) +
+                                                  sq64(box_gap(lo[2], gl[2], oz, side - 1u));
+                    pruned = g2 > p.rprune;
+                }
+                // boundary check: the box meets the cell enlarged to 0.6 side,
+                // 10 g <= 6 side, i.e. g <= floor(3 side / 5) for an integer g
+                const uint32_t blim = (uint32_t)((3ull << (32u - lev)) / 5ull);
+                bnear = point_gap(ox + (side >> 1), lo[0], gl[0]) <= blim &&
+                        point_gap(oy + (side >> 1), lo[1], gl[1]) <= blim &&
+                        point_gap(oz + (side >> 1), lo[2], gl[2]) <= blim;
+            }
+            if (!pruned) {
+                if (bnear) {
+                    open = true;
+                } else {
+                    if (kOpen == OG_OPEN_BH) open = open_bh(gx, gy, gz, l2f, l2, p);
+                    else open = open_rel(gx, gy, gz, l2f, l2, r.m, r.M, arelf, arel, p);
+                }
+                emit = !open;
+                push_ref = r.ref;
+                push_cnt = r.info & 0x3ffffffu;
+            }
+        }
+    }
+    return Cls{emit, open, isnode, near, ent, push_ref, push_cnt};
+}
+
 template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot = false>
 __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a);
 
@@ -445,6 +533,8 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
                 if (lane == 0) atomicOr(a.status, ST_INTERNAL);
                 break;
             }
+            // a round takes up to 64 child records from the top ranges of the
+            // stack: slot l and slot l + 32 go to lane l
             const int nr = sp < 32 ? sp : 32;
             uint2 Rg = make_uint2(0u, 0u);
             if (lane < nr) Rg = stk[sp - 1 - lane];
@@ -456,120 +546,62 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
                 if (lane >= d) incl += o;
             }
             const uint32_t excl = incl - cnt;
-            const unsigned fullm = __ballot_sync(FULL, lane < nr && incl <= 32u);
+            const unsigned fullm = __ballot_sync(FULL, lane < nr && incl <= 64u);
             const int nfull = __popc(fullm);
             const uint32_t total = __shfl_sync(FULL, incl, 31);
-            const int ntake = total < 32u ? (int)total : 32;
-            const unsigned bit = (lane < nr && excl < 32u) ? (1u << excl) : 0u;
-            const unsigned smask = __reduce_or_sync(FULL, bit);
+            const int ntake = total < 64u ? (int)total : 64;
+            // first slot of every range that starts in this round, slots 0..31 and 32..63
+            const unsigned slo = __reduce_or_sync(FULL, (lane < nr && excl < 32u) ? (1u << excl) : 0u);
+            const unsigned shi = __reduce_or_sync(
+                FULL, (lane < nr && excl >= 32u && excl < 64u) ? (1u << (excl - 32u)) : 0u);
             __syncwarp();
             const int sp_new = sp - nfull;
-            if (lane == nfull && lane < nr && excl < 32u) {
-                const uint32_t used = 32u - excl;
+            if (lane == nfull && lane < nr && excl < 64u) {
+                const uint32_t used = 64u - excl;
                 stk[sp - 1 - nfull] = make_uint2(Rg.x + used, Rg.y - used);
             }
-            // this lane's child slot
-            const unsigned upto = lane == 31 ? smask : (smask & ((2u << lane) - 1u));
-            const int rj = __popc(upto) - 1;
-            const uint32_t rcb = __shfl_sync(FULL, Rg.x, rj < 0 ? 0 : rj);
-            const uint32_t rex = __shfl_sync(FULL, excl, rj < 0 ? 0 : rj);
-            const bool has = lane < ntake;
-            const uint32_t ci = rcb + ((uint32_t)lane - rex);
-
-            bool emit = false, open = false, isnode = false, near = false;
-            uint4 ent = make_uint4(0u, 0u, 0u, 0u);
-            uint32_t push_ref = 0u, push_cnt = 0u;
-            if (has && ci < T.nchild) {
-                const CRec r = T.crec[ci];
-                ent = make_uint4(r.x, r.y, r.z, __float_as_uint(r.m));
-                isnode = (r.info >> 31) != 0u;
-                const uint32_t gx = point_gap(r.x, lo[0], gl[0]);
-                const uint32_t gy = point_gap(r.y, lo[1], gl[1]);
-                const uint32_t gz = point_gap(r.z, lo[2], gl[2]);
-                const unsigned long long pg2 = sq64(gx) + sq64(gy) + sq64(gz);
-                near = pg2 < p.hnear2;
-                if (!isnode) {
-                    emit = !kSplit || pg2 <= p.rprune;
-                } else {
-                    bool pruned = false, bnear;
-                    float l2f;
-                    double l2;
-                    if (kRefit) {
-                        // the node's extent: its cell joined with its drifted members
-                        const CExt e = T.cext[ci];
-                        const unsigned long long ell =
-                            (unsigned long long)max(e.lx, max(e.ly, e.lz)) + 1ull;
-                        l2 = (double)ell * (double)ell;
-                        l2f = (float)l2;
-                        if (kSplit) {
-                            const unsigned long long g2 = sq64(box_gap(lo[0], gl[0], e.sx, e.lx)) +
-                                                          sq64(box_gap(lo[1], gl[1], e.sy, e.ly)) +
-                                                          sq64(box_gap(lo[2], gl[2], e.sz, e.lz));
-                            pruned = g2 > p.rprune;
-                        }
-                        // boundary check: the box meets the cube of side 1.2 ell
-                        // centred on the extent: 10 g <= 6 ell, i.e. g <= floor(3 ell / 5)
-                        // (ell <= 2^32, so the limit fits in 32 bits)
-                        const uint32_t blim = (uint32_t)((3ull * ell) / 5ull);
-                        bnear = point_gap(e.sx + (uint32_t)(((unsigned long long)e.lx + 1ull) >> 1), lo[0], gl[0]) <= blim &&
-                                point_gap(e.sy + (uint32_t)(((unsigned long long)e.ly + 1ull) >> 1), lo[1], gl[1]) <= blim &&
-                                point_gap(e.sz + (uint32_t)(((unsigned long long)e.lz + 1ull) >> 1), lo[2], gl[2]) <= blim;
-                    } else {
-                        // the node's cell, from its level and centre of mass
-                        const uint32_t lev = (r.info >> 26) & 31u;
-                        const uint32_t side = 1u << (32u - lev);
-                        const uint32_t msk = ~(side - 1u);
-                        const uint32_t ox = r.x & msk, oy = r.y & msk, oz = r.z & msk;
-                        l2f = __uint_as_float((uint32_t)(127 + 64 - 2 * lev) << 23);
-                        l2 = __longlong_as_double((long long)(1023 + 64 - 2 * lev) << 52);
-                        if (kSplit) {
-                            const unsigned long long g2 = sq64(box_gap(lo[0], gl[0], ox, side - 1u)) +
-                                                          sq64(box_gap(lo[1], gl[1], oy, side - 1u)) +
-                                                          sq64(box_gap(lo[2], gl[2], oz, side - 1u));
-                            pruned = g2 > p.rprune;
-                        }
-                        // boundary check: the box meets the cell enlarged to 0.6 side,
-                        // 10 g <= 6 side, i.e. g <= floor(3 side / 5) for an integer g
-                        const uint32_t blim = (uint32_t)((3ull << (32u - lev)) / 5ull);
-                        bnear = point_gap(ox + (side >> 1), lo[0], gl[0]) <= blim &&
-                                point_gap(oy + (side >> 1), lo[1], gl[1]) <= blim &&
-                                point_gap(oz + (side >> 1), lo[2], gl[2]) <= blim;
-                    }
-                    if (!pruned) {
-                        if (bnear) {
-                            open = true;
-                        } else {
-                            if (kOpen == OG_OPEN_BH) open = open_bh(gx, gy, gz, l2f, l2, p);
-                            else open = open_rel(gx, gy, gz, l2f, l2, r.m, r.M, arelf, arel, p);
-                        }
-                        emit = !open;
-                        push_ref = r.ref;
-                        push_cnt = r.info & 0x3ffffffu;
-                    }
-                }
-            }
+            // this lane's two child slots: the range of a slot is the last one
+            // starting at or before it
+            const unsigned upm = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+            const int rj0 = __popc(slo & upm) - 1;
+            const int rj1 = __popc(slo) + __popc(shi & upm) - 1;
+            const int rs0 = rj0 < 0 ? 0 : rj0, rs1 = rj1 < 0 ? 0 : (rj1 > 31 ? 31 : rj1);
+            const uint32_t rcb0 = __shfl_sync(FULL, Rg.x, rs0), rex0 = __shfl_sync(FULL, excl, rs0);
+            const uint32_t rcb1 = __shfl_sync(FULL, Rg.x, rs1), rex1 = __shfl_sync(FULL, excl, rs1);
+            const uint32_t ci0 = rcb0 + ((uint32_t)lane - rex0);
+            const uint32_t ci1 = rcb1 + ((uint32_t)lane + 32u - rex1);
+            const Cls c0 = classify<kOpen, kSplit, kRefit>(T, ci0, lane < ntake, lo, gl, p, arelf, arel);
+            const Cls c1 = classify<kOpen, kSplit, kRefit>(T, ci1, lane + 32 < ntake, lo, gl, p, arelf, arel);
             // push opened ranges
-            const unsigned bo = __ballot_sync(FULL, open);
-            const int npush = __popc(bo);
+            const unsigned bo0 = __ballot_sync(FULL, c0.open), bo1 = __ballot_sync(FULL, c1.open);
+            const int np0 = __popc(bo0), npush = np0 + __popc(bo1);
             if (sp_new + npush > kStackCap) {
                 overflow = true;
                 break;
             }
-            if (open) {
-                // a node always has children; a zero count would stall the walk
-                stk[sp_new + __popc(bo & lt)] = make_uint2(push_ref, push_cnt > 0u ? push_cnt : 1u);
-                if (push_cnt == 0u || (uint64_t)push_ref + push_cnt > (uint64_t)T.nchild)
+            // a node always has children; a zero count would stall the walk
+            if (c0.open) {
+                stk[sp_new + __popc(bo0 & lt)] = make_uint2(c0.push_ref, c0.push_cnt > 0u ? c0.push_cnt : 1u);
+                if (c0.push_cnt == 0u || (uint64_t)c0.push_ref + c0.push_cnt > (uint64_t)T.nchild)
+                    atomicOr(a.status, ST_INTERNAL);
+            }
+            if (c1.open) {
+                stk[sp_new + np0 + __popc(bo1 & lt)] =
+                    make_uint2(c1.push_ref, c1.push_cnt > 0u ? c1.push_cnt : 1u);
+                if (c1.push_cnt == 0u || (uint64_t)c1.push_ref + c1.push_cnt > (uint64_t)T.nchild)
                     atomicOr(a.status, ST_INTERNAL);
             }
             sp = sp_new + npush;
-            // append entries to the far / near chunks
-            const unsigned be = __ballot_sync(FULL, emit);
-            const unsigned bn = __ballot_sync(FULL, isnode);
-            const unsigned bnear = __ballot_sync(FULL, emit && near);
-            const unsigned bfar = be & ~bnear;
-            cnt_pn += __popc(be & bn);
-            cnt_pp += __popc(be & ~bn);
-            const int nfar = __popc(bfar), nnear = __popc(bnear);
+            // append entries to the far / near chunks (at most 64 each per round)
+            const unsigned be0 = __ballot_sync(FULL, c0.emit), be1 = __ballot_sync(FULL, c1.emit);
+            const unsigned bn0 = __ballot_sync(FULL, c0.isnode), bn1 = __ballot_sync(FULL, c1.isnode);
+            const unsigned bq0 = __ballot_sync(FULL, c0.emit && c0.near);
+            const unsigned bq1 = __ballot_sync(FULL, c1.emit && c1.near);
+            const unsigned bf0 = be0 & ~bq0, bf1 = be1 & ~bq1;
+            cnt_pn += __popc(be0 & bn0) + __popc(be1 & bn1);
+            cnt_pp += __popc(be0 & ~bn0) + __popc(be1 & ~bn1);
+            const int nf0 = __popc(bf0), nfar = nf0 + __popc(bf1);
+            const int nq0 = __popc(bq0), nnear = nq0 + __popc(bq1);
             if (cf + nfar > chunk) {
                 __syncwarp();
                 float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
@@ -588,20 +620,33 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
                 cn = 0;
                 __syncwarp();
             }
-            if (emit) {
-                if (near) chn[cn + __popc(bnear & lt)] = ent;
-                else chf[cf + __popc(bfar & lt)] = ent;
+            if (c0.emit) {
+                if (c0.near) chn[cn + __popc(bq0 & lt)] = c0.ent;
+                else chf[cf + __popc(bf0 & lt)] = c0.ent;
+            }
+            if (c1.emit) {
+                if (c1.near) chn[cn + nq0 + __popc(bq1 & lt)] = c1.ent;
+                else chf[cf + nf0 + __popc(bf1 & lt)] = c1.ent;
             }
             if (kDump && (nfar + nnear) > 0) {
                 const int nem = nfar + nnear;
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(a.list_cursor, (unsigned long long)nem);
                 base = __shfl_sync(FULL, base, 0);
-                if (emit) {
-                    unsigned long long pos = base + __popc(be & lt);
-                    if (pos < (unsigned long long)a.list_cap) {
-                        a.lists[2 * pos] = (uint32_t)g;
-                        a.lists[2 * pos + 1] = ci;
+                const unsigned long long pos0 = base + __popc(be0 & lt);
+                const unsigned long long pos1 = base + __popc(be0) + __popc(be1 & lt);
+                if (c0.emit) {
+                    if (pos0 < (unsigned long long)a.list_cap) {
+                        a.lists[2 * pos0] = (uint32_t)g;
+                        a.lists[2 * pos0 + 1] = ci0;
+                    } else {
+                        atomicOr(a.status, ST_LIST_OVF);
+                    }
+                }
+                if (c1.emit) {
+                    if (pos1 < (unsigned long long)a.list_cap) {
+                        a.lists[2 * pos1] = (uint32_t)g;
+                        a.lists[2 * pos1 + 1] = ci1;
                     } else {
                         atomicOr(a.status, ST_LIST_OVF);
                     }

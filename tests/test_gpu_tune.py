@@ -86,7 +86,7 @@ def test_load_rejects_other_files(ctx, tmp_path):
     bad = tmp_path / "bad.jsonl"
     for line in ('{"n_log2": 14, "opening": 0, "split": 1, "group_max": 99, "walk_warps": 4, "walk_chunk": 256}',
                  '{"n_log2": 14, "opening": 0, "split": 1, "group_max": 32, "walk_warps": 9, "walk_chunk": 256}',
-                 '{"n_log2": 14, "opening": 0, "split": 1, "group_max": 32, "walk_warps": 4, "walk_chunk": 16}',
+                 '{"n_log2": 14, "opening": 0, "split": 1, "group_max": 32, "walk_warps": 4, "walk_chunk": 48}',
                  '{"n_log2": 14, "opening": 0, "split": 1, "group_max": 32}'):
         bad.write_text(line + "\n")
         with pytest.raises(og.OGError) as e:
@@ -109,7 +109,7 @@ def test_launch_shapes(ctx, opening):
     ot = oracle.Tree(pos, mass, prm)
     a1, _, _ = og.Tree(ctx, pos, mass, dict(prm, opening=gi.OPEN_BH)).force(counts=False)
     oref = ot.force(a_old=a1) if opening == gi.OPEN_REL else ot.force()
-    for w, c in ((2, 32), (8, 1024), (3, 100)):
+    for w, c in ((2, 64), (8, 1024), (3, 100)):
         t = og.Tree(ctx, pos, mass, dict(prm, walk_warps=w, walk_chunk=c))
         a, p, n = t.force(a_old=a1) if opening == gi.OPEN_REL else t.force()
         assert np.array_equal(p, p0) and np.array_equal(n, n0), (w, c)
@@ -119,7 +119,7 @@ def test_launch_shapes(ctx, opening):
 
 def test_invalid_launch_shapes(ctx):
     pos, mass, prm = gi.config("uniform-32k", n=1000)
-    for bad in (dict(walk_warps=9), dict(walk_warps=-1), dict(walk_chunk=31), dict(walk_chunk=1025)):
+    for bad in (dict(walk_warps=9), dict(walk_warps=-1), dict(walk_chunk=63), dict(walk_chunk=1025)):
         with pytest.raises(og.OGError) as e:
             og.Tree(ctx, pos, mass, dict(prm, **bad))
         assert e.value.status == og.OG_ERR_ARG
