@@ -50,7 +50,9 @@ typedef enum {
     OG_ERR_ARG = -1,         /* invalid argument (NaN position, N out of range, ...) */
     OG_ERR_OOM = -2,         /* device or host allocation failed */
     OG_ERR_CUDA = -3,        /* a CUDA runtime call failed */
-    OG_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out */
+    OG_ERR_TIMEOUT = -4,     /* reserved for a bounded device-side wait that ran out; no
+                                kernel of this library waits on another block, so no
+                                call returns it */
     OG_ERR_BUDGET = -5,      /* the request does not fit the HBM budget */
     OG_ERR_OVERFLOW = -6,    /* a fixed-capacity device buffer overflowed */
     OG_ERR_STATE = -7        /* call not valid in the handle's state */
