@@ -223,7 +223,7 @@ __device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, in
 // pairs (the f32x2 multiply and fused multiply-add of sm_100 and later:
 // each half is the same IEEE operation as the scalar one, so the cutoff
 // decision is unchanged); an odd last entry goes alone.
-template <bool kSplit, bool kPot = false>
+template <bool kSplit, bool kPot = false, int kUnroll = 2>
 __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int R, uint32_t xi,
                                          uint32_t yi, uint32_t zi, const WalkParams &p,
                                          float &ax, float &ay, float &az, float &ap) {
@@ -237,7 +237,7 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
     const float2 c_tsp = make_float2(kTwoOverSqrtPi, kTwoOverSqrtPi);
     float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
     int e = rep;
-#pragma unroll 2
+#pragma unroll kUnroll
     for (; e + R < cnt; e += 2 * R) {
         const uint4 s0 = ch[e], s1 = ch[e + R];
         const float2 fx = make_float2((float)(int)(s0.x - xi), (float)(int)(s1.x - xi));
@@ -452,6 +452,9 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
     // blockDim.x = 32 * a.warps and the launch sizes smem to match
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int chunk = a.chunk;
+    // far-entry pairs in flight per lane: 4 in the Barnes-Hut kernels, 2 where
+    // the relative test's extra registers would spill
+    constexpr int kFarUnroll = kOpen == OG_OPEN_BH ? 4 : 2;
     unsigned char *wbase = smem + (size_t)warp * warp_smem(chunk);
     uint2 *stk = reinterpret_cast<uint2 *>(wbase);
     uint4 *chn = reinterpret_cast<uint4 *>(wbase + kStackCap * sizeof(uint2));
@@ -605,7 +608,7 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
             if (cf + nfar > chunk) {
                 __syncwarp();
                 float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
-                eval_far<kSplit, kPot>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
+                eval_far<kSplit, kPot, kFarUnroll>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
                 acc.add(tx, ty, tz);
                 if (kPot) kahan_add(psum, pcomp, tp);
                 cf = 0;
@@ -664,7 +667,7 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
         __syncwarp();
         {
             float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
-            eval_far<kSplit, kPot>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
+            eval_far<kSplit, kPot, kFarUnroll>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
             acc.add(tx, ty, tz);
             if (kPot) kahan_add(psum, pcomp, tp);
             tx = ty = tz = tp = 0.f;
