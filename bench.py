@@ -81,6 +81,16 @@ def profiled_traffic(workload):
         return None
 
 
+def walk_traffic_per_launch(workload, prm):
+    """DRAM bytes per walk launch, like `achieved` (which divides the flops of
+    the step's walk launches by their time): the step's traffic over its
+    launches, two for the relative criterion (a Barnes-Hut first pass), else one."""
+    per_step = profiled_traffic(workload)
+    if per_step is None:
+        return None
+    return per_step / (2 if prm.get("opening") == gi.OPEN_REL else 1)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -523,8 +533,8 @@ def main():
     peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     achieved = inter_step * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
-            "traffic_unit": "bytes per step (both walk launches)",
+            "frac": achieved / peak, "traffic": walk_traffic_per_launch(args.workload, prm),
+            "traffic_unit": "bytes per walk launch (mean over the step's launches)",
             "kernel": "k_walk (both passes)",
             "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
             "frac_at_observed_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 *
