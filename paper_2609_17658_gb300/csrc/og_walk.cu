@@ -108,7 +108,7 @@ struct WalkArgs {
 };
 
 // multi-function-unit approximations (PTX .approx with flush-to-zero); the
-// operands here are never subnormal: r^2 >= 1 in grid units, see eval_chunk
+// operands here are never subnormal: r^2 >= 1 in grid units, see eval_near
 __device__ __forceinline__ float rsqrt_ftz(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -146,17 +146,18 @@ __device__ __forceinline__ unsigned long long sq64(uint32_t g) {
     return (unsigned long long)g * (unsigned long long)g;
 }
 
-// Chunk evaluation for one target per lane.  Entries e = rep, rep + R, ...
-// are this lane's share.  r^2 is guarded from below by 1 (a nonzero integer
+// Near-chunk evaluation for one target per lane (entries closer than h to
+// the group box: the softened kernel may apply).  Entries e = rep, rep + R,
+// ... are this lane's share.  r^2 is guarded from below by 1 (a nonzero integer
 // separation has r^2 >= 1 in grid units); a zero separation then contributes
 // f * 0 = 0 exactly, the self term included.
 // kPot: also the short-range potential sum of m erfc(r / 2 r_s) psi(r), psi the
 // potential kernel of the spline (1/r beyond h); the self term (r = 0) is left
 // out explicitly, it has no force to vanish with.
-template <bool kSplit, bool kNear, bool kPot = false>
-__device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, int R, uint32_t xi,
-                                           uint32_t yi, uint32_t zi, const WalkParams &p,
-                                           float &ax, float &ay, float &az, float &ap) {
+template <bool kSplit, bool kPot = false>
+__device__ __forceinline__ void eval_near(const uint4 *ch, int cnt, int rep, int R, uint32_t xi,
+                                          uint32_t yi, uint32_t zi, const WalkParams &p,
+                                          float &ax, float &ay, float &az, float &ap) {
     const float rc2 = p.rc2, inv_2rs = p.inv_2rs, kexp = p.kexp;
     const float h = p.h, inv_h = p.inv_h;
     const float hinv3 = inv_h * inv_h * inv_h;
@@ -172,9 +173,8 @@ __device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, in
         const float r2c = fmaxf(r2, 1.0f);
         const float rinv = rsqrt_ftz(r2c);
         float mS = m;
-        float r = 0.0f;
+        const float r = r2c * rinv;
         float erfcv = 1.0f;
-        if (kSplit || kNear) r = r2c * rinv;
         if (kSplit) {
             const float us = r * inv_2rs;
             const float t = rcp_ftz(fmaf(kAsP, us, 1.0f));
@@ -185,7 +185,7 @@ __device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, in
         }
         if (kPot) {
             float psi = rinv;
-            if (kNear) {
+            {
                 const float u = r * inv_h;
                 const float u2 = u * u;
                 const float pin = fmaf(u2, fmaf(u2, fmaf(-32.0f / 5.0f, u, 48.0f / 5.0f), -16.0f / 3.0f),
@@ -199,7 +199,7 @@ __device__ __forceinline__ void eval_chunk(const uint4 *ch, int cnt, int rep, in
             ap = fmaf((r2 > 0.0f ? m : 0.0f) * erfcv, psi, ap);
         }
         float g = rinv * rinv * rinv;
-        if (kNear) {
+        {
             // cubic-spline softened kernel inside h (Monaghan 1985 form)
             const float u = r * inv_h;
             const float u2 = u * u;
@@ -617,7 +617,7 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
             if (cn + nnear > kNearChunk) {
                 __syncwarp();
                 float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
-                eval_chunk<kSplit, true, kPot>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
+                eval_near<kSplit, kPot>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
                 acc.add(tx, ty, tz);
                 if (kPot) kahan_add(psum, pcomp, tp);
                 cn = 0;
@@ -671,7 +671,7 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
             acc.add(tx, ty, tz);
             if (kPot) kahan_add(psum, pcomp, tp);
             tx = ty = tz = tp = 0.f;
-            eval_chunk<kSplit, true, kPot>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
+            eval_near<kSplit, kPot>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
             acc.add(tx, ty, tz);
             if (kPot) kahan_add(psum, pcomp, tp);
         }
