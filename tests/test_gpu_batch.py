@@ -110,3 +110,43 @@ def test_batch_rejects_mixed_criteria(ctx):
     with pytest.raises(og.OGError) as e:
         og.og_batch_force(ctx.h, descs)
     assert e.value.status == og.OG_ERR_ARG
+
+
+def test_fullsize_batch_sampled(ctx):
+    """The batched workload at full size, in the launch configuration the
+    benchmark times: 512 boxes with N log-uniform in [4096, 262144] (about
+    35M particles), device pointers, one og_batch_force call.  Six boxes (the
+    largest, the smallest and four drawn at random) are checked against the
+    oracle on sampled groups: counts exact, accelerations within tolerance,
+    and every box's counts are those of its own tree's group sizes."""
+    torch = pytest.importorskip("torch")
+    boxes = gi.batch_boxes(512)
+    descs = []
+    for b in boxes:
+        n = len(b.mass)
+        descs.append(dict(pos=torch.from_numpy(b.pos).cuda(), mass=torch.from_numpy(b.mass).cuda(),
+                          params=b.params,
+                          acc=torch.empty((n, 3), dtype=torch.float32, device="cuda"),
+                          n_pp=torch.empty(n, dtype=torch.int32, device="cuda"),
+                          n_pn=torch.empty(n, dtype=torch.int32, device="cuda")))
+    info = og.og_batch_force(ctx.h, descs)
+    torch.cuda.synchronize()
+    sizes = np.array([len(b.mass) for b in boxes])
+    assert info["boxes"] == 512 and info["particles"] == int(sizes.sum())
+    r = np.random.default_rng(17)
+    pick = {int(sizes.argmax()), int(sizes.argmin())}
+    while len(pick) < 6:
+        pick.add(int(r.integers(0, len(boxes))))
+    for k in sorted(pick):
+        b = boxes[k]
+        acc = descs[k]["acc"].cpu().numpy()
+        npp = descs[k]["n_pp"].cpu().numpy().view(np.uint32)
+        npn = descs[k]["n_pn"].cpu().numpy().view(np.uint32)
+        ot = oracle.Tree(b.pos, b.mass, b.params)
+        sel = np.sort(r.choice(ot.ngroups, size=min(60, ot.ngroups), replace=False)).astype(np.int64)
+        ref, rpp, rpn = ot.force(groups=sel)
+        perm = ot.get(oracle.F_PERM)
+        gb, ge = ot.get(oracle.F_GBEG), ot.get(oracle.F_GEND)
+        tgt = np.concatenate([perm[gb[g]:ge[g]] for g in sel])
+        assert np.array_equal(npp[tgt], rpp[tgt]) and np.array_equal(npn[tgt], rpn[tgt]), k
+        parity.check_accel(acc[tgt], ref[tgt])
