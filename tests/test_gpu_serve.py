@@ -106,3 +106,23 @@ def test_budget_admission_and_errors():
         with pytest.raises(og.OGError):
             og.og_serve_submit(ctx.h, reqs[0].pos, reqs[0].vel, reqs[0].mass,
                                dict(reqs[0].params, opening=gi.OPEN_REL))
+
+
+def test_fullsize_requests_same_alone_and_in_the_mix():
+    """The served workload's size range (N log-uniform in [1e4, 2e6],
+    halo-clustered, 8 kick-drift steps), plus one request at the top of the
+    range: each result is bitwise the same served alone and in the mix."""
+    B.build()
+    reqs = gi.request_stream(1000.0, 10.0, seed=21, max_requests=5)
+    big = gi.request_stream(1000.0, 10.0, seed=22, n_lo=2_000_000, n_hi=2_000_000,
+                            max_requests=1)
+    reqs = reqs + big
+    assert max(len(q.mass) for q in reqs) == 2_000_000
+    with og.Context(0) as ctx:
+        mixed, res_m = _serve(ctx, reqs)
+    with og.Context(0) as ctx:
+        alone, res_a = _serve(ctx, reqs, wait_each=True)
+    for (am, pm), (aa, pa), r, q in zip(mixed, alone, res_m, reqs):
+        assert r["steps"] == q.nsteps and r["n"] == len(q.mass)
+        assert np.isfinite(am).all() and np.abs(am).max() > 0
+        assert np.array_equal(am, aa) and np.array_equal(pm, pa)
