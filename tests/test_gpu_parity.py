@@ -237,3 +237,27 @@ def test_quantization_of_special_values(ctx, box):
     for a in range(3):
         want = np.array([oracle.quantize1(float(x), box) for x in pos[perm, a]], dtype=np.uint32)
         assert np.array_equal(spos[a], want)
+
+
+@pytest.mark.parametrize("opening", [gi.OPEN_BH, gi.OPEN_REL])
+def test_massless_particles_and_nodes(ctx, opening):
+    """Zero masses: a massless node takes its cell centre as its centre of
+    mass, massless sources add nothing, and the relative criterion sees
+    a_min = 0 for groups of massless targets.  Tree bit-exact, counts exact,
+    forces within the tolerance against the oracle."""
+    pos, mass, prm = gi.config("clustered-2m", n=20000)
+    mass = mass.copy()
+    r = np.random.default_rng(19)
+    mass[r.random(len(mass)) < 0.3] = 0.0            # scattered massless particles
+    mass[np.argsort(pos[:, 0])[:2000]] = 0.0         # a massless slab: whole massless nodes
+    prm = dict(prm, opening=opening)
+    gt = og.Tree(ctx, pos, mass, prm)
+    ot = oracle.Tree(pos, mass, prm)
+    parity.compare_build(gt, ot)
+    a1 = None
+    if opening == gi.OPEN_REL:
+        a1, _, _ = og.Tree(ctx, pos, mass, dict(prm, opening=gi.OPEN_BH)).force(counts=False)
+    acc, npp, npn = gt.force(a_old=a1)
+    ref, rpp, rpn = ot.force(a_old=a1)
+    assert np.array_equal(npp, rpp) and np.array_equal(npn, rpn)
+    parity.check_accel(acc, ref)
