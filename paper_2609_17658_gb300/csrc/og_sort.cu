@@ -6,7 +6,7 @@
 //   1. upsweep:   per 2048-key tile, a 256-bin digit histogram (shared-memory
 //                 atomics, one sub-histogram per warp), stored digit-major;
 //   2. scan:      exclusive scan over (digit, tile) -> global offsets;
-//   3. downsweep: stable in-tile ranking with __match_any_sync (each warp owns
+//   3. downsweep: stable in-tile ranking by warp peer masks (each warp owns
 //                 256 consecutive keys, 8 rounds of 32), keys staged in shared
 //                 memory in digit order, then written out so that runs of one
 //                 digit stay contiguous in global memory.
@@ -141,7 +141,15 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const uint64_t *__restri
     for (int r = 0; r < kItems; ++r) {
         int64_t i = base + warp * kPerWarp + r * 32 + lane;
         uint32_t d = (i < n) ? ((uint32_t)(k[r] >> shift) & 0xffu) : (uint32_t)kRadix;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        // lanes with the same digit (9 bits: 256 marks an invalid key), from
+        // one ballot per bit plane
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int bit = 0; bit < 9; ++bit) {
+            const bool on = (d >> bit) & 1u;
+            const unsigned bb = __ballot_sync(0xffffffffu, on);
+            peers &= on ? bb : ~bb;
+        }
         int leader = __ffs(peers) - 1;
         uint32_t before = (d < kRadix) ? S.wcnt[warp][d] : 0u;
         __syncwarp();
