@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,9 +36,20 @@ METRIC = "tree-force particles/s & interactions/s at 2.1M; served p50/p99 latenc
 UNIT = "particles/s"
 # Algorithmic FP32 work of one interaction in the walk's evaluation loop (the
 # instruction mix of eval_chunk, counting an FMA as 2 flops and a
-# multi-function unit op or a conversion as 1): see the design notes.
+# multi-function unit op or a conversion as 1).
 FLOPS_PER_INTERACTION = 38
 FP32_LANES_PER_SM = 128
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+MEASURED = _measured_peaks()
 
 
 WALK_SOURCE = "paper_2609_17658_gb300/csrc/og_walk.cu"
@@ -103,6 +115,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-kdk", action="store_true")
+    ap.add_argument("--no-pm", action="store_true")
     ap.add_argument("--no-fp32-peak", action="store_true",
                     help="skip the FP32 FMA-rate measurement after the timed region")
     ap.add_argument("--served-seconds", type=float, default=6.0)
@@ -427,6 +440,44 @@ def describe(name, prm):
             f"cutoff {prm['rcut_over_rs']:g} r_s, {crit}")
 
 
+def pm_bench(og, ctx, torch, dev, stream, dpos, dmass, prm, steps, flush):
+    """Long-range particle-mesh force (og_tree_pm_force) of the step's workload on
+    the mesh with r_s = 1.25 mesh cells (256^3 for r_s = 1.25/256): device
+    buffers, L2 flushed before every call, CUDA events on the launching
+    stream.  Algorithmic bytes, each array read or written once per step:
+    zeroing the 8-byte fixed-point mesh, the assignment's read-modify-write of
+    it, the conversion (8 B in, 4 B out per point), the FFTs and the Green's
+    multiplication (4 B in and 4 B out per point each: 8 + 8 + 8), the
+    interpolation's potential read (4 B per point); per particle 16 B of
+    positions and mass in, 4 B of permutation and 12 B of acceleration."""
+    mesh = 1 << int(round(math.log2(1.25 * prm["box"] / prm["r_s"])))
+    n = int(dmass.shape[0])
+    acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    h = og.og_tree_build(ctx.h, dpos, dmass, prm)
+    ms = []
+    for k in range(3 + steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        og.og_tree_pm_force(h, mesh, acc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            ms.append(e0.elapsed_time(e1))
+    og.og_tree_free(h)
+    cells = mesh ** 3
+    algo = cells * (8 + 16 + 12 + 8 + 8 + 8 + 4) + n * (16 + 4 + 12)
+    t = statistics.median(ms)
+    peak = MEASURED.get("hbm_gbs")
+    gbs = algo / (t * 1e-3) / 1e9
+    return {"workload": f"{n} particles of the step's workload, mesh {mesh}^3 "
+                        f"(r_s = {prm['r_s'] * mesh / prm['box']:.2f} cells), FP32 cuFFT",
+            "ms": t, "particles_per_s": n / (t * 1e-3),
+            "roofline": {"bound": "hbm", "algorithmic_bytes": algo, "achieved": gbs, "peak": peak,
+                         "unit": "GB/s", "frac": gbs / peak if peak else None}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -555,6 +606,11 @@ def main():
     if not args.no_served and rank == 0:
         served = served_bench(og, torch, dev, seconds=args.served_seconds)
 
+    pmr = None
+    if not args.no_pm:
+        pmr = pm_bench(og, ctx, torch, dev, stream, dpos, dmass, prm, max(3, args.steps), flush)
+        pmr["treepm_ms_per_step"] = ms_per_step + pmr["ms"]
+
     kdk = None
     if not args.no_kdk and rank == 0:
         kdk = kdk_bench(og, ctx)
@@ -577,7 +633,7 @@ def main():
                "walk_interactions_per_s": inter_step / (walk_ms * 1e-3),
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                "roofline": roof, "cpu_baseline": cpu, "batched": batched, "served": served,
-               "individual_steps": kdk}
+               "individual_steps": kdk, "pm_long_range": pmr}
         print(json.dumps(out), flush=True)
     ctx.close()
     if ws > 1:

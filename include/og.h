@@ -108,6 +108,7 @@ typedef struct {
     int32_t walk_warps;      /* the walk launch shape the tree's force calls use */
     int32_t walk_chunk;
     int32_t pad;
+    double  ms_pm;           /* device time of the last og_tree_pm_force call (ms) */
 } og_tree_info;
 
 /* ---- context ----------------------------------------------------------- */
@@ -161,6 +162,26 @@ og_status og_tree_force_f64(og_tree *t, const float *a_old, double *acc, uint32_
                             uint32_t *n_pn);
 
 og_status og_tree_info_get(const og_tree *t, og_tree_info *info);
+
+/* Long-range particle-mesh acceleration of every particle (Sect. 3.3
+ * "Particle Mesh"): the erf part of the split potential, which og_tree_force
+ * leaves out, so that og_tree_force + og_tree_pm_force is the TreePM force.
+ * The tree's particles are assigned to an Ng^3 mesh by cloud-in-cell
+ * (mesh point (i, j, l) at (i, j, l) L / Ng); the density is Fourier
+ * transformed (cuFFT, FP32), multiplied by -4 pi G / k^2 exp(-k^2 r_s^2)
+ * divided by the squared CIC window prod_a sinc^4(k_a L / 2 Ng) (the k = 0 mode
+ * is zero), and transformed back; a = -grad phi by the fourth-order central
+ * difference on the mesh, interpolated to the particles with the CIC weights.
+ * The assignment sums 64-bit fixed-point integers, so the result does not
+ * depend on the order of the additions.
+ *   mesh: Ng, a power of two in [2, 1024]; r_s = the tree's og_params.r_s > 0.
+ *   acc:  float[N][3] out, G M / L^2, the caller's particle order (device
+ *         memory if the tree was built with OG_DEVICE_PTRS).
+ * Device memory: 16 B per mesh point (plus cuFFT's work area), allocated and
+ * freed on the context's stream; OG_ERR_BUDGET if above the context budget.
+ * Trees of og_tree_build only (one box); OG_ERR_ARG otherwise, for a bad mesh
+ * size or r_s <= 0; OG_ERR_CUDA if cuFFT cannot be loaded or fails. */
+og_status og_tree_pm_force(og_tree *t, int32_t mesh, float *acc);
 
 /* ---- many independent boxes in one launch ------------------------------ */
 

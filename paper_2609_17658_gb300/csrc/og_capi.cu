@@ -263,6 +263,7 @@ og_status og_destroy(og_ctx *c) {
     if (!c) return OG_OK;
     serve_shutdown(c);
     og::tune_free(c);
+    og::pm_free(c);
     if (c->live) {
         // trees the caller did not free
         LiveTrees *L = static_cast<LiveTrees *>(c->live);
@@ -760,6 +761,7 @@ og_status og_tree_info_get(const og_tree *t, og_tree_info *info) {
     info->walk_warps = t->prm.walk_warps;
     info->walk_chunk = t->prm.walk_chunk;
     info->pad = 0;
+    info->ms_pm = t->ms_pm;
     return OG_OK;
 }
 

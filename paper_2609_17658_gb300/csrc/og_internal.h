@@ -75,6 +75,7 @@ struct og_ctx {
     void *serve = nullptr;            // serving state (og_serve.cu)
     void *tune = nullptr;             // measured group sizes (og_tune.cu)
     void *live = nullptr;             // trees of og_tree_build not yet freed (og_capi.cu)
+    void *pm = nullptr;               // cuFFT plans of the particle mesh (og_pm.cu)
 };
 
 struct og_tree {
@@ -131,7 +132,7 @@ struct og_tree {
     int64_t list_cap = 0, list_len = 0;
     // stats
     int64_t interactions = 0, interactions_last = 0;
-    double ms_build = 0, ms_force = 0, ms_walk = 0;
+    double ms_build = 0, ms_force = 0, ms_walk = 0, ms_pm = 0;
     float *pot_next = nullptr;
     bool unscaled_out = false;        // the last pass leaves accelerations in grid units        // potential output of the next force call (sorted order)
     // one allocation holds every array above
@@ -168,6 +169,7 @@ inline bool valid_walk_shape(int warps, int chunk) {
     return warps >= 1 && warps <= 8 && chunk >= 64 && chunk <= 1024;
 }
 void tune_free(og_ctx *c);
+void pm_free(og_ctx *c);   // og_pm.cu: the context's cuFFT plans
 // count of kernels launched by this library in this process
 void note_launch();
 og_status cuda_fail(cudaError_t e, const char *what);

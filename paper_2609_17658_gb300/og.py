@@ -59,7 +59,7 @@ class og_tree_info(C.Structure):
                 ("interactions", C.c_int64), ("interactions_last_pass", C.c_int64),
                 ("ms_build", C.c_double), ("ms_force", C.c_double), ("ms_walk", C.c_double),
                 ("group_max", C.c_int32), ("walk_warps", C.c_int32), ("walk_chunk", C.c_int32),
-                ("pad", C.c_int32)]
+                ("pad", C.c_int32), ("ms_pm", C.c_double)]
 
 
 class og_box(C.Structure):
@@ -127,6 +127,8 @@ def lib():
         L.og_tree_force_pot.argtypes = [P, P, P, P, P, P]
         L.og_tree_force_f64.argtypes = [P, P, P, P, P]
         L.og_tree_force_f64.restype = C.c_int
+        L.og_tree_pm_force.argtypes = [P, C.c_int32, P]
+        L.og_tree_pm_force.restype = C.c_int
         L.og_tree_force_pot.restype = C.c_int
         L.og_kdk_run.argtypes = [P, i64, P, P, P, C.POINTER(og_params), C.POINTER(og_kdk_params), P, P,
                                  C.POINTER(og_kdk_stats)]
@@ -279,6 +281,12 @@ def og_tree_force(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
         pp = None if n_pp is None else _host_ptr(n_pp, np.uint32)
         np_ = None if n_pn is None else _host_ptr(n_pn, np.uint32)
     _check(lib().og_tree_force(tree, op, ap, pp, np_))
+
+
+def og_tree_pm_force(tree, mesh: int, acc) -> None:
+    """Long-range particle-mesh acceleration, acc float32 [N,3] (caller order)."""
+    ap = _dev_ptr(acc, "float32") if _is_torch_cuda(acc) else _host_ptr(acc, np.float32, (3,))
+    _check(lib().og_tree_pm_force(tree, int(mesh), ap))
 
 
 def og_tree_force_f64(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
@@ -538,6 +546,12 @@ class Tree:
         ao = None if a_old is None else np.ascontiguousarray(a_old, dtype=np.float32)
         og_tree_force(self.h, acc, ao, npp, npn)
         return acc, npp, npn
+
+    def pm_force(self, mesh: int):
+        """Long-range particle-mesh acceleration float32 [N,3] (og_tree_pm_force)."""
+        acc = np.zeros((self.n, 3), dtype=np.float32)
+        og_tree_pm_force(self.h, mesh, acc)
+        return acc
 
     def force_pot(self, a_old=None):
         """(acc, n_pp, n_pn, pot) of one force call with the potential output."""
