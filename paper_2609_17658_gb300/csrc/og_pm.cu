@@ -7,7 +7,9 @@
 //   k_pm_deposit   cloud-in-cell assignment: every particle adds m * w to the 8
 //                  mesh points around it, as 64-bit fixed-point integers
 //                  (atomicAdd of integers is exact, so the density does not
-//                  depend on the order of the additions: one value per input)
+//                  depend on the order of the additions: one value per input);
+//                  a warp first sums the contributions of its runs of
+//                  particles that share a cell
 //   k_pm_density   fixed point -> FP32 density (the FFT's input)
 //   cuFFT R2C      forward transform (library call, FP32)
 //   k_pm_green     multiply every mode by the filtered Green's function
@@ -134,18 +136,32 @@ __device__ __forceinline__ float fix_scale(double mtot) {
     return __int_as_float((x + 127) << 23);
 }
 
+// Particles come in key order, so the particles of one mesh cell (same CIC
+// base point, the key's top 3 log2 Ng bits) are contiguous.  Each warp sums the
+// contributions of every such run with a segmented suffix sum (integers: the
+// order does not change the result) and the run's first lane adds the 8 sums,
+// so a dense cell costs 8 atomics per warp instead of 8 per particle.
 __global__ void k_pm_deposit(int64_t n, int shift, int ng, const uint32_t *__restrict__ px,
                              const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
                              const float *__restrict__ pm32, const NodeMom *__restrict__ root,
                              unsigned long long *__restrict__ mesh) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) >= n) return;  // whole warps only
+    const bool valid = i < n;
+    const unsigned lane = threadIdx.x & 31u;
     const float sc = fix_scale(root->M);
-    const uint32_t qx = px[i], qy = py[i], qz = pz[i];
+    const uint32_t qx = valid ? px[i] : 0u, qy = valid ? py[i] : 0u, qz = valid ? pz[i] : 0u;
     const int m1 = ng - 1;
     const int ix = (int)(qx >> shift), iy = (int)(qy >> shift), iz = (int)(qz >> shift);
     const float fx = frac_of(qx, shift), fy = frac_of(qy, shift), fz = frac_of(qz, shift);
-    const float m = pm32[i] * sc;
+    const float m = valid ? pm32[i] * sc : 0.0f;
+    // runs of equal base points within the warp (past-the-end lanes form their own run)
+    const uint32_t cell = valid ? (uint32_t)(((ix * ng) + iy) * ng + iz) : 0xffffffffu;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, cell, 1);
+    const bool head = lane == 0 || cell != prev;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned later = lane == 31 ? 0u : heads & (0xfffffffeu << lane);
+    const unsigned end = later ? (unsigned)__ffs(later) - 2u : 31u;   // last lane of this run
     const float wx[2] = {1.0f - fx, fx}, wy[2] = {1.0f - fy, fy}, wz[2] = {1.0f - fz, fz};
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
@@ -157,8 +173,13 @@ __global__ void k_pm_deposit(int64_t n, int shift, int ng, const uint32_t *__res
             const float mab = ma * wy[b];
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const unsigned long long v = __float2ull_rn(mab * wz[c]);
-                if (v) atomicAdd(&mesh[by + ((iz + c) & m1)], v);
+                unsigned long long v = __float2ull_rn(mab * wz[c]);
+#pragma unroll
+                for (unsigned d = 1; d < 32; d <<= 1) {
+                    const unsigned long long u = __shfl_down_sync(0xffffffffu, v, d);
+                    if (lane + d <= end) v += u;
+                }
+                if (head && valid && v) atomicAdd(&mesh[by + ((iz + c) & m1)], v);
             }
         }
     }
