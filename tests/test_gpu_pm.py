@@ -87,6 +87,20 @@ def test_edge_cases(ctx):
     _check(acc, ref)
 
 
+def test_tree_plus_mesh_is_the_periodic_force(ctx):
+    # the library's short-range tree force (theta = 0) plus its mesh force against the exact
+    # periodic force (an Ewald sum with another split scale): the same bar as the oracle's
+    from tests.test_oracle_pm import ewald_accel, treepm_case
+    pos, mass, prm, x = treepm_case()
+    t = og.Tree(ctx, pos, mass, prm)
+    short, _, _ = t.force(counts=False)
+    long_ = t.pm_force(32)
+    ew = ewald_accel(x, mass, 1.0, 0.6 * prm["r_s"])
+    rms = np.sqrt((ew ** 2).sum(axis=1).mean())
+    e = np.linalg.norm(short.astype(np.float64) + long_ - ew, axis=1)
+    assert e.max() < 3e-3 * rms and np.sqrt((e ** 2).mean()) < 1.2e-3 * rms, e.max() / rms
+
+
 def test_invalid_arguments(ctx):
     pos, mass, prm = gi.config("uniform-32k", n=500)
     t = og.Tree(ctx, pos, mass, prm)

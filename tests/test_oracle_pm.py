@@ -10,7 +10,11 @@ filtered by exp(-k^2 r_s^2).  The references here do not use the oracle's mesh:
     where the erf part is the whole force;
   - conservation laws of cloud-in-cell with an antisymmetric gradient and an
     even Green's function: zero self-force, zero total momentum change, mass
-    conservation of the assignment, zero force on a lattice that fills the mesh.
+    conservation of the assignment, zero force on a lattice that fills the mesh;
+  - the whole TreePM split: the tree's short-range sum plus the mesh equals the
+    exact periodic Newtonian force, an Ewald sum with a different split scale
+    (Ewald sums do not depend on it), so a mismatch between the erfc of the
+    tree and the exp(-k^2 r_s^2) of the mesh shows.
 """
 from __future__ import annotations
 
@@ -39,6 +43,62 @@ def fourier_series_accel(x, m, targets, box, G, r_s):
             s = np.sin(kv @ (x[i] - x[j]))
             out[a] -= (4.0 * math.pi * G / box ** 3) * m[j] * ((w * s)[:, None] * kv).sum(axis=0)
     return out
+
+
+def ewald_accel(x, m, G, r_e):
+    """Exact periodic Newtonian acceleration in the unit box by Ewald summation with
+    the split scale r_e: real-space images within one box plus the Fourier series."""
+    from scipy.special import erfc
+    al = 1.0 / (2.0 * r_e)
+    d0 = x[:, None, :] - x[None, :, :]
+    d0 -= np.round(d0)
+    a = np.zeros_like(x)
+    for img in np.ndindex(3, 3, 3):
+        d = d0 + (np.array(img) - 1.0)
+        r = np.linalg.norm(d, axis=2)
+        self_ = img == (1, 1, 1)
+        if self_:
+            np.fill_diagonal(r, 1.0)
+        f = (erfc(al * r) + 2.0 * al * r / math.sqrt(math.pi) * np.exp(-al * al * r * r)) / r ** 3
+        if self_:
+            np.fill_diagonal(f, 0.0)
+        a -= G * (m[None, :, None] * f[:, :, None] * d).sum(axis=1)
+    nmax = int(math.ceil(math.sqrt(40.0) / r_e / (2.0 * math.pi)))
+    k1 = 2.0 * math.pi * np.arange(-nmax, nmax + 1)
+    KX, KY, KZ = np.meshgrid(k1, k1, k1, indexing="ij")
+    K2 = KX * KX + KY * KY + KZ * KZ
+    sel = K2 > 0
+    kv = np.stack([KX[sel], KY[sel], KZ[sel]], axis=1)
+    w = np.exp(-K2[sel] * r_e * r_e) / K2[sel]
+    ph = x @ kv.T
+    c = (m[:, None] * np.cos(ph)).sum(axis=0)
+    s = (m[:, None] * np.sin(ph)).sum(axis=0)
+    a -= 4.0 * math.pi * G * ((w * (np.sin(ph) * c - np.cos(ph) * s)) @ kv)   # sum_j m_j sin(k.(x_i - x_j))
+    return a
+
+
+def treepm_case():
+    """300 random particles in the unit box, a 32^3 mesh, r_s = 3 mesh cells."""
+    rng = np.random.default_rng(4)
+    pos = rng.uniform(0, 1, (300, 3))
+    mass = rng.uniform(0.5, 1.5, 300) / 300
+    prm = dict(box=1.0, G=1.0, eps=1e-7, r_s=3.0 / 32, rcut_over_rs=4.5, opening=0, theta=0.0,
+               alpha=0.005, theta_first_pass=0.5, leaf_max=1, group_max=32, flags=0)
+    x = pm.quantize(pos).astype(np.float64) / 2.0 ** 32
+    return pos, mass, prm, x
+
+
+def test_tree_plus_mesh_is_the_periodic_force():
+    pos, mass, prm, x = treepm_case()
+    ew = ewald_accel(x, mass, 1.0, 0.6 * prm["r_s"])
+    assert np.abs(ew - ewald_accel(x, mass, 1.0, 1.3 * prm["r_s"])).max() < 1e-12 * np.abs(ew).max()
+    short = oracle.direct(pos, mass, prm)                       # the tree at theta = 0
+    rms = np.sqrt((ew ** 2).sum(axis=1).mean())
+    for r_s_mesh, ok in ((prm["r_s"], True), (2.0 * prm["r_s"], False)):
+        long_ = pm.pm_accel(pm.quantize(pos), mass, 32, 1.0, 1.0, r_s_mesh)
+        e = np.linalg.norm(short + long_ - ew, axis=1)
+        fits = e.max() < 3e-3 * rms and np.sqrt((e ** 2).mean()) < 1.2e-3 * rms
+        assert fits == ok, (r_s_mesh, e.max() / rms)
 
 
 def _pairs(rng, mesh, box, seps_cells, per_sep):
