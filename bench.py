@@ -116,6 +116,7 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-kdk", action="store_true")
     ap.add_argument("--no-pm", action="store_true")
+    ap.add_argument("--no-sph", action="store_true")
     ap.add_argument("--no-fp32-peak", action="store_true",
                     help="skip the FP32 FMA-rate measurement after the timed region")
     ap.add_argument("--served-seconds", type=float, default=6.0)
@@ -478,6 +479,41 @@ def pm_bench(og, ctx, torch, dev, stream, dpos, dmass, prm, steps, flush):
                          "unit": "GB/s", "frac": gbs / peak if peak else None}}
 
 
+def sph_bench(og, ctx, torch, dev, stream, pos, dpos, dmass, prm, steps, flush):
+    """SPH density (og_tree_sph_density, cubic spline) of the step's workload with
+    h_i the distance to the 32nd nearest other particle, the paper's default
+    neighbour number for that kernel in 3D (found on the host with a periodic
+    k-d tree before timing).  Device buffers, L2 flushed before every call,
+    CUDA events on the launching stream."""
+    from scipy.spatial import cKDTree
+    x = np.floor(pos / prm["box"] * 4294967296.0) % 4294967296.0 * (prm["box"] / 4294967296.0)
+    d, _ = cKDTree(x, boxsize=prm["box"]).query(x, k=33, workers=-1)
+    h = torch.from_numpy(d[:, -1].astype(np.float32)).to(dev)
+    n = int(dmass.shape[0])
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    t = og.og_tree_build(ctx.h, dpos, dmass, prm)
+    ms = []
+    for k in range(3 + steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        og.og_tree_sph_density(t, h, rho, cnt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            ms.append(e0.elapsed_time(e1))
+    groups = og.og_tree_info_get(t)["groups"]
+    og.og_tree_free(t)
+    tm = statistics.median(ms)
+    pairs = float(cnt.double().sum().item())
+    return {"workload": f"{n} particles of the step's workload, h = distance to the 32nd "
+                        f"neighbour, cubic spline, {groups} group searches",
+            "ms": tm, "particles_per_s": n / (tm * 1e-3), "neighbour_pairs": pairs,
+            "neighbour_pairs_per_s": pairs / (tm * 1e-3)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -611,6 +647,10 @@ def main():
         pmr = pm_bench(og, ctx, torch, dev, stream, dpos, dmass, prm, max(3, args.steps), flush)
         pmr["treepm_ms_per_step"] = ms_per_step + pmr["ms"]
 
+    sphr = None
+    if not args.no_sph:
+        sphr = sph_bench(og, ctx, torch, dev, stream, pos, dpos, dmass, prm, max(3, args.steps), flush)
+
     kdk = None
     if not args.no_kdk and rank == 0:
         kdk = kdk_bench(og, ctx)
@@ -633,7 +673,8 @@ def main():
                "walk_interactions_per_s": inter_step / (walk_ms * 1e-3),
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                "roofline": roof, "cpu_baseline": cpu, "batched": batched, "served": served,
-               "individual_steps": kdk, "pm_long_range": pmr}
+               "individual_steps": kdk, "pm_long_range": pmr,
+               "sph_density": sphr}
         print(json.dumps(out), flush=True)
     ctx.close()
     if ws > 1:

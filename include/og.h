@@ -109,6 +109,7 @@ typedef struct {
     int32_t walk_chunk;
     int32_t pad;
     double  ms_pm;           /* device time of the last og_tree_pm_force call (ms) */
+    double  ms_sph;          /* device time of the last og_tree_sph_density call (ms) */
 } og_tree_info;
 
 /* ---- context ----------------------------------------------------------- */
@@ -182,6 +183,24 @@ og_status og_tree_info_get(const og_tree *t, og_tree_info *info);
  * Trees of og_tree_build only (one box); OG_ERR_ARG otherwise, for a bad mesh
  * size or r_s <= 0; OG_ERR_CUDA if cuFFT cannot be loaded or fails. */
 og_status og_tree_pm_force(og_tree *t, int32_t mesh, float *acc);
+
+/* SPH density of every particle at given smoothing lengths (Sect. 5 "Smoothed
+ * Particle Hydrodynamics"), with the grouped neighbour search of Sect. 3.7:
+ * rho_i = sum_j m_j W(|x_i - x_j|, h_i) over the particles j closer than h_i,
+ * i itself included, with the cubic spline W = 8 / (pi h^3) w(r / h),
+ * w(q) = 1 - 6 q^2 + 6 q^3 (q < 1/2), 2 (1 - q)^3 (1/2 <= q < 1).  The search
+ * runs once per walk group of the tree.  j is a neighbour of i iff
+ * r2 < h2 in float32, r2 = (fx fx + fy fy) + fz fz with f the float32 of the
+ * exact minimum-image grid separation and h2 = hg hg, hg = float32(h 2^32 / L)
+ * (each operation rounded on its own), so n_ngb is an exact integer of those
+ * inputs.  The density sums in float32.
+ *   h:     float[N] in, 0 < h < L / 2, the caller's particle order.
+ *   rho:   float[N] out (mass / L^3 units of the inputs), the caller's order.
+ *   n_ngb: uint32[N] out or NULL: the neighbour count, i itself included.
+ * Device pointers if the tree was built with OG_DEVICE_PTRS.  Trees of
+ * og_tree_build only (one box), not refitted (OG_ERR_STATE); an h out of range
+ * gives OG_ERR_ARG. */
+og_status og_tree_sph_density(og_tree *t, const float *h, float *rho, uint32_t *n_ngb);
 
 /* ---- many independent boxes in one launch ------------------------------ */
 

@@ -157,7 +157,7 @@ og_status check_status(og_ctx *c) {
     cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream);
     cudaStreamSynchronize(c->stream);
     if (st & ST_BAD_INPUT) {
-        set_error("non-finite position or negative/non-finite mass");
+        set_error("non-finite position, negative/non-finite mass, or a smoothing length out of (0, L/2)");
         return OG_ERR_ARG;
     }
     if (st & ST_STACK_OVF) {
@@ -762,6 +762,7 @@ og_status og_tree_info_get(const og_tree *t, og_tree_info *info) {
     info->walk_chunk = t->prm.walk_chunk;
     info->pad = 0;
     info->ms_pm = t->ms_pm;
+    info->ms_sph = t->ms_sph;
     return OG_OK;
 }
 

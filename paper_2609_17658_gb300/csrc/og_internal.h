@@ -132,7 +132,7 @@ struct og_tree {
     int64_t list_cap = 0, list_len = 0;
     // stats
     int64_t interactions = 0, interactions_last = 0;
-    double ms_build = 0, ms_force = 0, ms_walk = 0, ms_pm = 0;
+    double ms_build = 0, ms_force = 0, ms_walk = 0, ms_pm = 0, ms_sph = 0;
     float *pot_next = nullptr;
     bool unscaled_out = false;        // the last pass leaves accelerations in grid units        // potential output of the next force call (sorted order)
     // one allocation holds every array above

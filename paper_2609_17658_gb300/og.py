@@ -59,7 +59,7 @@ class og_tree_info(C.Structure):
                 ("interactions", C.c_int64), ("interactions_last_pass", C.c_int64),
                 ("ms_build", C.c_double), ("ms_force", C.c_double), ("ms_walk", C.c_double),
                 ("group_max", C.c_int32), ("walk_warps", C.c_int32), ("walk_chunk", C.c_int32),
-                ("pad", C.c_int32), ("ms_pm", C.c_double)]
+                ("pad", C.c_int32), ("ms_pm", C.c_double), ("ms_sph", C.c_double)]
 
 
 class og_box(C.Structure):
@@ -129,6 +129,8 @@ def lib():
         L.og_tree_force_f64.restype = C.c_int
         L.og_tree_pm_force.argtypes = [P, C.c_int32, P]
         L.og_tree_pm_force.restype = C.c_int
+        L.og_tree_sph_density.argtypes = [P, P, P, P]
+        L.og_tree_sph_density.restype = C.c_int
         L.og_tree_force_pot.restype = C.c_int
         L.og_kdk_run.argtypes = [P, i64, P, P, P, C.POINTER(og_params), C.POINTER(og_kdk_params), P, P,
                                  C.POINTER(og_kdk_stats)]
@@ -287,6 +289,19 @@ def og_tree_pm_force(tree, mesh: int, acc) -> None:
     """Long-range particle-mesh acceleration, acc float32 [N,3] (caller order)."""
     ap = _dev_ptr(acc, "float32") if _is_torch_cuda(acc) else _host_ptr(acc, np.float32, (3,))
     _check(lib().og_tree_pm_force(tree, int(mesh), ap))
+
+
+def og_tree_sph_density(tree, h, rho, n_ngb=None) -> None:
+    """SPH density at the smoothing lengths h float32 [N]: rho float32 [N], n_ngb uint32 [N]."""
+    if _is_torch_cuda(rho):
+        hp = _dev_ptr(h, "float32")
+        rp = _dev_ptr(rho, "float32")
+        cp = None if n_ngb is None else _dev_ptr(n_ngb, "int32")
+    else:
+        hp = _host_ptr(h, np.float32)
+        rp = _host_ptr(rho, np.float32)
+        cp = None if n_ngb is None else _host_ptr(n_ngb, np.uint32)
+    _check(lib().og_tree_sph_density(tree, hp, rp, cp))
 
 
 def og_tree_force_f64(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
@@ -552,6 +567,13 @@ class Tree:
         acc = np.zeros((self.n, 3), dtype=np.float32)
         og_tree_pm_force(self.h, mesh, acc)
         return acc
+
+    def sph_density(self, h):
+        """(rho float32 [N], n_ngb uint32 [N]) at the smoothing lengths h (og_tree_sph_density)."""
+        rho = np.zeros(self.n, dtype=np.float32)
+        cnt = np.zeros(self.n, dtype=np.uint32)
+        og_tree_sph_density(self.h, np.ascontiguousarray(h, dtype=np.float32), rho, cnt)
+        return rho, cnt
 
     def force_pot(self, a_old=None):
         """(acc, n_pp, n_pn, pot) of one force call with the potential output."""
