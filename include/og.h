@@ -202,6 +202,26 @@ og_status og_tree_pm_force(og_tree *t, int32_t mesh, float *acc);
  * gives OG_ERR_ARG. */
 og_status og_tree_sph_density(og_tree *t, const float *h, float *rho, uint32_t *n_ngb);
 
+/* Smoothing lengths from the paper's neighbour relation (Sect. 5):
+ * (4 pi / 3) h_i^3 rho_i = N m_i, N = n_target, with the density and search of
+ * og_tree_sph_density.  Per particle, N_eff = (4 pi / 3) h^3 rho / m (FP64 of
+ * the FP32 density) is compared with N: within tol N the particle is done;
+ * else h is multiplied (too few neighbours) or divided (too many) by 1.26 until
+ * a bracket [lo, hi] is known, then set to cbrt((lo^3 + hi^3) / 2).  Each
+ * iteration searches only the groups with a particle not yet done.  A particle
+ * that needs h near L / 2 stops at 0.999 L / 2; a massless particle keeps its
+ * h.  After the iterations, rho and n_ngb are those of og_tree_sph_density at
+ * the final h.
+ *   n_target: N > 32/3 (the self term alone gives N_eff = 32/3 for equal
+ *             masses); tol in (0, 1); max_iter in [1, 1000].
+ *   h:        float[N] in (the starting guesses, 0 < h < L / 2) and out.
+ *   rho, n_ngb: as og_tree_sph_density (n_ngb may be NULL).
+ *   iters:    out, or NULL: iterations run (max_iter if some particle did not
+ *             converge).
+ * Same trees, pointers and errors as og_tree_sph_density. */
+og_status og_tree_sph_smoothing(og_tree *t, double n_target, double tol, int32_t max_iter,
+                                float *h, float *rho, uint32_t *n_ngb, int32_t *iters);
+
 /* ---- many independent boxes in one launch ------------------------------ */
 
 /* One independent periodic system of a batch. */

@@ -30,6 +30,8 @@
 // capacity would still only set the stack-overflow status and drop the range.
 // The round count is bounded by the number of nodes plus the buckets' extra
 // rounds.
+#include <cmath>
+
 #include "og_internal.h"
 
 namespace og {
@@ -47,13 +49,14 @@ struct SphArgs {
     const uint32_t *ncbeg, *nccnt;
     const uint32_t *gbeg, *gend, *gbox;
     const uint32_t *px, *py, *pz;
-    const uint32_t *perm;
+    const uint32_t *perm;   // outputs to the caller's order; null: key order
+    const uint8_t *done;    // null, or per particle (key order): converged, skip
     const float *hg;        // smoothing length in grid units, sorted order
     int64_t ngroups;
     int64_t max_rounds;     // nodes + 2 + buckets' extra rounds (<= n / 32)
     double dens;            // 8 / pi * (2^32 / L)^3
-    float *rho;             // caller order
-    uint32_t *nngb;         // caller order, or null
+    float *rho;             // caller order (key order without perm)
+    uint32_t *nngb;         // same order, or null
     uint32_t *status;
 };
 
@@ -80,7 +83,7 @@ __global__ void k_sph_prep(int64_t n, const uint32_t *__restrict__ perm, const f
                            double to_grid, float *__restrict__ hg, uint32_t *status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double v = (double)h[perm[i]];
+    const double v = (double)h[perm ? perm[i] : (uint32_t)i];
     if (!(v > 0.0) || !(v * to_grid < 2147483648.0)) {   // also false for NaN
         atomicOr(status, ST_BAD_INPUT);
         hg[i] = 0.0f;
@@ -104,6 +107,7 @@ __global__ void __launch_bounds__(32 * kSphWarps) k_sph_density(SphArgs a) {
     const uint32_t me = b + lane;
     const bool active = me < e;
     const uint32_t xi = active ? a.px[me] : 0u, yi = active ? a.py[me] : 0u, zi = active ? a.pz[me] : 0u;
+    if (a.done && __all_sync(0xffffffffu, !active || a.done[me] != 0)) return;  // nothing to redo
     const float hgi = active ? a.hg[me] : 0.0f;
     const float h2i = __fmul_rn(hgi, hgi);
     const float inv_h = active && hgi > 0.0f ? 1.0f / hgi : 0.0f;
@@ -216,11 +220,69 @@ __global__ void __launch_bounds__(32 * kSphWarps) k_sph_density(SphArgs a) {
     if (sp > 0) atomicOr(a.status, ST_INTERNAL);   // the round bound was reached
     flush(nc);
     if (active) {
-        const uint32_t i = a.perm[me];
+        const uint32_t i = a.perm ? a.perm[me] : me;
         const double hd = (double)hgi;
         a.rho[i] = __double2float_rn(a.dens * (double)sum / (hd * hd * hd));
         if (a.nngb) a.nngb[i] = cnt;
     }
+}
+
+// One step of the smoothing-length iteration for every particle not yet
+// converged (key order): N_eff = (4 pi / 3) h^3 rho / m against the target N.
+// Within tol N it is done; else the step keeps a bracket [lo, hi] of h (lo:
+// too few neighbours, hi: too many), expands or shrinks h by 1.26 until both
+// ends are known, then bisects in volume, h = cbrt((lo^3 + hi^3) / 2).  A
+// particle whose h would reach the cap (just below L / 2) stops there.
+__global__ void k_sph_update(int64_t n, double nt, double tol, double hcap, const double *__restrict__ m,
+                             const float *__restrict__ rho, float *__restrict__ h, float *__restrict__ lo,
+                             float *__restrict__ hi, uint8_t *__restrict__ done,
+                             unsigned long long *__restrict__ left) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || done[i]) return;
+    const double hh = (double)h[i];
+    if (!(m[i] > 0.0)) {   // a massless particle has no neighbour relation to meet
+        done[i] = 1;
+        return;
+    }
+    const double neff = (4.0 * M_PI / 3.0) * hh * hh * hh * (double)rho[i] / m[i];
+    if (fabs(neff - nt) <= tol * nt) {
+        done[i] = 1;
+        return;
+    }
+    double l = (double)lo[i], u = (double)hi[i];
+    if (neff < nt) l = hh; else u = hh;
+    double next;
+    if (l > 0.0 && u > 0.0) next = cbrt(0.5 * (l * l * l + u * u * u));
+    else next = (neff < nt) ? hh * 1.26 : hh / 1.26;
+    lo[i] = (float)l;
+    hi[i] = (float)u;
+    if (next >= hcap) {
+        next = hcap;
+        if (hh >= hcap) {   // already at the cap and still too few neighbours
+            done[i] = 1;
+            return;
+        }
+    }
+    h[i] = (float)next;
+    atomicAdd(left, 1ull);
+}
+
+__global__ void k_sph_to_caller(int64_t n, const uint32_t *__restrict__ perm, const float *__restrict__ hs,
+                                const float *__restrict__ rs, const uint32_t *__restrict__ cs,
+                                float *__restrict__ h, float *__restrict__ rho, uint32_t *__restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    h[j] = hs[i];
+    rho[j] = rs[i];
+    if (cnt) cnt[j] = cs[i];
+}
+
+__global__ void k_sph_gather(int64_t n, const uint32_t *__restrict__ perm, const float *__restrict__ h,
+                             float *__restrict__ hs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    hs[i] = h[perm[i]];
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -282,6 +344,7 @@ extern "C" og_status og_tree_sph_density(og_tree *t, const float *h, float *rho,
     a.py = t->py;
     a.pz = t->pz;
     a.perm = t->perm;
+    a.done = nullptr;
     a.hg = hg;
     a.ngroups = t->ngroups;
     a.max_rounds = t->nnodes + 2 + (n + 31) / 32;
@@ -308,5 +371,117 @@ extern "C" og_status og_tree_sph_density(og_tree *t, const float *h, float *rho,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     t->ms_sph = ms;
+    return check_status(c);
+}
+
+extern "C" og_status og_tree_sph_smoothing(og_tree *t, double n_target, double tol, int32_t max_iter,
+                                           float *h, float *rho, uint32_t *n_ngb, int32_t *iters) {
+    if (!t || !h || !rho) { set_error("og_tree_sph_smoothing: NULL argument"); return OG_ERR_ARG; }
+    if (t->nseg != 1) { set_error("og_tree_sph_smoothing: a tree of one box only"); return OG_ERR_ARG; }
+    if (t->refit) { set_error("og_tree_sph_smoothing: a refitted tree (rebuild it)"); return OG_ERR_STATE; }
+    if (!(n_target > 32.0 / 3.0) || !std::isfinite(n_target) || !(tol > 0.0) || !(tol < 1.0) ||
+        max_iter < 1 || max_iter > 1000) {
+        set_error("og_tree_sph_smoothing: need N > 32/3 (the self term), 0 < tol < 1, 1 <= max_iter <= 1000");
+        return OG_ERR_ARG;
+    }
+    og_ctx *c = t->ctx;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int64_t n = t->n;
+    const bool dev = (t->prm.flags & OG_DEVICE_PTRS) != 0;
+    const double half = 0.5 * t->prm.box;
+    if (!dev)
+        for (int64_t i = 0; i < n; ++i)
+            if (!(h[i] > 0.0f) || !((double)h[i] < half)) {
+                set_error("og_tree_sph_smoothing: h[%lld] = %g is not in (0, L/2)", (long long)i, (double)h[i]);
+                return OG_ERR_ARG;
+            }
+    // key-order state: h, lo, hi, grid h, rho, counts (4 B each), done (1 B); a
+    // counter; host staging of h in/out, rho and counts out
+    const size_t b4 = ((size_t)n * 4 + 255) & ~(size_t)255, b1 = ((size_t)n + 255) & ~(size_t)255;
+    const size_t total = 6 * b4 + b1 + 256 + (dev ? 0 : 3 * b4);
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(&buf, total, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (sph smoothing)");
+    float *hs = reinterpret_cast<float *>(buf), *lo = reinterpret_cast<float *>(buf + b4);
+    float *hi = reinterpret_cast<float *>(buf + 2 * b4), *hg = reinterpret_cast<float *>(buf + 3 * b4);
+    float *rs = reinterpret_cast<float *>(buf + 4 * b4);
+    uint32_t *cs = reinterpret_cast<uint32_t *>(buf + 5 * b4);
+    uint8_t *done = reinterpret_cast<uint8_t *>(buf + 6 * b4);
+    unsigned long long *left = reinterpret_cast<unsigned long long *>(buf + 6 * b4 + b1);
+    float *d_h = h, *d_rho = rho;
+    uint32_t *d_cnt = n_ngb;
+    if (!dev) {
+        char *st = buf + 6 * b4 + b1 + 256;
+        d_h = reinterpret_cast<float *>(st);
+        d_rho = reinterpret_cast<float *>(st + b4);
+        d_cnt = n_ngb ? reinterpret_cast<uint32_t *>(st + 2 * b4) : nullptr;
+        cudaMemcpyAsync(d_h, h, (size_t)n * 4, cudaMemcpyHostToDevice, s);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    k_sph_gather<<<nblk(n, 256), 256, 0, s>>>(n, t->perm, d_h, hs); note_launch();
+    cudaMemsetAsync(lo, 0, 2 * b4, s);   // lo and hi: no bracket yet
+    cudaMemsetAsync(done, 0, b1, s);
+    const double to_grid = 4294967296.0 / t->prm.box;
+    SphArgs a;
+    a.crec = t->crec;
+    a.ncbeg = t->ncbeg;
+    a.nccnt = t->nccnt;
+    a.gbeg = t->gbeg;
+    a.gend = t->gend;
+    a.gbox = t->gbox;
+    a.px = t->px;
+    a.py = t->py;
+    a.pz = t->pz;
+    a.perm = nullptr;
+    a.done = done;
+    a.hg = hg;
+    a.ngroups = t->ngroups;
+    a.max_rounds = t->nnodes + 2 + (n + 31) / 32;
+    a.dens = 8.0 / M_PI * to_grid * to_grid * to_grid;
+    a.rho = rs;
+    a.nngb = cs;
+    a.status = c->d_status;
+    const double hcap = std::nextafter((float)(half * 0.999), 0.0f);
+    int32_t it = 0;
+    og_status st = OG_OK;
+    while (it < max_iter) {
+        k_sph_prep<<<nblk(n, 256), 256, 0, s>>>(n, nullptr, hs, to_grid, hg, c->d_status); note_launch();
+        k_sph_density<<<nblk(t->ngroups, kSphWarps), 32 * kSphWarps, kSphSmem, s>>>(a); note_launch();
+        ++it;
+        cudaMemsetAsync(left, 0, sizeof(unsigned long long), s);
+        k_sph_update<<<nblk(n, 256), 256, 0, s>>>(n, n_target, tol, hcap, t->pm64, rs, hs, lo, hi, done, left);
+        note_launch();
+        unsigned long long h_left = 0;
+        cudaMemcpyAsync(&h_left, left, sizeof(h_left), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { st = cuda_fail(e, "sph smoothing"); break; }
+        if (h_left == 0) break;
+    }
+    if (st == OG_OK) {
+        // the densities and counts at the final h (a particle that moved in the
+        // last step needs them at its new h)
+        a.done = nullptr;
+        k_sph_prep<<<nblk(n, 256), 256, 0, s>>>(n, nullptr, hs, to_grid, hg, c->d_status); note_launch();
+        k_sph_density<<<nblk(t->ngroups, kSphWarps), 32 * kSphWarps, kSphSmem, s>>>(a); note_launch();
+        k_sph_to_caller<<<nblk(n, 256), 256, 0, s>>>(n, t->perm, hs, rs, cs, d_h, d_rho, d_cnt); note_launch();
+        cudaEventRecord(e1, s);
+        if (!dev) {
+            cudaMemcpyAsync(h, d_h, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(rho, d_rho, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+            if (n_ngb) cudaMemcpyAsync(n_ngb, d_cnt, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+        }
+    }
+    cudaFreeAsync(buf, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess && st == OG_OK) st = cuda_fail(e, "sph smoothing");
+    float ms = 0.f;
+    if (st == OG_OK) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    t->ms_sph = ms;
+    if (iters) *iters = it;
     return check_status(c);
 }

@@ -131,6 +131,9 @@ def lib():
         L.og_tree_pm_force.restype = C.c_int
         L.og_tree_sph_density.argtypes = [P, P, P, P]
         L.og_tree_sph_density.restype = C.c_int
+        L.og_tree_sph_smoothing.argtypes = [P, C.c_double, C.c_double, C.c_int32, P, P, P,
+                                            C.POINTER(C.c_int32)]
+        L.og_tree_sph_smoothing.restype = C.c_int
         L.og_tree_force_pot.restype = C.c_int
         L.og_kdk_run.argtypes = [P, i64, P, P, P, C.POINTER(og_params), C.POINTER(og_kdk_params), P, P,
                                  C.POINTER(og_kdk_stats)]
@@ -302,6 +305,22 @@ def og_tree_sph_density(tree, h, rho, n_ngb=None) -> None:
         rp = _host_ptr(rho, np.float32)
         cp = None if n_ngb is None else _host_ptr(n_ngb, np.uint32)
     _check(lib().og_tree_sph_density(tree, hp, rp, cp))
+
+
+def og_tree_sph_smoothing(tree, n_target: float, tol: float, max_iter: int, h, rho, n_ngb=None) -> int:
+    """Smoothing lengths from (4 pi / 3) h^3 rho = N m, h float32 [N] in/out; returns the iterations."""
+    if _is_torch_cuda(rho):
+        hp = _dev_ptr(h, "float32")
+        rp = _dev_ptr(rho, "float32")
+        cp = None if n_ngb is None else _dev_ptr(n_ngb, "int32")
+    else:
+        hp = _host_ptr(h, np.float32)
+        rp = _host_ptr(rho, np.float32)
+        cp = None if n_ngb is None else _host_ptr(n_ngb, np.uint32)
+    it = C.c_int32(0)
+    _check(lib().og_tree_sph_smoothing(tree, float(n_target), float(tol), int(max_iter), hp, rp, cp,
+                                       C.byref(it)))
+    return int(it.value)
 
 
 def og_tree_force_f64(tree, acc, a_old=None, n_pp=None, n_pn=None) -> None:
@@ -574,6 +593,14 @@ class Tree:
         cnt = np.zeros(self.n, dtype=np.uint32)
         og_tree_sph_density(self.h, np.ascontiguousarray(h, dtype=np.float32), rho, cnt)
         return rho, cnt
+
+    def sph_smoothing(self, h0, n_target=32.0, tol=0.01, max_iter=100):
+        """(h, rho, n_ngb, iterations) of og_tree_sph_smoothing from the guesses h0."""
+        h = np.ascontiguousarray(h0, dtype=np.float32).copy()
+        rho = np.zeros(self.n, dtype=np.float32)
+        cnt = np.zeros(self.n, dtype=np.uint32)
+        it = og_tree_sph_smoothing(self.h, n_target, tol, max_iter, h, rho, cnt)
+        return h, rho, cnt, it
 
     def force_pot(self, a_old=None):
         """(acc, n_pp, n_pn, pot) of one force call with the potential output."""

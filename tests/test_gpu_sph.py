@@ -126,3 +126,53 @@ def test_device_pointers(ctx):
     og.og_tree_sph_density(dev.h, torch.from_numpy(h).cuda(), rd, cd)
     torch.cuda.synchronize()
     assert np.array_equal(rd.cpu().numpy(), rh) and np.array_equal(cd.cpu().numpy().view(np.uint32), ch)
+
+
+def _neff_ok(pos, mass, box, h, n_target, tol, targets=None):
+    """The paper's relation checked with the oracle's density at the given h."""
+    rho, _ = sph.density(pm.quantize(pos, box), mass, h, box, targets=targets)
+    t = np.arange(len(mass)) if targets is None else targets
+    hh = h[t].astype(np.float64)
+    neff = (4.0 * np.pi / 3.0) * hh ** 3 * rho / mass[t]
+    return np.abs(neff - n_target) <= tol * n_target + 1e-3, neff
+
+
+@pytest.mark.parametrize("start", ["above", "uniform"])
+def test_smoothing_lengths_meet_the_neighbour_relation(ctx, start):
+    pos, mass, prm = gi.config("clustered-2m", n=100000)
+    if start == "above":
+        h0 = np.minimum(2.0 * knn_h(pos, prm["box"]), 0.4)
+    else:
+        h0 = np.full(len(mass), prm["box"] * (3.0 * 32 / (4.0 * np.pi * len(mass))) ** (1.0 / 3.0))
+    t = og.Tree(ctx, pos, mass, prm)
+    h, rho, cnt, it = t.sph_smoothing(h0.astype(np.float32), 32.0, 0.01, 100)
+    assert it < 100
+    ok, neff = _neff_ok(pos, mass, prm["box"], h, 32.0, 0.01)
+    assert ok.all(), (np.count_nonzero(~ok), neff[~ok][:5])
+    r2, c2 = t.sph_density(h)                       # the outputs are the density call's at that h
+    assert np.array_equal(r2, rho) and np.array_equal(c2, cnt)
+
+
+def test_smoothing_full_size_workload(ctx):
+    pos, mass, prm = gi.config("clustered-2m")
+    h0 = np.full(len(mass), (3.0 * 32 / (4.0 * np.pi * len(mass))) ** (1.0 / 3.0), np.float32)
+    t = og.Tree(ctx, pos, mass, prm)
+    h, rho, cnt, it = t.sph_smoothing(h0, 32.0, 0.01, 200)
+    assert it < 200
+    sample = np.random.default_rng(4).choice(len(mass), 100000, replace=False)
+    ok, _ = _neff_ok(pos, mass, prm["box"], h, 32.0, 0.01, targets=sample)
+    assert ok.all()
+
+
+def test_smoothing_invalid_arguments(ctx):
+    pos, mass, prm = gi.config("uniform-32k", n=500)
+    t = og.Tree(ctx, pos, mass, prm)
+    h0 = np.full(500, 0.05, np.float32)
+    for n_t, tol, mi in ((10.0, 0.01, 50), (32.0, 0.0, 50), (32.0, 1.0, 50), (32.0, 0.01, 0), (np.nan, 0.01, 5)):
+        with pytest.raises(og.OGError) as e:
+            t.sph_smoothing(h0, n_t, tol, mi)
+        assert e.value.status == og.OG_ERR_ARG
+    bad = h0.copy()
+    bad[7] = -1.0
+    with pytest.raises(og.OGError):
+        t.sph_smoothing(bad)
