@@ -30,8 +30,7 @@
  *       Newtonian force times the erfc split factor, periodic minimum image
  *   a9  relative criterion: a second pass with the previous accelerations
  *
- * Readings of points the paper leaves open (each one is also listed in the
- * design notes of the repository):
+ * Readings of points the paper leaves open:
  *   - units: G and the box length L are parameters; positions are reduced to
  *     the torus [0, L)^3.
  *   - fixed point: u = floor(frac(t) * 2^32) with t = x/L in FP64, evaluated
