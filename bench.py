@@ -657,12 +657,12 @@ def main():
         served = served_bench(og, torch, dev, seconds=args.served_seconds)
 
     pmr = None
-    if not args.no_pm:
+    if not args.no_pm and rank == 0:
         pmr = pm_bench(og, ctx, torch, dev, stream, dpos, dmass, prm, max(3, args.steps), flush)
         pmr["treepm_ms_per_step"] = ms_per_step + pmr["ms"]
 
     sphr = None
-    if not args.no_sph:
+    if not args.no_sph and rank == 0:
         sphr = sph_bench(og, ctx, torch, dev, stream, pos, dpos, dmass, prm, max(3, args.steps), flush)
 
     kdk = None
