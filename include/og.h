@@ -16,7 +16,7 @@
  *                 equivalent);
  *   - Sect. 4.2   "Particle Mesh": the short-range potential
  *                 phi_s = -G m erfc(r / 2 r_s) / r of the force split;
- *   - Sect. 3.4 / 19.2: one walk per group of spatially close particles.
+ *   - Sect. 3.4 / 18.2: one walk per group of spatially close particles.
  *
  * Conventions for every entry point:
  *   - All calls return og_status.  Errors are negative, never abort the
@@ -164,7 +164,7 @@ og_status og_tree_force_f64(og_tree *t, const float *a_old, double *acc, uint32_
 
 og_status og_tree_info_get(const og_tree *t, og_tree_info *info);
 
-/* Long-range particle-mesh acceleration of every particle (Sect. 3.3
+/* Long-range particle-mesh acceleration of every particle (Sect. 4.2
  * "Particle Mesh"): the erf part of the split potential, which og_tree_force
  * leaves out, so that og_tree_force + og_tree_pm_force is the TreePM force.
  * The tree's particles are assigned to an Ng^3 mesh by cloud-in-cell
@@ -184,8 +184,8 @@ og_status og_tree_info_get(const og_tree *t, og_tree_info *info);
  * size or r_s <= 0; OG_ERR_CUDA if cuFFT cannot be loaded or fails. */
 og_status og_tree_pm_force(og_tree *t, int32_t mesh, float *acc);
 
-/* SPH density of every particle at given smoothing lengths (Sect. 5 "Smoothed
- * Particle Hydrodynamics"), with the grouped neighbour search of Sect. 3.7:
+/* SPH density of every particle at given smoothing lengths (Sect. 6 "Smoothed
+ * Particle Hydrodynamics"), with the grouped neighbour search of Sect. 3.4:
  * rho_i = sum_j m_j W(|x_i - x_j|, h_i) over the particles j closer than h_i,
  * i itself included, with the cubic spline W = 8 / (pi h^3) w(r / h),
  * w(q) = 1 - 6 q^2 + 6 q^3 (q < 1/2), 2 (1 - q)^3 (1/2 <= q < 1).  The search
@@ -202,7 +202,7 @@ og_status og_tree_pm_force(og_tree *t, int32_t mesh, float *acc);
  * gives OG_ERR_ARG. */
 og_status og_tree_sph_density(og_tree *t, const float *h, float *rho, uint32_t *n_ngb);
 
-/* Smoothing lengths from the paper's neighbour relation (Sect. 5):
+/* Smoothing lengths from the paper's neighbour relation (Sect. 6):
  * (4 pi / 3) h_i^3 rho_i = N m_i, N = n_target, with the density and search of
  * og_tree_sph_density.  Per particle, N_eff = (4 pi / 3) h^3 rho / m (FP64 of
  * the FP32 density) is compared with N: within tol N the particle is done;
@@ -401,7 +401,7 @@ og_status og_kdk_run(og_ctx *ctx, int64_t n, double *pos, double *vel, const dou
 /* ---- group size: measured choice ---------------------------------------- */
 
 /* The group size G (targets sharing one interaction list, Sect. 3.4 and
- * 19.2: one walk per group of nearby particles) trades list building against
+ * 18.2: one walk per group of nearby particles) trades list building against
  * evaluation; the paper fixes no value, nor the walk's launch shape (warps
  * per block, entries of the shared far-entry chunk).  og_tune_walk measures
  * all three for inputs of this kind: the key is (floor(log2 n), opening
@@ -460,13 +460,19 @@ og_status og_measure_fp32_peak(og_ctx *ctx, double *tflops_fma, double *tflops_f
  *   perm_out: device uint32[n], perm_out[i] = index in keys_in of the i-th key
  *             (equal keys keep their input order);
  *   stream:   cudaStream_t of the current device, or NULL for the default stream.
+ * The three buffers are device memory of the current device (else
+ * OG_ERR_ARG); keys_out may be keys_in, and no other two of them may overlap
+ * (OG_ERR_ARG).  All 64 key bits are sorted.
  * 1 <= n <= OG_NOALLOC_MAX_N, else OG_ERR_ARG.  The work is queued on `stream`
  * on the current device and the call returns before it finishes; synchronise
  * the stream before reading the outputs.
  * The scratch is a fixed static device array of about 16 MB that every GPU
  * loading this library holds until the process exits.  The first call on a
  * device looks up that array's device address (once per device, with the
- * device current); make that first call before any stream capture.  All
+ * device current); make that first call before any stream capture.  With
+ * CUDA's lazy module loading that first call may also be when the array is
+ * reserved, and it fails with OG_ERR_CUDA if the device has no room left:
+ * make it at set-up, before committing the rest of the device's memory.  All
  * calls share the one array: calls whose work overlaps on the GPU (on
  * different streams, or from different threads) race and corrupt each
  * other's results; serialise them on one stream.  The array carries no state
@@ -477,6 +483,13 @@ og_status og_sort_keys_noalloc(const uint64_t *keys_in, uint64_t *keys_out, uint
 /* Number of CUDA kernels this library has launched in this process so far
  * (for benchmarks that count their own launches in a timed region). */
 int64_t og_kernel_launches(void);
+
+/* The compute capability the library's device code was compiled for, as
+ * major * 10 + minor of the code the current device runs (103 for sm_103a).
+ * A diagnostic with no counterpart in the paper: it lets a caller confirm
+ * that native GB300 code is loaded rather than PTX compiled at run time.
+ * version: out.  OG_ERR_ARG on NULL; OG_ERR_CUDA without a usable device. */
+og_status og_device_code_version(int32_t *version);
 
 #ifdef __cplusplus
 }

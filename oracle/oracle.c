@@ -21,7 +21,7 @@
  *   a4' the two-pointer threading of Sect. 4.1.1 (nextnode / sibling) in a
  *       unified index space: particles 0..N-1, nodes N..N+M-1, end = -1
  *   a5  bottom-up monopole moments: mass and centre of mass
- *   a6  groups of spatially close particles (Sect. 3.4 and 19.2: one walk
+ *   a6  groups of spatially close particles (Sect. 3.4 and 18.2: one walk
  *       per group of nearby particles)
  *   a7  per group: tree walk with Barnes-Hut or relative opening, a boundary
  *       check, and the short-range cutoff, producing particle-node (PN) and

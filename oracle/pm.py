@@ -2,7 +2,7 @@
 of og_tree_pm_force; only the tests, the smoke check and the benchmark's CPU
 leg use it).
 
-What it computes, in the order of the paper (Sect. 3.3 "Particle Mesh"): the
+What it computes, in the order of the paper (Sect. 4.2 "Particle Mesh"): the
 Newtonian potential is split as 1/r = erfc(r / 2 A_smth) / r + erf(r / 2 A_smth) / r
 (A_smth = r_s); the tree takes the erfc part, the mesh the erf part.  The
 particles are assigned to a mesh, the density is Fourier transformed, multiplied

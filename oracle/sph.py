@@ -2,14 +2,14 @@
 og_tree_sph_density; only the tests, the smoke check and the benchmark's CPU
 leg use it).
 
-What it computes (Sect. 5 "Smoothed Particle Hydrodynamics" and Sect. 3.7
+What it computes (Sect. 6 "Smoothed Particle Hydrodynamics" and Sect. 3.4
 "Neighbour search"): the kernel-averaged density of every particle,
 
     rho_i = sum_j m_j W(|x_i - x_j|, h_i),
 
 over all particles j (itself included) closer than h_i, with the cubic spline
 of Monaghan (1985), the paper's default kernel for 3D with 32 neighbours
-(Table of Sect. 5.3; the expression of the kernel appendix):
+(Table of Sect. 6.5; the expression of the kernel appendix):
 
     W(r, h) = 8 / (pi h^3) * { 1 - 6 q^2 + 6 q^3   for q = r / h < 1/2,
                                2 (1 - q)^3         for 1/2 <= q < 1,

@@ -206,6 +206,18 @@ const char *og_last_error(void) { return g_err; }
 
 int64_t og_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+og_status og_device_code_version(int32_t *version) {
+    if (!version) {
+        set_error("og_device_code_version: NULL pointer");
+        return OG_ERR_ARG;
+    }
+    cudaFuncAttributes at;
+    cudaError_t e = cudaFuncGetAttributes(&at, k_unpermute);
+    if (e != cudaSuccess) return cuda_fail(e, "og_device_code_version: cudaFuncGetAttributes");
+    *version = at.binaryVersion;
+    return OG_OK;
+}
+
 og_status og_params_default(og_params *p) {
     if (!p) return OG_ERR_ARG;
     std::memset(p, 0, sizeof(*p));

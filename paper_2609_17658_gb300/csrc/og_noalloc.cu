@@ -5,11 +5,15 @@
 // whole HBM budget to resident trees must not grow its footprint, and a
 // latency-critical loop cannot afford cudaMalloc / cudaFree, which can
 // synchronise the whole device.  og_sort_keys_noalloc therefore sorts keys
-// with a fixed scratch area that is reserved once, when the library is
-// loaded, instead of allocating per call.
+// in a fixed scratch area that belongs to the library's device code instead
+// of allocating per call.
 //
 // The scratch is one file-scope static __device__ array (size below).  Every
-// GPU that loads the library holds it until the process exits.  Host code
+// GPU that loads the library's device code holds it until the process exits.
+// With CUDA's lazy module loading that can happen at the first call on a
+// device (inside its cudaGetSymbolAddress), and if the device has no room
+// left then, that first call fails with OG_ERR_CUDA: a caller that is about
+// to commit its whole budget makes one call first, at set-up.  Host code
 // must not use the array's name as a device address (in host code that name
 // refers to a host-side stand-in); the device address is obtained once per
 // device with cudaGetSymbolAddress, with that device current, on the first
@@ -34,6 +38,22 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+
+// true iff p is device (or managed) memory of device dev
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
+// byte ranges [a, a + na) and [b, b + nb) share at least one byte
+bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
 
 __global__ void k_iota(int64_t n, uint32_t *v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -66,6 +86,18 @@ extern "C" og_status og_sort_keys_noalloc(const uint64_t *keys_in, uint64_t *key
     if (e != cudaSuccess) return cuda_fail(e, "og_sort_keys_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) {
         set_error("og_sort_keys_noalloc: device index %d not supported", dev);
+        return OG_ERR_ARG;
+    }
+    if (!on_device(keys_in, dev) || !on_device(keys_out, dev) || !on_device(perm_out, dev)) {
+        set_error("og_sort_keys_noalloc: keys_in, keys_out and perm_out must be device memory "
+                  "of the current device (%d)", dev);
+        return OG_ERR_ARG;
+    }
+    const size_t kb = (size_t)n * sizeof(uint64_t), pb = (size_t)n * sizeof(uint32_t);
+    if ((keys_out != keys_in && overlap(keys_in, kb, keys_out, kb)) ||
+        overlap(perm_out, pb, keys_in, kb) || overlap(perm_out, pb, keys_out, kb)) {
+        set_error("og_sort_keys_noalloc: buffers overlap (keys_out may equal keys_in; no other "
+                  "overlap is allowed)");
         return OG_ERR_ARG;
     }
     void *base = nullptr;

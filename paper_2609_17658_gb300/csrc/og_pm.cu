@@ -1,4 +1,4 @@
-// og_pm.cu -- long-range particle-mesh (PM) force of a built tree (Sect. 3.3
+// og_pm.cu -- long-range particle-mesh (PM) force of a built tree (Sect. 4.2
 // "Particle Mesh").
 //
 // The tree walk evaluates the erfc part of the split potential; the mesh gives

@@ -1,7 +1,7 @@
 // og_sort.cu -- stable LSD radix sort of (63-bit Morton key, u32 index) pairs.
 //
-// The paper inserts particles "sequentially following their Peano-Hilbert
-// ordering" (Sect. 4.1.1); here the order is a Morton order produced by a
+// The paper builds its tree by inserting the particles one after another in
+// Peano-Hilbert order (Sect. 4.1.1); here the order is a Morton order made by a
 // least-significant-digit radix sort, 8 bits per pass.  Each pass is
 //   1. upsweep:   per 2048-key tile, a 256-bin digit histogram (shared-memory
 //                 atomics, one sub-histogram per warp), stored digit-major;

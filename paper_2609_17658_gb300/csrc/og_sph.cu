@@ -1,5 +1,5 @@
 // og_sph.cu -- grouped neighbour search and SPH density at given smoothing
-// lengths (Sect. 3.7 "Neighbour search", Sect. 5 "Smoothed Particle
+// lengths (Sect. 3.4 "Neighbour search", Sect. 6 "Smoothed Particle
 // Hydrodynamics").
 //
 // rho_i = sum_j m_j W(|x_i - x_j|, h_i) over the particles j (i included)

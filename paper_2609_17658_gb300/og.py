@@ -114,6 +114,8 @@ def lib():
         L.og_tree_free.argtypes = [P]
         L.og_last_error.restype = C.c_char_p
         L.og_kernel_launches.restype = C.c_int64
+        L.og_device_code_version.argtypes = [C.POINTER(C.c_int32)]
+        L.og_device_code_version.restype = C.c_int
         L.og_sort_keys_noalloc.argtypes = [P, P, P, i64, P]
         L.og_batch_force.argtypes = [P, i64, C.POINTER(og_box), C.POINTER(og_batch_info)]
         L.og_batch_force.restype = C.c_int
@@ -165,6 +167,13 @@ def og_kernel_launches() -> int:
     return int(lib().og_kernel_launches())
 
 
+def og_device_code_version() -> int:
+    """Compute capability of the device code the current GPU runs (103: sm_103a)."""
+    v = C.c_int32()
+    _check(lib().og_device_code_version(C.byref(v)))
+    return int(v.value)
+
+
 def _check(st: int):
     if st < 0:
         raise OGError(st, og_last_error())
@@ -197,8 +206,17 @@ def _host_ptr(a: np.ndarray, dtype, shape_tail=()):
 
 
 def _dev_ptr(t, dtype_name: str):
+    """Device address of a contiguous CUDA tensor on the current device.  A CPU
+    tensor, or one on another GPU, is rejected here: its address would reach
+    the kernels as if it were this device's memory."""
+    if not _is_torch_cuda(t):
+        raise TypeError(f"expected a CUDA tensor of {dtype_name}, got a host object")
     if str(t.dtype) != f"torch.{dtype_name}" or not t.is_contiguous():
         raise TypeError(f"expected a contiguous CUDA tensor of {dtype_name}")
+    import torch
+    cur = torch.cuda.current_device()
+    if t.device.index != cur:
+        raise ValueError(f"tensor on cuda:{t.device.index}, but the current device is cuda:{cur}")
     return C.c_void_p(t.data_ptr())
 
 

@@ -59,12 +59,15 @@ def test_binding_has_the_c_names():
         assert hasattr(og, name), name
 
 
-def test_sm103a_cubin_in_library(libpath):
-    # the fatbinary must carry sm_103a code (checked by name, not by reading it)
-    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+def test_build_targets_sm103a_only():
+    # one -gencode, native sm_103a code and no PTX for run-time compilation
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.gpu
+def test_device_code_is_sm103a(libpath):
+    from paper_2609_17658_gb300 import og
+    assert og.og_device_code_version() == 103
 
 
 def test_params_defaults_without_gpu(libpath):

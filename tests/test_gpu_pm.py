@@ -1,4 +1,4 @@
-"""og_tree_pm_force: the long-range particle-mesh force (Sect. 3.3 "Particle Mesh")
+"""og_tree_pm_force: the long-range particle-mesh force (Sect. 4.2 "Particle Mesh")
 against the oracle (oracle/pm.py) on the same u32 positions and masses.
 
 The CUDA path computes in FP32: CIC weights and masses in FP32, the assignment

@@ -1,5 +1,5 @@
-"""og_tree_sph_density: grouped neighbour search and SPH density (Sect. 3.7,
-Sect. 5) against the oracle (oracle/sph.py) on the same u32 positions.
+"""og_tree_sph_density: grouped neighbour search and SPH density (Sect. 3.4,
+Sect. 6) against the oracle (oracle/sph.py) on the same u32 positions.
 
 The neighbour decision is float32 arithmetic on exact integers on both sides,
 so the neighbour counts must be equal.  The density sums up to a few thousand

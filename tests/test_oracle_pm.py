@@ -1,6 +1,6 @@
 """Pins of the particle-mesh oracle (oracle/pm.py), independent of its code.
 
-Sect. 3.3 "Particle Mesh": the mesh carries the erf part of the split potential,
+Sect. 4.2 "Particle Mesh": the mesh carries the erf part of the split potential,
 filtered by exp(-k^2 r_s^2).  The references here do not use the oracle's mesh:
 
   - the exact long-range force of point masses in a periodic box, as the

@@ -1,6 +1,6 @@
 """Pins of the SPH density oracle (oracle/sph.py), independent of its code.
 
-Sect. 5: rho_i = sum_j m_j W(|x_i - x_j|, h_i) with the cubic spline of
+Sect. 6: rho_i = sum_j m_j W(|x_i - x_j|, h_i) with the cubic spline of
 Monaghan (1985).  The references: all pairs by brute force (no k-d tree), the
 kernel's normalisation 4 pi int_0^h r^2 W dr = 1 and its continuity by
 quadrature, one and two particles in closed form, and a periodic lattice, whose
