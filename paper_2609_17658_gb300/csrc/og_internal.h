@@ -212,6 +212,7 @@ struct WalkParams {
     float rc2;         // cutoff^2 in grid units (single precision)
     unsigned long long rprune;  // prune threshold, squared grid units
     unsigned long long hnear2;  // entries closer than this (squared grid units) may need softening
+    float hnear2f;     // hnear2 raised by more than the FP32 error of a squared distance
     float h;           // softening length, grid units
     float inv_h;
     float inv_2rs;     // 1 / (2 r_s), grid units

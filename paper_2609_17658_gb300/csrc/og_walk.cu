@@ -321,11 +321,19 @@ struct Acc {
     }
 };
 
-// Barnes-Hut: open iff l2 > th2 * d2 with d2 = (dx*dx + dy*dy) + dz*dz in FP64.
-__device__ __forceinline__ bool open_bh(uint32_t gx, uint32_t gy, uint32_t gz, float l2f,
-                                        double l2, const WalkParams &p) {
+// The squared distance of the gaps (gx, gy, gz) in single precision: each
+// gap rounded once, then fma(fx, fx, fma(fy, fy, fz * fz)).  Its relative
+// error is below 5 * 2^-24.
+__device__ __forceinline__ float dist2f(uint32_t gx, uint32_t gy, uint32_t gz) {
     const float fx = (float)gx, fy = (float)gy, fz = (float)gz;
-    const float d2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+    return fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+}
+
+// Barnes-Hut: open iff l2 > th2 * d2 with d2 = (dx*dx + dy*dy) + dz*dz in FP64.
+// The FP32 value d2f decides when it is farther from the threshold than its
+// error bound; inside that band the FP64 expression does.
+__device__ __forceinline__ bool open_bh(uint32_t gx, uint32_t gy, uint32_t gz, float d2f, float l2f,
+                                        double l2, const WalkParams &p) {
     const float q = p.th2f * d2f;
     if (l2f > q * kFilterHi) return true;
     if (l2f < q * kFilterLo) return false;
@@ -335,11 +343,9 @@ __device__ __forceinline__ bool open_bh(uint32_t gx, uint32_t gy, uint32_t gz, f
 }
 
 // relative: open iff (G M) l2 > arel (d2 d2), arel = (alpha a_min) s^2, in FP64.
-__device__ __forceinline__ bool open_rel(uint32_t gx, uint32_t gy, uint32_t gz, float l2f,
+__device__ __forceinline__ bool open_rel(uint32_t gx, uint32_t gy, uint32_t gz, float d2f, float l2f,
                                          double l2, float Mf, double M, float arelf, double arel,
                                          const WalkParams &p) {
-    const float fx = (float)gx, fy = (float)gy, fz = (float)gz;
-    const float d2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
     const float lhs = (p.Gf * Mf) * l2f;
     const float rhs = (arelf * d2f) * d2f;
     const bool normal = lhs >= 1e-30f && lhs <= 1e30f && rhs >= 1e-30f && rhs <= 1e30f;
@@ -350,6 +356,25 @@ __device__ __forceinline__ bool open_rel(uint32_t gx, uint32_t gy, uint32_t gz, 
     const double dx = (double)gx, dy = (double)gy, dz = (double)gz;
     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     return __dmul_rn(__dmul_rn(p.G, M), l2) > __dmul_rn(arel, __dmul_rn(d2, d2));
+}
+
+// Gap between a node's cell and the group box on one axis, from the cell's
+// centre c (cell [c - s2, c + s2 - 1], s2 = half the side).  d = c - lo on
+// the circle; outside the box the centre is fwd = d - len past its far end or
+// back = -d before its near end.  The centre's own gap is dc = min(fwd, back)
+// (0 inside); the cell's gap is dc - s2 when the box lies before the cell
+// (fwd side) and dc - s2 + 1 when it lies after it (back side, the cell ends
+// at c + s2 - 1), and 0 when that is not positive (they meet).  Equal to the
+// interval gap of the cell and the box, exactly.
+__device__ __forceinline__ void cell_gap(uint32_t c, uint32_t lo, uint32_t len, uint32_t s2,
+                                         uint32_t &dc, uint32_t &cg) {
+    const uint32_t d = c - lo;
+    const uint32_t fwd = d - len, back = 0u - d;
+    const bool inside = d <= len;
+    const bool onback = back < fwd;
+    dc = inside ? 0u : (onback ? back : fwd);
+    const int e = (int)(dc - s2 + (onback ? 1u : 0u));
+    cg = e > 0 ? (uint32_t)e : 0u;
 }
 
 // Registers: at most 96 per thread (64 KB / (96 x 128) gives 5 blocks of 4
@@ -374,12 +399,13 @@ __device__ __forceinline__ Cls classify(const TreeView &T, uint32_t ci, bool has
         const CRec r = T.crec[ci];
         ent = make_uint4(r.x, r.y, r.z, __float_as_uint(r.m));
         isnode = (r.info >> 31) != 0u;
+        // gaps of the particle, or of the node's centre of mass, to the group box
         const uint32_t gx = point_gap(r.x, lo[0], gl[0]);
         const uint32_t gy = point_gap(r.y, lo[1], gl[1]);
         const uint32_t gz = point_gap(r.z, lo[2], gl[2]);
-        const unsigned long long pg2 = sq64(gx) + sq64(gy) + sq64(gz);
-        near = pg2 < p.hnear2;
         if (!isnode) {
+            const unsigned long long pg2 = sq64(gx) + sq64(gy) + sq64(gz);
+            near = pg2 < p.hnear2;
             emit = !kSplit || pg2 <= p.rprune;
         } else {
             bool pruned = false, bnear;
@@ -406,34 +432,35 @@ __device__ __forceinline__ Cls classify(const TreeView &T, uint32_t ci, bool has
                         point_gap(e.sy + (uint32_t)(((unsigned long long)e.ly + 1ull) >> 1), lo[1], gl[1]) <= blim &&
                         point_gap(e.sz + (uint32_t)(((unsigned long long)e.lz + 1ull) >> 1), lo[2], gl[2]) <= blim;
             } else {
-                // the node's cell, from its level and centre of mass
+                // the node's cell, from its level and centre of mass: half side
+                // s2 = 2^(31 - lev), centre = (COM with the low 32 - lev bits
+                // cleared) + s2
                 const uint32_t lev = (r.info >> 26) & 31u;
-                const uint32_t side = 1u << (32u - lev);
-                const uint32_t msk = ~(side - 1u);
-                const uint32_t ox = r.x & msk, oy = r.y & msk, oz = r.z & msk;
+                const uint32_t s2 = 0x80000000u >> lev;
+                const uint32_t keep = ~(2u * s2 - 1u);
                 l2f = __uint_as_float((uint32_t)(127 + 64 - 2 * lev) << 23);
                 l2 = __longlong_as_double((long long)(1023 + 64 - 2 * lev) << 52);
-                if (kSplit) {
-                    const unsigned long long g2 = sq64(box_gap(lo[0], gl[0], ox, side - 1u)) +
-                                                  sq64(box_gap(lo[1], gl[1], oy, side - 1u)) +
-                                                  sq64(box_gap(lo[2], gl[2], oz, side - 1u));
-                    pruned = g2 > p.rprune;
-                }
+                uint32_t dcx, dcy, dcz, cgx, cgy, cgz;
+                cell_gap((r.x & keep) | s2, lo[0], gl[0], s2, dcx, cgx);
+                cell_gap((r.y & keep) | s2, lo[1], gl[1], s2, dcy, cgy);
+                cell_gap((r.z & keep) | s2, lo[2], gl[2], s2, dcz, cgz);
+                if (kSplit) pruned = sq64(cgx) + sq64(cgy) + sq64(cgz) > p.rprune;
                 // boundary check: the box meets the cell enlarged to 0.6 side,
-                // 10 g <= 6 side, i.e. g <= floor(3 side / 5) for an integer g
-                const uint32_t blim = (uint32_t)((3ull << (32u - lev)) / 5ull);
-                bnear = point_gap(ox + (side >> 1), lo[0], gl[0]) <= blim &&
-                        point_gap(oy + (side >> 1), lo[1], gl[1]) <= blim &&
-                        point_gap(oz + (side >> 1), lo[2], gl[2]) <= blim;
+                // 10 dc <= 6 side, i.e. dc <= floor(6 s2 / 5) = s2 + floor(s2 / 5)
+                const uint32_t blim = s2 + (__umulhi(s2, 0xCCCCCCCDu) >> 2);
+                bnear = dcx <= blim && dcy <= blim && dcz <= blim;
             }
             if (!pruned) {
+                const float d2f = dist2f(gx, gy, gz);
                 if (bnear) {
                     open = true;
                 } else {
-                    if (kOpen == OG_OPEN_BH) open = open_bh(gx, gy, gz, l2f, l2, p);
-                    else open = open_rel(gx, gy, gz, l2f, l2, r.m, r.M, arelf, arel, p);
+                    if (kOpen == OG_OPEN_BH) open = open_bh(gx, gy, gz, d2f, l2f, l2, p);
+                    else open = open_rel(gx, gy, gz, d2f, l2f, l2, r.m, r.M, arelf, arel, p);
                 }
                 emit = !open;
+                // conservative: in single precision with a margin above its error
+                near = !(d2f >= p.hnear2f);
                 push_ref = r.ref;
                 push_cnt = r.info & 0x3ffffffu;
             }
@@ -883,6 +910,9 @@ WalkParams make_walk_params(const og_params &p, int opening, double theta) {
     // near, so a far entry is at r^2 >= 1 from every target.
     const double hn = hg * (1.0 + 1.0 / 256.0) + 2.0;
     w.hnear2 = hg > 0.0 ? (unsigned long long)(hn * hn) : 1ull;
+    // the single-precision square of an integer distance errs by less than
+    // 5 * 2^-24 relative, so d2f >= hnear2f implies an exact square >= hnear2
+    w.hnear2f = nextafterf((float)((double)w.hnear2 * (1.0 + 1.0 / (1 << 20))), __builtin_huge_valf());
     w.out_scale = (float)(p.G * (two32 / p.box) * (two32 / p.box));
     w.pot_scale = (float)(p.G * (two32 / p.box));
     return w;
