@@ -34,10 +34,15 @@ import og_inputs as gi  # noqa: E402
 
 METRIC = "tree-force particles/s & interactions/s at 2.1M; served p50/p99 latency"
 UNIT = "particles/s"
-# Algorithmic FP32 work of one interaction in the walk's evaluation loop (the
-# instruction mix of eval_chunk, counting an FMA as 2 flops and a
-# multi-function unit op or a conversion as 1).
-FLOPS_PER_INTERACTION = 38
+# Algorithmic FP32 work of one interaction (one target and one list entry):
+# the nominal count of the pair arithmetic -- int-to-float and scaling 3,
+# r^2 5, rsqrt and r 2, u 1, erfc polynomial 12 and exp 3, split factor 3,
+# r^-3 2, m S r^-3 2, accumulation 6 -- with a fused multiply-add as 2 flops
+# and a multi-function op as 1.
+FLOPS_PER_INTERACTION = 45
+# The same count taken from the far-entry evaluation loop's own instruction
+# mix (reported beside it; it leaves out the compares and selects).
+FLOPS_PER_INTERACTION_MIX = 38
 FP32_LANES_PER_SM = 128
 
 
@@ -119,7 +124,10 @@ def parse():
     ap.add_argument("--no-sph", action="store_true")
     ap.add_argument("--no-fp32-peak", action="store_true",
                     help="skip the FP32 FMA-rate measurement after the timed region")
-    ap.add_argument("--served-seconds", type=float, default=6.0)
+    ap.add_argument("--served-scale", type=float, default=1.0,
+                    help="multiplies every served rate's arrival window")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 32k uniform and 16.7M clustered workloads")
     ap.add_argument("--batched-boxes", type=int, default=512)
     return ap.parse_args()
 
@@ -139,6 +147,18 @@ def max_over_ranks(x: float, ws: int, device) -> float:
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_run(step, steps: int, ws: int, device):
+    """The per-rank part of the timed region: ``steps`` calls of ``step()``,
+    each returning (its duration in ms, its result), then one all-reduce that
+    gives every rank the slowest rank's total.  Returns (the job's time per
+    step in ms, the last result)."""
+    total, res = 0.0, None
+    for _ in range(steps):
+        ms, res = step()
+        total += ms
+    return max_over_ranks(total, ws, device) / steps, res
 
 
 def job_value(n_per_rank: int, ws: int, ms_per_step: float) -> float:
@@ -206,9 +226,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _oracle_passes(ot, prm, sel, nthreads):
+    """Both walk passes of the oracle for the selected groups (the relative
+    criterion after its own Barnes-Hut first pass, else one pass)."""
+    a1, _, _ = ot.force(opening=gi.OPEN_BH, theta=prm.get("theta_first_pass", prm["theta"])
+                        if prm["opening"] == gi.OPEN_REL else prm["theta"], groups=sel,
+                        nthreads=nthreads)
+    if prm["opening"] == gi.OPEN_REL:
+        a_old = np.nan_to_num(a1).astype(np.float32)
+        ot.force(opening=gi.OPEN_REL, a_old=a_old, groups=sel, nthreads=nthreads)
+
+
 def cpu_baseline(pos, mass, prm, budget_s=20.0):
-    """The FP64 oracle on the host cores: full tree build plus the walk of a
-    bounded sample of groups, extrapolated to the whole system."""
+    """The FP64 oracle on the host cores.  Its tree build is single-threaded
+    by construction and is timed on all particles; the walk (both passes) is
+    timed with one thread and with every core on random samples of groups,
+    each sample grown until it takes about a quarter of the budget.  The
+    whole-step rate is N / (build + force time per target x N)."""
     import oracle
     oracle.build()
     nthreads = os.cpu_count() or 1
@@ -217,28 +251,66 @@ def cpu_baseline(pos, mass, prm, budget_s=20.0):
     t_build = time.perf_counter() - t0
     ng = ot.ngroups
     gb, ge = ot.get(oracle.F_GBEG), ot.get(oracle.F_GEND)
-    r = np.random.default_rng(1)
-    k = 64
-    done_groups, targets, t_force = 0, 0, 0.0
-    order = r.permutation(ng)
-    while t_force < budget_s * 0.5 and done_groups < ng:
-        sel = np.sort(order[done_groups:done_groups + k])
-        t0 = time.perf_counter()
-        a1, _, _ = ot.force(opening=gi.OPEN_BH, theta=prm["theta_first_pass"], groups=sel,
-                            nthreads=nthreads)
-        if prm["opening"] == gi.OPEN_REL:
-            a_old = np.nan_to_num(a1).astype(np.float32)
-            ot.force(opening=gi.OPEN_REL, a_old=a_old, groups=sel, nthreads=nthreads)
-        t_force += time.perf_counter() - t0
-        done_groups += len(sel)
-        targets += int((ge[sel] - gb[sel]).sum())
-        k *= 2
+    order = np.random.default_rng(1).permutation(ng)
+    force = {}
+    for label, nth, share in (("1_thread", 1, 0.15), ("all_threads", nthreads, 0.35)):
+        k, done, targets, t = 16, 0, 0, 0.0
+        while t < budget_s * share and done < ng:
+            sel = np.sort(order[done:done + k])
+            t0 = time.perf_counter()
+            _oracle_passes(ot, prm, sel, nth)
+            t += time.perf_counter() - t0
+            done += len(sel)
+            targets += int((ge[sel] - gb[sel]).sum())
+            k *= 2
+        force[label] = {"groups": done, "targets": targets, "seconds": t,
+                        "us_per_target": t / max(targets, 1) * 1e6}
     n = len(mass)
-    t_total = t_build + t_force * (n / max(targets, 1))
+    per_target = force["all_threads"]["seconds"] / max(force["all_threads"]["targets"], 1)
+    t_total = t_build + per_target * n
+    per_target1 = force["1_thread"]["seconds"] / max(force["1_thread"]["targets"], 1)
     return {"value": n / t_total, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"full FP64 tree build of all {n} particles ({t_build:.2f} s) + both walk "
-                      f"passes for {targets} targets in {done_groups} random groups "
-                      f"({t_force:.2f} s), force time scaled to all {n} targets"}
+            "build_s": t_build, "build_threads": 1,
+            "force_1_thread": force["1_thread"], "force_all_threads": force["all_threads"],
+            "value_1_thread": n / (t_build + per_target1 * n),
+            "sample": f"FP64 tree build of all {n} particles ({t_build:.2f} s, single-threaded) + "
+                      f"the walk (both passes for the relative criterion) for {force['all_threads']['targets']} targets in "
+                      f"{force['all_threads']['groups']} random groups on {nthreads} threads "
+                      f"({force['all_threads']['seconds']:.2f} s) and for "
+                      f"{force['1_thread']['targets']} targets on 1 thread "
+                      f"({force['1_thread']['seconds']:.2f} s); force time per target scaled to "
+                      f"all {n} targets"}
+
+
+def accuracy(og, ctx, pos, mass, prm, ngroups=300, seed=7, ot=None):
+    """Error of the library's accelerations against the FP64 oracle on the
+    same lists (the relative criterion fed the library's own first-pass
+    accelerations on both sides), on a random sample of whole groups:
+    per-particle |a - a_oracle| / |a_oracle|, p99, rms and max."""
+    import oracle
+    if ot is None:
+        ot = oracle.Tree(pos, mass, prm)
+    a_old = None
+    if prm["opening"] == gi.OPEN_REL:
+        bh = dict(prm, opening=gi.OPEN_BH, theta=prm["theta_first_pass"])
+        t1 = og.Tree(ctx, pos, mass, bh)
+        a_old, _, _ = t1.force()
+        t1.free()
+    t = og.Tree(ctx, pos, mass, prm)
+    acc, _, _ = t.force(a_old=a_old)
+    t.free()
+    sel = np.sort(np.random.default_rng(seed).choice(ot.ngroups, min(ngroups, ot.ngroups),
+                                                      replace=False))
+    ref, _, _ = ot.force(a_old=a_old, groups=sel, nthreads=os.cpu_count() or 1)
+    m = ~np.isnan(ref[:, 0])
+    na = np.linalg.norm(ref[m], axis=1)
+    e = np.linalg.norm(acc[m].astype(np.float64) - ref[m], axis=1)
+    rms_a = float(np.sqrt(np.mean(na ** 2)))
+    keep = na >= 1e-6 * rms_a
+    rel = e[keep] / na[keep]
+    return {"targets": int(m.sum()), "groups": int(len(sel)),
+            "p99_rel_err": float(np.quantile(rel, 0.99)), "rms_rel_err": float(np.sqrt(np.mean(rel ** 2))),
+            "max_rel_err": float(rel.max()), "bound": "p99 <= 1e-4, rms <= 2e-5"}
 
 
 def batched_bench(og, ctx, torch, dev, stream, nboxes, steps):
@@ -332,12 +404,18 @@ def kdk_bench(og, ctx, n=2097152, max_bin=6, dt_max=0.02, rebuild_every=8):
             "speedup": t_glob / t_ind}
 
 
-def served_bench(og, torch, dev, rates=(10.0, 30.0, 100.0), seconds=6.0, pool_size=16):
+SERVED_RATES = ((10.0, 20.0), (30.0, 20.0), (100.0, 10.0), (300.0, 4.0), (1000.0, 1.5))
+
+
+def served_bench(og, torch, dev, rates=SERVED_RATES, scale=1.0, pool_size=16):
     """Served stream: Poisson arrivals of systems with N log-uniform in
     [1e4, 2e6] (halo-clustered, 8 kick-drift steps each, HBM budget 40 GB)
     against the plain per-box path (build + force per step, then kick and
     drift, one request after another), both on this GPU from host arrays,
-    results left on the device."""
+    results left on the device.  ``rates``: (arrivals per second, window in
+    seconds) pairs; above the service rate the queue grows for the whole
+    window, so the overloaded rates get short windows (their latencies then
+    measure that window's backlog)."""
     pool = gi.request_stream(1e9, 1e9, seed=12349, max_requests=pool_size)
     # plain path
     ctx = og.Context(dev.index or 0)
@@ -369,7 +447,8 @@ def served_bench(og, torch, dev, rates=(10.0, 30.0, 100.0), seconds=6.0, pool_si
     out = {"workload": "Poisson arrivals, N log-uniform [1e4, 2e6], halo-clustered, 8 kick-drift "
                        "steps, v Gaussian sigma 1e-3 box/step, BH theta 0.5, budget 40 GB",
            "plain_particle_steps_per_s": plain, "rates": []}
-    for rate in rates:
+    for rate, window in rates:
+        seconds = window * scale
         r = np.random.default_rng(int(rate))
         arrivals = np.cumsum(r.exponential(1.0 / rate, size=int(rate * seconds * 3) + 8))
         arrivals = arrivals[arrivals < seconds]
@@ -391,7 +470,7 @@ def served_bench(og, torch, dev, rates=(10.0, 30.0, 100.0), seconds=6.0, pool_si
         lat = np.array([x["t_done"] - x["t_submit"] for x, _ in res])
         span = max(x["t_done"] for x, _ in res) - min(x["t_submit"] for x, _ in res)
         work = sum(w for _, w in res)
-        out["rates"].append({"rate_per_s": rate, "requests": len(res),
+        out["rates"].append({"rate_per_s": rate, "window_s": seconds, "requests": len(res),
                              "particle_steps_per_s": work / span,
                              "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
                              "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
@@ -399,30 +478,74 @@ def served_bench(og, torch, dev, rates=(10.0, 30.0, 100.0), seconds=6.0, pool_si
                              "rebuilds": int(sum(x["rebuilds"] for x, _ in res))})
     best = max(x["particle_steps_per_s"] for x in out["rates"])
     out["served_over_plain"] = best / plain
+    # the service rate: requests per second the saturated engine completes
+    mean_work = float(np.mean([len(q.mass) * q.nsteps for q in pool]))
+    out["saturation_requests_per_s"] = best / mean_work
+    out["refits"] = int(sum(x["refits"] for x in out["rates"]))
+    out["rebuilds"] = int(sum(x["rebuilds"] for x in out["rates"]))
     return out
 
 
 def run_reference(args):
     """--impl reference: the FP64 oracle (the paper's method as the CPU program
-    of this repository) timed on the host cores, each step a bounded sample."""
+    of this repository) timed on the host cores.  Each step is one bounded
+    sample of the workload: the oracle's tree build of all N particles
+    (single-threaded by construction) and both walk passes for the targets of
+    a fresh random set of groups on every core.  ms_per_step is that step's
+    wall time; the value is the whole-step rate the sample measures,
+    N / (build time + force time per target x N).  The warm-up steps size the
+    group set so that a step takes about two seconds."""
+    import oracle
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    oracle.build()
     pos, mass, prm = gi.config(args.workload)
-    vals = []
-    for s in range(args.warmup + args.steps):
-        cb = cpu_baseline(pos, mass, prm, budget_s=8.0)
-        if s >= args.warmup:
-            vals.append(cb["value"])
+    n = len(mass)
+    nthreads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ot = oracle.Tree(pos, mass, prm)
+    ng = ot.ngroups
+    gb, ge = ot.get(oracle.F_GBEG), ot.get(oracle.F_GEND)
+    del ot
+    order = np.random.default_rng(2).permutation(ng)
+    k = min(ng, 256)
+    pos_in_order = 0
+    vals, ms, samples = [], [], []
+    for step in range(args.warmup + args.steps):
+        if pos_in_order + k > ng:
+            pos_in_order = 0
+        sel = np.sort(order[pos_in_order:pos_in_order + k])
+        pos_in_order += k
+        t0 = time.perf_counter()
+        ot = oracle.Tree(pos, mass, prm)
+        tb = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        _oracle_passes(ot, prm, sel, nthreads)
+        tf = time.perf_counter() - t1
+        del ot
+        targets = int((ge[sel] - gb[sel]).sum())
+        if step < args.warmup:
+            # size the sample for a force time of about 1.5 s
+            k = int(min(ng, max(16, k * 1.5 / max(tf, 1e-3))))
+            continue
+        vals.append(n / (tb + tf / max(targets, 1) * n))
+        ms.append((tb + tf) * 1e3)
+        samples.append((tb, tf, targets, len(sel)))
     v = statistics.median(vals)
+    tb, tf, targets, groups = samples[len(samples) // 2]
+    sample = (f"per step: FP64 tree build of all {n} particles (single-threaded, about {tb:.2f} s) + "
+              f"the walk (both passes for the relative criterion) for about {targets} targets in {groups} random groups on "
+              f"{nthreads} threads (about {tf:.2f} s); force time per target scaled to all {n} "
+              f"targets")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": len(mass) / v * 1e3,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(ms),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": f"{args.workload}: N={len(mass)} per GPU, " + describe(args.workload, prm),
+           "config": {"workload": f"{args.workload}: N={n} per GPU, " + describe(args.workload, prm),
                       "l2": "n/a (CPU)"},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                            "sample": cb["sample"]},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -528,6 +651,73 @@ def sph_bench(og, ctx, torch, dev, stream, pos, dpos, dmass, prm, steps, flush):
                           "ms": e0.elapsed_time(e1)}}
 
 
+def device_steps(og, ctx, torch, stream, dpos, dmass, prm, steps, warmup, flush):
+    """W untimed and K timed steps (build + force, L2 flushed before each),
+    CUDA events on the launching stream; returns per-step lists."""
+    n = int(dmass.shape[0])
+    acc = torch.empty((n, 3), dtype=torch.float32, device=dpos.device)
+    npp = torch.empty(n, dtype=torch.int32, device=dpos.device)
+    npn = torch.empty(n, dtype=torch.int32, device=dpos.device)
+    out = {"ms": [], "walk": [], "build": [], "inter": []}
+    for k in range(warmup + steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = og.og_tree_build(ctx.h, dpos, dmass, prm)
+        og.og_tree_force(h, acc, None, npp, npn)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info = og.og_tree_info_get(h)
+        og.og_tree_free(h)
+        if k >= warmup:
+            out["ms"].append(e0.elapsed_time(e1))
+            out["walk"].append(info["ms_walk"])
+            out["build"].append(info["ms_build"])
+            out["inter"].append(info["interactions"])
+    return out
+
+
+def walk_roofline(inter_step, walk_ms, sms, max_mhz, sm_mhz=None):
+    """The walk's FP32 work (FLOPS_PER_INTERACTION per interaction) over its
+    CUDA-event time, against the unit-count FP32 peak."""
+    peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    achieved = inter_step * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "flops_per_interaction": FLOPS_PER_INTERACTION,
+           "frac_by_instruction_mix": achieved / peak * FLOPS_PER_INTERACTION_MIX / FLOPS_PER_INTERACTION,
+           "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz"}
+    if sm_mhz:
+        out["frac_at_observed_clock"] = achieved / (sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12)
+    return out
+
+
+def config_bench(og, ctx, torch, dev, stream, name, steps, warmup, flush, sms, max_mhz, cpu,
+                 oracle_budget_s):
+    """Another named workload, timed like the main one: device-resident
+    inputs, L2 flushed between steps; the error against the oracle on sampled
+    groups and (if ``cpu``) the oracle's own rate on the host cores."""
+    pos, mass, prm = gi.config(name)
+    n = len(mass)
+    dpos = torch.from_numpy(pos).to(dev)
+    dmass = torch.from_numpy(mass).to(dev)
+    r = device_steps(og, ctx, torch, stream, dpos, dmass, prm, steps, warmup, flush)
+    del dpos, dmass
+    ms = float(np.mean(r["ms"]))
+    walk = float(np.mean(r["walk"]))
+    inter = float(np.mean(r["inter"]))
+    out = {"workload": f"{name}: N={n}, " + describe(name, prm), "steps": steps, "warmup": warmup,
+           "ms_per_step": ms, "particles_per_s": n / (ms * 1e-3),
+           "interactions_per_step": inter, "interactions_per_s": inter / (ms * 1e-3),
+           "walk_ms_per_step": walk, "build_ms_per_step": float(np.mean(r["build"])),
+           "walk_interactions_per_s": inter / (walk * 1e-3),
+           "roofline": walk_roofline(inter, walk, sms, max_mhz)}
+    out["accuracy"] = accuracy(og, ctx, pos, mass, prm, ngroups=200)
+    if cpu:
+        out["cpu_baseline"] = cpu_baseline(pos, mass, prm, budget_s=oracle_budget_s)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -579,7 +769,8 @@ def main():
     time.sleep(0.3)
     ms_steps, ms_walk, inter, ms_build = [], [], [], []
     launches0 = og.og_kernel_launches()
-    for _ in range(args.steps):
+
+    def timed_step():
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -591,13 +782,17 @@ def main():
         ms_walk.append(info["ms_walk"])
         ms_build.append(info["ms_build"])
         inter.append(info["interactions"])
-    launches = og.og_kernel_launches() - launches0
-    clocks = sampler.stop()
+        return ms_steps[-1], info
+
+    launches = None
+    try:
+        ms_per_step, _ = rank_run(timed_step, args.steps, ws, dev)
+    finally:
+        launches = og.og_kernel_launches() - launches0
+        clocks = sampler.stop()
     torch.cuda.synchronize()
-    total_ms = max_over_ranks(float(sum(ms_steps)), ws, dev)
     if ws > 1:
         dist.barrier()
-    ms_per_step = total_ms / args.steps
     value = job_value(n, ws, ms_per_step)
     inter_step = float(np.mean(inter))
     walk_ms = float(np.mean(ms_walk))
@@ -631,16 +826,11 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
-    peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-    achieved = inter_step * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": walk_traffic_per_launch(args.workload, prm),
-            "traffic_unit": "bytes per walk launch (mean over the step's launches)",
-            "kernel": "k_walk (both passes)",
-            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
-            "frac_at_observed_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 *
-                                                   clocks["sm_mhz"] * 1e6 / 1e12)
-                                       if clocks.get("sm_mhz") else None)}
+    roof = walk_roofline(inter_step, walk_ms, sms, max_mhz, clocks.get("sm_mhz"))
+    achieved = roof["achieved"]
+    roof.update({"traffic": walk_traffic_per_launch(args.workload, prm),
+                 "traffic_unit": "bytes per walk launch (mean over the step's launches)",
+                 "kernel": "k_walk (both passes)"})
     # the FP32 rate this GPU sustains on independent FMA chains, measured after
     # the timed region (not a denominator: the peak above is the unit count)
     if not args.no_fp32_peak:
@@ -654,7 +844,7 @@ def main():
 
     served = None
     if not args.no_served and rank == 0:
-        served = served_bench(og, torch, dev, seconds=args.served_seconds)
+        served = served_bench(og, torch, dev, scale=args.served_scale)
 
     pmr = None
     if not args.no_pm and rank == 0:
@@ -669,9 +859,19 @@ def main():
     if not args.no_kdk and rank == 0:
         kdk = kdk_bench(og, ctx)
 
-    cpu = None
+    cpu = acc_err = None
     if rank == 0 and ws == 1 and not args.no_cpu:
+        acc_err = accuracy(og, ctx, pos, mass, prm, ngroups=300)
         cpu = cpu_baseline(pos, mass, prm)
+
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = {}
+        for name, st, budget in (("uniform-32k", max(args.steps, 10), 6.0),
+                                 ("clustered-16m", max(3, min(args.steps, 5)), 16.0)):
+            configs[name] = config_bench(og, ctx, torch, dev, stream, name, st, 3, flush, sms,
+                                         max_mhz, cpu=(ws == 1 and not args.no_cpu),
+                                         oracle_budget_s=budget)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -686,7 +886,8 @@ def main():
                "build_ms_per_step": float(np.mean(ms_build)),
                "walk_interactions_per_s": inter_step / (walk_ms * 1e-3),
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-               "roofline": roof, "cpu_baseline": cpu, "batched": batched, "served": served,
+               "roofline": roof, "cpu_baseline": cpu, "accuracy": acc_err,
+               "configs": configs, "batched": batched, "served": served,
                "individual_steps": kdk, "pm_long_range": pmr,
                "sph_density": sphr}
         print(json.dumps(out), flush=True)

@@ -999,7 +999,10 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
 
     // ---- box table
     {
-        std::vector<SegGeom> hg((size_t)B);
+        // the host copies live in the tree, which outlives the asynchronous
+        // copies, so the stream need not be drained here
+        std::vector<SegGeom> &hg = t->h_geom;
+        hg.assign((size_t)B, SegGeom{});
         for (int64_t b = 0; b < B; ++b) {
             int e2 = 0;
             hg[b].box = t->seg_prm[b].box;
@@ -1009,8 +1012,6 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         }
         cudaMemcpyAsync(t->seg_off, t->h_seg_off.data(), (B + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(t->geom, hg.data(), B * sizeof(SegGeom), cudaMemcpyHostToDevice, s);
-        // the host vector must outlive the copy
-        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "build (boxes)");
     }
 
     // ---- scratch

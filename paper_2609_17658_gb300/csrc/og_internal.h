@@ -87,6 +87,7 @@ struct og_tree {
     std::vector<og_params> seg_prm;   // per-box parameters
     std::vector<og::WalkParams> h_wp; // host staging of the per-box walk parameters
     std::vector<uint32_t> h_seg_off;  // first particle of each box, plus n
+    std::vector<og::SegGeom> h_geom;  // geometry of each box (source of an async copy)
     uint32_t *seg_off = nullptr;      // device copy
     og::SegGeom *geom = nullptr;
     og::WalkParams *segp = nullptr;   // per-box walk parameters of the current pass
@@ -231,10 +232,11 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
                     float *pot_sorted = nullptr);
 // One walk launch over the groups of several trees (the serving loop), in
 // decreasing order of their previous list lengths.  Every tree's per-box
-// parameters must agree on split on/off.
+// parameters must agree on split on/off.  tree_interactions (or null): the
+// interactions evaluated for each tree.
 og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int opening,
                      const float *const *a_old_sorted, float *const *acc_sorted, float *ms_out,
-                     int64_t *interactions);
+                     int64_t *interactions, int64_t *tree_interactions = nullptr);
 // cell extents for a built tree (so that it can join a walk of refitted trees)
 og_status cell_extents(og_tree *t);
 WalkParams make_walk_params(const og_params &p, int opening, double theta);

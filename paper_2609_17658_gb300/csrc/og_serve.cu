@@ -6,10 +6,19 @@
 // admitted system keeps its tree, positions, velocities and last
 // accelerations on the device until its last step.  One engine step walks
 // the groups of all active systems in a single launch (longest lists first),
-// then kicks and drifts every system and refits its tree, or rebuilds it when
-// the drift since the last build exceeds a quarter of the mean group box side
-// or after four refits.  Newly arrived requests join at the next engine step,
-// so their work overlaps with that of systems already in flight.
+// then kicks and drifts every system and refits its tree, or rebuilds it.
+// A refitted tree stays exact, but its node extents grow with the drift and
+// its lists with them.  The walk reports every tree's interactions, and the
+// engine prices the next step both ways in walk interactions: a rebuild
+// costs a build plus a fresh tree's walk, a refit costs a refit plus the
+// walk of the grown lists, predicted from the growth of the last refitted
+// step (or, before any refit, a fourfold growth, so only systems whose walk
+// is small beside a build try one).  Costs are modelled from measured build,
+// refit and walk rates.  The rule uses only the system's own interaction
+// counts, never a timing, so a system takes the same decisions, and gets the
+// same bits, alone or in a mix.
+// Newly arrived requests join at the next engine step, so their work
+// overlaps with that of systems already in flight.
 //
 // The engine runs on its own thread and on a private context (stream and
 // status word) of the same device.
@@ -33,7 +42,16 @@ namespace {
 constexpr int kT = 256;
 inline unsigned nblk(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
 constexpr int kMaxActive = 256;
-constexpr int kMaxRefits = 4;
+constexpr int kMaxRefits = 64;   // refits between builds at most
+// costs in walk interactions (about 2e-12 s each on the multi-tree walk): a
+// build about 0.5 ms of launch-bound work plus 0.4 ns per particle, a refit
+// about 0.3 ms plus 0.2 ns per particle; a refitted tree's walk costs 13 %
+// more per interaction (it reads node extents); measured on GB300 at
+// 2e4, 2e5 and 2e6 particles
+constexpr double kBuildFixedInter = 2.6e8, kBuildPerParticleInter = 200.0;
+constexpr double kRefitFixedInter = 1.5e8, kRefitPerParticleInter = 100.0;
+constexpr double kRefitWalkFactor = 1.13;
+constexpr double kTrialGrowth = 4.0;
 // systems are built on this many private streams at once: a small build is
 // bound by launch and synchronisation latency, so builds of several systems
 // overlap on the device
@@ -44,40 +62,18 @@ double now_s() {
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
-// v += a dt_kick; x += v dt_drift; largest per-axis displacement since the
-// last build (minimum image), as float bits for an integer atomic max
+// v += a dt_kick; x += v dt_drift, x wrapped into [0, box)
 __global__ void k_kick_drift(int64_t n, const float *__restrict__ acc, double *vel, double *pos,
-                             const double *__restrict__ xbuild, double dt_kick, double dt_drift,
-                             double box, unsigned int *maxdrift) {
+                             double dt_kick, double dt_drift, double box) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float dmax = 0.0f;
-    if (i < n) {
-        for (int a = 0; a < 3; ++a) {
-            const double v = vel[3 * i + a] + (double)acc[3 * i + a] * dt_kick;
-            vel[3 * i + a] = v;
-            double x = pos[3 * i + a] + v * dt_drift;
-            x -= box * floor(x / box);
-            pos[3 * i + a] = x;
-            double d = x - xbuild[3 * i + a];
-            d -= box * rint(d / box);
-            dmax = fmaxf(dmax, (float)fabs(d));
-        }
+    if (i >= n) return;
+    for (int a = 0; a < 3; ++a) {
+        const double v = vel[3 * i + a] + (double)acc[3 * i + a] * dt_kick;
+        vel[3 * i + a] = v;
+        double x = pos[3 * i + a] + v * dt_drift;
+        x -= box * floor(x / box);
+        pos[3 * i + a] = x;
     }
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    if ((threadIdx.x & 31) == 0 && dmax > 0.0f) atomicMax(maxdrift, __float_as_uint(dmax));
-}
-
-// mean over groups of the largest side of the group box (grid units)
-__global__ void k_group_side_sum(int64_t ng, const uint32_t *__restrict__ gbox, unsigned long long *sum) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long v = 0;
-    if (g < ng) {
-        uint32_t m = 0;
-        for (int a = 0; a < 3; ++a) m = max(m, gbox[6 * g + 3 + a] - gbox[6 * g + a]);
-        v = m;
-    }
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(sum, v);
 }
 
 __global__ void k_unpermute_acc(int64_t n, const uint32_t *__restrict__ perm,
@@ -102,18 +98,19 @@ struct System {
     size_t bytes = 0;
     // device state
     void *dmem = nullptr;
-    double *d_pos = nullptr, *d_vel = nullptr, *d_mass = nullptr, *d_xbuild = nullptr;
+    double *d_pos = nullptr, *d_vel = nullptr, *d_mass = nullptr;
     float *d_acc = nullptr;
     og_tree *tree = nullptr;
     int step = 0, refits_since_build = 0;
-    double rebuild_thr = 0;  // box units
+    int64_t inter_base = -1; // interactions of the first walk after the last build
+    int64_t inter_prev = 0, inter_last = 0;  // the two latest walks
+    bool rebuild_next = false;
     og_result res{};
 };
 
 // a build stream: its own context (stream, status word, counters)
 struct Worker {
     og_ctx *ctx = nullptr;
-    unsigned long long *d_side = nullptr;
 };
 
 struct Server {
@@ -130,14 +127,12 @@ struct Server {
     size_t budget = 0, used = 0;
     bool stop = false;
     std::thread engine;
-    unsigned int *d_drift = nullptr;
-    unsigned long long *d_side = nullptr;
     int64_t interactions = 0, engine_steps = 0;
 };
 
 size_t estimate_bytes(int64_t n) {
     // tree arena and build scratch, plus the system's own state
-    return (size_t)n * (320 + 180 + 8 * 3 * 8 + 12) + ((size_t)1 << 20);
+    return (size_t)n * (320 + 180 + 8 * 3 * 7 + 12) + ((size_t)1 << 20);
 }
 
 og_status free_system(Server *S, System *sy) {
@@ -177,34 +172,41 @@ og_status build_system(Server *S, System *sy, const Worker &w) {
     }
     sy->tree = t;
     sy->refits_since_build = 0;
-    cudaMemcpyAsync(sy->d_xbuild, sy->d_pos, (size_t)sy->n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    // rebuild threshold: a quarter of the mean group box side
-    cudaMemsetAsync(w.d_side, 0, sizeof(unsigned long long), s);
-    k_group_side_sum<<<nblk(t->ngroups), kT, 0, s>>>(t->ngroups, t->gbox, w.d_side); note_launch();
-    unsigned long long side = 0;
-    cudaMemcpyAsync(&side, w.d_side, sizeof(side), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     t->ctx = S->ctx;
     if (e != cudaSuccess) return cuda_fail(e, "serve build");
     st = check_status(w.ctx);
     if (st) return st;
-    const double mean_side = t->ngroups ? (double)side / (double)t->ngroups : 0.0;
-    sy->rebuild_thr = 0.25 * mean_side * (sy->prm.box / 4294967296.0);
+    sy->inter_base = -1;
     sy->res.rebuilds++;
     return OG_OK;
+}
+
+// Refit a system's tree on a worker's stream (the engine's stream is free for
+// the next walk's set-up); the tree goes back to the engine's context after.
+og_status refit_system(Server *S, System *sy, const Worker &w) {
+    og_tree *t = sy->tree;
+    t->ctx = w.ctx;
+    og_status st = refit_tree(t, sy->d_pos);
+    t->ctx = S->ctx;
+    if (st == OG_OK) st = check_status(w.ctx);
+    if (st == OG_OK) {
+        sy->refits_since_build++;
+        sy->res.refits++;
+    }
+    return st;
 }
 
 og_status admit_system(Server *S, System *sy, const Worker &w) {
     cudaStream_t s = w.ctx->stream;
     const int64_t n = sy->n;
-    size_t bytes = (size_t)n * (3 * 8 * 3 + 8 + 3 * 4) + 4096;
+    size_t bytes = (size_t)n * (3 * 8 * 2 + 8 + 3 * 4) + 4096;
     cudaError_t e;
     if ((e = cudaMallocAsync(&sy->dmem, bytes, s)) != cudaSuccess) return cuda_fail(e, "serve admission");
     char *q = static_cast<char *>(sy->dmem);
     sy->d_pos = reinterpret_cast<double *>(q);
     sy->d_vel = sy->d_pos + 3 * n;
-    sy->d_xbuild = sy->d_vel + 3 * n;
-    sy->d_mass = sy->d_xbuild + 3 * n;
+    sy->d_mass = sy->d_vel + 3 * n;
     sy->d_acc = reinterpret_cast<float *>(sy->d_mass + n);
     cudaMemcpyAsync(sy->d_pos, sy->h_pos.data(), (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(sy->d_vel, sy->h_vel.data(), (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -263,8 +265,36 @@ void engine_step(Server *S) {
     }
     float ms = 0;
     int64_t inter = 0;
-    og_status st = walk_multi(c, trees.data(), (int64_t)trees.size(), OG_OPEN_BH, nullptr, accs.data(),
-                              &ms, &inter);
+    std::vector<int64_t> tinter(act.size(), 0);
+    // refitted trees and freshly built ones in separate launches: a launch
+    // with one refitted tree reads node extents for all of its trees
+    og_status st = OG_OK;
+    for (int pass = 0; pass < 2 && st == OG_OK; ++pass) {
+        std::vector<og_tree *> tv;
+        std::vector<float *> av;
+        std::vector<size_t> idx;
+        for (size_t k = 0; k < act.size(); ++k)
+            if (trees[k]->refit == (pass == 1)) {
+                tv.push_back(trees[k]);
+                av.push_back(accs[k]);
+                idx.push_back(k);
+            }
+        if (tv.empty()) continue;
+        float ms1 = 0;
+        int64_t in1 = 0;
+        std::vector<int64_t> ti(tv.size(), 0);
+        st = walk_multi(c, tv.data(), (int64_t)tv.size(), OG_OPEN_BH, nullptr, av.data(), &ms1, &in1,
+                        ti.data());
+        ms += ms1;
+        inter += in1;
+        for (size_t q = 0; q < idx.size(); ++q) tinter[idx[q]] = ti[q];
+    }
+    for (size_t k = 0; k < act.size(); ++k) {
+        System *sy = act[k];
+        sy->inter_prev = sy->inter_last;
+        sy->inter_last = tinter[k];
+        if (sy->inter_base < 0) sy->inter_base = tinter[k];
+    }
     if (st == OG_OK) {
         uint32_t stw = 0;
         cudaMemcpyAsync(&stw, c->d_status, sizeof(stw), cudaMemcpyDeviceToHost, s);
@@ -284,25 +314,20 @@ void engine_step(Server *S) {
         act.clear();
         return;
     }
-    // kick and drift every system, measure the drift since its last build
-    cudaMemsetAsync(S->d_drift, 0, act.size() * sizeof(unsigned int), s);
+    // kick and drift every system
     for (size_t k = 0; k < act.size(); ++k) {
         System *sy = act[k];
         og_tree *t = sy->tree;
         k_unpermute_acc<<<nblk(sy->n), kT, 0, s>>>(sy->n, t->perm, t->a_sorted, sy->d_acc); note_launch();
-        k_kick_drift<<<nblk(sy->n), kT, 0, s>>>(sy->n, sy->d_acc, sy->d_vel, sy->d_pos, sy->d_xbuild,
-                                                 sy->dt_kick, sy->dt_drift, sy->prm.box, S->d_drift + k); note_launch();
+        k_kick_drift<<<nblk(sy->n), kT, 0, s>>>(sy->n, sy->d_acc, sy->d_vel, sy->d_pos, sy->dt_kick,
+                                                 sy->dt_drift, sy->prm.box); note_launch();
     }
-    std::vector<unsigned int> drift(act.size(), 0u);
-    cudaMemcpyAsync(drift.data(), S->d_drift, act.size() * sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    std::vector<System *> keep, rebuild;
+    std::vector<System *> keep, update;
     for (size_t k = 0; k < act.size(); ++k) {
         System *sy = act[k];
         sy->step++;
         sy->res.steps = sy->step;
-        float dmax;
-        std::memcpy(&dmax, &drift[k], sizeof(float));
         if (sy->step >= sy->nsteps) {
             // accelerations of the last force evaluation and the final positions
             if (sy->acc_out)
@@ -316,25 +341,27 @@ void engine_step(Server *S) {
             delete sy;
             continue;
         }
-        if ((double)dmax > sy->rebuild_thr || sy->refits_since_build >= kMaxRefits) {
-            rebuild.push_back(sy);
-            continue;
-        }
-        og_status st2 = refit_tree(sy->tree, sy->d_pos);
-        sy->refits_since_build++;
-        sy->res.refits++;
-        if (st2 != OG_OK) {
-            free_system(S, sy);
-            finish(S, sy, st2);
-            delete sy;
-            continue;
-        }
-        keep.push_back(sy);
+        // the next step priced both ways, in walk interactions
+        const double nn = (double)sy->n;
+        const double last = (double)sy->inter_last;
+        const double growth = sy->refits_since_build == 0
+                                  ? kTrialGrowth
+                                  : std::max(1.0, last / std::max(1.0, (double)sy->inter_prev));
+        const double cost_refit = kRefitFixedInter + kRefitPerParticleInter * nn +
+                                  kRefitWalkFactor * last * growth;
+        const double cost_build = kBuildFixedInter + kBuildPerParticleInter * nn + (double)sy->inter_base;
+        sy->rebuild_next = cost_refit > cost_build || sy->refits_since_build >= kMaxRefits;
+        update.push_back(sy);
     }
-    if (!rebuild.empty()) {
+    // refits and rebuilds on the build workers' streams, several at once
+    if (!update.empty()) {
         std::vector<System *> order;
         std::vector<og_status> st2 = on_workers(
-            S, rebuild, [S](System *sy, const Worker &w) { return build_system(S, sy, w); }, &order);
+            S, update,
+            [S](System *sy, const Worker &w) {
+                return sy->rebuild_next ? build_system(S, sy, w) : refit_system(S, sy, w);
+            },
+            &order);
         for (size_t k = 0; k < order.size(); ++k) {
             if (st2[k] != OG_OK) {
                 free_system(S, order[k]);
@@ -410,24 +437,12 @@ og_status ensure_server(og_ctx *c, Server **out) {
         delete S;
         return st;
     }
-    cudaError_t e = cudaMalloc(&S->d_drift, kMaxActive * sizeof(unsigned int) + 64);
-    if (e != cudaSuccess) {
-        og_destroy(S->ctx);
-        delete S;
-        return cuda_fail(e, "serve setup");
-    }
-    S->d_side = reinterpret_cast<unsigned long long *>(S->d_drift + kMaxActive);
     for (int w = 0; w < kBuildWorkers; ++w) {
         Worker W;
         st = og_create(&W.ctx, c->device, 0);
-        if (st == OG_OK && (e = cudaMalloc(&W.d_side, 64)) != cudaSuccess) st = cuda_fail(e, "serve setup");
         if (st != OG_OK) {
             if (W.ctx) og_destroy(W.ctx);
-            for (Worker &x : S->workers) {
-                cudaFree(x.d_side);
-                og_destroy(x.ctx);
-            }
-            cudaFree(S->d_drift);
+            for (Worker &x : S->workers) og_destroy(x.ctx);
             og_destroy(S->ctx);
             delete S;
             return st;
@@ -458,11 +473,7 @@ void serve_shutdown(og_ctx *c) {
     S->cv_work.notify_all();
     if (S->engine.joinable()) S->engine.join();
     cudaSetDevice(S->ctx->device);
-    cudaFree(S->d_drift);
-    for (Worker &w : S->workers) {
-        cudaFree(w.d_side);
-        og_destroy(w.ctx);
-    }
+    for (Worker &w : S->workers) og_destroy(w.ctx);
     og_destroy(S->ctx);
     delete S;
     c->serve = nullptr;

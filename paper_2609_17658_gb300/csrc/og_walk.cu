@@ -104,6 +104,7 @@ struct WalkArgs {
     unsigned long long *work;     // item counter
     int warps, chunk;             // launch shape: warps per block, far-chunk entries
     unsigned long long *inter;    // interactions evaluated
+    unsigned long long *tree_inter;  // several trees: interactions per tree, or null
     uint32_t *status;
 };
 
@@ -723,7 +724,9 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
         }
         if (lane == 0) {
             T.gcost[g] = cnt_pp + cnt_pn;
-            atomicAdd(a.inter, (unsigned long long)gsize * (unsigned long long)(cnt_pp - 1u + cnt_pn));
+            const unsigned long long ni = (unsigned long long)gsize * (unsigned long long)(cnt_pp - 1u + cnt_pn);
+            atomicAdd(a.inter, ni);
+            if (kMulti && a.tree_inter) atomicAdd(a.tree_inter + ti, ni);
         }
     }
 }
@@ -1022,7 +1025,7 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
 
 og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int opening,
                      const float *const *a_old_sorted, float *const *acc_sorted, float *ms_out,
-                     int64_t *interactions) {
+                     int64_t *interactions, int64_t *tree_interactions) {
     cudaStream_t s = c->stream;
     if (ntrees < 1) return OG_OK;
     std::vector<TreeView> hv((size_t)ntrees);
@@ -1056,7 +1059,7 @@ og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int openi
     }
     const int64_t nitems = (int64_t)total;
     size_t bytes = (size_t)ntrees * sizeof(TreeView) + (size_t)(ntrees + 1) * 8 + (size_t)nitems * 24 +
-                   radix_sort_scratch_bytes(nitems) + 4096;
+                   radix_sort_scratch_bytes(nitems) + (size_t)ntrees * 8 + 4096;
     void *tmp = nullptr;
     cudaError_t err;
     if ((err = cudaMallocAsync(&tmp, bytes, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (walk items)");
@@ -1069,7 +1072,9 @@ og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int openi
     uint64_t *k1 = k0 + nitems;
     uint32_t *v0 = reinterpret_cast<uint32_t *>(k1 + nitems);
     uint32_t *v1 = v0 + nitems;
-    void *scr = v1 + nitems + 64;
+    unsigned long long *tint = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(v1 + nitems) + 255) & ~(uintptr_t)255);
+    void *scr = tint + ntrees + 32;
     cudaMemcpyAsync(dv, hv.data(), ntrees * sizeof(TreeView), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(doff, hoff.data(), (ntrees + 1) * 8, cudaMemcpyHostToDevice, s);
     k_item_keys<<<(unsigned)((nitems + 255) / 256), 256, 0, s>>>(nitems, ntrees, doff, dv, k0, v0); note_launch();
@@ -1082,6 +1087,8 @@ og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int openi
     a.items = alt ? v1 : v0;
     a.ntrees = ntrees;
     a.nitems = nitems;
+    a.tree_inter = tint;
+    cudaMemsetAsync(tint, 0, (size_t)ntrees * sizeof(unsigned long long), s);
     cudaMemsetAsync(c->d_counters, 0, 3 * sizeof(unsigned long long), s);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1089,12 +1096,17 @@ og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int openi
     cudaEventRecord(e0, s);
     launch(a, opening, split, false, refit, true, nitems, s);
     cudaEventRecord(e1, s);
+    std::vector<unsigned long long> hti(tree_interactions ? (size_t)ntrees : 0);
+    if (tree_interactions)
+        cudaMemcpyAsync(hti.data(), tint, (size_t)ntrees * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(tmp, s);
     unsigned long long h[3] = {0, 0, 0};
     og_status st = finish_pass(c, e0, e1, ms_out, h);
     if (st) return st;
     for (int64_t k = 0; k < ntrees; ++k) trees[k]->have_cost = true;
     if (interactions) *interactions = (int64_t)h[1];
+    if (tree_interactions)
+        for (int64_t k = 0; k < ntrees; ++k) tree_interactions[k] = (int64_t)hti[(size_t)k];
     return OG_OK;
 }
 

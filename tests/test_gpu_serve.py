@@ -55,13 +55,18 @@ def test_each_result_same_alone_and_in_the_mix():
         mixed, res_m = _serve(ctx, reqs)
     with og.Context(0) as ctx:
         alone, res_a = _serve(ctx, reqs, wait_each=True)
-    for (am, pm), (aa, pa), r, q in zip(mixed, alone, res_m, reqs):
+    for (am, pm), (aa, pa), r, ra, q in zip(mixed, alone, res_m, res_a, reqs):
         assert r["steps"] == q.nsteps and r["n"] == len(q.mass)
         assert np.isfinite(am).all() and np.abs(am).max() > 0
         assert np.array_equal(am, aa)
         assert np.array_equal(pm, pa)
         assert r["rebuilds"] >= 1 and r["rebuilds"] + r["refits"] == q.nsteps
         assert r["t_submit"] <= r["t_start"] <= r["t_done"]
+        # the refit-or-rebuild decisions depend only on the system itself
+        assert (r["rebuilds"], r["refits"]) == (ra["rebuilds"], ra["refits"])
+    # systems of at most 6e4 particles: their lists grow too little over eight
+    # steps to pay for a rebuild after every step, so refits outnumber builds
+    assert sum(r["refits"] for r in res_m) >= sum(r["rebuilds"] for r in res_m)
 
 
 def test_positions_follow_kick_and_drift():
@@ -122,7 +127,7 @@ def test_fullsize_requests_same_alone_and_in_the_mix():
         mixed, res_m = _serve(ctx, reqs)
     with og.Context(0) as ctx:
         alone, res_a = _serve(ctx, reqs, wait_each=True)
-    for (am, pm), (aa, pa), r, q in zip(mixed, alone, res_m, reqs):
+    for (am, pm), (aa, pa), r, ra, q in zip(mixed, alone, res_m, res_a, reqs):
         assert r["steps"] == q.nsteps and r["n"] == len(q.mass)
         assert np.isfinite(am).all() and np.abs(am).max() > 0
         assert np.array_equal(am, aa) and np.array_equal(pm, pa)
