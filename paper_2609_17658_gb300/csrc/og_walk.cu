@@ -103,6 +103,8 @@ struct WalkArgs {
     int64_t list_cap;
     unsigned long long *work;     // item counter
     int warps, chunk;             // launch shape: warps per block, far-chunk entries
+    int one_seg;                  // a single tree of one box: its parameters are p0
+    WalkParams p0;                // the box's parameters, in the launch's own argument space
     unsigned long long *inter;    // interactions evaluated
     unsigned long long *tree_inter;  // several trees: interactions per tree, or null
     uint32_t *status;
@@ -470,19 +472,23 @@ __device__ __forceinline__ Cls classify(const TreeView &T, uint32_t ci, bool has
     return Cls{emit, open, isnode, near, ent, push_ref, push_cnt};
 }
 
-template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot = false>
+// kOneSeg: a single tree of one box, whose parameters come from the launch
+// argument (constant operands) instead of a per-box record in global memory.
+template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot = false,
+          bool kOneSeg = false>
 __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a);
 
-template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot>
+template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot, bool kOneSeg>
 __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: per warp, its stack, near chunk and far chunk (warp_smem bytes);
     // blockDim.x = 32 * a.warps and the launch sizes smem to match
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int chunk = a.chunk;
-    // far-entry pairs in flight per lane: 4 in the Barnes-Hut kernels, 2 where
+    // far-entry pairs in flight per lane: 4 in the Barnes-Hut kernels and in
+    // the one-box kernels (their parameters are constant operands), 2 where
     // the relative test's extra registers would spill
-    constexpr int kFarUnroll = kOpen == OG_OPEN_BH ? 4 : 2;
+    constexpr int kFarUnroll = (kOpen == OG_OPEN_BH || kOneSeg) ? 4 : 2;
     unsigned char *wbase = smem + (size_t)warp * warp_smem(chunk);
     uint2 *stk = reinterpret_cast<uint2 *>(wbase);
     uint4 *chn = reinterpret_cast<uint4 *>(wbase + kStackCap * sizeof(uint2));
@@ -511,8 +517,8 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
             g = a.tree0.gorder ? (int64_t)a.tree0.gorder[gq] : (int64_t)gq;
         }
         const TreeView &T = kMulti ? a.trees[ti] : a.tree0;
-        const uint32_t seg = T.gseg[g];
-        const WalkParams &p = T.segp[seg];
+        const uint32_t seg = kOneSeg ? 0u : T.gseg[g];
+        const WalkParams &p = kOneSeg ? a.p0 : T.segp[seg];
         const uint32_t gb = T.gbeg[g], ge = T.gend[g];
         const uint32_t gsize = ge - gb;
         uint32_t lo[3], gl[3];  // the group box: [lo, lo + gl] per axis
@@ -731,10 +737,11 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
     }
 }
 
-template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot = false>
+template <int kOpen, bool kSplit, bool kDump, bool kRefit, bool kMulti, bool kPot = false,
+          bool kOneSeg = false>
 void launch_walk_t(const WalkArgs &a, int64_t nitems, cudaStream_t s, int sms) {
     const size_t smem = (size_t)a.warps * warp_smem(a.chunk);
-    auto kern = k_walk<kOpen, kSplit, kDump, kRefit, kMulti, kPot>;
+    auto kern = k_walk<kOpen, kSplit, kDump, kRefit, kMulti, kPot, kOneSeg>;
     // resident blocks per SM of each launch shape, queried once per shape
     static std::mutex mu;
     static std::map<std::pair<int, int>, int> per_sm_of;
@@ -771,6 +778,9 @@ void launch_walk(const WalkArgs &a, bool dump, bool refit, bool multi, bool pot,
     } else if (dump) {
         if (refit) launch_walk_t<kOpen, kSplit, true, true, false>(a, nitems, s, sms);
         else launch_walk_t<kOpen, kSplit, true, false, false>(a, nitems, s, sms);
+    } else if (a.one_seg) {
+        if (refit) launch_walk_t<kOpen, kSplit, false, true, false, false, true>(a, nitems, s, sms);
+        else launch_walk_t<kOpen, kSplit, false, false, false, false, true>(a, nitems, s, sms);
     } else {
         if (refit) launch_walk_t<kOpen, kSplit, false, true, false>(a, nitems, s, sms);
         else launch_walk_t<kOpen, kSplit, false, false, false>(a, nitems, s, sms);
@@ -969,6 +979,8 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
     og_status st = prepare_view(t, opening, first_pass, a_old_sorted, acc_sorted, &a.tree0, &wp);
     if (st) return st;
     fill_common(a, t->ctx, t);
+    a.one_seg = t->nseg == 1 ? 1 : 0;
+    a.p0 = t->h_wp[0];
     cudaError_t err;
     void *sort_tmp = nullptr;
     if (subset) {
