@@ -294,12 +294,14 @@ __device__ __forceinline__ int split_at(const uint8_t *lv, int64_t j, int64_t n)
 }
 
 // parent of every non-root node, owner of every particle, octant occupancy
-__global__ void k_link(int64_t n, int64_t m, int64_t B, const uint64_t *__restrict__ skey,
+__global__ void k_link(int64_t n, const uint32_t *__restrict__ nsplit, int64_t B,
+                       const uint64_t *__restrict__ skey,
                        const uint8_t *__restrict__ lv, const uint32_t *__restrict__ sid,
                        const uint32_t *__restrict__ sseg, const uint8_t *__restrict__ nlev,
                        const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
                        int32_t *npar, uint32_t *owner, uint32_t *occ, uint32_t *nnc,
                        uint32_t *status) {
+    const int64_t m = B + (int64_t)*nsplit;  // nodes: the roots and one per first split
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) {
         const int64_t p = t;
@@ -333,19 +335,23 @@ __global__ void k_link(int64_t n, int64_t m, int64_t B, const uint64_t *__restri
     }
 }
 
-__global__ void k_ccnt(int64_t m, const uint8_t *__restrict__ nlev,
+__global__ void k_ccnt(const uint32_t *__restrict__ nsplit, int64_t B, const uint8_t *__restrict__ nlev,
                        const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
                        const uint32_t *__restrict__ occ, uint32_t *nccnt) {
+    const int64_t m = B + (int64_t)*nsplit;
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= m) return;
     nccnt[id] = nlev[id] == kLevels ? nend[id] - nbeg[id] : (uint32_t)__popc(occ[id]);
 }
 
-__global__ void k_place(int64_t n, int64_t m, int64_t B, const uint64_t *__restrict__ skey,
+__global__ void k_place(int64_t n, const uint32_t *__restrict__ nsplit, int64_t B,
+                        const uint64_t *__restrict__ skey,
                         const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ nbeg,
                         const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
                         const int32_t *__restrict__ npar, const uint32_t *__restrict__ owner,
-                        uint32_t *child, uint32_t *npos, int64_t nchild, uint32_t *status) {
+                        uint32_t *child, uint32_t *npos, uint32_t *status) {
+    const int64_t m = B + (int64_t)*nsplit;
+    const int64_t nchild = n + (m - B);
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) {
         const int64_t p = t;
@@ -371,12 +377,14 @@ __global__ void k_place(int64_t n, int64_t m, int64_t B, const uint64_t *__restr
     }
 }
 
-__global__ void k_threading(int64_t n, int64_t m, int64_t B, int64_t nchild,
+__global__ void k_threading(int64_t n, const uint32_t *__restrict__ nsplit, int64_t B,
                             const uint32_t *__restrict__ child,
                             const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ nccnt,
                             const int32_t *__restrict__ npar, const uint32_t *__restrict__ npos,
                             const uint32_t *__restrict__ owner, int32_t *nnext, int32_t *nsib,
                             int32_t *pnext, uint32_t *status) {
+    const int64_t m = B + (int64_t)*nsplit;
+    const int64_t nchild = n + (m - B);
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c < m) {
         nnext[c] = (int32_t)child[ncbeg[c]];
@@ -405,8 +413,10 @@ __global__ void k_threading(int64_t n, int64_t m, int64_t B, int64_t nchild,
 constexpr int kLvItems = 16;  // nodes per thread in the level bucketing
 
 // per-block shared-memory histograms, one global atomic per level and block
-__global__ void __launch_bounds__(kT) k_level_hist(int64_t m, const uint8_t *__restrict__ nlev,
+__global__ void __launch_bounds__(kT) k_level_hist(const uint32_t *__restrict__ nsplit, int64_t B,
+                                                   const uint8_t *__restrict__ nlev,
                                                    uint32_t *lcount) {
+    const int64_t m = B + (int64_t)*nsplit;
     __shared__ uint32_t h[kLevels + 1];
     if (threadIdx.x <= kLevels) h[threadIdx.x] = 0;
     __syncthreads();
@@ -430,9 +440,11 @@ __global__ void k_level_offsets(uint32_t *lcount, uint32_t *loff, uint32_t *lcur
     loff[kLevels + 1] = run;
 }
 
-__global__ void __launch_bounds__(kT) k_level_scatter(int64_t m, const uint8_t *__restrict__ nlev,
+__global__ void __launch_bounds__(kT) k_level_scatter(const uint32_t *__restrict__ nsplit, int64_t B,
+                                                      const uint8_t *__restrict__ nlev,
                                                       const uint32_t *__restrict__ loff,
                                                       uint32_t *lcursor, uint32_t *lnodes) {
+    const int64_t m = B + (int64_t)*nsplit;
     __shared__ uint32_t h[kLevels + 1], hb[kLevels + 1];
     if (threadIdx.x <= kLevels) h[threadIdx.x] = 0;
     __syncthreads();
@@ -1088,46 +1100,45 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     }
     k_permute<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, d_mass, t->px, t->py, t->pz, t->pm32,
                                      t->pm64); note_launch();
-    // a4: nodes from splits
+    // a4: nodes from splits.  The node count stays on the device (d_tot[0]
+    // counts the first splits, m = B + that): the kernels up to the groups
+    // read it there and are sized for the most nodes a tree can have, so the
+    // host does not wait for it.
     uint32_t h_tot[4] = {0, 0, 0, 0};
     int64_t nsplit = n - 1;
+    cudaMemsetAsync(d_tot, 0, 4 * sizeof(uint32_t), s);
     if (nsplit > 0) {
         k_split_levels<<<nblk(nsplit), kT, 0, s>>>(t->skey, t->sseg, n, lv); note_launch();
         k_split_nodes<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, t->sseg, t->seg_off, n, sbeg, send,
                                                   first); note_launch();
         scan_exclusive_u32(first, nid, nsplit, d_tot, scan_scratch, s);
-        cudaMemcpyAsync(h_tot, d_tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) {
-            cudaFreeAsync(scratch, s);
-            return cuda_fail(err, "build (sort)");
-        }
     }
-    const int64_t m = B + (int64_t)h_tot[0];
-    t->nnodes = m;
+    const uint32_t *nsp = d_tot;
     k_node_init<<<nblk(nsplit > B ? nsplit : B), kT, 0, s>>>(n, B, t->seg_off, first, nid, lv, sbeg,
                                                             send, t->px, t->py, t->pz, t->nlev,
                                                             t->nbeg, t->nend, t->norg); note_launch();
     if (nsplit > 0) {
         k_split_node_id<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, sbeg, first, nid, t->sseg, n, B, sid); note_launch();
     }
-    cudaMemsetAsync(occ, 0, m * sizeof(uint32_t), s);
-    cudaMemsetAsync(nnc, 0, m * sizeof(uint32_t), s);
-    k_link<<<nblk(n + m), kT, 0, s>>>(n, m, B, t->skey, lv, sid, t->sseg, t->nlev, t->nbeg, t->nend,
-                                      t->npar, t->owner, occ, nnc, status); note_launch();
-    k_ccnt<<<nblk(m), kT, 0, s>>>(m, t->nlev, t->nbeg, t->nend, occ, t->nccnt); note_launch();
-    scan_exclusive_u32(t->nccnt, t->ncbeg, m, d_tot + 1, scan_scratch, s);
-    const int64_t nchild = n + (m - B);
-    t->nchild = nchild;
-    k_place<<<nblk(n + m), kT, 0, s>>>(n, m, B, t->skey, t->nlev, t->nbeg, t->ncbeg, occ, t->npar,
-                                       t->owner, t->child, t->npos, nchild, status); note_launch();
-    k_threading<<<nblk(nchild), kT, 0, s>>>(n, m, B, nchild, t->child, t->ncbeg, t->nccnt, t->npar,
-                                            t->npos, t->owner, t->nnext, t->nsib, t->pnext, status); note_launch();
+    cudaMemsetAsync(occ, 0, mcap * sizeof(uint32_t), s);
+    cudaMemsetAsync(nnc, 0, mcap * sizeof(uint32_t), s);
+    // child counts beyond the last node stay 0, so the scan over mcap entries
+    // gives the node's child offsets and, as its total, the child entries
+    cudaMemsetAsync(t->nccnt, 0, mcap * sizeof(uint32_t), s);
+    k_link<<<nblk(n + mcap), kT, 0, s>>>(n, nsp, B, t->skey, lv, sid, t->sseg, t->nlev, t->nbeg,
+                                         t->nend, t->npar, t->owner, occ, nnc, status); note_launch();
+    k_ccnt<<<nblk(mcap), kT, 0, s>>>(nsp, B, t->nlev, t->nbeg, t->nend, occ, t->nccnt); note_launch();
+    scan_exclusive_u32(t->nccnt, t->ncbeg, mcap, d_tot + 1, scan_scratch, s);
+    k_place<<<nblk(n + mcap), kT, 0, s>>>(n, nsp, B, t->skey, t->nlev, t->nbeg, t->ncbeg, occ,
+                                          t->npar, t->owner, t->child, t->npos, status); note_launch();
+    k_threading<<<nblk(ccap), kT, 0, s>>>(n, nsp, B, t->child, t->ncbeg, t->nccnt, t->npar,
+                                          t->npos, t->owner, t->nnext, t->nsib, t->pnext, status); note_launch();
     // a5 (part 1): node ids by level
     cudaMemsetAsync(lcount, 0, (kLevels + 2) * sizeof(uint32_t), s);
-    const unsigned lv_blocks = (unsigned)((m + (int64_t)kT * kLvItems - 1) / ((int64_t)kT * kLvItems));
-    k_level_hist<<<lv_blocks, kT, 0, s>>>(m, t->nlev, lcount); note_launch();
+    const unsigned lv_blocks = (unsigned)((mcap + (int64_t)kT * kLvItems - 1) / ((int64_t)kT * kLvItems));
+    k_level_hist<<<lv_blocks, kT, 0, s>>>(nsp, B, t->nlev, lcount); note_launch();
     k_level_offsets<<<1, 32, 0, s>>>(lcount, loff, lcursor); note_launch();
-    k_level_scatter<<<lv_blocks, kT, 0, s>>>(m, t->nlev, loff, lcursor, lnodes); note_launch();
+    k_level_scatter<<<lv_blocks, kT, 0, s>>>(nsp, B, t->nlev, loff, lcursor, lnodes); note_launch();
     // a6: groups (one group size for the whole forest)
     const int G = t->prm.group_max;
     k_frontier<<<nblk(n), kT, 0, s>>>(n, B, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit); note_launch();
@@ -1136,12 +1147,21 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     k_groupmark<<<nblk(n), kT, 0, s>>>(n, G, rs, fp, unit, t->nbeg, t->nend, gs); note_launch();
     scan_exclusive_u32(gs, gid, n, d_tot + 2, scan_scratch, s);
     k_group_init<<<nblk(n), kT, 0, s>>>(n, gs, gid, t->gbeg); note_launch();
-    cudaMemcpyAsync(h_tot + 1, d_tot + 1, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h_tot, d_tot, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     uint32_t h_lcount[kLevels + 2];
     cudaMemcpyAsync(h_lcount, lcount, (kLevels + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) {
         cudaFreeAsync(scratch, s);
         return cuda_fail(err, "build (topology)");
+    }
+    const int64_t m = B + (int64_t)h_tot[0];
+    t->nnodes = m;
+    const int64_t nchild = n + (m - B);
+    t->nchild = nchild;
+    if (m > mcap) {
+        cudaFreeAsync(scratch, s);
+        set_error("internal: node count %lld above its bound %lld", (long long)m, (long long)mcap);
+        return OG_ERR_STATE;
     }
     if ((int64_t)h_tot[1] != nchild) {
         cudaFreeAsync(scratch, s);
