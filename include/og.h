@@ -55,7 +55,8 @@ typedef enum {
                                 call returns it */
     OG_ERR_BUDGET = -5,      /* the request does not fit the HBM budget */
     OG_ERR_OVERFLOW = -6,    /* a fixed-capacity device buffer overflowed */
-    OG_ERR_STATE = -7        /* call not valid in the handle's state */
+    OG_ERR_STATE = -7,       /* call not valid in the handle's state */
+    OG_ERR_CANCELLED = -8    /* og_serve_poll: the request was cancelled */
 } og_status;
 
 typedef enum {
@@ -341,10 +342,12 @@ typedef struct {
  * systems stays within the context's hbm_budget_bytes (0: no bound) and at
  * most 256 are active; it keeps each admitted system's tree, positions,
  * velocities and accelerations on the device, walks all active systems in
- * one launch per step, and refits a tree after a step unless the drift since
- * its build exceeds a quarter of its mean group box side (or four refits
- * have passed), in which case it rebuilds.  OG_ERR_BUDGET if the system
- * alone exceeds the budget.  Thread safe. */
+ * one launch per step, and after each step refits a system's tree or
+ * rebuilds it, whichever its own interaction counts price lower for the next
+ * step (a refitted tree is exact, but its lists grow with the drift).  The
+ * decisions depend only on the system, so a request gets the same bits
+ * served alone or in a mix.  OG_ERR_BUDGET if the system alone exceeds the
+ * budget.  Thread safe. */
 og_status og_serve_submit(og_ctx *ctx, const og_request *req, uint64_t *ticket);
 
 /* Device memory the admission control charges for a request of n particles
@@ -356,6 +359,16 @@ size_t og_serve_request_bytes(int64_t n);
  * OG_PENDING if not done yet, a negative status if the request failed.
  * Thread safe. */
 og_status og_serve_poll(og_ctx *ctx, uint64_t ticket, og_result *out, int timeout_ms);
+
+/* Cancel a queued or running request (a service of the serving loop; the
+ * paper has no counterpart).  OG_OK: the cancellation is recorded.  A queued
+ * request is dropped at once; a running one is dropped before its next
+ * engine step, its device memory is freed, and its output arrays are not
+ * written after that.  og_serve_poll then returns OG_ERR_CANCELLED, or OG_OK
+ * if the request finished its last step before the engine took the
+ * cancellation.  OG_ERR_STATE if the request has already finished or been
+ * collected, OG_ERR_ARG for an unknown ticket.  Thread safe. */
+og_status og_serve_cancel(og_ctx *ctx, uint64_t ticket);
 
 /* ---- time integration: individual power-of-two time steps -------------- */
 
@@ -490,6 +503,15 @@ int64_t og_kernel_launches(void);
  * that native GB300 code is loaded rather than PTX compiled at run time.
  * version: out.  OG_ERR_ARG on NULL; OG_ERR_CUDA without a usable device. */
 og_status og_device_code_version(int32_t *version);
+
+/* Failure injection for tests of error handling (the paper has no
+ * counterpart): of the device allocations the library makes next, in any
+ * context, the first `skip` go through and the following `count` fail as if
+ * the device had no memory left, so each affected call returns OG_ERR_OOM
+ * and leaves its context usable.  count = 0 clears the injection.
+ * OG_ERR_ARG if skip or count < 0.  Nothing reaches the GPU: the failure is
+ * made on the host, before the allocation is asked for. */
+og_status og_debug_fail_allocations(int32_t skip, int32_t count);
 
 #ifdef __cplusplus
 }

@@ -885,7 +885,7 @@ static og_status alloc_extents(og_tree *t) {
     cudaError_t err;
     size_t bytes = (size_t)m * 6 * sizeof(uint32_t) + (size_t)t->nchild * sizeof(CExt) + 1024;
     void *p = nullptr;
-    if ((err = cudaMallocAsync(&p, bytes, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (extents)");
+    if ((err = dev_malloc_async(&p, bytes, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (extents)");
     t->ext_arena = p;
     t->next_s = static_cast<uint32_t *>(p);
     t->next_l = t->next_s + 3 * m;
@@ -915,7 +915,7 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
     }
     size_t sb = (size_t)n * (3 * 4 + 8 + 4 + 4) + 4096;
     void *scratch = nullptr;
-    if ((err = cudaMallocAsync(&scratch, sb, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (refit)");
+    if ((err = dev_malloc_async(&scratch, sb, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (refit)");
     Bump W(scratch, sb);
     uint32_t *qx = W.take<uint32_t>(n), *qy = W.take<uint32_t>(n), *qz = W.take<uint32_t>(n);
     uint64_t *keys = W.take<uint64_t>(n);
@@ -960,7 +960,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
 
     // ---- persistent arrays
     size_t tb = tree_bytes(n, B);
-    if ((err = cudaMallocAsync(&t->arena, tb, s)) != cudaSuccess) {
+    if ((err = dev_malloc_async(&t->arena, tb, s)) != cudaSuccess) {
         t->arena = nullptr;
         return err == cudaErrorMemoryAllocation ? (set_error("device allocation of %zu bytes failed", tb), OG_ERR_OOM)
                                                 : cuda_fail(err, "cudaMallocAsync");
@@ -1038,7 +1038,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + B + 8) + 4096;
     }
     void *scratch = nullptr;
-    if ((err = cudaMallocAsync(&scratch, sb_bytes, s)) != cudaSuccess)
+    if ((err = dev_malloc_async(&scratch, sb_bytes, s)) != cudaSuccess)
         return err == cudaErrorMemoryAllocation ? (set_error("device allocation of %zu bytes failed", sb_bytes), OG_ERR_OOM)
                                                 : cuda_fail(err, "cudaMallocAsync");
     Bump W(scratch, sb_bytes);

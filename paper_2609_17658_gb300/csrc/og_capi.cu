@@ -36,6 +36,29 @@ og_status cuda_fail(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? OG_ERR_OOM : OG_ERR_CUDA;
 }
 
+// injected allocation failures (og_debug_fail_allocations): allocations to
+// let through first, then allocations to fail
+static std::mutex g_inject_mu;
+static int64_t g_inject_skip = 0, g_inject_fail = 0;
+static std::atomic<bool> g_inject_on{false};
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes, cudaStream_t s) {
+    if (g_inject_on.load(std::memory_order_relaxed)) {
+        std::lock_guard<std::mutex> lk(g_inject_mu);
+        if (g_inject_fail > 0) {
+            if (g_inject_skip > 0) {
+                --g_inject_skip;
+            } else {
+                --g_inject_fail;
+                if (g_inject_fail == 0) g_inject_on.store(false);
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+        }
+    }
+    return cudaMallocAsync(p, bytes, s);
+}
+
 namespace {
 
 constexpr int kT = 256;
@@ -206,6 +229,18 @@ const char *og_last_error(void) { return g_err; }
 
 int64_t og_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+og_status og_debug_fail_allocations(int32_t skip, int32_t count) {
+    if (skip < 0 || count < 0) {
+        set_error("og_debug_fail_allocations: skip and count must be >= 0");
+        return OG_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_inject_skip = skip;
+    g_inject_fail = count;
+    g_inject_on.store(count > 0);
+    return OG_OK;
+}
+
 og_status og_device_code_version(int32_t *version) {
     if (!version) {
         set_error("og_device_code_version: NULL pointer");
@@ -323,7 +358,7 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
     cudaError_t e;
     if (!(p->flags & OG_DEVICE_PTRS)) {
         size_t bytes = (size_t)n * 4 * sizeof(double);
-        if ((e = cudaMallocAsync(&staging, bytes, s)) != cudaSuccess) {
+        if ((e = dev_malloc_async(&staging, bytes, s)) != cudaSuccess) {
             delete t;
             return cuda_fail(e, "cudaMallocAsync (inputs)");
         }
@@ -430,7 +465,7 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
     if (t->prm.opening == OG_OPEN_REL && a_old) {
         d_aold = a_old;
         if (!dev) {
-            if ((e = cudaMallocAsync(&tmp, (size_t)n * 3 * sizeof(float), s)) != cudaSuccess)
+            if ((e = dev_malloc_async(&tmp, (size_t)n * 3 * sizeof(float), s)) != cudaSuccess)
                 return cuda_fail(e, "cudaMallocAsync (a_old)");
             cudaMemcpyAsync(tmp, a_old, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
             d_aold = static_cast<const float *>(tmp);
@@ -445,7 +480,7 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
     void *out_tmp = nullptr;
     if (!dev) {
         size_t bytes = (size_t)n * 3 * sizeof(float) + 2 * (size_t)n * sizeof(uint32_t) + 512;
-        if ((e = cudaMallocAsync(&out_tmp, bytes, s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (out)");
+        if ((e = dev_malloc_async(&out_tmp, bytes, s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (out)");
         d_acc = static_cast<float *>(out_tmp);
         d_npp = n_pp ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) : nullptr;
         d_npn = n_pn ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) + n : nullptr;
@@ -488,7 +523,7 @@ og_status og_tree_force_f64(og_tree *t, const float *a_old, double *acc, uint32_
     if (t->prm.opening == OG_OPEN_REL && a_old) {
         d_aold = a_old;
         if (!dev) {
-            if ((e = cudaMallocAsync(&tmp, (size_t)n * 3 * sizeof(float), s)) != cudaSuccess)
+            if ((e = dev_malloc_async(&tmp, (size_t)n * 3 * sizeof(float), s)) != cudaSuccess)
                 return cuda_fail(e, "cudaMallocAsync (a_old)");
             cudaMemcpyAsync(tmp, a_old, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
             d_aold = static_cast<const float *>(tmp);
@@ -506,7 +541,7 @@ og_status og_tree_force_f64(og_tree *t, const float *a_old, double *acc, uint32_
     void *out_tmp = nullptr;
     if (!dev) {
         size_t bytes = (size_t)n * 3 * sizeof(double) + 2 * (size_t)n * sizeof(uint32_t) + 512;
-        if ((e = cudaMallocAsync(&out_tmp, bytes, s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (out)");
+        if ((e = dev_malloc_async(&out_tmp, bytes, s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (out)");
         d_acc = static_cast<double *>(out_tmp);
         d_npp = n_pp ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) : nullptr;
         d_npn = n_pn ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) + n : nullptr;
@@ -539,7 +574,7 @@ og_status og_tree_force_pot(og_tree *t, const float *a_old, float *acc, float *p
     const bool dev = (t->prm.flags & OG_DEVICE_PTRS) != 0;
     cudaError_t e;
     void *tmp = nullptr;
-    if ((e = cudaMallocAsync(&tmp, (size_t)n * 2 * sizeof(float) + 512, s)) != cudaSuccess)
+    if ((e = dev_malloc_async(&tmp, (size_t)n * 2 * sizeof(float) + 512, s)) != cudaSuccess)
         return cuda_fail(e, "cudaMallocAsync (potential)");
     float *pot_sorted = static_cast<float *>(tmp);
     float *d_pot = dev ? pot : pot_sorted + ((n + 63) & ~(int64_t)63);
@@ -579,7 +614,7 @@ og_status og_tree_force_active(og_tree *t, const uint8_t *active, const float *a
     const size_t b_out = dev ? 0 : up((size_t)n * 3 * sizeof(float)) + 2 * up((size_t)n * sizeof(uint32_t));
     const size_t b_aold = (!dev && a_old && t->prm.opening == OG_OPEN_REL) ? up((size_t)n * 3 * sizeof(float)) : 0;
     void *tmp = nullptr;
-    if ((e = cudaMallocAsync(&tmp, b_mask + 3 * b_g + al + b_scan + b_out + b_aold, s)) != cudaSuccess)
+    if ((e = dev_malloc_async(&tmp, b_mask + 3 * b_g + al + b_scan + b_out + b_aold, s)) != cudaSuccess)
         return cuda_fail(e, "cudaMallocAsync (active set)");
     char *q = static_cast<char *>(tmp);
     const uint8_t *d_active = active;
@@ -702,7 +737,7 @@ og_status og_batch_force(og_ctx *c, int64_t nbox, const og_box *boxes, og_batch_
     size_t in_bytes = (size_t)total * 4 * sizeof(double) + (have_aold ? (size_t)total * 3 * sizeof(float) : 0) + 512;
     void *in = nullptr;
     cudaError_t e;
-    if ((e = cudaMallocAsync(&in, in_bytes, s)) != cudaSuccess) { delete t; return cuda_fail(e, "cudaMallocAsync (batch inputs)"); }
+    if ((e = dev_malloc_async(&in, in_bytes, s)) != cudaSuccess) { delete t; return cuda_fail(e, "cudaMallocAsync (batch inputs)"); }
     double *d_pos = static_cast<double *>(in);
     double *d_mass = d_pos + 3 * total;
     float *d_aold = have_aold ? reinterpret_cast<float *>(d_mass + total) : nullptr;
@@ -724,7 +759,7 @@ og_status og_batch_force(og_ctx *c, int64_t nbox, const og_box *boxes, og_batch_
     // results back to every box in its own order
     void *out = nullptr;
     size_t out_bytes = (size_t)total * (3 * sizeof(float) + 2 * sizeof(uint32_t)) + 512;
-    if ((e = cudaMallocAsync(&out, out_bytes, s)) != cudaSuccess) { og_tree_free(t); return cuda_fail(e, "cudaMallocAsync (batch outputs)"); }
+    if ((e = dev_malloc_async(&out, out_bytes, s)) != cudaSuccess) { og_tree_free(t); return cuda_fail(e, "cudaMallocAsync (batch outputs)"); }
     float *o_acc = static_cast<float *>(out);
     uint32_t *o_pp = reinterpret_cast<uint32_t *>(o_acc + 3 * total);
     uint32_t *o_pn = o_pp + total;
@@ -858,7 +893,7 @@ og_status og_tree_refit(og_tree *t, const double *pos) {
     void *tmp = nullptr;
     cudaError_t e;
     if (!(t->prm.flags & OG_DEVICE_PTRS)) {
-        if ((e = cudaMallocAsync(&tmp, (size_t)n * 3 * sizeof(double), s)) != cudaSuccess)
+        if ((e = dev_malloc_async(&tmp, (size_t)n * 3 * sizeof(double), s)) != cudaSuccess)
             return cuda_fail(e, "cudaMallocAsync (refit)");
         cudaMemcpyAsync(tmp, pos, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
         d_pos = static_cast<const double *>(tmp);

@@ -174,6 +174,16 @@ void pm_free(og_ctx *c);   // og_pm.cu: the context's cuFFT plans
 // count of kernels launched by this library in this process
 void note_launch();
 og_status cuda_fail(cudaError_t e, const char *what);
+// stream-ordered device allocation; fails without asking the device while
+// og_debug_fail_allocations has injected failures left (og_capi.cu)
+cudaError_t dev_malloc_raw(void **p, size_t bytes, cudaStream_t s);
+template <class T>
+cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t s) {
+    void *q = nullptr;
+    const cudaError_t e = dev_malloc_raw(&q, bytes, s);
+    *p = static_cast<T *>(q);
+    return e;
+}
 
 // device scans (og_scan.cu); n elements, exclusive, total written to *d_total
 // when d_total != nullptr.  scratch must hold scan_scratch_bytes(n).

@@ -123,7 +123,7 @@ extern "C" og_status og_kdk_run(og_ctx *c, int64_t n, double *pos, double *vel, 
                          up((size_t)n * 3 * sizeof(float)) + up((size_t)n * sizeof(int32_t)) +
                          up((size_t)n) + up(64);
     void *mem = nullptr;
-    if ((e = cudaMallocAsync(&mem, bytes, s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (kdk)");
+    if ((e = dev_malloc_async(&mem, bytes, s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (kdk)");
     char *q = static_cast<char *>(mem);
     auto take = [&](size_t b) { char *r = q; q += up(b); return r; };
     double *d_pos = reinterpret_cast<double *>(take(b_v));

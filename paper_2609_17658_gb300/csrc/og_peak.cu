@@ -65,7 +65,7 @@ extern "C" og_status og_measure_fp32_peak(og_ctx *c, double *tflops_fma, double 
     const unsigned grid = (unsigned)(sms * per_sm);
     const int iters = 4096;
     float *out = nullptr;
-    cudaError_t e = cudaMallocAsync(&out, sizeof(float), s);
+    cudaError_t e = dev_malloc_async(&out, sizeof(float), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (peak)");
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

@@ -325,7 +325,7 @@ extern "C" og_status og_tree_pm_force(og_tree *t, int32_t mesh, float *acc) {
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync(&buf, total, s);
+    cudaError_t e = dev_malloc_async(&buf, total, s);
     if (e != cudaSuccess) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

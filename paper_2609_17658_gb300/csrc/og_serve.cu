@@ -32,6 +32,7 @@
 #include <new>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "og_internal.h"
@@ -123,6 +124,8 @@ struct Server {
     std::vector<System *> active;
     std::unordered_map<uint64_t, og_result> done;
     std::unordered_map<uint64_t, og_status> failed;
+    std::vector<uint64_t> cancel;     // running requests to drop before their next step
+    std::unordered_set<uint64_t> live;  // submitted and not finished
     uint64_t next_ticket = 1;
     size_t budget = 0, used = 0;
     bool stop = false;
@@ -202,7 +205,7 @@ og_status admit_system(Server *S, System *sy, const Worker &w) {
     const int64_t n = sy->n;
     size_t bytes = (size_t)n * (3 * 8 * 2 + 8 + 3 * 4) + 4096;
     cudaError_t e;
-    if ((e = cudaMallocAsync(&sy->dmem, bytes, s)) != cudaSuccess) return cuda_fail(e, "serve admission");
+    if ((e = dev_malloc_async(&sy->dmem, bytes, s)) != cudaSuccess) return cuda_fail(e, "serve admission");
     char *q = static_cast<char *>(sy->dmem);
     sy->d_pos = reinterpret_cast<double *>(q);
     sy->d_vel = sy->d_pos + 3 * n;
@@ -246,6 +249,7 @@ std::vector<og_status> on_workers(Server *S, std::vector<System *> v, F fn, std:
 
 void finish(Server *S, System *sy, og_status st) {
     std::lock_guard<std::mutex> lk(S->mu);
+    S->live.erase(sy->ticket);
     S->used -= std::min(S->used, sy->bytes);
     if (st == OG_OK) S->done[sy->ticket] = sy->res;
     else S->failed[sy->ticket] = st;
@@ -412,6 +416,26 @@ void engine_main(Server *S) {
                 }
             }
         }
+        // cancellations of running requests, taken before the next step
+        std::vector<uint64_t> drop;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            drop.swap(S->cancel);
+        }
+        if (!drop.empty()) {
+            std::vector<System *> keep;
+            for (System *sy : S->active) {
+                if (std::find(drop.begin(), drop.end(), sy->ticket) != drop.end()) {
+                    cudaStreamSynchronize(S->ctx->stream);
+                    free_system(S, sy);
+                    finish(S, sy, OG_ERR_CANCELLED);
+                    delete sy;
+                } else {
+                    keep.push_back(sy);
+                }
+            }
+            S->active.swap(keep);
+        }
         if (S->active.empty()) continue;
         engine_step(S);
     }
@@ -536,7 +560,37 @@ extern "C" og_status og_serve_submit(og_ctx *c, const og_request *req, uint64_t 
         std::lock_guard<std::mutex> lk(S->mu);
         sy->ticket = S->next_ticket++;
         *ticket = sy->ticket;
+        S->live.insert(sy->ticket);
         S->pending.push_back(sy);
+    }
+    S->cv_work.notify_all();
+    return OG_OK;
+}
+
+extern "C" og_status og_serve_cancel(og_ctx *c, uint64_t ticket) {
+    if (!c) { set_error("og_serve_cancel: NULL argument"); return OG_ERR_ARG; }
+    if (!c->serve) { set_error("og_serve_cancel: nothing submitted on this context"); return OG_ERR_ARG; }
+    Server *S = static_cast<Server *>(c->serve);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (ticket == 0 || ticket >= S->next_ticket) { set_error("og_serve_cancel: unknown ticket"); return OG_ERR_ARG; }
+        if (!S->live.count(ticket)) {
+            set_error("og_serve_cancel: request %llu has already finished", (unsigned long long)ticket);
+            return OG_ERR_STATE;
+        }
+        for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
+            if ((*it)->ticket == ticket) {
+                // not admitted yet: nothing on the device
+                S->failed[ticket] = OG_ERR_CANCELLED;
+                S->live.erase(ticket);
+                delete *it;
+                S->pending.erase(it);
+                S->cv_done.notify_all();
+                return OG_OK;
+            }
+        }
+        if (std::find(S->cancel.begin(), S->cancel.end(), ticket) == S->cancel.end())
+            S->cancel.push_back(ticket);
     }
     S->cv_work.notify_all();
     return OG_OK;
@@ -563,7 +617,9 @@ extern "C" og_status og_serve_poll(og_ctx *c, uint64_t ticket, og_result *out, i
     if (f != S->failed.end()) {
         og_status st = f->second;
         S->failed.erase(f);
-        set_error("og_serve_poll: request %llu failed", (unsigned long long)ticket);
+        set_error(st == OG_ERR_CANCELLED ? "og_serve_poll: request %llu was cancelled"
+                                         : "og_serve_poll: request %llu failed",
+                  (unsigned long long)ticket);
         return st;
     }
     return OG_PENDING;

@@ -314,7 +314,7 @@ extern "C" og_status og_tree_sph_density(og_tree *t, const float *h, float *rho,
     const size_t off_in = (bh + 255) & ~(size_t)255;
     const size_t total = off_in + (dev ? 0 : 3 * off_in);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync(&buf, total, s);
+    cudaError_t e = dev_malloc_async(&buf, total, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (sph)");
     float *hg = reinterpret_cast<float *>(buf);
     const float *d_h = h;
@@ -401,7 +401,7 @@ extern "C" og_status og_tree_sph_smoothing(og_tree *t, double n_target, double t
     const size_t b4 = ((size_t)n * 4 + 255) & ~(size_t)255, b1 = ((size_t)n + 255) & ~(size_t)255;
     const size_t total = 6 * b4 + b1 + 256 + (dev ? 0 : 3 * b4);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync(&buf, total, s);
+    cudaError_t e = dev_malloc_async(&buf, total, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (sph smoothing)");
     float *hs = reinterpret_cast<float *>(buf), *lo = reinterpret_cast<float *>(buf + b4);
     float *hi = reinterpret_cast<float *>(buf + 2 * b4), *hg = reinterpret_cast<float *>(buf + 3 * b4);

@@ -158,7 +158,7 @@ og_status og_tune_walk(og_ctx *c, const double *pos, const double *mass, int64_t
     void *staging = nullptr;
     cudaError_t e;
     if (!(p->flags & OG_DEVICE_PTRS)) {
-        if ((e = cudaMallocAsync(&staging, (size_t)n * 4 * sizeof(double), s)) != cudaSuccess)
+        if ((e = og::dev_malloc_async(&staging, (size_t)n * 4 * sizeof(double), s)) != cudaSuccess)
             return og::cuda_fail(e, "cudaMallocAsync (inputs)");
         double *dp = static_cast<double *>(staging);
         cudaMemcpyAsync(dp, pos, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, s);

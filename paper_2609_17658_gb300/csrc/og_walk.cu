@@ -991,7 +991,7 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
         // longest list first, from the costs of the previous pass on this tree
         const int64_t ng = t->ngroups;
         size_t bytes = (size_t)ng * 24 + radix_sort_scratch_bytes(ng) + 1024;
-        if ((err = cudaMallocAsync(&sort_tmp, bytes, s)) != cudaSuccess)
+        if ((err = dev_malloc_async(&sort_tmp, bytes, s)) != cudaSuccess)
             return cuda_fail(err, "cudaMallocAsync (group order)");
         char *q = static_cast<char *>(sort_tmp);
         uint64_t *k0 = reinterpret_cast<uint64_t *>(q);
@@ -1074,7 +1074,7 @@ og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int openi
                    radix_sort_scratch_bytes(nitems) + (size_t)ntrees * 8 + 4096;
     void *tmp = nullptr;
     cudaError_t err;
-    if ((err = cudaMallocAsync(&tmp, bytes, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (walk items)");
+    if ((err = dev_malloc_async(&tmp, bytes, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (walk items)");
     char *q = static_cast<char *>(tmp);
     TreeView *dv = reinterpret_cast<TreeView *>(q);
     q += ((size_t)ntrees * sizeof(TreeView) + 255) & ~(size_t)255;

@@ -28,6 +28,7 @@ OG_ERR_TIMEOUT = -4
 OG_ERR_BUDGET = -5
 OG_ERR_OVERFLOW = -6
 OG_ERR_STATE = -7
+OG_ERR_CANCELLED = -8
 
 OG_OPEN_BH = 0
 OG_OPEN_REL = 1
@@ -116,6 +117,10 @@ def lib():
         L.og_kernel_launches.restype = C.c_int64
         L.og_device_code_version.argtypes = [C.POINTER(C.c_int32)]
         L.og_device_code_version.restype = C.c_int
+        L.og_debug_fail_allocations.argtypes = [C.c_int32, C.c_int32]
+        L.og_debug_fail_allocations.restype = C.c_int
+        L.og_serve_cancel.argtypes = [P, C.c_uint64]
+        L.og_serve_cancel.restype = C.c_int
         L.og_sort_keys_noalloc.argtypes = [P, P, P, i64, P]
         L.og_batch_force.argtypes = [P, i64, C.POINTER(og_box), C.POINTER(og_batch_info)]
         L.og_batch_force.restype = C.c_int
@@ -165,6 +170,18 @@ def og_last_error() -> str:
 
 def og_kernel_launches() -> int:
     return int(lib().og_kernel_launches())
+
+
+def og_debug_fail_allocations(count: int, skip: int = 0) -> None:
+    """Let the library's next ``skip`` device allocations through and make
+    the ``count`` after them fail (tests of error handling; see
+    include/og.h).  count = 0 clears it."""
+    _check(lib().og_debug_fail_allocations(int(skip), int(count)))
+
+
+def og_serve_cancel(ctx, ticket: int) -> None:
+    """Cancel a queued or running served request (see include/og.h)."""
+    _check(lib().og_serve_cancel(ctx, C.c_uint64(ticket)))
 
 
 def og_device_code_version() -> int:

@@ -70,6 +70,14 @@ def test_device_code_is_sm103a(libpath):
     assert og.og_device_code_version() == 103
 
 
+def test_failure_injection_arguments_without_gpu(libpath):
+    from paper_2609_17658_gb300 import og
+    L = og.lib()
+    assert L.og_debug_fail_allocations(0, -1) == og.OG_ERR_ARG
+    assert L.og_debug_fail_allocations(-1, 1) == og.OG_ERR_ARG
+    assert L.og_debug_fail_allocations(0, 0) == og.OG_OK
+
+
 def test_params_defaults_without_gpu(libpath):
     from paper_2609_17658_gb300 import og
     p = og.og_params()
