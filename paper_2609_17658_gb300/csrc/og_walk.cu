@@ -791,7 +791,14 @@ __global__ void k_cost_keys(int64_t ng, const uint32_t *__restrict__ gcost, uint
                             uint32_t *vals) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng) return;
-    keys[g] = (uint64_t)(0xffffffffu - gcost[g]);  // decreasing cost, ties in key order
+    // longest list first in coarse classes, a quarter octave of list length
+    // each (the exponent and the next two bits of cost + 1), key order within
+    // a class: the long groups still start first, and groups walked together
+    // stay close in space, so more of their tree records are still in L2
+    const uint32_t c = gcost[g] + 1u;
+    const uint32_t e = 31u - __clz(c);
+    const uint32_t code = (e << 2) | (e >= 2u ? ((c >> (e - 2u)) & 3u) : 0u);
+    keys[g] = (uint64_t)(255u - code);
     vals[g] = (uint32_t)g;
 }
 
@@ -1001,7 +1008,7 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
         void *scr = v1 + ng + 64;
         k_cost_keys<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(ng, t->gcost, k0, v0); note_launch();
         bool alt = false;
-        radix_sort_pairs(k0, v0, k1, v1, ng, 32, scr, s, &alt);
+        radix_sort_pairs(k0, v0, k1, v1, ng, 8, scr, s, &alt);
         cudaMemcpyAsync(t->gorder, alt ? v1 : v0, ng * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         a.tree0.gorder = t->gorder;
     }
