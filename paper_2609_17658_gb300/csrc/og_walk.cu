@@ -814,7 +814,11 @@ __global__ void k_item_keys(int64_t nitems, int64_t ntrees, const uint64_t *__re
     }
     const TreeView &T = trees[lo];
     const uint32_t cost = T.has_cost ? T.gcost[q - goff[lo]] : 0u;
-    keys[q] = (uint64_t)(0xffffffffu - cost);
+    // the classes of k_cost_keys: longest first, tree and key order within
+    const uint32_t c = cost + 1u;
+    const uint32_t e = 31u - __clz(c);
+    const uint32_t code = (e << 2) | (e >= 2u ? ((c >> (e - 2u)) & 3u) : 0u);
+    keys[q] = (uint64_t)(255u - code);
     vals[q] = (uint32_t)q;
 }
 
@@ -1098,7 +1102,7 @@ og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int openi
     cudaMemcpyAsync(doff, hoff.data(), (ntrees + 1) * 8, cudaMemcpyHostToDevice, s);
     k_item_keys<<<(unsigned)((nitems + 255) / 256), 256, 0, s>>>(nitems, ntrees, doff, dv, k0, v0); note_launch();
     bool alt = false;
-    radix_sort_pairs(k0, v0, k1, v1, nitems, 32, scr, s, &alt);
+    radix_sort_pairs(k0, v0, k1, v1, nitems, 8, scr, s, &alt);
     WalkArgs a{};
     fill_common(a, c, nullptr);
     a.trees = dv;
