@@ -625,7 +625,7 @@ struct LevelRun {
     uint32_t off[kLevels + 1], cnt[kLevels + 1];
 };
 constexpr int kRunThreads = 512;
-constexpr uint32_t kRunMaxNodes = 1024;        // a level of at most 2 rounds of the block
+constexpr uint32_t kRunMaxNodes = 256;         // larger levels get a grid of their own
 
 __global__ void __launch_bounds__(kRunThreads) k_moments_run(
     int64_t n, int64_t m, const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
