@@ -12,12 +12,19 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   groups                    partition and size invariants
   lists                     partition invariant (every neighbour covered once),
                             theta = 0 reduces to all particles within the cutoff
+  opening decision          hand-placed one-node trees at every threshold of the
+                            Barnes-Hut, relative and boundary tests, exact
+                            rationals (tests/test_oracle_opening.py)
+  cutoff decision           single precision on the exact integer separation,
+                            recomputed with exact integers and 24-bit rounding
   force                     two-body closed form from the spline mass profile
                             and the erfc potential (numerical quadrature and
                             differentiation), theta = 0 equals direct summation,
                             uniform sphere interior, lattice zero force,
                             momentum conservation as theta -> 0
-  tree error at theta > 0   parity unpinned (the paper prints no numbers)
+  size of the tree error    no value to pin it to: the paper prints no accuracy
+  at theta > 0              numbers for its tree; every step that produces it is
+                            pinned above, and theta -> 0 reaches the direct sum
 """
 from __future__ import annotations
 
