@@ -8,7 +8,8 @@ what each routine computes and which passage of the paper it follows.
 Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   quantize / morton         brute force, closed form on lattices
   tree build (topology)     brute-force node-set definition over all levels
-  moments                   exact rational centre of mass (within one grid unit)
+  moments                   exact rational sums rounded once and the rounded
+                            exact centre of mass (Python fractions), bitwise
   groups                    partition and size invariants
   lists                     partition invariant (every neighbour covered once),
                             theta = 0 reduces to all particles within the cutoff

@@ -20,7 +20,7 @@
  *       than leaf_max particles (coincident keys) are buckets
  *   a4' the two-pointer threading of Sect. 4.1.1 (nextnode / sibling) in a
  *       unified index space: particles 0..N-1, nodes N..N+M-1, end = -1
- *   a5  bottom-up monopole moments: mass and centre of mass
+ *   a5  monopole moments: mass and centre of mass, exact sums rounded once
  *   a6  groups of spatially close particles (Sect. 3.4 and 18.2: one walk
  *       per group of nearby particles)
  *   a7  per group: tree walk with Barnes-Hut or relative opening, a boundary
@@ -55,12 +55,13 @@
  *     nearest), r2 = fma(dx, dx, fma(dy, dy, dz*dz)) in grid units, compared
  *     with (float)(rcut_grid^2).  Everything after the decision is FP64.
  *   - tree: see a4 above; children ordered by key.
- *   - moments: per node, slots 0..7 are the child octants; slot values
- *     (M, sum m x) are summed sequentially in key order inside a slot and
- *     combined as ((0+1)+(2+3))+((4+5)+(6+7)); an empty slot is +0.0; a
- *     bucket sums its particles sequentially in key order.  The centre of
- *     mass is rounded half-to-even to the integer grid.  No fused multiply
- *     adds (compiled with -ffp-contract=off).
+ *   - moments (FP64 monopoles, Sect. 4.1.1): a node's mass M and its sums
+ *     S = sum m x per axis (x the integer grid coordinates of its particles)
+ *     are the exact real sums, each rounded once to the nearest double (ties
+ *     to even), so no order of additions is implied.  The centre of mass is
+ *     the grid point nearest to the exact S / M, ties to even; a massless
+ *     node takes its cell centre.  The sums are carried exactly as integers
+ *     (see a5).  Elsewhere no fused multiply adds (-ffp-contract=off).
  *   - groups: children with more than G particles are recursed into.  At a
  *     node that holds at most 8 G particles (and at the root), maximal runs of
  *     consecutive "small" children (particles, or nodes with at most G
@@ -174,6 +175,7 @@ struct ora_tree {
     uint32_t *ox, *oy, *oz; /* cell origin of each node (fixed by the build) */
     uint32_t *es, *el;      /* after a refit: extent start and length, 3 per node */
     int refit;
+    int fb, fnl;            /* exact sums: units of 2^fb, fnl 64-bit limbs */
     /* groups */
     int64_t *gbeg, *gend;
     uint32_t *glo, *ghi;    /* 3 per group */
@@ -268,58 +270,187 @@ static int64_t build_node(ora_tree *t, int level, int64_t b, int64_t e, int64_t 
     return id;
 }
 
-/* a5: monopole moments of one node from its (already final) children */
-static void node_moments(ora_tree *t, int64_t id)
+/* ------------------------------------------------------------------------ */
+/* a5: monopole moments, exact                                               */
+/* ------------------------------------------------------------------------ */
+
+/* A nonzero mass is m = s 2^e with an integer s < 2^53 (frexp).  With b the
+ * lowest exponent of a set bit over all masses of the tree, every mass is an
+ * integer multiple of 2^b, and so is every product m x with x an integer grid
+ * coordinate.  The sums are kept as unsigned integers of t->fnl 64-bit limbs
+ * (least significant first) in units of 2^b, so they are exact whatever the
+ * order of the additions, and are rounded once at the end. */
+
+static void fx_zero(uint64_t *a, int nl) { memset(a, 0, (size_t)nl * 8); }
+
+static void fx_add(uint64_t *a, const uint64_t *c, int nl)
+{
+    uint64_t carry = 0;
+    for (int k = 0; k < nl; ++k) {
+        uint64_t s = a[k] + carry;
+        uint64_t c1 = s < carry;
+        uint64_t r = s + c[k];
+        a[k] = r;
+        carry = c1 + (r < s);
+    }
+}
+
+static void fx_sub(uint64_t *a, const uint64_t *c, int nl) /* a -= c, a >= c */
+{
+    uint64_t borrow = 0;
+    for (int k = 0; k < nl; ++k) {
+        uint64_t d = a[k] - c[k];
+        uint64_t b1 = a[k] < c[k];
+        uint64_t r = d - borrow;
+        b1 += d < borrow;
+        a[k] = r;
+        borrow = b1;
+    }
+}
+
+static int fx_cmp(const uint64_t *a, const uint64_t *c, int nl)
+{
+    for (int k = nl - 1; k >= 0; --k)
+        if (a[k] != c[k]) return a[k] < c[k] ? -1 : 1;
+    return 0;
+}
+
+/* out (nl limbs) = a (nl limbs) * x; the product fits nl limbs */
+static void fx_mul_u32(const uint64_t *a, uint32_t x, uint64_t *out, int nl)
+{
+    unsigned __int128 carry = 0;
+    for (int k = 0; k < nl; ++k) {
+        unsigned __int128 p = (unsigned __int128)a[k] * x + carry;
+        out[k] = (uint64_t)p;
+        carry = p >> 64;
+    }
+}
+
+/* index of the highest set bit, -1 for zero */
+static int fx_top(const uint64_t *a, int nl)
+{
+    for (int k = nl - 1; k >= 0; --k)
+        if (a[k]) return 64 * k + 63 - __builtin_clzll(a[k]);
+    return -1;
+}
+
+static int fx_bit(const uint64_t *a, int nl, int i)
+{
+    if (i < 0 || i >= 64 * nl) return 0;
+    return (int)((a[i / 64] >> (i % 64)) & 1u);
+}
+
+/* bits [lo, lo + 53) of a as an integer (bits below 0 read as zero) */
+static uint64_t fx_bits53(const uint64_t *a, int nl, int lo)
+{
+    uint64_t v = 0;
+    for (int i = 52; i >= 0; --i) v = (v << 1) | (uint64_t)fx_bit(a, nl, lo + i);
+    return v;
+}
+
+/* the mass as an integer in units of 2^b */
+static void fx_mass(double m, int b, uint64_t *out, int nl)
+{
+    fx_zero(out, nl);
+    if (m == 0.0) return;
+    int e;
+    double fr = frexp(m, &e);                        /* m = fr 2^e, fr in [1/2, 1) */
+    uint64_t s = (uint64_t)ldexp(fr, 53);           /* m = s 2^(e - 53), exactly */
+    for (int i = 0; i < 53; ++i) {
+        if (!((s >> i) & 1u)) continue;
+        int pos = i + e - 53 - b;                   /* >= 0 by the choice of b */
+        out[pos / 64] |= (uint64_t)1 << (pos % 64);
+    }
+}
+
+/* a 2^b rounded to the nearest double, ties to even (subnormal results and
+ * overflow to infinity as IEEE 754 rounds them) */
+static double fx_to_double(const uint64_t *a, int nl, int b)
+{
+    int p = fx_top(a, nl);
+    if (p < 0) return 0.0;
+    /* position of the last kept bit: 53 significant bits, or the 2^-1074 grid */
+    int lsb = (p + b >= -1022) ? p - 52 : -1074 - b;
+    uint64_t mant = fx_bits53(a, nl, lsb);
+    if (lsb > 0 && fx_bit(a, nl, lsb - 1)) {
+        int sticky = 0;
+        for (int i = 0; i < lsb - 1 && !sticky; ++i) sticky = fx_bit(a, nl, i);
+        if (sticky || (mant & 1u)) mant += 1;
+    }
+    return ldexp((double)mant, lsb + b);
+}
+
+/* the integer nearest to S / M (M > 0, S / M < 2^32), ties to even */
+static uint32_t fx_round_ratio(const uint64_t *S, const uint64_t *M, int nl)
+{
+    uint64_t qM[64], R[64], twoR[64];
+    int pS = fx_top(S, nl), pM = fx_top(M, nl);
+    int64_t q = 0;
+    if (pS >= 0) {
+        /* a first guess from the leading bits; the loops below make it exact */
+        double r = ldexp((double)fx_bits53(S, nl, pS - 52) / (double)fx_bits53(M, nl, pM - 52),
+                         pS - pM);
+        q = (int64_t)floor(r);
+        if (q < 0) q = 0;
+        if (q > 4294967295ll) q = 4294967295ll;
+    }
+    fx_mul_u32(M, (uint32_t)q, qM, nl);
+    while (q > 0 && fx_cmp(qM, S, nl) > 0) { q -= 1; fx_sub(qM, M, nl); }
+    for (;;) {                                       /* largest q with q M <= S */
+        memcpy(R, qM, (size_t)nl * 8);
+        fx_add(R, M, nl);
+        if (fx_cmp(R, S, nl) > 0) break;
+        q += 1;
+        memcpy(qM, R, (size_t)nl * 8);
+    }
+    memcpy(R, S, (size_t)nl * 8);
+    fx_sub(R, qM, nl);                               /* R = S - q M in [0, M) */
+    memcpy(twoR, R, (size_t)nl * 8);
+    fx_add(twoR, R, nl);
+    int c = fx_cmp(twoR, M, nl);
+    if (c > 0 || (c == 0 && (q & 1))) q += 1;
+    return (uint32_t)q;
+}
+
+/* Exact sums of the node's particles (mass and m x, m y, m z: 4 nl limbs at
+ * acc), from its children: particles directly, child nodes by recursion.
+ * Stores the node's mass and sums rounded once to FP64 and its centre of mass
+ * on the grid.  acc + 4 nl onwards is scratch for the deeper levels. */
+static void node_sums(ora_tree *t, int64_t id, uint64_t *acc)
 {
     const int64_t n = t->n;
-    int level = t->level[id];
-    double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
-    if (level == KEY_LEVELS) {
-        for (int64_t k = 0; k < t->ccnt[id]; ++k) {
-            int64_t q = t->child[t->cbeg[id] + k];
-            double m = t->sm[q];
-            M = M + m;
-            Sx = Sx + m * (double)t->sx[q];
-            Sy = Sy + m * (double)t->sy[q];
-            Sz = Sz + m * (double)t->sz[q];
+    const int nl = t->fnl;
+    uint64_t *sub = acc + 4 * nl;
+    uint64_t v[64], w[64];
+    fx_zero(acc, 4 * nl);
+    for (int64_t k = 0; k < t->ccnt[id]; ++k) {
+        int64_t c = t->child[t->cbeg[id] + k];
+        if (c < n) {
+            fx_mass(t->sm[c], t->fb, v, nl);
+            fx_add(acc, v, nl);
+            fx_mul_u32(v, t->sx[c], w, nl);
+            fx_add(acc + nl, w, nl);
+            fx_mul_u32(v, t->sy[c], w, nl);
+            fx_add(acc + 2 * nl, w, nl);
+            fx_mul_u32(v, t->sz[c], w, nl);
+            fx_add(acc + 3 * nl, w, nl);
+        } else {
+            node_sums(t, c - n, sub);
+            for (int q = 0; q < 4; ++q) fx_add(acc + q * nl, sub + q * nl, nl);
         }
-    } else {
-        double sM[8], sX[8], sY[8], sZ[8];
-        for (int s = 0; s < 8; ++s) sM[s] = sX[s] = sY[s] = sZ[s] = 0.0;
-        for (int64_t k = 0; k < t->ccnt[id]; ++k) {
-            int64_t c = t->child[t->cbeg[id] + k];
-            if (c < n) {
-                int s = digit_at(t->skey[c], level + 1);
-                double m = t->sm[c];
-                sM[s] = sM[s] + m;
-                sX[s] = sX[s] + m * (double)t->sx[c];
-                sY[s] = sY[s] + m * (double)t->sy[c];
-                sZ[s] = sZ[s] + m * (double)t->sz[c];
-            } else {
-                int64_t j = c - n;
-                int s = digit_at(t->skey[t->beg[j]], level + 1);
-                sM[s] = sM[s] + t->M[j];
-                sX[s] = sX[s] + t->Sx[j];
-                sY[s] = sY[s] + t->Sy[j];
-                sZ[s] = sZ[s] + t->Sz[j];
-            }
-        }
-        M = ((sM[0] + sM[1]) + (sM[2] + sM[3])) + ((sM[4] + sM[5]) + (sM[6] + sM[7]));
-        Sx = ((sX[0] + sX[1]) + (sX[2] + sX[3])) + ((sX[4] + sX[5]) + (sX[6] + sX[7]));
-        Sy = ((sY[0] + sY[1]) + (sY[2] + sY[3])) + ((sY[4] + sY[5]) + (sY[6] + sY[7]));
-        Sz = ((sZ[0] + sZ[1]) + (sZ[2] + sZ[3])) + ((sZ[4] + sZ[5]) + (sZ[6] + sZ[7]));
     }
-    t->M[id] = M;
-    t->Sx[id] = Sx;
-    t->Sy[id] = Sy;
-    t->Sz[id] = Sz;
-    uint32_t side_shift = 32 - level; /* cell side = 2^(32-level) grid units */
-    if (M > 0.0) {
-        t->cx[id] = (uint32_t)rint(Sx / M);
-        t->cy[id] = (uint32_t)rint(Sy / M);
-        t->cz[id] = (uint32_t)rint(Sz / M);
+    t->M[id] = fx_to_double(acc, nl, t->fb);
+    t->Sx[id] = fx_to_double(acc + nl, nl, t->fb);
+    t->Sy[id] = fx_to_double(acc + 2 * nl, nl, t->fb);
+    t->Sz[id] = fx_to_double(acc + 3 * nl, nl, t->fb);
+    if (fx_top(acc, nl) >= 0) {
+        t->cx[id] = fx_round_ratio(acc + nl, acc, nl);
+        t->cy[id] = fx_round_ratio(acc + 2 * nl, acc, nl);
+        t->cz[id] = fx_round_ratio(acc + 3 * nl, acc, nl);
     } else {
         /* massless node: the cell centre */
+        const int level = t->level[id];
+        uint32_t side_shift = 32 - level; /* cell side = 2^(32-level) grid units */
         uint64_t half = (uint64_t)1 << (side_shift - 1);
         uint64_t mask = (level == 0) ? 0 : ~(((uint64_t)1 << side_shift) - 1);
         uint64_t q = t->beg[id];
@@ -329,7 +460,39 @@ static void node_moments(ora_tree *t, int64_t id)
     }
 }
 
-/* a4': nextnode / sibling threading in the unified index space */
+/* the fixed-point format of a tree's masses: b and the limb count */
+static int mass_format(ora_tree *t)
+{
+    int lo = 0, hi = 0, any = 0;
+    for (int64_t i = 0; i < t->n; ++i) {
+        double m = t->sm[i];
+        if (m == 0.0) continue;
+        int e;
+        double fr = frexp(m, &e);
+        uint64_t s = (uint64_t)ldexp(fr, 53);
+        int l = e - 53 + __builtin_ctzll(s);          /* lowest set bit of m */
+        if (!any || l < lo) lo = l;
+        if (!any || e > hi) hi = e;                   /* m < 2^e */
+        any = 1;
+    }
+    t->fb = any ? lo : 0;
+    /* a mass below 2^(hi - lo), a coordinate below 2^32, fewer than 2^63
+       terms: hi - lo + 95 bits hold every sum */
+    int bits = (any ? hi - lo : 1) + 95;
+    t->fnl = (bits + 63) / 64;
+    return t->fnl <= 40 ? ORA_OK : ORA_ERR_ARG;      /* finite doubles need at most 38 */
+}
+
+/* moments of every node, from the root down and back up */
+static int all_moments(ora_tree *t)
+{
+    uint64_t *work = (uint64_t *)calloc((size_t)(KEY_LEVELS + 3) * 4 * t->fnl, 8);
+    if (!work) return ORA_ERR_OOM;
+    node_sums(t, 0, work);
+    free(work);
+    return ORA_OK;
+}
+
 static void thread_node(ora_tree *t, int64_t id, int64_t after)
 {
     const int64_t n = t->n;
@@ -474,8 +637,13 @@ int ora_tree_build(const double *pos, const double *mass, int64_t n, const ora_p
     }
     /* a4: the root is level 0 and covers the whole box */
     build_node(t, 0, 0, n, -1);
-    /* a5: bottom-up; in preorder every child has a larger id than its parent */
-    for (int64_t id = t->nnodes - 1; id >= 0; --id) node_moments(t, id);
+    /* a5 */
+    int rc = mass_format(t);
+    if (rc == ORA_OK) rc = all_moments(t);
+    if (rc != ORA_OK) {
+        ora_tree_free(t);
+        return rc;
+    }
     /* a4' */
     t->sibling[0] = -1;
     thread_node(t, 0, -1);
@@ -525,8 +693,8 @@ static int64_t min_image(uint32_t xj, uint32_t xi)
 /* ------------------------------------------------------------------------ */
 
 /* Refit for drifted positions of the same particles (input order): the
- * topology, the groups and the octant slots of the build stay; masses, sums
- * and centres of mass are recomputed in the same slot order; every node gets
+ * topology, the groups and the octant slots of the build stay; sums and
+ * centres of mass are recomputed (exactly, as in the build); every node gets
  * an extent, its cell joined with the members' positions (offsets from the
  * cell origin as 32-bit differences, so drift across the periodic boundary
  * stays local); group boxes are recomputed. */
@@ -545,8 +713,10 @@ int ora_tree_refit(ora_tree *t, const double *pos)
         t->sy[i] = t->y[j];
         t->sz[i] = t->z[j];
     }
+    int rc = all_moments(t);
+    if (rc != ORA_OK) return rc;
+    /* extents bottom-up: in preorder every child has a larger id than its parent */
     for (int64_t id = t->nnodes - 1; id >= 0; --id) {
-        node_moments(t, id);
         const uint32_t o[3] = {t->ox[id], t->oy[id], t->oz[id]};
         const int lev = t->level[id];
         const int64_t side = (int64_t)1 << (32 - lev);

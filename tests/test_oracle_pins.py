@@ -175,27 +175,103 @@ def test_threading_visits_preorder():
         assert int(sib[i]) == (order[k] if k < len(order) else -1)
 
 
-def test_moments_exact_com():
-    pos, mass = gi.halo_mix(1500, 10, n_halo=4)
-    mass = mass * (1.0 + 0.5 * np.random.default_rng(0).random(mass.shape))  # unequal masses
-    t = oracle.Tree(pos, mass, gi.default_params())
+def _rn(f: Fraction) -> float:
+    """The nearest double to an exact rational, ties to even (Python's integer
+    true division rounds correctly); infinity past the largest double."""
+    try:
+        return float(f)
+    except OverflowError:
+        return math.inf
+
+
+def _check_exact_moments(pos, mass, prm):
+    """Every node's mass and sums of m x are the exact sums over its particles
+    rounded once to the nearest double, and its centre of mass is the grid
+    point nearest to the exact ratio (ties to even), or the cell centre of a
+    massless node."""
+    t = oracle.Tree(pos, mass, prm)
     perm = t.get(oracle.F_PERM)
     xs = [t.get(f)[perm] for f in (oracle.F_X, oracle.F_Y, oracle.F_Z)]
     sm = mass[perm]
-    M, com = t.get(oracle.F_MASS), t.get(oracle.F_COM)
-    beg, end = t.get(oracle.F_BEG), t.get(oracle.F_END)
-    for i in range(t.nnodes):
-        b, e = beg[i], end[i]
-        exact_m = math.fsum(sm[b:e])
-        assert abs(M[i] - exact_m) <= 8 * (e - b) * np.finfo(float).eps * exact_m
-        ex = brute.exact_com([c[b:e] for c in xs], sm[b:e])
+    M, S, com = t.get(oracle.F_MASS), t.get(oracle.F_MSUM), t.get(oracle.F_COM)
+    beg, end, lev = t.get(oracle.F_BEG), t.get(oracle.F_END), t.get(oracle.F_LEVEL)
+    pm = [Fraction(0)]
+    ps = [[Fraction(0)] for _ in range(3)]
+    for q, v in enumerate(sm):
+        f = Fraction(float(v))
+        pm.append(pm[-1] + f)
         for a in range(3):
-            assert abs(Fraction(int(com[i, a])) - ex[a]) <= Fraction(1, 1) / 2 + Fraction(1, 1 << 20)
-            # the centre of mass lies in the node's cell
-            lev = int(t.get(oracle.F_LEVEL)[i])
-            if lev > 0:
-                sh = 32 - lev
-                assert (int(com[i, a]) >> sh) == (int(xs[a][b]) >> sh)
+            ps[a].append(ps[a][-1] + f * int(xs[a][q]))
+    massless = 0
+    for i in range(t.nnodes):
+        b, e = int(beg[i]), int(end[i])
+        em = pm[e] - pm[b]
+        assert M[i] == _rn(em) and not np.signbit(M[i]), i
+        for a in range(3):
+            es = ps[a][e] - ps[a][b]
+            assert S[i, a] == _rn(es) and not np.signbit(S[i, a]), (i, a)
+            if em > 0:
+                assert int(com[i, a]) == round(es / em), (i, a)
+            else:
+                sh = 32 - int(lev[i])
+                cell = 0 if lev[i] == 0 else (int(xs[a][b]) >> sh) << sh
+                assert int(com[i, a]) == cell + (1 << (sh - 1))
+        massless += em == 0
+    return t, massless
+
+
+def test_moments_exact_equal_and_unequal_masses():
+    pos, mass = gi.halo_mix(1500, 10, n_halo=4)
+    _check_exact_moments(pos, mass, gi.default_params())
+    mass = mass * (1.0 + 0.5 * np.random.default_rng(0).random(mass.shape))
+    _check_exact_moments(pos, mass, gi.default_params())
+
+
+def test_moments_exact_wide_mass_range_and_massless_nodes():
+    r = np.random.default_rng(1)
+    pos, mass = gi.halo_mix(1200, 11, n_halo=3)
+    mass = np.ldexp(1.0 + r.random(len(mass)), r.integers(-90, 90, len(mass)))
+    mass[r.random(len(mass)) < 0.3] = 0.0                   # scattered massless particles
+    mass[np.argsort(pos[:, 0])[:200]] = 0.0                  # a massless slab: whole massless nodes
+    _, massless = _check_exact_moments(pos, mass, gi.default_params())
+    assert massless > 0
+
+
+def test_moments_exact_subnormal_and_overflowing_sums():
+    r = np.random.default_rng(2)
+    pos, _ = gi.halo_mix(600, 12, n_halo=2)
+    tiny = 5e-324 * r.integers(1, 1 << 20, len(pos)).astype(np.float64)   # subnormal masses
+    tiny[::7] = 2.0 ** -1022 * (1.0 + r.random(len(tiny[::7])))           # and the smallest normals
+    _check_exact_moments(pos, tiny, gi.default_params())
+    huge = 1e300 * (1.0 + r.random(len(pos)))               # m x overflows, M does not
+    t, _ = _check_exact_moments(pos, huge, gi.default_params())
+    assert np.isinf(t.get(oracle.F_MSUM)).any() and np.isfinite(t.get(oracle.F_MASS)).all()
+
+
+def test_moments_exact_coincident_keys():
+    r = np.random.default_rng(3)
+    pos, mass = gi.halo_mix(400, 13, n_halo=2)
+    pos = np.concatenate([pos, np.repeat(pos[:20], 5, axis=0)])           # buckets of equal keys
+    mass = np.concatenate([mass, r.random(100) * mass[0]])
+    t, _ = _check_exact_moments(pos, mass, gi.default_params())
+    assert (t.get(oracle.F_LEVEL) == 21).any()
+
+
+def test_centre_of_mass_ties_round_to_even():
+    # two equal masses one grid unit apart: the exact centre is a half-integer
+    g = 2.0 ** -32
+    for x0 in (1000, 1001):
+        pos = np.array([[x0 * g, 0.25, 0.25], [(x0 + 1) * g, 0.25, 0.25]])
+        t = oracle.Tree(pos, np.array([0.5, 0.5]), gi.default_params())
+        com = t.get(oracle.F_COM)[0]
+        assert int(com[0]) == (x0 if x0 % 2 == 0 else x0 + 1)
+        assert int(com[1]) == 1 << 30
+    # unequal masses: the nearest grid point, not the truncation
+    pos = np.array([[0.0, 0.0, 0.0], [3 * g, 0.0, 0.0]])
+    t = oracle.Tree(pos, np.array([2.0, 1.0]), gi.default_params())
+    assert int(t.get(oracle.F_COM)[0][0]) == 1                     # exact centre 1
+    t = oracle.Tree(pos, np.array([1.0, 2.0]), gi.default_params())
+    assert int(t.get(oracle.F_COM)[0][0]) == 2                     # exact centre 2
 
 
 @pytest.mark.parametrize("G", [1, 8, 32])
