@@ -132,13 +132,20 @@ og_status og_params_default(og_params *p);
 /* Build the tree of N particles (Sect. 4.1.1): fixed point, Morton keys,
  * radix sort, octree topology and threading, moments, groups.
  * pos: double[N][3], mass: double[N] (finite, >= 0).  1 <= N < 2^26.
- * Returns OG_ERR_ARG for NaN/inf inputs, bad parameters or r_cut >= L/2. */
+ * A node's mass and sums of m x are the exact sums over its particles, each
+ * rounded once to double; its centre of mass is the grid point nearest to the
+ * exact ratio (ties to even).  They are carried exactly in 192-bit integers,
+ * so the nonzero masses may span at most 128 binary orders, from the lowest
+ * set bit of the smallest to the top of the largest (equal masses, or masses
+ * within a factor 2^75 of each other, always do).
+ * Returns OG_ERR_ARG for NaN/inf inputs, negative masses, masses spanning
+ * more than 128 binary orders, bad parameters or r_cut >= L/2. */
 og_status og_tree_build(og_ctx *ctx, const double *pos, const double *mass, int64_t n,
                         const og_params *p, og_tree **out);
 
 /* Refit for drifted positions of the same N particles (caller order, same
  * pointer convention as the build): the topology, groups and octant slots
- * of the build are kept; masses, centres of mass, group boxes and node
+ * of the build are kept; node sums, centres of mass, group boxes and node
  * extents are recomputed.  A node's extent is its cell joined with its
  * drifted members (per axis an interval on the periodic circle); the walk's
  * prune, boundary and opening tests then use the extent and its largest
@@ -275,11 +282,12 @@ og_status og_batch_force(og_ctx *ctx, int64_t nbox, const og_box *boxes, og_batc
  *   OG_F_LISTS    uint32[list_entries][2] (group, unified ref) pairs of the
  *                 last OG_DEBUG_DUMP_LISTS force call, in no particular order
  *   OG_F_EXTENT   uint32[2][nodes][3] after a refit: extent start per axis, then
- *                 extent length per axis (intervals on the circle of 2^32 units) */
+ *                 extent length per axis (intervals on the circle of 2^32 units)
+ *   OG_F_MSUM     double[nodes][3] sum of m x per axis, x in grid units */
 enum {
     OG_F_SKEY = 0, OG_F_PERM, OG_F_SPOS, OG_F_LEVEL, OG_F_NBEG, OG_F_NEND, OG_F_PARENT,
     OG_F_CBEG, OG_F_CCNT, OG_F_CHILD, OG_F_MASS, OG_F_COM, OG_F_NEXTNODE, OG_F_SIBLING,
-    OG_F_PNEXT, OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS, OG_F_EXTENT
+    OG_F_PNEXT, OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS, OG_F_EXTENT, OG_F_MSUM
 };
 og_status og_tree_export(const og_tree *t, int field, void *host_dst, size_t bytes);
 

@@ -19,17 +19,17 @@
 //                           octant-occupancy bits of every node
 //          k_place          child array in key order, grouped by parent
 //          k_threading      nextnode / sibling threading (unified index space)
-//   a5     k_level_hist .. k_level_scatter   node ids bucketed by tree level
-//          k_moments_level  bottom-up FP64 mass and sum m x, one thread per node and
-//                           one launch per large level, deepest first; the 8 octant
-//                           slots combine in the fixed order ((0+1)+(2+3))+((4+5)+(6+7))
-//          k_moments_run    a run of small levels in one block (a barrier per level)
-//          k_com            centre of mass of every node, round-half-even(S / M)
+//   a5     exact node moments and centres of mass (og_moments.cu): prefix
+//                           sums over the sorted particles, one pass over the nodes
+//          k_level_hist .. k_level_scatter   node ids bucketed by tree level (a
+//                           refit's extents only, made on the first refit)
+//          k_extents_level  a refit's node extents, one launch per large level
+//          k_extents_run    a run of small levels in one block (a barrier per level)
 //   a6     k_frontier .. k_group_fin   walk groups and their integer boxes
 //          k_records        32-byte child records read by the walk
 //
-// Every decision is integer or IEEE FP64 with a fixed operation order, so the
-// result is identical to the oracle's recursive construction.
+// Every decision is integer or exact, so the result is identical to the
+// oracle's recursive construction.
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -406,10 +406,8 @@ __global__ void k_threading(int64_t n, const uint32_t *__restrict__ nsplit, int6
     else nsib[item - n] = after;
 }
 
-// a5: moments, level by level from the deepest level up, one thread per node:
-// every FP64 instruction then serves 32 nodes (the FP64 rate of the chip is
-// 1/64 of its FP32 rate).  Slot s holds the child in octant s (a particle or
-// a node) or +0.0; the slots combine as ((0+1)+(2+3))+((4+5)+(6+7)).
+// Node ids bucketed by tree level, for the bottom-up pass of a refit's
+// extents (a node's extent joins its children's).
 constexpr int kLvItems = 16;  // nodes per thread in the level bucketing
 
 // per-block shared-memory histograms, one global atomic per level and block
@@ -467,145 +465,69 @@ __global__ void __launch_bounds__(kT) k_level_scatter(const uint32_t *__restrict
     }
 }
 
-struct Slot {
-    double M, x, y, z;
-};
-
-__device__ __forceinline__ Slot slot_add(const Slot &a, const Slot &b) {
-    return {__dadd_rn(a.M, b.M), __dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y), __dadd_rn(a.z, b.z)};
-}
-
-// moments (and, for a refit, the extent) of one node of this level; the
-// nodes of deeper levels are done
-__device__ __forceinline__ void moments_node(
-    int64_t n, int64_t m, const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
+// extent of one node of this level after a refit: its cell joined with its
+// members' positions, as 32-bit offsets from the cell origin (drift stays
+// local across the periodic boundary); the nodes of deeper levels are done
+__device__ __forceinline__ void extent_node(
+    int64_t n, const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
     const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
     const uint32_t *__restrict__ child, const uint32_t *__restrict__ px,
-    const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
-    const double *__restrict__ pm64, NodeMom *nmom, uint32_t *ncom, int64_t nchild,
-    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l, uint32_t node, int level) {
-    if (ext_s) {
-        // refit: the extent is the cell joined with the members' positions,
-        // as 32-bit offsets from the cell origin (drift stays local across
-        // the periodic boundary)
-        const uint32_t o[3] = {norg[3 * node + 0], norg[3 * node + 1], norg[3 * node + 2]};
-        const int64_t side = (int64_t)1 << (32 - level);
-        int64_t lo[3] = {0, 0, 0}, hi[3] = {side - 1, side - 1, side - 1};
-        auto add_point = [&](uint32_t x, uint32_t y, uint32_t z) {
-            const int64_t d[3] = {(int64_t)(int32_t)(x - o[0]), (int64_t)(int32_t)(y - o[1]),
-                                  (int64_t)(int32_t)(z - o[2])};
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = d[a] < lo[a] ? d[a] : lo[a];
-                hi[a] = d[a] > hi[a] ? d[a] : hi[a];
-            }
-        };
-        if (level == kLevels) {
-            for (uint32_t q = nbeg[node]; q < nend[node]; ++q) add_point(px[q], py[q], pz[q]);
-        } else {
-            const uint32_t oc = occ[node];
-            const uint32_t cb = ncbeg[node];
-            for (int sidx = 0; sidx < 8; ++sidx) {
-                const uint32_t slot = cb + __popc(oc & ((1u << sidx) - 1u));
-                if (!((oc >> sidx) & 1u) || slot >= (uint64_t)nchild) continue;
-                const uint32_t item = child[slot];
-                if (item < n) {
-                    add_point(px[item], py[item], pz[item]);
-                } else {
-                    const int64_t j = item - n;
-                    for (int a = 0; a < 3; ++a) {
-                        const int64_t clo = (int64_t)(int32_t)(ext_s[3 * j + a] - o[a]);
-                        const int64_t chi = clo + (int64_t)ext_l[3 * j + a];
-                        lo[a] = clo < lo[a] ? clo : lo[a];
-                        hi[a] = chi > hi[a] ? chi : hi[a];
-                    }
-                }
-            }
-        }
+    const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz, int64_t nchild,
+    const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l, uint32_t node, int level) {
+    const uint32_t o[3] = {norg[3 * node + 0], norg[3 * node + 1], norg[3 * node + 2]};
+    const int64_t side = (int64_t)1 << (32 - level);
+    int64_t lo[3] = {0, 0, 0}, hi[3] = {side - 1, side - 1, side - 1};
+    auto add_point = [&](uint32_t x, uint32_t y, uint32_t z) {
+        const int64_t d[3] = {(int64_t)(int32_t)(x - o[0]), (int64_t)(int32_t)(y - o[1]),
+                              (int64_t)(int32_t)(z - o[2])};
         for (int a = 0; a < 3; ++a) {
-            if (hi[a] - lo[a] >= (int64_t)0xffffffffll) {
-                ext_s[3 * node + a] = 0u;  // the whole circle
-                ext_l[3 * node + a] = 0xffffffffu;
-            } else {
-                ext_s[3 * node + a] = o[a] + (uint32_t)lo[a];
-                ext_l[3 * node + a] = (uint32_t)(hi[a] - lo[a]);
-            }
+            lo[a] = d[a] < lo[a] ? d[a] : lo[a];
+            hi[a] = d[a] > hi[a] ? d[a] : hi[a];
         }
-    }
-    Slot tot = {0.0, 0.0, 0.0, 0.0};
+    };
     if (level == kLevels) {
-        // bucket of coincident keys: sequential in key order
-        for (uint32_t q = nbeg[node]; q < nend[node]; ++q) {
-            const double mq = pm64[q];
-            tot.M = __dadd_rn(tot.M, mq);
-            tot.x = __dadd_rn(tot.x, __dmul_rn(mq, (double)px[q]));
-            tot.y = __dadd_rn(tot.y, __dmul_rn(mq, (double)py[q]));
-            tot.z = __dadd_rn(tot.z, __dmul_rn(mq, (double)pz[q]));
-        }
+        for (uint32_t q = nbeg[node]; q < nend[node]; ++q) add_point(px[q], py[q], pz[q]);
     } else {
-        const uint32_t o = occ[node];
+        const uint32_t oc = occ[node];
         const uint32_t cb = ncbeg[node];
-        Slot sl[8];
-#pragma unroll
         for (int sidx = 0; sidx < 8; ++sidx) {
-            sl[sidx] = {0.0, 0.0, 0.0, 0.0};
-            const uint32_t slot = cb + __popc(o & ((1u << sidx) - 1u));
-            if (((o >> sidx) & 1u) && slot < (uint64_t)nchild) {
-                const uint32_t item = child[slot];
-                if (item < n) {
-                    const double mq = pm64[item];
-                    sl[sidx] = {mq, __dmul_rn(mq, (double)px[item]), __dmul_rn(mq, (double)py[item]),
-                                __dmul_rn(mq, (double)pz[item])};
-                } else {
-                    const int64_t j = item - n;
-                    const NodeMom q = nmom[j];
-                    sl[sidx] = {q.M, q.Sx, q.Sy, q.Sz};
+            const uint32_t slot = cb + __popc(oc & ((1u << sidx) - 1u));
+            if (!((oc >> sidx) & 1u) || slot >= (uint64_t)nchild) continue;
+            const uint32_t item = child[slot];
+            if (item < n) {
+                add_point(px[item], py[item], pz[item]);
+            } else {
+                const int64_t j = item - n;
+                for (int a = 0; a < 3; ++a) {
+                    const int64_t clo = (int64_t)(int32_t)(ext_s[3 * j + a] - o[a]);
+                    const int64_t chi = clo + (int64_t)ext_l[3 * j + a];
+                    lo[a] = clo < lo[a] ? clo : lo[a];
+                    hi[a] = chi > hi[a] ? chi : hi[a];
                 }
             }
         }
-        tot = slot_add(slot_add(slot_add(sl[0], sl[1]), slot_add(sl[2], sl[3])),
-                       slot_add(slot_add(sl[4], sl[5]), slot_add(sl[6], sl[7])));
     }
-    nmom[node] = NodeMom{tot.M, tot.x, tot.y, tot.z};
+    for (int a = 0; a < 3; ++a) {
+        if (hi[a] - lo[a] >= (int64_t)0xffffffffll) {
+            ext_s[3 * node + a] = 0u;  // the whole circle
+            ext_l[3 * node + a] = 0xffffffffu;
+        } else {
+            ext_s[3 * node + a] = o[a] + (uint32_t)lo[a];
+            ext_l[3 * node + a] = (uint32_t)(hi[a] - lo[a]);
+        }
+    }
 }
 
-// centre of mass of every node on the grid, COM = round-half-even(S / M), once
-// all moments are done: the divisions stay off the level-by-level chain
-__global__ void k_com(int64_t m, const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ nbeg,
-                      const uint32_t *__restrict__ px, const uint32_t *__restrict__ py,
-                      const uint32_t *__restrict__ pz, const NodeMom *__restrict__ nmom,
-                      uint32_t *ncom) {
-    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= m) return;
-    const NodeMom q = nmom[node];
-    uint32_t c[3];
-    if (q.M > 0.0) {
-        c[0] = (uint32_t)rint(__ddiv_rn(q.Sx, q.M));
-        c[1] = (uint32_t)rint(__ddiv_rn(q.Sy, q.M));
-        c[2] = (uint32_t)rint(__ddiv_rn(q.Sz, q.M));
-    } else {
-        // massless node: the cell centre
-        const int level = nlev[node];
-        const uint32_t b = nbeg[node];
-        const uint32_t pc[3] = {px[b], py[b], pz[b]};
-        const uint64_t mask = level == 0 ? 0ull : ~((1ull << (32 - level)) - 1ull);
-        for (int a = 0; a < 3; ++a) c[a] = (uint32_t)(((uint64_t)pc[a] & mask) + (1ull << (31 - level)));
-    }
-    ncom[3 * node + 0] = c[0];
-    ncom[3 * node + 1] = c[1];
-    ncom[3 * node + 2] = c[2];
-}
-
-#define OG_MOMENT_ARGS n, m, nbeg, nend, ncbeg, occ, child, px, py, pz, pm64, nmom, ncom, nchild, \
-                       status, norg, ext_s, ext_l
+#define OG_EXTENT_ARGS n, nbeg, nend, ncbeg, occ, child, px, py, pz, nchild, norg, ext_s, ext_l
 
 // one level with many nodes: a thread per node
-__global__ void __launch_bounds__(kT) k_moments_level(
+__global__ void __launch_bounds__(kT) k_extents_level(
     int64_t n, int64_t m, const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
     const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
     const uint32_t *__restrict__ child, const uint32_t *__restrict__ px,
-    const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
-    const double *__restrict__ pm64, NodeMom *nmom, uint32_t *ncom, int64_t nchild,
-    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l, int level, const uint32_t *__restrict__ lnodes, uint32_t cnt) {
+    const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz, int64_t nchild,
+    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l, int level,
+    const uint32_t *__restrict__ lnodes, uint32_t cnt) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cnt) return;
     const uint32_t node = lnodes[k];
@@ -613,7 +535,7 @@ __global__ void __launch_bounds__(kT) k_moments_level(
         atomicOr(status, ST_INTERNAL);
         return;
     }
-    moments_node(OG_MOMENT_ARGS, node, level);
+    extent_node(OG_EXTENT_ARGS, node, level);
 }
 
 // consecutive levels with few nodes each, deepest first, in one block: a level
@@ -627,13 +549,13 @@ struct LevelRun {
 constexpr int kRunThreads = 512;
 constexpr uint32_t kRunMaxNodes = 256;         // larger levels get a grid of their own
 
-__global__ void __launch_bounds__(kRunThreads) k_moments_run(
+__global__ void __launch_bounds__(kRunThreads) k_extents_run(
     int64_t n, int64_t m, const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
     const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
     const uint32_t *__restrict__ child, const uint32_t *__restrict__ px,
-    const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
-    const double *__restrict__ pm64, NodeMom *nmom, uint32_t *ncom, int64_t nchild,
-    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l, const uint32_t *__restrict__ lnodes, LevelRun run) {
+    const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz, int64_t nchild,
+    uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l,
+    const uint32_t *__restrict__ lnodes, LevelRun run) {
     for (int l = run.hi; l >= run.lo; --l) {
         for (uint32_t k = threadIdx.x; k < run.cnt[l]; k += blockDim.x) {
             const uint32_t node = lnodes[run.off[l] + k];
@@ -641,7 +563,7 @@ __global__ void __launch_bounds__(kRunThreads) k_moments_run(
                 atomicOr(status, ST_INTERNAL);
                 continue;
             }
-            moments_node(OG_MOMENT_ARGS, node, l);
+            extent_node(OG_EXTENT_ARGS, node, l);
         }
         __syncthreads();
     }
@@ -695,12 +617,13 @@ __global__ void k_group_init(int64_t n, const uint32_t *__restrict__ gs,
     gbeg[gid[p]] = (uint32_t)p;
 }
 
-__global__ void k_group_fin(int64_t n, int64_t ng, const uint32_t *__restrict__ gbeg,
-                            uint32_t *gend, const uint32_t *__restrict__ px,
-                            const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
-                            const uint32_t *__restrict__ sseg, uint32_t *gbox, uint32_t *gseg) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
+__device__ __forceinline__ void group_box(int64_t n, int64_t ng, int64_t g,
+                                          const uint32_t *__restrict__ gbeg, uint32_t *gend,
+                                          const uint32_t *__restrict__ px,
+                                          const uint32_t *__restrict__ py,
+                                          const uint32_t *__restrict__ pz,
+                                          const uint32_t *__restrict__ sseg, uint32_t *gbox,
+                                          uint32_t *gseg) {
     uint32_t b = gbeg[g];
     gseg[g] = sseg[b];
     uint32_t e = (g + 1 < ng) ? gbeg[g + 1] : (uint32_t)n;
@@ -721,6 +644,21 @@ __global__ void k_group_fin(int64_t n, int64_t ng, const uint32_t *__restrict__ 
         gbox[6 * g + a] = ref[a] + (uint32_t)lo[a];
         gbox[6 * g + 3 + a] = ref[a] + (uint32_t)hi[a];
     }
+}
+
+
+// group ends and boxes; the group count is *d_ng (the build, before the host
+// knows it) or ng (a refit)
+__global__ void k_group_fin(int64_t n, const uint32_t *__restrict__ d_ng, int64_t ng_host,
+                            const uint32_t *__restrict__ gbeg, uint32_t *gend,
+                            const uint32_t *__restrict__ px, const uint32_t *__restrict__ py,
+                            const uint32_t *__restrict__ pz, const uint32_t *__restrict__ sseg,
+                            uint32_t *gbox, uint32_t *gseg) {
+    int64_t ng = d_ng ? (int64_t)*d_ng : ng_host;
+    if (ng > n) ng = n;                        // the host reports a bad count
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng;
+         g += (int64_t)gridDim.x * blockDim.x)
+        group_box(n, ng, g, gbeg, gend, px, py, pz, sseg, gbox, gseg);
 }
 
 __global__ void k_ext_records(int64_t n, int64_t nchild, const uint32_t *__restrict__ child,
@@ -762,41 +700,47 @@ __global__ void k_repos(int64_t n, const uint32_t *__restrict__ perm, const uint
     pz[i] = qz[j];
 }
 
-__global__ void k_records(int64_t n, int64_t nchild, const uint32_t *__restrict__ child,
+// the walk's child records; the child count is *d_nchild (the build) or
+// nchild_host (a refit), at most ccap
+__global__ void k_records(int64_t n, const uint32_t *__restrict__ d_nchild, int64_t nchild_host,
+                          int64_t ccap, const uint32_t *__restrict__ child,
                           const uint32_t *__restrict__ px, const uint32_t *__restrict__ py,
                           const uint32_t *__restrict__ pz, const float *__restrict__ pm32,
                           const double *__restrict__ pm64, const uint8_t *__restrict__ nlev,
                           const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ nccnt,
                           const NodeMom *__restrict__ nmom, const uint32_t *__restrict__ ncom,
                           CRec *crec, uint32_t *status) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nchild) return;
-    uint32_t item = child[c];
-    CRec r;
-    if (item < n) {
-        r.x = px[item];
-        r.y = py[item];
-        r.z = pz[item];
-        r.m = pm32[item];
-        r.M = pm64[item];
-        r.info = 0;
-        r.ref = item;
-    } else {
-        int64_t j = item - n;
-        r.x = ncom[3 * j + 0];
-        r.y = ncom[3 * j + 1];
-        r.z = ncom[3 * j + 2];
-        r.M = nmom[j].M;
-        r.m = __double2float_rn(r.M);
-        r.info = (1u << 31) | ((uint32_t)nlev[j] << 26) | (nccnt[j] & 0x3ffffffu);
-        r.ref = ncbeg[j];
-        // the walk pushes (ref, count) unchecked: a node has children, inside
-        // the child array, and is never a root
-        if (nccnt[j] == 0u || nccnt[j] > 0x3ffffffu || nlev[j] == 0u || nlev[j] > kLevels ||
-            (uint64_t)ncbeg[j] + nccnt[j] > (uint64_t)nchild)
-            atomicOr(status, ST_INTERNAL);
+    int64_t nchild = d_nchild ? (int64_t)*d_nchild : nchild_host;
+    if (nchild > ccap) nchild = ccap;          // the host reports a bad count
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchild;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t item = child[c];
+        CRec r;
+        if (item < n) {
+            r.x = px[item];
+            r.y = py[item];
+            r.z = pz[item];
+            r.m = pm32[item];
+            r.M = pm64[item];
+            r.info = 0;
+            r.ref = item;
+        } else {
+            int64_t j = item - n;
+            r.x = ncom[3 * j + 0];
+            r.y = ncom[3 * j + 1];
+            r.z = ncom[3 * j + 2];
+            r.M = nmom[j].M;
+            r.m = __double2float_rn(r.M);
+            r.info = (1u << 31) | ((uint32_t)nlev[j] << 26) | (nccnt[j] & 0x3ffffffu);
+            r.ref = ncbeg[j];
+            // the walk pushes (ref, count) unchecked: a node has children, inside
+            // the child array, and is never a root
+            if (nccnt[j] == 0u || nccnt[j] > 0x3ffffffu || nlev[j] == 0u || nlev[j] > kLevels ||
+                (uint64_t)ncbeg[j] + nccnt[j] > (uint64_t)nchild)
+                atomicOr(status, ST_INTERNAL);
+        }
+        crec[c] = r;
     }
-    crec[c] = r;
 }
 
 inline unsigned nblk(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
@@ -831,15 +775,38 @@ static size_t tree_bytes(int64_t n, int64_t B) {
     add(4, n); add(4, n); add(4, 6 * n); add(4, n); add(4, n); add(4, n);           // groups
     add(4, 3 * n); add(4, 3 * n); add(4, n); add(4, n);                             // force arrays
     add(4, B + 1); add(sizeof(SegGeom), B); add(sizeof(WalkParams), 2 * B);         // boxes
-    add(4, 3 * m); add(4, m); add(4, m);                                            // norg nocc lnodes
+    add(4, 3 * m); add(4, m); add(4, m); add(4, 2);                                 // norg nocc lnodes mbits
     return b + 4096;
 }
 
-// Moments (and, for a refit, extents) level by level from the deepest level
-// up; each level reads only nodes of deeper levels, finished by the previous
-// launches (or, inside a run of small levels, before the block barrier); then
-// the centres of mass of all nodes.
-static void moments_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
+// Node ids by level (t->lnodes) and the count of each level (t->h_lcount),
+// for the bottom-up pass over a refit's extents; once per tree.  lcount holds
+// 3 (kLevels + 2) words of device scratch.
+static og_status level_lists(og_tree *t, uint32_t *lcount) {
+    if (!t->h_lcount.empty()) return OG_OK;
+    cudaStream_t s = t->ctx->stream;
+    const int64_t B = t->nseg, m = t->nnodes;
+    uint32_t *loff = lcount + (kLevels + 2), *lcursor = lcount + 2 * (kLevels + 2);
+    uint32_t *d_nsplit = lcount + 3 * (kLevels + 2);
+    const uint32_t nsplit = (uint32_t)(m - B);
+    cudaMemsetAsync(lcount, 0, (kLevels + 2) * sizeof(uint32_t), s);
+    cudaMemcpyAsync(d_nsplit, &nsplit, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    const unsigned lv_blocks = (unsigned)((m + (int64_t)kT * kLvItems - 1) / ((int64_t)kT * kLvItems));
+    k_level_hist<<<lv_blocks, kT, 0, s>>>(d_nsplit, B, t->nlev, lcount); note_launch();
+    k_level_offsets<<<1, 32, 0, s>>>(lcount, loff, lcursor); note_launch();
+    k_level_scatter<<<lv_blocks, kT, 0, s>>>(d_nsplit, B, t->nlev, loff, lcursor, t->lnodes); note_launch();
+    uint32_t h[kLevels + 2];
+    cudaMemcpyAsync(h, lcount, (kLevels + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "level lists");
+    t->h_lcount.assign(h, h + kLevels + 1);
+    return OG_OK;
+}
+
+// A refit's node extents, level by level from the deepest level up; each level
+// reads only nodes of deeper levels, finished by the previous launches (or,
+// inside a run of small levels, before the block barrier).
+static void extents_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
     cudaStream_t s = t->ctx->stream;
     const int64_t n = t->n, m = t->nnodes;
     uint32_t off = 0;
@@ -853,9 +820,9 @@ static void moments_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
     run.hi = -1;
     auto flush = [&]() {
         if (run.hi < 0) return;
-        k_moments_run<<<1, kRunThreads, 0, s>>>(
-            n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child, t->px, t->py, t->pz, t->pm64,
-            t->nmom, t->ncom, t->nchild, t->ctx->d_status, t->norg, ext_s, ext_l, t->lnodes, run); note_launch();
+        k_extents_run<<<1, kRunThreads, 0, s>>>(n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child,
+                                                t->px, t->py, t->pz, t->nchild, t->ctx->d_status,
+                                                t->norg, ext_s, ext_l, t->lnodes, run); note_launch();
         run.hi = -1;
     };
     for (int l = kLevels; l >= 0; --l) {
@@ -869,13 +836,11 @@ static void moments_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
             continue;
         }
         flush();
-        k_moments_level<<<nblk(cnt), kT, 0, s>>>(
-            n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child, t->px, t->py, t->pz, t->pm64,
-            t->nmom, t->ncom, t->nchild, t->ctx->d_status, t->norg, ext_s, ext_l, l,
-            t->lnodes + offs[l], cnt); note_launch();
+        k_extents_level<<<nblk(cnt), kT, 0, s>>>(n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child,
+                                                 t->px, t->py, t->pz, t->nchild, t->ctx->d_status,
+                                                 t->norg, ext_s, ext_l, l, t->lnodes + offs[l], cnt); note_launch();
     }
     flush();
-    k_com<<<nblk(m), kT, 0, s>>>(m, t->nlev, t->nbeg, t->px, t->py, t->pz, t->nmom, t->ncom); note_launch();
 }
 
 static og_status alloc_extents(og_tree *t) {
@@ -904,16 +869,23 @@ og_status cell_extents(og_tree *t) {
     return OG_OK;
 }
 
+// grid of a grid-stride kernel over at most `bound` items
+static unsigned stride_grid(int64_t bound) {
+    const int64_t b = (bound + kT - 1) / kT;
+    return (unsigned)(b < 1 ? 1 : b > 4096 ? 4096 : b);
+}
+
 og_status refit_tree(og_tree *t, const double *d_pos) {
     cudaStream_t s = t->ctx->stream;
-    const int64_t n = t->n, B = t->nseg, m = t->nnodes;
+    const int64_t n = t->n, B = t->nseg;
     cudaError_t err;
     if (!t->cext) {
         // extents live in their own allocation, made on the first refit
         og_status st = alloc_extents(t);
         if (st) return st;
     }
-    size_t sb = (size_t)n * (3 * 4 + 8 + 4 + 4) + 4096;
+    const size_t mom_bytes = moments_scratch_bytes(n);
+    size_t sb = (size_t)n * (3 * 4 + 8 + 4 + 4) + 4096 + mom_bytes + 4 * (kLevels + 3) * sizeof(uint32_t) + 256;
     void *scratch = nullptr;
     if ((err = dev_malloc_async(&scratch, sb, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (refit)");
     Bump W(scratch, sb);
@@ -921,6 +893,13 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
     uint64_t *keys = W.take<uint64_t>(n);
     uint32_t *idx = W.take<uint32_t>(n);
     uint32_t *pseg = W.take<uint32_t>(n);
+    uint32_t *lcount = W.take<uint32_t>(4 * (kLevels + 3));
+    void *mom_scratch = W.take<char>((int64_t)mom_bytes);
+    og_status st = level_lists(t, lcount);
+    if (st) {
+        cudaFreeAsync(scratch, s);
+        return st;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -931,12 +910,13 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
     k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, nullptr, n, B > 1 ? pseg : nullptr, t->geom, qx,
                                            qy, qz, keys, nullptr, idx, t->ctx->d_status); note_launch();
     k_repos<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, t->px, t->py, t->pz); note_launch();
-    moments_bottom_up(t, t->next_s, t->next_l);
-    k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
-                                                t->pz, t->sseg, t->gbox, t->gseg); note_launch();
-    k_records<<<nblk(t->nchild), kT, 0, s>>>(n, t->nchild, t->child, t->px, t->py, t->pz, t->pm32,
-                                             t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nmom, t->ncom,
-                                             t->crec, t->ctx->d_status); note_launch();
+    node_moments(t, nullptr, t->nnodes, mom_scratch, s);
+    extents_bottom_up(t, t->next_s, t->next_l);
+    k_group_fin<<<stride_grid(t->ngroups), kT, 0, s>>>(n, nullptr, t->ngroups, t->gbeg, t->gend, t->px,
+                                                       t->py, t->pz, t->sseg, t->gbox, t->gseg); note_launch();
+    k_records<<<stride_grid(t->nchild), kT, 0, s>>>(n, nullptr, t->nchild, t->nchild, t->child, t->px,
+                                                    t->py, t->pz, t->pm32, t->pm64, t->nlev, t->ncbeg,
+                                                    t->nccnt, t->nmom, t->ncom, t->crec, t->ctx->d_status); note_launch();
     k_ext_records<<<nblk(t->nchild), kT, 0, s>>>(n, t->nchild, t->child, t->next_s, t->next_l,
                                                  t->cext); note_launch();
     cudaEventRecord(e1, s);
@@ -948,7 +928,6 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     t->refit = true;
-    (void)m;
     return OG_OK;
 }
 
@@ -1007,6 +986,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     t->norg = A.take<uint32_t>(3 * mcap);
     t->nocc = A.take<uint32_t>(mcap);
     t->lnodes = A.take<uint32_t>(mcap);
+    t->mbits = A.take<int>(2);
     if (A.off > tb) { set_error("internal: arena overflow"); return OG_ERR_STATE; }
 
     // ---- box table
@@ -1033,9 +1013,10 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         add(4, n); add(4, n); add(4, n);                        // qx qy qz
         add(8, n); add(4, n); add(8, n); add(4, n); add(8, n); add(4, n);  // keys, idx, alt, key copy, pseg
         add(1, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // lv sb se first nid sid
-        add(4, n + B); add(4, 3 * 24);  // nnc levels
+        add(4, n + B);                  // nnc
         add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs gid unit
-        sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + B + 8) + 4096;
+        sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + B + 8) +
+                    moments_scratch_bytes(n) + 4096;
     }
     void *scratch = nullptr;
     if ((err = dev_malloc_async(&scratch, sb_bytes, s)) != cudaSuccess)
@@ -1053,14 +1034,12 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     uint32_t *sbeg = W.take<uint32_t>(n), *send = W.take<uint32_t>(n);
     uint32_t *first = W.take<uint32_t>(n), *nid = W.take<uint32_t>(n), *sid = W.take<uint32_t>(n);
     uint32_t *occ = t->nocc, *nnc = W.take<uint32_t>(n + B);
-    uint32_t *lnodes = t->lnodes;
-    uint32_t *lcount = W.take<uint32_t>(3 * (kLevels + 2));
-    uint32_t *loff = lcount + (kLevels + 2), *lcursor = lcount + 2 * (kLevels + 2);
     uint32_t *fp = W.take<uint32_t>(n), *rs = W.take<uint32_t>(n), *gs = W.take<uint32_t>(n);
     uint32_t *gid = W.take<uint32_t>(n);
     uint32_t *unit = W.take<uint32_t>(n);
     void *sort_scratch = W.take<char>((int64_t)radix_sort_scratch_bytes(n));
     void *scan_scratch = W.take<char>((int64_t)scan_scratch_bytes(2 * n + B + 8));
+    void *mom_scratch = W.take<char>((int64_t)moments_scratch_bytes(n));
     uint32_t *d_tot = W.take<uint32_t>(4);
     uint32_t *status = t->ctx->d_status;
 
@@ -1133,12 +1112,10 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
                                           t->npar, t->owner, t->child, t->npos, status); note_launch();
     k_threading<<<nblk(ccap), kT, 0, s>>>(n, nsp, B, t->child, t->ncbeg, t->nccnt, t->npar,
                                           t->npos, t->owner, t->nnext, t->nsib, t->pnext, status); note_launch();
-    // a5 (part 1): node ids by level
-    cudaMemsetAsync(lcount, 0, (kLevels + 2) * sizeof(uint32_t), s);
-    const unsigned lv_blocks = (unsigned)((mcap + (int64_t)kT * kLvItems - 1) / ((int64_t)kT * kLvItems));
-    k_level_hist<<<lv_blocks, kT, 0, s>>>(nsp, B, t->nlev, lcount); note_launch();
-    k_level_offsets<<<1, 32, 0, s>>>(lcount, loff, lcursor); note_launch();
-    k_level_scatter<<<lv_blocks, kT, 0, s>>>(nsp, B, t->nlev, loff, lcursor, lnodes); note_launch();
+    // a5: exact moments and centres of mass of every node (the masses' set-bit
+    // span first: it fixes the integer units)
+    mass_span(t, s);
+    node_moments(t, nsp, mcap, mom_scratch, s);
     // a6: groups (one group size for the whole forest)
     const int G = t->prm.group_max;
     k_frontier<<<nblk(n), kT, 0, s>>>(n, B, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit); note_launch();
@@ -1147,45 +1124,41 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     k_groupmark<<<nblk(n), kT, 0, s>>>(n, G, rs, fp, unit, t->nbeg, t->nend, gs); note_launch();
     scan_exclusive_u32(gs, gid, n, d_tot + 2, scan_scratch, s);
     k_group_init<<<nblk(n), kT, 0, s>>>(n, gs, gid, t->gbeg); note_launch();
-    cudaMemcpyAsync(h_tot, d_tot, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-    uint32_t h_lcount[kLevels + 2];
-    cudaMemcpyAsync(h_lcount, lcount, (kLevels + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) {
-        cudaFreeAsync(scratch, s);
-        return cuda_fail(err, "build (topology)");
-    }
-    const int64_t m = B + (int64_t)h_tot[0];
-    t->nnodes = m;
-    const int64_t nchild = n + (m - B);
-    t->nchild = nchild;
-    if (m > mcap) {
-        cudaFreeAsync(scratch, s);
-        set_error("internal: node count %lld above its bound %lld", (long long)m, (long long)mcap);
-        return OG_ERR_STATE;
-    }
-    if ((int64_t)h_tot[1] != nchild) {
-        cudaFreeAsync(scratch, s);
-        set_error("internal: child count %u != %lld", h_tot[1], (long long)nchild);
-        return OG_ERR_STATE;
-    }
-    t->ngroups = h_tot[2];
-    t->h_lcount.assign(h_lcount, h_lcount + kLevels + 1);
-    // a5 (part 2): moments from the deepest level up
-    moments_bottom_up(t, nullptr, nullptr);
-    k_group_fin<<<nblk(t->ngroups), kT, 0, s>>>(n, t->ngroups, t->gbeg, t->gend, t->px, t->py,
-                                                t->pz, t->sseg, t->gbox, t->gseg); note_launch();
-    k_records<<<nblk(nchild), kT, 0, s>>>(n, nchild, t->child, t->px, t->py, t->pz, t->pm32,
-                                          t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nmom, t->ncom,
-                                          t->crec, t->ctx->d_status); note_launch();
+    // group count (d_tot[2]) and child count (d_tot[1]) from the device
+    k_group_fin<<<stride_grid(n), kT, 0, s>>>(n, d_tot + 2, 0, t->gbeg, t->gend, t->px, t->py, t->pz,
+                                              t->sseg, t->gbox, t->gseg); note_launch();
+    k_records<<<stride_grid(ccap), kT, 0, s>>>(n, d_tot + 1, 0, ccap, t->child, t->px, t->py, t->pz,
+                                               t->pm32, t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nmom,
+                                               t->ncom, t->crec, status); note_launch();
     cudaEventRecord(e1, s);
+    // the counts and the status word, read once the build is complete (its
+    // only host synchronisation)
+    uint32_t *hc = pinned_counts(t->ctx), *hs = pinned_status(t->ctx);
+    cudaMemcpyAsync(hc, d_tot, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(hs, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(scratch, s);
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "build");
+    for (int k = 0; k < 3; ++k) h_tot[k] = hc[k];
+    t->build_status = *hs;
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     t->ms_build = ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if ((err = cudaGetLastError()) != cudaSuccess) return cuda_fail(err, "build launch");
+    const int64_t m = B + (int64_t)h_tot[0];
+    if (m > mcap) {
+        set_error("internal: node count %lld above its bound %lld", (long long)m, (long long)mcap);
+        return OG_ERR_STATE;
+    }
+    t->nnodes = m;
+    const int64_t nchild = n + (m - B);
+    t->nchild = nchild;
+    if ((int64_t)h_tot[1] != nchild) {
+        set_error("internal: child count %u != %lld", h_tot[1], (long long)nchild);
+        return OG_ERR_STATE;
+    }
+    t->ngroups = h_tot[2];
     return OG_OK;
 }
 

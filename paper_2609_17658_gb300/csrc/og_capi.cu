@@ -172,15 +172,24 @@ void live_remove(og_tree *t) {
 }
 
 og_status check_status(og_ctx *c) {
-    uint32_t st = 0;
-    cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
+    uint32_t *h = pinned_status(c);
+    cudaError_t e = cudaMemcpyAsync(h, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "status read");
+    return status_from(c, *h);
+}
+
+og_status status_from(og_ctx *c, uint32_t st) {
     if (st == 0) return OG_OK;
     cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream);
     cudaStreamSynchronize(c->stream);
     if (st & ST_BAD_INPUT) {
         set_error("non-finite position, negative/non-finite mass, or a smoothing length out of (0, L/2)");
+        return OG_ERR_ARG;
+    }
+    if (st & ST_MASS_RANGE) {
+        set_error("masses span more than 128 binary orders (from the lowest set bit of the smallest "
+                  "to the top of the largest): the exact node moments hold at most that");
         return OG_ERR_ARG;
     }
     if (st & ST_STACK_OVF) {
@@ -300,6 +309,13 @@ og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
         return cuda_fail(e, "cudaMalloc");
     }
     c->d_counters = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(c->d_status) + 64);
+    if ((e = cudaMallocHost(&c->h_pinned, 256)) != cudaSuccess) {
+        cudaFree(c->d_status);
+        cudaStreamDestroy(c->own_stream);
+        delete c;
+        return cuda_fail(e, "cudaMallocHost");
+    }
+    memset(c->h_pinned, 0, 256);
     cudaMemset(c->d_status, 0, 256);
     cudaDeviceSynchronize();
     *out = c;
@@ -326,6 +342,7 @@ og_status og_destroy(og_ctx *c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     cudaFree(c->d_status);
+    cudaFreeHost(c->h_pinned);
     cudaStreamDestroy(c->own_stream);
     delete c;
     return OG_OK;
@@ -387,7 +404,7 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
     t->seg_prm.assign(1, t->prm);
     st = build_tree(t, d_pos, d_mass);
     if (staging) cudaFreeAsync(staging, s);
-    if (st == OG_OK) st = check_status(c);
+    if (st == OG_OK) st = status_from(c, t->build_status);   // read by the build's synchronisation
     if (st != OG_OK) {
         og_tree_free(t);
         return st;
@@ -405,7 +422,7 @@ namespace og {
 // t->a_sorted, t->npp_sorted, t->npn_sorted).  d_aold: previous accelerations
 // in input order on the device, or null.
 og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out, const uint32_t *subset,
-                       int64_t nsubset, float *pot_sorted) {
+                       int64_t nsubset, float *pot_sorted, bool defer) {
     cudaStream_t s = t->ctx->stream;
     const int64_t n = t->n;
     cudaError_t e;
@@ -428,14 +445,14 @@ og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out, cons
         } else {
             // first pass: Barnes-Hut with theta_first_pass
             og_status st = walk_pass(t, OG_OPEN_BH, true, nullptr, t->a_old_sorted, &ms, false,
-                                     subset, nsubset);
+                                     subset, nsubset, nullptr, defer);
             if (st) return st;
             ms_walk += ms;
         }
         a_old_sorted = t->a_old_sorted;
     }
     og_status st = walk_pass(t, t->prm.opening, false, a_old_sorted, t->a_sorted, &ms, true,
-                             subset, nsubset, pot_sorted);
+                             subset, nsubset, pot_sorted, defer);
     if (st) return st;
     ms_walk += ms;
     if (ms_walk_out) *ms_walk_out = ms_walk;
@@ -455,13 +472,15 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
     const int64_t n = t->n;
     const bool dev = (t->prm.flags & OG_DEVICE_PTRS) != 0;
     cudaError_t e;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
     float ms_walk = 0, ms = 0;
     void *tmp = nullptr;
     const float *d_aold = nullptr;
+    // on an error after passes were enqueued: wait for them, then drop them
+    auto fail = [&](og_status st) {
+        cudaStreamSynchronize(s);
+        finish_deferred(t, nullptr);
+        return st;
+    };
     if (t->prm.opening == OG_OPEN_REL && a_old) {
         d_aold = a_old;
         if (!dev) {
@@ -471,20 +490,30 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
             d_aold = static_cast<const float *>(tmp);
         }
     }
-    og_status st = force_sorted(t, d_aold, &ms_walk, nullptr, 0, t->pot_next);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    // the passes are enqueued without waiting: one host synchronisation for
+    // the whole call, after the results and the status word are copied back
+    og_status st = force_sorted(t, d_aold, &ms_walk, nullptr, 0, t->pot_next, true);
     if (tmp) cudaFreeAsync(tmp, s);
-    if (st) return st;
-    // back to caller order
     float *d_acc = acc;
     uint32_t *d_npp = n_pp, *d_npn = n_pn;
     void *out_tmp = nullptr;
-    if (!dev) {
+    if (st == OG_OK && !dev) {
         size_t bytes = (size_t)n * 3 * sizeof(float) + 2 * (size_t)n * sizeof(uint32_t) + 512;
-        if ((e = dev_malloc_async(&out_tmp, bytes, s)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (out)");
+        if ((e = dev_malloc_async(&out_tmp, bytes, s)) != cudaSuccess) st = cuda_fail(e, "cudaMallocAsync (out)");
         d_acc = static_cast<float *>(out_tmp);
         d_npp = n_pp ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) : nullptr;
         d_npn = n_pn ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) + n : nullptr;
     }
+    if (st != OG_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(st);
+    }
+    // back to caller order
     k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
                                        d_acc, d_npp, d_npn); note_launch();
     if (!dev) {
@@ -494,13 +523,18 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
         cudaFreeAsync(out_tmp, s);
     }
     cudaEventRecord(e1, s);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "force");
+    uint32_t *hst = pinned_status(c);
+    cudaMemcpyAsync(hst, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    st = finish_deferred(t, &ms_walk);
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "force");
+    if (st != OG_OK) return st;
     t->ms_force = ms;
     t->ms_walk = ms_walk;
-    return check_status(c);
+    return status_from(c, *hst);
 }
 
 og_status og_tree_force_f64(og_tree *t, const float *a_old, double *acc, uint32_t *n_pp,
@@ -842,6 +876,7 @@ og_status og_tree_export(const og_tree *t, int field, void *dst, size_t bytes) {
         if (!t->refit) { set_error("no extents before a refit"); return OG_ERR_STATE; }
         need = 6 * m * 4;
         break;
+    case OG_F_MSUM: need = 3 * m * 8; break;
     default: set_error("unknown field %d", field); return OG_ERR_ARG;
     }
     if (bytes != need) { set_error("field %d needs %zu bytes, got %zu", field, need, bytes); return OG_ERR_ARG; }
@@ -856,6 +891,10 @@ og_status og_tree_export(const og_tree *t, int field, void *dst, size_t bytes) {
         // the masses out of the nodes' 32-byte moment records
         cudaMemcpy2DAsync(dst, sizeof(double), &t->nmom[0].M, sizeof(NodeMom), sizeof(double), m,
                           cudaMemcpyDeviceToHost, s);
+    } else if (field == OG_F_MSUM) {
+        // the three sums out of the nodes' 32-byte moment records
+        cudaMemcpy2DAsync(dst, 3 * sizeof(double), &t->nmom[0].Sx, sizeof(NodeMom), 3 * sizeof(double),
+                          m, cudaMemcpyDeviceToHost, s);
     } else if (field == OG_F_SPOS) {
         char *d = static_cast<char *>(dst);
         cudaMemcpyAsync(d, t->px, n * 4, cudaMemcpyDeviceToHost, s);

@@ -28,6 +28,7 @@ enum : uint32_t {
     ST_STACK_OVF = 1u << 1,   // walk stack overflow
     ST_LIST_OVF = 1u << 2,    // debug list buffer overflow
     ST_INTERNAL = 1u << 3,    // an internal consistency check failed
+    ST_MASS_RANGE = 1u << 4,  // masses span too many binary orders for exact moments
 };
 
 // 32-byte record of one child slot, read by the walk (particle or node)
@@ -71,6 +72,8 @@ struct og_ctx {
     cudaStream_t stream = nullptr;
     size_t hbm_budget = 0;
     uint32_t *d_status = nullptr;     // device status word
+    void *h_pinned = nullptr;         // page-locked host words read back without a sync of
+                                      // their own: pass counters, status, build counts
     unsigned long long *d_counters = nullptr;  // scratch counters (work queues, totals)
     void *serve = nullptr;            // serving state (og_serve.cu)
     void *tune = nullptr;             // measured group sizes (og_tune.cu)
@@ -105,6 +108,7 @@ struct og_tree {
     uint32_t *npos = nullptr;
     int32_t *npar = nullptr, *nnext = nullptr, *nsib = nullptr;
     og::NodeMom *nmom = nullptr;      // mass and sum of m x per node
+    int *mbits = nullptr;             // lowest and highest set-bit exponent over the masses
     uint32_t *ncom = nullptr;
     int32_t *pnext = nullptr;
     uint32_t *owner = nullptr;        // node a particle hangs from
@@ -124,6 +128,11 @@ struct og_tree {
     uint32_t *gcost = nullptr;        // list length of each group in the last walk pass
     uint32_t *gorder = nullptr;       // groups by decreasing cost
     bool have_cost = false;
+    // walk passes enqueued without a host synchronisation (og_tree_force):
+    // their events and counter slots, read after the call's one synchronisation
+    cudaEvent_t pend_e0[2] = {nullptr, nullptr}, pend_e1[2] = {nullptr, nullptr};
+    int npend = 0;
+    uint32_t build_status = 0;        // status word read at the end of the build
     // force work arrays (sorted order)
     float *a_sorted = nullptr;        // last pass accelerations, [3][n]
     float *a_old_sorted = nullptr;    // previous accelerations, [3][n]
@@ -152,9 +161,26 @@ og_status validate(const og_params *p, int64_t n);
 og_status check_status(og_ctx *c);
 // both force passes on a built tree, results in sorted order (og_capi.cu);
 // subset: only these groups (device array of nsubset group ids)
+// defer: enqueue the passes without waiting for them; the caller synchronises
+// the stream and then calls finish_deferred (ms_walk_out is not set).
 og_status force_sorted(og_tree *t, const float *d_aold, float *ms_walk_out,
                        const uint32_t *subset = nullptr, int64_t nsubset = 0,
-                       float *pot_sorted = nullptr);
+                       float *pot_sorted = nullptr, bool defer = false);
+// after the stream is synchronised: the deferred passes' times (summed into
+// *ms_walk when not null) and interaction counts
+og_status finish_deferred(og_tree *t, float *ms_walk);
+// the error of a status word read back from the device (clears it there)
+og_status status_from(og_ctx *c, uint32_t st);
+// page-locked host words of a context: [0, 6) pass counters, 8 status, 9.. build counts
+inline unsigned long long *pinned_counters(og_ctx *c, int pass) {
+    return static_cast<unsigned long long *>(c->h_pinned) + 3 * pass;
+}
+inline uint32_t *pinned_status(og_ctx *c) {
+    return reinterpret_cast<uint32_t *>(static_cast<unsigned long long *>(c->h_pinned) + 8);
+}
+inline uint32_t *pinned_counts(og_ctx *c) {
+    return reinterpret_cast<uint32_t *>(static_cast<unsigned long long *>(c->h_pinned) + 9);
+}
 // default launch shape of the walk (og_params.walk_warps / walk_chunk = 0)
 constexpr int kDefaultWalkWarps = 4;
 constexpr int kDefaultWalkChunk = 256;
@@ -204,6 +230,14 @@ void radix_sort_pairs_every_pass(uint64_t *keys, uint32_t *vals, uint64_t *keys_
                                  uint32_t *vals_alt, int64_t n, int bits, void *scratch,
                                  cudaStream_t s);
 
+// exact node moments (og_moments.cu): prefix sums over the sorted particles,
+// then every node's mass, sums and centre of mass.  The node count is
+// B + *d_nsplit (device) or, with d_nsplit null, t->nnodes; at most mcap.
+size_t moments_scratch_bytes(int64_t n);
+// t->mbits: the lowest and highest set-bit exponents over the sorted masses
+void mass_span(og_tree *t, cudaStream_t s);
+void node_moments(og_tree *t, const uint32_t *d_nsplit, int64_t mcap, void *scratch, cudaStream_t s);
+
 // build stages (og_build.cu)
 og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass);
 // refit for drifted positions (input order, device): same topology and groups
@@ -236,10 +270,11 @@ struct WalkParams {
 // theta_first_pass).  use_order: take the groups longest list first, by the
 // list lengths of the previous pass on this tree (if any).  subset: walk only
 // these nsubset groups, in this order (device array), instead of all groups.
+// defer: no host synchronisation (see force_sorted); not with list dumps.
 og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
                     float *acc_sorted, float *ms_out, bool use_order,
                     const uint32_t *subset = nullptr, int64_t nsubset = 0,
-                    float *pot_sorted = nullptr);
+                    float *pot_sorted = nullptr, bool defer = false);
 // One walk launch over the groups of several trees (the serving loop), in
 // decreasing order of their previous list lengths.  Every tree's per-box
 // parameters must agree on split on/off.  tree_interactions (or null): the

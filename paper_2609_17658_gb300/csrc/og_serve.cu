@@ -134,8 +134,9 @@ struct Server {
 };
 
 size_t estimate_bytes(int64_t n) {
-    // tree arena and build scratch, plus the system's own state
-    return (size_t)n * (320 + 180 + 8 * 3 * 7 + 12) + ((size_t)1 << 20);
+    // tree arena and build scratch (96 bytes a particle of it for the exact
+    // moments' prefix sums), plus the system's own state
+    return (size_t)n * (320 + 180 + 96 + 8 * 3 * 7 + 12) + ((size_t)1 << 20);
 }
 
 og_status free_system(Server *S, System *sy) {

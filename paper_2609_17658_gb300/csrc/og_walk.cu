@@ -981,9 +981,28 @@ static og_status grow_lists(og_tree *t, int64_t need) {
     return OG_OK;
 }
 
+og_status finish_deferred(og_tree *t, float *ms_walk) {
+    og_status st = OG_OK;
+    for (int k = 0; k < t->npend; ++k) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, t->pend_e0[k], t->pend_e1[k]) == cudaSuccess && ms_walk)
+            *ms_walk += ms;
+        cudaEventDestroy(t->pend_e0[k]);
+        cudaEventDestroy(t->pend_e1[k]);
+        t->pend_e0[k] = t->pend_e1[k] = nullptr;
+        const unsigned long long *h = pinned_counters(t->ctx, k);
+        t->interactions_last = (int64_t)h[1];
+        t->interactions += (int64_t)h[1];
+    }
+    t->npend = 0;
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) st = cuda_fail(err, "walk launch");
+    return st;
+}
+
 og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old_sorted,
                     float *acc_sorted, float *ms_out, bool use_order, const uint32_t *subset,
-                    int64_t nsubset, float *pot_sorted) {
+                    int64_t nsubset, float *pot_sorted, bool defer) {
     cudaStream_t s = t->ctx->stream;
     WalkArgs a{};
     WalkParams wp;
@@ -1015,6 +1034,26 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
         radix_sort_pairs(k0, v0, k1, v1, ng, 8, scr, s, &alt);
         cudaMemcpyAsync(t->gorder, alt ? v1 : v0, ng * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         a.tree0.gorder = t->gorder;
+    }
+    if (defer && !wp.dump && t->npend < 2) {
+        // no host synchronisation: the counters go to a page-locked slot and
+        // the times to events, both read by finish_deferred
+        const int k = t->npend;
+        cudaMemsetAsync(t->ctx->d_counters, 0, 3 * sizeof(unsigned long long), s);
+        cudaEventCreate(&t->pend_e0[k]);
+        cudaEventCreate(&t->pend_e1[k]);
+        cudaEventRecord(t->pend_e0[k], s);
+        a.tree0.pot = pot_sorted;
+        launch(a, opening, wp.split, false, t->refit, false, a.tree0.ngroups, s, pot_sorted != nullptr);
+        cudaEventRecord(t->pend_e1[k], s);
+        cudaMemcpyAsync(pinned_counters(t->ctx, k), t->ctx->d_counters, 3 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s);
+        t->npend = k + 1;
+        if (sort_tmp) cudaFreeAsync(sort_tmp, s);
+        // the next pass may take this one's list lengths: stream order makes them ready
+        t->have_cost = true;
+        if (ms_out) *ms_out = 0.0f;
+        return OG_OK;
     }
     unsigned long long h[3] = {0, 0, 0};
     for (int attempt = 0; attempt < 2; ++attempt) {

@@ -37,7 +37,7 @@ OG_DEBUG_DUMP_LISTS = 2
 
 (OG_F_SKEY, OG_F_PERM, OG_F_SPOS, OG_F_LEVEL, OG_F_NBEG, OG_F_NEND, OG_F_PARENT, OG_F_CBEG,
  OG_F_CCNT, OG_F_CHILD, OG_F_MASS, OG_F_COM, OG_F_NEXTNODE, OG_F_SIBLING, OG_F_PNEXT,
- OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS, OG_F_EXTENT) = range(20)
+ OG_F_GBEG, OG_F_GEND, OG_F_GBOX, OG_F_LISTS, OG_F_EXTENT, OG_F_MSUM) = range(21)
 
 
 class OGError(RuntimeError):
@@ -459,6 +459,7 @@ _FIELD_SPEC = {
     OG_F_GEND: ("groups", np.uint32, ()), OG_F_GBOX: ("groups", np.uint32, (6,)),
     OG_F_LISTS: ("list_entries", np.uint32, (2,)),
     OG_F_EXTENT: ("nodes", np.uint32, "2x3"),
+    OG_F_MSUM: ("nodes", np.float64, (3,)),
 }
 
 

@@ -73,6 +73,8 @@ def compare_build(gt: og.Tree, ot: oracle.Tree):
     assert np.array_equal(g_child[idx], o_child), "child lists"
     g_mass = gt.export(og.OG_F_MASS)[inv]
     assert np.array_equal(g_mass.view(np.uint64), ot.get(oracle.F_MASS).view(np.uint64)), "node mass (bitwise)"
+    assert np.array_equal(gt.export(og.OG_F_MSUM)[inv].view(np.uint64),
+                          ot.get(oracle.F_MSUM).view(np.uint64)), "node sums of m x (bitwise)"
     assert np.array_equal(gt.export(og.OG_F_COM)[inv], ot.get(oracle.F_COM)), "centre of mass"
     g_next = map_unified(gt.export(og.OG_F_NEXTNODE), n, gmap)[inv]
     assert np.array_equal(g_next, ot.get(oracle.F_NEXTNODE)), "nextnode"

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA library through the C-ABI against the FP64 oracle.
 
 Bit-exact: keys, permutation, fixed-point positions, node table, threading,
-moments (mass bitwise, centre of mass), groups, interaction lists, counts.
+moments (mass and sums of m x bitwise, centre of mass), groups, interaction
+lists, counts.
 Tolerance: accelerations, p99 relative error <= 1e-4 and rms <= 2e-5 against
 the oracle evaluated on the same lists.
 """
@@ -261,3 +262,47 @@ def test_massless_particles_and_nodes(ctx, opening):
     ref, rpp, rpn = ot.force(a_old=a1)
     assert np.array_equal(npp, rpp) and np.array_equal(npn, rpn)
     parity.check_accel(acc, ref)
+
+
+@pytest.mark.parametrize("kind", ["unequal", "spread", "subnormal", "overflow", "coincident"])
+def test_exact_moments_mass_distributions(ctx, kind):
+    """Node masses and sums of m x bitwise the oracle's exact sums rounded once,
+    centres of mass exact: unequal masses, masses spread over 2^-30..2^30,
+    subnormal masses, masses whose sums of m x overflow to infinity, and
+    buckets of coincident keys."""
+    r = np.random.default_rng(23)
+    pos, mass, prm = gi.config("clustered-2m", n=30000)
+    n = len(mass)
+    if kind == "unequal":
+        mass = mass * (0.5 + r.random(n))
+    elif kind == "spread":
+        mass = np.ldexp(1.0 + r.random(n), r.integers(-30, 31, n))
+    elif kind == "subnormal":
+        mass = 5e-324 * r.integers(1, 1 << 20, n).astype(np.float64)
+    elif kind == "overflow":
+        mass = 1e300 * (1.0 + r.random(n))
+    else:
+        pos = np.concatenate([pos, np.repeat(pos[:500], 4, axis=0)])
+        mass = np.concatenate([mass, mass[0] * r.random(2000)])
+    gt = og.Tree(ctx, pos, mass, prm)
+    ot = oracle.Tree(pos, mass, prm)
+    parity.compare_build(gt, ot)
+    if kind == "overflow":
+        assert np.isinf(gt.export(og.OG_F_MSUM)).any()
+
+
+def test_mass_span_limit(ctx):
+    """Masses may span 128 binary orders (lowest set bit of the smallest to the
+    top of the largest); one more is OG_ERR_ARG, and the context stays usable."""
+    pos, _, prm = gi.config("uniform-32k", n=3000)
+    mass = np.ones(len(pos))
+    mass[7] = 2.0 ** -75 * (1.0 + 2.0 ** -52)              # span 1 - (-127) = 128
+    gt = og.Tree(ctx, pos, mass, prm)
+    parity.compare_build(gt, oracle.Tree(pos, mass, prm))
+    gt.free()
+    mass[7] = 2.0 ** -76 * (1.0 + 2.0 ** -52)              # span 129
+    with pytest.raises(og.OGError) as e:
+        og.Tree(ctx, pos, mass, prm)
+    assert e.value.status == og.OG_ERR_ARG and "128" in str(e.value)
+    mass[7] = 1.0
+    parity.compare_build(og.Tree(ctx, pos, mass, prm), oracle.Tree(pos, mass, prm))
