@@ -42,7 +42,7 @@ UNIT = "particles/s"
 FLOPS_PER_INTERACTION = 45
 # The same count taken from the far-entry evaluation loop's own instruction
 # mix (reported beside it; it leaves out the compares and selects).
-FLOPS_PER_INTERACTION_MIX = 38
+FLOPS_PER_INTERACTION_MIX = 36
 FP32_LANES_PER_SM = 128
 
 

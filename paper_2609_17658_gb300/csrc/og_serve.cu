@@ -49,7 +49,7 @@ constexpr int kMaxRefits = 64;   // refits between builds at most
 // about 0.3 ms plus 0.2 ns per particle; a refitted tree's walk costs 13 %
 // more per interaction (it reads node extents); measured on GB300 at
 // 2e4, 2e5 and 2e6 particles
-constexpr double kBuildFixedInter = 2.6e8, kBuildPerParticleInter = 200.0;
+constexpr double kBuildFixedInter = 2.2e8, kBuildPerParticleInter = 160.0;
 constexpr double kRefitFixedInter = 1.5e8, kRefitPerParticleInter = 100.0;
 constexpr double kRefitWalkFactor = 1.13;
 constexpr double kTrialGrowth = 4.0;

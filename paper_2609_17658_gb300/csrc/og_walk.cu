@@ -161,7 +161,9 @@ template <bool kSplit, bool kPot = false>
 __device__ __forceinline__ void eval_near(const uint4 *ch, int cnt, int rep, int R, uint32_t xi,
                                           uint32_t yi, uint32_t zi, const WalkParams &p,
                                           float &ax, float &ay, float &az, float &ap) {
-    const float rc2 = p.rc2, inv_2rs = p.inv_2rs, kexp = p.kexp;
+    const float rc2 = p.rc2, kexp = p.kexp;
+    // u = r / (2 r_s) only enters as p u and (2 / sqrt(pi)) u
+    const float c_pr = kAsP * p.inv_2rs, c_tspr = kTwoOverSqrtPi * p.inv_2rs;
     const float h = p.h, inv_h = p.inv_h;
     const float hinv3 = inv_h * inv_h * inv_h;
 #pragma unroll 4
@@ -179,11 +181,10 @@ __device__ __forceinline__ void eval_near(const uint4 *ch, int cnt, int rep, int
         const float r = r2c * rinv;
         float erfcv = 1.0f;
         if (kSplit) {
-            const float us = r * inv_2rs;
-            const float t = rcp_ftz(fmaf(kAsP, us, 1.0f));
+            const float t = rcp_ftz(fmaf(c_pr, r, 1.0f));
             const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, kAs5, kAs4), kAs3), kAs2), kAs1);
             const float ex = ex2_ftz(r2c * kexp);
-            mS = m * (ex * fmaf(kTwoOverSqrtPi, us, poly));
+            mS = m * (ex * fmaf(c_tspr, r, poly));
             if (kPot) erfcv = ex * poly;
         }
         if (kPot) {
@@ -231,13 +232,14 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
                                          uint32_t yi, uint32_t zi, const WalkParams &p,
                                          float &ax, float &ay, float &az, float &ap) {
     const float rc2 = p.rc2;
-    const float2 c_inv2rs = make_float2(p.inv_2rs, p.inv_2rs);
     const float2 c_kexp = make_float2(p.kexp, p.kexp);
-    const float2 c_p = make_float2(kAsP, kAsP), c_one = make_float2(1.0f, 1.0f);
+    const float2 c_one = make_float2(1.0f, 1.0f);
     const float2 c5 = make_float2(kAs5, kAs5), c4 = make_float2(kAs4, kAs4);
     const float2 c3 = make_float2(kAs3, kAs3), c2 = make_float2(kAs2, kAs2);
     const float2 c1 = make_float2(kAs1, kAs1);
-    const float2 c_tsp = make_float2(kTwoOverSqrtPi, kTwoOverSqrtPi);
+    // u = r / (2 r_s) only enters as p u and (2 / sqrt(pi)) u: 1 / (2 r_s) folds into both
+    const float2 c_pr = make_float2(kAsP * p.inv_2rs, kAsP * p.inv_2rs);
+    const float2 c_tspr = make_float2(kTwoOverSqrtPi * p.inv_2rs, kTwoOverSqrtPi * p.inv_2rs);
     float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
     int e = rep;
 #pragma unroll kUnroll
@@ -253,11 +255,12 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
             m.y = (r2.y < rc2) ? m.y : 0.0f;
         }
         const float2 rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-        float2 mS = m;
-        float2 mP = m;
+        float2 f;
         if (kSplit) {
-            const float2 us = __fmul2_rn(__fmul2_rn(r2, rinv), c_inv2rs);
-            const float2 den = __ffma2_rn(c_p, us, c_one);
+            // S(r) r^-3 = (erfc(u) + (2 / sqrt(pi)) u exp(-u^2)) r^-3, with the
+            // second term's r r^-1 taken as 1: (poly rinv + c) exp(-u^2) rinv^2
+            const float2 r = __fmul2_rn(r2, rinv);
+            const float2 den = __ffma2_rn(c_pr, r, c_one);
             const float2 t = make_float2(rcp_ftz(den.x), rcp_ftz(den.y));
             float2 q = __ffma2_rn(t, c5, c4);
             q = __ffma2_rn(t, q, c3);
@@ -266,11 +269,13 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
             const float2 poly = __fmul2_rn(t, q);
             const float2 arg = __fmul2_rn(r2, c_kexp);
             const float2 ex = make_float2(ex2_ftz(arg.x), ex2_ftz(arg.y));
-            mS = __fmul2_rn(m, __fmul2_rn(ex, __ffma2_rn(c_tsp, us, poly)));
-            if (kPot) mP = __fmul2_rn(m, __fmul2_rn(ex, poly));
+            const float2 mex = __fmul2_rn(m, ex);
+            if (kPot) sp = __ffma2_rn(__fmul2_rn(mex, poly), rinv, sp);
+            f = __fmul2_rn(mex, __fmul2_rn(__ffma2_rn(poly, rinv, c_tspr), __fmul2_rn(rinv, rinv)));
+        } else {
+            if (kPot) sp = __ffma2_rn(m, rinv, sp);
+            f = __fmul2_rn(m, __fmul2_rn(rinv, __fmul2_rn(rinv, rinv)));
         }
-        if (kPot) sp = __ffma2_rn(mP, rinv, sp);
-        const float2 f = __fmul2_rn(mS, __fmul2_rn(rinv, __fmul2_rn(rinv, rinv)));
         sx = __ffma2_rn(f, fx, sx);
         sy = __ffma2_rn(f, fy, sy);
         sz = __ffma2_rn(f, fz, sz);
@@ -286,18 +291,19 @@ __device__ __forceinline__ void eval_far(const uint4 *ch, int cnt, int rep, int 
         float m = __uint_as_float(s.w);
         if (kSplit) m = (r2 < rc2) ? m : 0.0f;
         const float rinv = rsqrt_ftz(r2);
-        float mS = m;
-        float mP = m;
+        float f;
         if (kSplit) {
-            const float us = (r2 * rinv) * p.inv_2rs;
-            const float t = rcp_ftz(fmaf(kAsP, us, 1.0f));
+            const float r = r2 * rinv;
+            const float t = rcp_ftz(fmaf(c_pr.x, r, 1.0f));
             const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, kAs5, kAs4), kAs3), kAs2), kAs1);
             const float ex = ex2_ftz(r2 * p.kexp);
-            mS = m * (ex * fmaf(kTwoOverSqrtPi, us, poly));
-            if (kPot) mP = m * (ex * poly);
+            const float mex = m * ex;
+            if (kPot) tp = fmaf(mex * poly, rinv, tp);
+            f = mex * (fmaf(poly, rinv, c_tspr.x) * (rinv * rinv));
+        } else {
+            if (kPot) tp = fmaf(m, rinv, tp);
+            f = m * (rinv * (rinv * rinv));
         }
-        if (kPot) tp = fmaf(mP, rinv, tp);
-        const float f = mS * (rinv * (rinv * rinv));
         tx = fmaf(f, fx, tx);
         ty = fmaf(f, fy, ty);
         tz = fmaf(f, fz, tz);
