@@ -166,7 +166,7 @@ __device__ __forceinline__ void eval_near(const uint4 *ch, int cnt, int rep, int
     const float c_pr = kAsP * p.inv_2rs, c_tspr = kTwoOverSqrtPi * p.inv_2rs;
     const float h = p.h, inv_h = p.inv_h;
     const float hinv3 = inv_h * inv_h * inv_h;
-#pragma unroll 4
+#pragma unroll 2
     for (int e = rep; e < cnt; e += R) {
         const uint4 s = ch[e];
         const float fx = (float)(int)(s.x - xi);
@@ -568,7 +568,10 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
         float psum = 0.f, pcomp = 0.f;   // potential total (kPot), compensated
         bool overflow = false;
 
-        while (sp > 0) {
+        // the last pass of this loop finds the stack empty: an empty round whose
+        // flush evaluates what the chunks still hold (one evaluation site)
+        while (true) {
+            const bool done = sp == 0;
             // every round consumes at least one child record and a record is
             // visited at most once per walk: more rounds than records is a bug
             if (++rounds > T.max_rounds) {
@@ -645,7 +648,7 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
             cnt_pp += __popc(be0 & ~bn0) + __popc(be1 & ~bn1);
             const int nf0 = __popc(bf0), nfar = nf0 + __popc(bf1);
             const int nq0 = __popc(bq0), nnear = nq0 + __popc(bq1);
-            if (cf + nfar > chunk) {
+            if (done || cf + nfar > chunk) {
                 __syncwarp();
                 float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
                 eval_far<kSplit, kPot, kFarUnroll>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
@@ -654,7 +657,7 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
                 cf = 0;
                 __syncwarp();
             }
-            if (cn + nnear > kNearChunk) {
+            if (done || cn + nnear > kNearChunk) {
                 __syncwarp();
                 float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
                 eval_near<kSplit, kPot>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
@@ -698,22 +701,12 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
             cf += nfar;
             cn += nnear;
             __syncwarp();
+            if (done) break;
         }
         if (overflow) {
             if (lane == 0) atomicOr(a.status, ST_STACK_OVF);
             __syncwarp();
             continue;
-        }
-        __syncwarp();
-        {
-            float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
-            eval_far<kSplit, kPot, kFarUnroll>(chf, cf, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
-            acc.add(tx, ty, tz);
-            if (kPot) kahan_add(psum, pcomp, tp);
-            tx = ty = tz = tp = 0.f;
-            eval_near<kSplit, kPot>(chn, cn, rep, R, xi, yi, zi, p, tx, ty, tz, tp);
-            acc.add(tx, ty, tz);
-            if (kPot) kahan_add(psum, pcomp, tp);
         }
         __syncwarp();
         float vx = __fsub_rn(acc.sx, acc.kx), vy = __fsub_rn(acc.sy, acc.ky),
