@@ -124,8 +124,7 @@ __global__ void k_fill_seg(int64_t n, int64_t B, const uint32_t *__restrict__ se
     pseg[i] = (uint32_t)lo;
 }
 
-__global__ void k_quantize_keys(const double *__restrict__ pos, const double *__restrict__ mass,
-                                int64_t n, const uint32_t *__restrict__ pseg,
+__global__ void k_quantize_keys(const double *__restrict__ pos, int64_t n, const uint32_t *__restrict__ pseg,
                                 const SegGeom *__restrict__ geom, uint32_t *qx, uint32_t *qy,
                                 uint32_t *qz, uint64_t *key, uint64_t *key_copy, uint32_t *idx,
                                 uint32_t *status) {
@@ -137,10 +136,6 @@ __global__ void k_quantize_keys(const double *__restrict__ pos, const double *__
     uint32_t x = quantize(pos[3 * i + 0], box, inv_box, pow2, g.shift, status);
     uint32_t y = quantize(pos[3 * i + 1], box, inv_box, pow2, g.shift, status);
     uint32_t z = quantize(pos[3 * i + 2], box, inv_box, pow2, g.shift, status);
-    if (mass) {  // a refit passes no masses (they do not change)
-        const double m = mass[i];
-        if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
-    }
     qx[i] = x;
     qy[i] = y;
     qz[i] = z;
@@ -171,7 +166,8 @@ __global__ void k_gather_keys(int64_t n, const uint32_t *__restrict__ perm,
 __global__ void k_permute(int64_t n, const uint32_t *__restrict__ perm,
                           const uint32_t *__restrict__ qx, const uint32_t *__restrict__ qy,
                           const uint32_t *__restrict__ qz, const double *__restrict__ mass,
-                          uint32_t *px, uint32_t *py, uint32_t *pz, float *pm32, double *pm64) {
+                          uint32_t *px, uint32_t *py, uint32_t *pz, float *pm32, double *pm64,
+                          uint32_t *status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t j = perm[i];
@@ -179,6 +175,7 @@ __global__ void k_permute(int64_t n, const uint32_t *__restrict__ perm,
     py[i] = qy[j];
     pz[i] = qz[j];
     double m = mass[j];
+    if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
     pm64[i] = m;
     pm32[i] = __double2float_rn(m);
 }
@@ -907,7 +904,7 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
     if (B > 1) {
         k_fill_seg<<<nblk(n), kT, 0, s>>>(n, B, t->seg_off, pseg); note_launch();
     }
-    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, nullptr, n, B > 1 ? pseg : nullptr, t->geom, qx,
+    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx,
                                            qy, qz, keys, nullptr, idx, t->ctx->d_status); note_launch();
     k_repos<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, t->px, t->py, t->pz); note_launch();
     node_moments(t, nullptr, t->nnodes, mom_scratch, s);
@@ -1052,7 +1049,9 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     if (B > 1) {
         k_fill_seg<<<nblk(n), kT, 0, s>>>(n, B, t->seg_off, pseg); note_launch();
     }
-    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, d_mass, n, B > 1 ? pseg : nullptr, t->geom, qx, qy,
+    // the masses are checked where they are first read (k_permute), so that a
+    // host copy of them can still be in flight here
+    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx, qy,
                                            qz, keys, B > 1 ? key0 : nullptr, idx, status); note_launch();
     // a3: by key, then (several boxes) stably by box
     bool in_alt = false;
@@ -1077,8 +1076,9 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         cudaMemsetAsync(t->sseg, 0, n * sizeof(uint32_t), s);
     }
+    if (t->mass_ready) cudaStreamWaitEvent(s, t->mass_ready, 0);
     k_permute<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, d_mass, t->px, t->py, t->pz, t->pm32,
-                                     t->pm64); note_launch();
+                                     t->pm64, status); note_launch();
     // a4: nodes from splits.  The node count stays on the device (d_tot[0]
     // counts the first splits, m = B + that): the kernels up to the groups
     // read it there and are sized for the most nodes a tree can have, so the

@@ -297,6 +297,15 @@ og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
         return cuda_fail(e, "cudaStreamCreate");
     }
     c->stream = c->own_stream;
+    if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_pos, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_mass, cudaEventDisableTiming)) != cudaSuccess) {
+        if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+        if (c->ev_pos) cudaEventDestroy(c->ev_pos);
+        cudaStreamDestroy(c->own_stream);
+        delete c;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
     // keep freed blocks in the stream-ordered pool: repeated builds reuse them
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -304,6 +313,9 @@ og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     if ((e = cudaMalloc(&c->d_status, 256)) != cudaSuccess) {
+        cudaEventDestroy(c->ev_pos);
+        cudaEventDestroy(c->ev_mass);
+        cudaStreamDestroy(c->copy_stream);
         cudaStreamDestroy(c->own_stream);
         delete c;
         return cuda_fail(e, "cudaMalloc");
@@ -311,6 +323,9 @@ og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
     c->d_counters = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(c->d_status) + 64);
     if ((e = cudaMallocHost(&c->h_pinned, 256)) != cudaSuccess) {
         cudaFree(c->d_status);
+        cudaEventDestroy(c->ev_pos);
+        cudaEventDestroy(c->ev_mass);
+        cudaStreamDestroy(c->copy_stream);
         cudaStreamDestroy(c->own_stream);
         delete c;
         return cuda_fail(e, "cudaMallocHost");
@@ -343,6 +358,10 @@ og_status og_destroy(og_ctx *c) {
     cudaStreamSynchronize(c->stream);
     cudaFree(c->d_status);
     cudaFreeHost(c->h_pinned);
+    cudaStreamSynchronize(c->copy_stream);
+    cudaEventDestroy(c->ev_pos);
+    cudaEventDestroy(c->ev_mass);
+    cudaStreamDestroy(c->copy_stream);
     cudaStreamDestroy(c->own_stream);
     delete c;
     return OG_OK;
@@ -381,13 +400,23 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
         }
         double *dp = static_cast<double *>(staging);
         cudaMemcpyAsync(dp, pos, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(dp + 3 * n, mass, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s);
+        // the masses follow on the side stream once the positions are in (the
+        // link is not shared with them), beside the quantization and the sort;
+        // the build waits for them before it first reads them
+        cudaEventRecord(c->ev_pos, s);
+        cudaStreamWaitEvent(c->copy_stream, c->ev_pos, 0);
+        cudaMemcpyAsync(dp + 3 * n, mass, (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                        c->copy_stream);
+        cudaEventRecord(c->ev_mass, c->copy_stream);
+        t->mass_ready = c->ev_mass;
         d_pos = dp;
         d_mass = dp + 3 * n;
     }
     if (t->prm.group_max == 0) {
         // measured group size and walk launch shape for this kind of input
-        // (og_tune.cu); explicit launch-shape fields stay as given
+        // (og_tune.cu); explicit launch-shape fields stay as given.  The
+        // tuner's builds read the masses at once.
+        if (t->mass_ready) cudaStreamWaitEvent(s, t->mass_ready, 0);
         WalkConfig w{32, kDefaultWalkWarps, kDefaultWalkChunk};
         st = tuned_walk(c, d_pos, d_mass, n, t->prm, &w);
         if (st) {
@@ -403,6 +432,10 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
     if (t->prm.walk_chunk == 0) t->prm.walk_chunk = kDefaultWalkChunk;
     t->seg_prm.assign(1, t->prm);
     st = build_tree(t, d_pos, d_mass);
+    // the staging buffer is freed in stream order after the masses' copy,
+    // also when the build stopped before it waited for them
+    if (t->mass_ready) cudaStreamWaitEvent(s, t->mass_ready, 0);
+    t->mass_ready = nullptr;
     if (staging) cudaFreeAsync(staging, s);
     if (st == OG_OK) st = status_from(c, t->build_status);   // read by the build's synchronisation
     if (st != OG_OK) {

@@ -69,6 +69,8 @@ struct WalkParams;
 struct og_ctx {
     int device = 0;
     cudaStream_t own_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // host masses copied beside the keys' sort
+    cudaEvent_t ev_pos = nullptr, ev_mass = nullptr;
     cudaStream_t stream = nullptr;
     size_t hbm_budget = 0;
     uint32_t *d_status = nullptr;     // device status word
@@ -133,6 +135,8 @@ struct og_tree {
     cudaEvent_t pend_e0[2] = {nullptr, nullptr}, pend_e1[2] = {nullptr, nullptr};
     int npend = 0;
     uint32_t build_status = 0;        // status word read at the end of the build
+    cudaEvent_t mass_ready = nullptr; // the masses' copy (host inputs): the build waits before
+                                      // its first use of the masses
     // force work arrays (sorted order)
     float *a_sorted = nullptr;        // last pass accelerations, [3][n]
     float *a_old_sorted = nullptr;    // previous accelerations, [3][n]
