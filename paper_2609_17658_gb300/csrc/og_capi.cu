@@ -81,9 +81,11 @@ __global__ void k_unpermute(int64_t n, const uint32_t *__restrict__ perm,
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t j = perm[i];
-    acc[3ull * j + 0] = acc_sorted[i];
-    acc[3ull * j + 1] = acc_sorted[n + i];
-    acc[3ull * j + 2] = acc_sorted[2 * n + i];
+    if (acc) {
+        acc[3ull * j + 0] = acc_sorted[i];
+        acc[3ull * j + 1] = acc_sorted[n + i];
+        acc[3ull * j + 2] = acc_sorted[2 * n + i];
+    }
     if (npp) npp[j] = npp_s[i];
     if (npn) npn[j] = npn_s[i];
 }
@@ -298,10 +300,10 @@ og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
     }
     c->stream = c->own_stream;
     if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c->ev_pos, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c->ev_mass, cudaEventDisableTiming)) != cudaSuccess) {
+        (e = cudaEventCreateWithFlags(&c->ev_to_side, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_from_side, cudaEventDisableTiming)) != cudaSuccess) {
         if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
-        if (c->ev_pos) cudaEventDestroy(c->ev_pos);
+        if (c->ev_to_side) cudaEventDestroy(c->ev_to_side);
         cudaStreamDestroy(c->own_stream);
         delete c;
         return cuda_fail(e, "cudaStreamCreate");
@@ -313,8 +315,8 @@ og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     if ((e = cudaMalloc(&c->d_status, 256)) != cudaSuccess) {
-        cudaEventDestroy(c->ev_pos);
-        cudaEventDestroy(c->ev_mass);
+        cudaEventDestroy(c->ev_to_side);
+        cudaEventDestroy(c->ev_from_side);
         cudaStreamDestroy(c->copy_stream);
         cudaStreamDestroy(c->own_stream);
         delete c;
@@ -323,8 +325,8 @@ og_status og_create(og_ctx **out, int device, size_t hbm_budget_bytes) {
     c->d_counters = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(c->d_status) + 64);
     if ((e = cudaMallocHost(&c->h_pinned, 256)) != cudaSuccess) {
         cudaFree(c->d_status);
-        cudaEventDestroy(c->ev_pos);
-        cudaEventDestroy(c->ev_mass);
+        cudaEventDestroy(c->ev_to_side);
+        cudaEventDestroy(c->ev_from_side);
         cudaStreamDestroy(c->copy_stream);
         cudaStreamDestroy(c->own_stream);
         delete c;
@@ -359,8 +361,8 @@ og_status og_destroy(og_ctx *c) {
     cudaFree(c->d_status);
     cudaFreeHost(c->h_pinned);
     cudaStreamSynchronize(c->copy_stream);
-    cudaEventDestroy(c->ev_pos);
-    cudaEventDestroy(c->ev_mass);
+    cudaEventDestroy(c->ev_to_side);
+    cudaEventDestroy(c->ev_from_side);
     cudaStreamDestroy(c->copy_stream);
     cudaStreamDestroy(c->own_stream);
     delete c;
@@ -403,12 +405,12 @@ og_status og_tree_build(og_ctx *c, const double *pos, const double *mass, int64_
         // the masses follow on the side stream once the positions are in (the
         // link is not shared with them), beside the quantization and the sort;
         // the build waits for them before it first reads them
-        cudaEventRecord(c->ev_pos, s);
-        cudaStreamWaitEvent(c->copy_stream, c->ev_pos, 0);
+        cudaEventRecord(c->ev_to_side, s);
+        cudaStreamWaitEvent(c->copy_stream, c->ev_to_side, 0);
         cudaMemcpyAsync(dp + 3 * n, mass, (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
                         c->copy_stream);
-        cudaEventRecord(c->ev_mass, c->copy_stream);
-        t->mass_ready = c->ev_mass;
+        cudaEventRecord(c->ev_from_side, c->copy_stream);
+        t->mass_ready = c->ev_from_side;
         d_pos = dp;
         d_mass = dp + 3 * n;
     }
@@ -547,13 +549,29 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
         return fail(st);
     }
     // back to caller order
-    k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
-                                       d_acc, d_npp, d_npn); note_launch();
-    if (!dev) {
+    if (!dev && (n_pp || n_pn)) {
+        // host outputs: the counts first, their copy on the side stream beside
+        // the accelerations' reordering (the copies share the link, the
+        // reordering does not)
+        k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+                                           nullptr, d_npp, d_npn); note_launch();
+        cudaEventRecord(c->ev_to_side, s);
+        cudaStreamWaitEvent(c->copy_stream, c->ev_to_side, 0);
+        if (n_pp) cudaMemcpyAsync(n_pp, d_npp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->copy_stream);
+        if (n_pn) cudaMemcpyAsync(n_pn, d_npn, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->copy_stream);
+        cudaEventRecord(c->ev_from_side, c->copy_stream);
+        k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+                                           d_acc, nullptr, nullptr); note_launch();
         cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
-        if (n_pp) cudaMemcpyAsync(n_pp, d_npp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-        if (n_pn) cudaMemcpyAsync(n_pn, d_npn, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        cudaStreamWaitEvent(s, c->ev_from_side, 0);
         cudaFreeAsync(out_tmp, s);
+    } else {
+        k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+                                           d_acc, d_npp, d_npn); note_launch();
+        if (!dev) {
+            cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
+            cudaFreeAsync(out_tmp, s);
+        }
     }
     cudaEventRecord(e1, s);
     uint32_t *hst = pinned_status(c);

@@ -69,8 +69,9 @@ struct WalkParams;
 struct og_ctx {
     int device = 0;
     cudaStream_t own_stream = nullptr;
-    cudaStream_t copy_stream = nullptr;  // host masses copied beside the keys' sort
-    cudaEvent_t ev_pos = nullptr, ev_mass = nullptr;
+    cudaStream_t copy_stream = nullptr;  // host copies beside kernels (the masses in a build,
+                                         // the counts in a force call)
+    cudaEvent_t ev_to_side = nullptr, ev_from_side = nullptr;  // main stream -> side stream, back
     cudaStream_t stream = nullptr;
     size_t hbm_budget = 0;
     uint32_t *d_status = nullptr;     // device status word
