@@ -114,6 +114,7 @@ __device__ __forceinline__ uint32_t quantize(double v, double box, double inv_bo
 
 // segment (box) of every particle of the concatenated input
 __global__ void k_fill_seg(int64_t n, int64_t B, const uint32_t *__restrict__ seg_off, uint32_t *pseg) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t lo = 0, hi = B;  // seg_off[lo] <= i < seg_off[hi]
@@ -128,6 +129,7 @@ __global__ void k_quantize_keys(const double *__restrict__ pos, int64_t n, const
                                 const SegGeom *__restrict__ geom, uint32_t *qx, uint32_t *qy,
                                 uint32_t *qz, uint64_t *key, uint64_t *key_copy, uint32_t *idx,
                                 uint32_t *status) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const SegGeom g = geom[pseg ? pseg[i] : 0];
@@ -148,6 +150,7 @@ __global__ void k_quantize_keys(const double *__restrict__ pos, int64_t n, const
 // after the key sort: sort key = box index of each particle (stable second pass)
 __global__ void k_seg_keys(int64_t n, const uint32_t *__restrict__ idx,
                            const uint32_t *__restrict__ pseg, uint64_t *segkey) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     segkey[i] = pseg[idx[i]];
@@ -156,6 +159,7 @@ __global__ void k_seg_keys(int64_t n, const uint32_t *__restrict__ idx,
 __global__ void k_gather_keys(int64_t n, const uint32_t *__restrict__ perm,
                               const uint64_t *__restrict__ key0, const uint32_t *__restrict__ pseg,
                               uint64_t *skey, uint32_t *sseg) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t j = perm[i];
@@ -168,6 +172,7 @@ __global__ void k_permute(int64_t n, const uint32_t *__restrict__ perm,
                           const uint32_t *__restrict__ qz, const double *__restrict__ mass,
                           uint32_t *px, uint32_t *py, uint32_t *pz, float *pm32, double *pm64,
                           uint32_t *status) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t j = perm[i];
@@ -182,6 +187,7 @@ __global__ void k_permute(int64_t n, const uint32_t *__restrict__ perm,
 
 __global__ void k_split_levels(const uint64_t *__restrict__ skey, const uint32_t *__restrict__ sseg,
                                int64_t n, uint8_t *lv) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     lv[i] = (sseg[i] != sseg[i + 1]) ? kSep : (uint8_t)lcp_levels(skey[i], skey[i + 1]);
@@ -193,6 +199,7 @@ __global__ void k_split_levels(const uint64_t *__restrict__ skey, const uint32_t
 __global__ void k_split_nodes(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ lv,
                               const uint32_t *__restrict__ sseg, const uint32_t *__restrict__ seg_off,
                               int64_t n, uint32_t *sb, uint32_t *se, uint32_t *first) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     if (lv[i] == kSep) {
@@ -242,6 +249,7 @@ __global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ s
                             const uint32_t *__restrict__ se, const uint32_t *__restrict__ px,
                             const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
                             uint8_t *nlev, uint32_t *nbeg, uint32_t *nend, uint32_t *norg) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < B) {  // the root of box i covers the whole box
         nlev[i] = 0;
@@ -267,6 +275,7 @@ __global__ void k_split_node_id(const uint64_t *__restrict__ skey, const uint8_t
                                 const uint32_t *__restrict__ sb, const uint32_t *__restrict__ first,
                                 const uint32_t *__restrict__ nid, const uint32_t *__restrict__ sseg,
                                 int64_t n, int64_t B, uint32_t *sid) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     const int L = lv[i];
@@ -298,6 +307,7 @@ __global__ void k_link(int64_t n, const uint32_t *__restrict__ nsplit, int64_t B
                        const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
                        int32_t *npar, uint32_t *owner, uint32_t *occ, uint32_t *nnc,
                        uint32_t *status) {
+    pdl_wait();
     const int64_t m = B + (int64_t)*nsplit;  // nodes: the roots and one per first split
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) {
@@ -335,6 +345,7 @@ __global__ void k_link(int64_t n, const uint32_t *__restrict__ nsplit, int64_t B
 __global__ void k_ccnt(const uint32_t *__restrict__ nsplit, int64_t B, const uint8_t *__restrict__ nlev,
                        const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
                        const uint32_t *__restrict__ occ, uint32_t *nccnt) {
+    pdl_wait();
     const int64_t m = B + (int64_t)*nsplit;
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= m) return;
@@ -347,6 +358,7 @@ __global__ void k_place(int64_t n, const uint32_t *__restrict__ nsplit, int64_t 
                         const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ occ,
                         const int32_t *__restrict__ npar, const uint32_t *__restrict__ owner,
                         uint32_t *child, uint32_t *npos, uint32_t *status) {
+    pdl_wait();
     const int64_t m = B + (int64_t)*nsplit;
     const int64_t nchild = n + (m - B);
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -380,6 +392,7 @@ __global__ void k_threading(int64_t n, const uint32_t *__restrict__ nsplit, int6
                             const int32_t *__restrict__ npar, const uint32_t *__restrict__ npos,
                             const uint32_t *__restrict__ owner, int32_t *nnext, int32_t *nsib,
                             int32_t *pnext, uint32_t *status) {
+    pdl_wait();
     const int64_t m = B + (int64_t)*nsplit;
     const int64_t nchild = n + (m - B);
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -411,6 +424,7 @@ constexpr int kLvItems = 16;  // nodes per thread in the level bucketing
 __global__ void __launch_bounds__(kT) k_level_hist(const uint32_t *__restrict__ nsplit, int64_t B,
                                                    const uint8_t *__restrict__ nlev,
                                                    uint32_t *lcount) {
+    pdl_wait();
     const int64_t m = B + (int64_t)*nsplit;
     __shared__ uint32_t h[kLevels + 1];
     if (threadIdx.x <= kLevels) h[threadIdx.x] = 0;
@@ -425,6 +439,7 @@ __global__ void __launch_bounds__(kT) k_level_hist(const uint32_t *__restrict__ 
 }
 
 __global__ void k_level_offsets(uint32_t *lcount, uint32_t *loff, uint32_t *lcursor) {
+    pdl_wait();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     uint32_t run = 0;
     for (int l = 0; l <= kLevels; ++l) {
@@ -439,6 +454,7 @@ __global__ void __launch_bounds__(kT) k_level_scatter(const uint32_t *__restrict
                                                       const uint8_t *__restrict__ nlev,
                                                       const uint32_t *__restrict__ loff,
                                                       uint32_t *lcursor, uint32_t *lnodes) {
+    pdl_wait();
     const int64_t m = B + (int64_t)*nsplit;
     __shared__ uint32_t h[kLevels + 1], hb[kLevels + 1];
     if (threadIdx.x <= kLevels) h[threadIdx.x] = 0;
@@ -525,6 +541,7 @@ __global__ void __launch_bounds__(kT) k_extents_level(
     const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz, int64_t nchild,
     uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l, int level,
     const uint32_t *__restrict__ lnodes, uint32_t cnt) {
+    pdl_wait();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cnt) return;
     const uint32_t node = lnodes[k];
@@ -553,6 +570,7 @@ __global__ void __launch_bounds__(kRunThreads) k_extents_run(
     const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz, int64_t nchild,
     uint32_t *status, const uint32_t *__restrict__ norg, uint32_t *ext_s, uint32_t *ext_l,
     const uint32_t *__restrict__ lnodes, LevelRun run) {
+    pdl_wait();
     for (int l = run.hi; l >= run.lo; --l) {
         for (uint32_t k = threadIdx.x; k < run.cnt[l]; k += blockDim.x) {
             const uint32_t node = lnodes[run.off[l] + k];
@@ -572,6 +590,7 @@ __global__ void __launch_bounds__(kRunThreads) k_extents_run(
 __global__ void k_frontier(int64_t n, int64_t B, int G, const uint32_t *__restrict__ owner,
                            const int32_t *__restrict__ npar, const uint32_t *__restrict__ nbeg,
                            const uint32_t *__restrict__ nend, uint32_t *fp, uint32_t *unit) {
+    pdl_wait();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     uint32_t node = owner[p];
@@ -587,6 +606,7 @@ __global__ void k_frontier(int64_t n, int64_t B, int G, const uint32_t *__restri
 }
 
 __global__ void k_runmark(int64_t n, const uint32_t *__restrict__ fp, uint32_t *rs) {
+    pdl_wait();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     rs[p] = (p == 0 || fp[p] != fp[p - 1]) ? (uint32_t)p : 0u;
@@ -599,6 +619,7 @@ __global__ void k_groupmark(int64_t n, int G, const uint32_t *__restrict__ runst
                             const uint32_t *__restrict__ fp, const uint32_t *__restrict__ unit,
                             const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
                             uint32_t *gs) {
+    pdl_wait();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const uint32_t f = fp[p];
@@ -609,6 +630,7 @@ __global__ void k_groupmark(int64_t n, int G, const uint32_t *__restrict__ runst
 
 __global__ void k_group_init(int64_t n, const uint32_t *__restrict__ gs,
                              const uint32_t *__restrict__ gid, uint32_t *gbeg) {
+    pdl_wait();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n || !gs[p]) return;
     gbeg[gid[p]] = (uint32_t)p;
@@ -651,6 +673,7 @@ __global__ void k_group_fin(int64_t n, const uint32_t *__restrict__ d_ng, int64_
                             const uint32_t *__restrict__ px, const uint32_t *__restrict__ py,
                             const uint32_t *__restrict__ pz, const uint32_t *__restrict__ sseg,
                             uint32_t *gbox, uint32_t *gseg) {
+    pdl_wait();
     int64_t ng = d_ng ? (int64_t)*d_ng : ng_host;
     if (ng > n) ng = n;                        // the host reports a bad count
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng;
@@ -661,6 +684,7 @@ __global__ void k_group_fin(int64_t n, const uint32_t *__restrict__ d_ng, int64_
 __global__ void k_ext_records(int64_t n, int64_t nchild, const uint32_t *__restrict__ child,
                               const uint32_t *__restrict__ ext_s, const uint32_t *__restrict__ ext_l,
                               CExt *cext) {
+    pdl_wait();
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nchild) return;
     const uint32_t item = child[c];
@@ -676,6 +700,7 @@ __global__ void k_ext_records(int64_t n, int64_t nchild, const uint32_t *__restr
 // a built tree's node extents: its cells
 __global__ void k_cell_ext(int64_t m, const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ norg,
                            uint32_t *ext_s, uint32_t *ext_l) {
+    pdl_wait();
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     const int L = nlev[j];
@@ -689,6 +714,7 @@ __global__ void k_cell_ext(int64_t m, const uint8_t *__restrict__ nlev, const ui
 __global__ void k_repos(int64_t n, const uint32_t *__restrict__ perm, const uint32_t *__restrict__ qx,
                         const uint32_t *__restrict__ qy, const uint32_t *__restrict__ qz,
                         uint32_t *px, uint32_t *py, uint32_t *pz) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t j = perm[i];
@@ -707,6 +733,7 @@ __global__ void k_records(int64_t n, const uint32_t *__restrict__ d_nchild, int6
                           const uint32_t *__restrict__ ncbeg, const uint32_t *__restrict__ nccnt,
                           const NodeMom *__restrict__ nmom, const uint32_t *__restrict__ ncom,
                           CRec *crec, uint32_t *status) {
+    pdl_wait();
     int64_t nchild = d_nchild ? (int64_t)*d_nchild : nchild_host;
     if (nchild > ccap) nchild = ccap;          // the host reports a bad count
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchild;
@@ -789,9 +816,9 @@ static og_status level_lists(og_tree *t, uint32_t *lcount) {
     cudaMemsetAsync(lcount, 0, (kLevels + 2) * sizeof(uint32_t), s);
     cudaMemcpyAsync(d_nsplit, &nsplit, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
     const unsigned lv_blocks = (unsigned)((m + (int64_t)kT * kLvItems - 1) / ((int64_t)kT * kLvItems));
-    k_level_hist<<<lv_blocks, kT, 0, s>>>(d_nsplit, B, t->nlev, lcount); note_launch();
-    k_level_offsets<<<1, 32, 0, s>>>(lcount, loff, lcursor); note_launch();
-    k_level_scatter<<<lv_blocks, kT, 0, s>>>(d_nsplit, B, t->nlev, loff, lcursor, t->lnodes); note_launch();
+    launch_pdl(k_level_hist, lv_blocks, kT, 0, s, d_nsplit, B, t->nlev, lcount);
+    launch_pdl(k_level_offsets, 1, 32, 0, s, lcount, loff, lcursor);
+    launch_pdl(k_level_scatter, lv_blocks, kT, 0, s, d_nsplit, B, t->nlev, loff, lcursor, t->lnodes);
     uint32_t h[kLevels + 2];
     cudaMemcpyAsync(h, lcount, (kLevels + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -817,9 +844,9 @@ static void extents_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
     run.hi = -1;
     auto flush = [&]() {
         if (run.hi < 0) return;
-        k_extents_run<<<1, kRunThreads, 0, s>>>(n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child,
+        launch_pdl(k_extents_run, 1, kRunThreads, 0, s, n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child,
                                                 t->px, t->py, t->pz, t->nchild, t->ctx->d_status,
-                                                t->norg, ext_s, ext_l, t->lnodes, run); note_launch();
+                                                t->norg, ext_s, ext_l, t->lnodes, run);
         run.hi = -1;
     };
     for (int l = kLevels; l >= 0; --l) {
@@ -833,9 +860,9 @@ static void extents_bottom_up(og_tree *t, uint32_t *ext_s, uint32_t *ext_l) {
             continue;
         }
         flush();
-        k_extents_level<<<nblk(cnt), kT, 0, s>>>(n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child,
+        launch_pdl(k_extents_level, nblk(cnt), kT, 0, s, n, m, t->nbeg, t->nend, t->ncbeg, t->nocc, t->child,
                                                  t->px, t->py, t->pz, t->nchild, t->ctx->d_status,
-                                                 t->norg, ext_s, ext_l, l, t->lnodes + offs[l], cnt); note_launch();
+                                                 t->norg, ext_s, ext_l, l, t->lnodes + offs[l], cnt);
     }
     flush();
 }
@@ -860,9 +887,9 @@ og_status cell_extents(og_tree *t) {
     og_status st = alloc_extents(t);
     if (st) return st;
     cudaStream_t s = t->ctx->stream;
-    k_cell_ext<<<nblk(t->nnodes), kT, 0, s>>>(t->nnodes, t->nlev, t->norg, t->next_s, t->next_l); note_launch();
-    k_ext_records<<<nblk(t->nchild), kT, 0, s>>>(t->n, t->nchild, t->child, t->next_s, t->next_l,
-                                                 t->cext); note_launch();
+    launch_pdl(k_cell_ext, nblk(t->nnodes), kT, 0, s, t->nnodes, t->nlev, t->norg, t->next_s, t->next_l);
+    launch_pdl(k_ext_records, nblk(t->nchild), kT, 0, s, t->n, t->nchild, t->child, t->next_s, t->next_l,
+                                                 t->cext);
     return OG_OK;
 }
 
@@ -902,20 +929,20 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
     if (B > 1) {
-        k_fill_seg<<<nblk(n), kT, 0, s>>>(n, B, t->seg_off, pseg); note_launch();
+        launch_pdl(k_fill_seg, nblk(n), kT, 0, s, n, B, t->seg_off, pseg);
     }
-    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx,
-                                           qy, qz, keys, nullptr, idx, t->ctx->d_status); note_launch();
-    k_repos<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, t->px, t->py, t->pz); note_launch();
+    launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx,
+                                           qy, qz, keys, nullptr, idx, t->ctx->d_status);
+    launch_pdl(k_repos, nblk(n), kT, 0, s, n, t->perm, qx, qy, qz, t->px, t->py, t->pz);
     node_moments(t, nullptr, t->nnodes, mom_scratch, s);
     extents_bottom_up(t, t->next_s, t->next_l);
-    k_group_fin<<<stride_grid(t->ngroups), kT, 0, s>>>(n, nullptr, t->ngroups, t->gbeg, t->gend, t->px,
-                                                       t->py, t->pz, t->sseg, t->gbox, t->gseg); note_launch();
-    k_records<<<stride_grid(t->nchild), kT, 0, s>>>(n, nullptr, t->nchild, t->nchild, t->child, t->px,
+    launch_pdl(k_group_fin, stride_grid(t->ngroups), kT, 0, s, n, nullptr, t->ngroups, t->gbeg, t->gend, t->px,
+                                                       t->py, t->pz, t->sseg, t->gbox, t->gseg);
+    launch_pdl(k_records, stride_grid(t->nchild), kT, 0, s, n, nullptr, t->nchild, t->nchild, t->child, t->px,
                                                     t->py, t->pz, t->pm32, t->pm64, t->nlev, t->ncbeg,
-                                                    t->nccnt, t->nmom, t->ncom, t->crec, t->ctx->d_status); note_launch();
-    k_ext_records<<<nblk(t->nchild), kT, 0, s>>>(n, t->nchild, t->child, t->next_s, t->next_l,
-                                                 t->cext); note_launch();
+                                                    t->nccnt, t->nmom, t->ncom, t->crec, t->ctx->d_status);
+    launch_pdl(k_ext_records, nblk(t->nchild), kT, 0, s, n, t->nchild, t->child, t->next_s, t->next_l,
+                                                 t->cext);
     cudaEventRecord(e1, s);
     cudaFreeAsync(scratch, s);
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "refit");
@@ -1047,12 +1074,12 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
 
     // a1, a2
     if (B > 1) {
-        k_fill_seg<<<nblk(n), kT, 0, s>>>(n, B, t->seg_off, pseg); note_launch();
+        launch_pdl(k_fill_seg, nblk(n), kT, 0, s, n, B, t->seg_off, pseg);
     }
     // the masses are checked where they are first read (k_permute), so that a
     // host copy of them can still be in flight here
-    k_quantize_keys<<<nblk(n), kT, 0, s>>>(d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx, qy,
-                                           qz, keys, B > 1 ? key0 : nullptr, idx, status); note_launch();
+    launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx, qy,
+                                           qz, keys, B > 1 ? key0 : nullptr, idx, status);
     // a3: by key, then (several boxes) stably by box
     bool in_alt = false;
     radix_sort_pairs(keys, idx, keys_alt, idx_alt, n, 63, sort_scratch, s, &in_alt);
@@ -1061,14 +1088,14 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         uint64_t *segkey = in_alt ? keys : keys_alt;      // the free key buffer
         uint64_t *segkey_alt = in_alt ? keys_alt : keys;
         uint32_t *perm1_alt = in_alt ? idx : idx_alt;
-        k_seg_keys<<<nblk(n), kT, 0, s>>>(n, perm1, pseg, segkey); note_launch();
+        launch_pdl(k_seg_keys, nblk(n), kT, 0, s, n, perm1, pseg, segkey);
         int bits = 1;
         while ((1ll << bits) < B) ++bits;
         bool alt2 = false;
         radix_sort_pairs(segkey, perm1, segkey_alt, perm1_alt, n, bits, sort_scratch, s, &alt2);
         const uint32_t *perm_src = alt2 ? perm1_alt : perm1;
         cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
-        k_gather_keys<<<nblk(n), kT, 0, s>>>(n, t->perm, key0, pseg, t->skey, t->sseg); note_launch();
+        launch_pdl(k_gather_keys, nblk(n), kT, 0, s, n, t->perm, key0, pseg, t->skey, t->sseg);
     } else {
         const uint64_t *skey_src = in_alt ? keys_alt : keys;
         const uint32_t *perm_src = in_alt ? idx_alt : idx;
@@ -1077,8 +1104,8 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         cudaMemsetAsync(t->sseg, 0, n * sizeof(uint32_t), s);
     }
     if (t->mass_ready) cudaStreamWaitEvent(s, t->mass_ready, 0);
-    k_permute<<<nblk(n), kT, 0, s>>>(n, t->perm, qx, qy, qz, d_mass, t->px, t->py, t->pz, t->pm32,
-                                     t->pm64, status); note_launch();
+    launch_pdl(k_permute, nblk(n), kT, 0, s, n, t->perm, qx, qy, qz, d_mass, t->px, t->py, t->pz, t->pm32,
+                                     t->pm64, status);
     // a4: nodes from splits.  The node count stays on the device (d_tot[0]
     // counts the first splits, m = B + that): the kernels up to the groups
     // read it there and are sized for the most nodes a tree can have, so the
@@ -1087,49 +1114,49 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     int64_t nsplit = n - 1;
     cudaMemsetAsync(d_tot, 0, 4 * sizeof(uint32_t), s);
     if (nsplit > 0) {
-        k_split_levels<<<nblk(nsplit), kT, 0, s>>>(t->skey, t->sseg, n, lv); note_launch();
-        k_split_nodes<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, t->sseg, t->seg_off, n, sbeg, send,
-                                                  first); note_launch();
+        launch_pdl(k_split_levels, nblk(nsplit), kT, 0, s, t->skey, t->sseg, n, lv);
+        launch_pdl(k_split_nodes, nblk(nsplit), kT, 0, s, t->skey, lv, t->sseg, t->seg_off, n, sbeg, send,
+                                                  first);
         scan_exclusive_u32(first, nid, nsplit, d_tot, scan_scratch, s);
     }
     const uint32_t *nsp = d_tot;
-    k_node_init<<<nblk(nsplit > B ? nsplit : B), kT, 0, s>>>(n, B, t->seg_off, first, nid, lv, sbeg,
+    launch_pdl(k_node_init, nblk(nsplit > B ? nsplit : B), kT, 0, s, n, B, t->seg_off, first, nid, lv, sbeg,
                                                             send, t->px, t->py, t->pz, t->nlev,
-                                                            t->nbeg, t->nend, t->norg); note_launch();
+                                                            t->nbeg, t->nend, t->norg);
     if (nsplit > 0) {
-        k_split_node_id<<<nblk(nsplit), kT, 0, s>>>(t->skey, lv, sbeg, first, nid, t->sseg, n, B, sid); note_launch();
+        launch_pdl(k_split_node_id, nblk(nsplit), kT, 0, s, t->skey, lv, sbeg, first, nid, t->sseg, n, B, sid);
     }
     cudaMemsetAsync(occ, 0, mcap * sizeof(uint32_t), s);
     cudaMemsetAsync(nnc, 0, mcap * sizeof(uint32_t), s);
     // child counts beyond the last node stay 0, so the scan over mcap entries
     // gives the node's child offsets and, as its total, the child entries
     cudaMemsetAsync(t->nccnt, 0, mcap * sizeof(uint32_t), s);
-    k_link<<<nblk(n + mcap), kT, 0, s>>>(n, nsp, B, t->skey, lv, sid, t->sseg, t->nlev, t->nbeg,
-                                         t->nend, t->npar, t->owner, occ, nnc, status); note_launch();
-    k_ccnt<<<nblk(mcap), kT, 0, s>>>(nsp, B, t->nlev, t->nbeg, t->nend, occ, t->nccnt); note_launch();
+    launch_pdl(k_link, nblk(n + mcap), kT, 0, s, n, nsp, B, t->skey, lv, sid, t->sseg, t->nlev, t->nbeg,
+                                         t->nend, t->npar, t->owner, occ, nnc, status);
+    launch_pdl(k_ccnt, nblk(mcap), kT, 0, s, nsp, B, t->nlev, t->nbeg, t->nend, occ, t->nccnt);
     scan_exclusive_u32(t->nccnt, t->ncbeg, mcap, d_tot + 1, scan_scratch, s);
-    k_place<<<nblk(n + mcap), kT, 0, s>>>(n, nsp, B, t->skey, t->nlev, t->nbeg, t->ncbeg, occ,
-                                          t->npar, t->owner, t->child, t->npos, status); note_launch();
-    k_threading<<<nblk(ccap), kT, 0, s>>>(n, nsp, B, t->child, t->ncbeg, t->nccnt, t->npar,
-                                          t->npos, t->owner, t->nnext, t->nsib, t->pnext, status); note_launch();
+    launch_pdl(k_place, nblk(n + mcap), kT, 0, s, n, nsp, B, t->skey, t->nlev, t->nbeg, t->ncbeg, occ,
+                                          t->npar, t->owner, t->child, t->npos, status);
+    launch_pdl(k_threading, nblk(ccap), kT, 0, s, n, nsp, B, t->child, t->ncbeg, t->nccnt, t->npar,
+                                          t->npos, t->owner, t->nnext, t->nsib, t->pnext, status);
     // a5: exact moments and centres of mass of every node (the masses' set-bit
     // span first: it fixes the integer units)
     mass_span(t, s);
     node_moments(t, nsp, mcap, mom_scratch, s);
     // a6: groups (one group size for the whole forest)
     const int G = t->prm.group_max;
-    k_frontier<<<nblk(n), kT, 0, s>>>(n, B, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit); note_launch();
-    k_runmark<<<nblk(n), kT, 0, s>>>(n, fp, rs); note_launch();
+    launch_pdl(k_frontier, nblk(n), kT, 0, s, n, B, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit);
+    launch_pdl(k_runmark, nblk(n), kT, 0, s, n, fp, rs);
     scan_inclusive_max_u32(rs, rs, n, scan_scratch, s);
-    k_groupmark<<<nblk(n), kT, 0, s>>>(n, G, rs, fp, unit, t->nbeg, t->nend, gs); note_launch();
+    launch_pdl(k_groupmark, nblk(n), kT, 0, s, n, G, rs, fp, unit, t->nbeg, t->nend, gs);
     scan_exclusive_u32(gs, gid, n, d_tot + 2, scan_scratch, s);
-    k_group_init<<<nblk(n), kT, 0, s>>>(n, gs, gid, t->gbeg); note_launch();
+    launch_pdl(k_group_init, nblk(n), kT, 0, s, n, gs, gid, t->gbeg);
     // group count (d_tot[2]) and child count (d_tot[1]) from the device
-    k_group_fin<<<stride_grid(n), kT, 0, s>>>(n, d_tot + 2, 0, t->gbeg, t->gend, t->px, t->py, t->pz,
-                                              t->sseg, t->gbox, t->gseg); note_launch();
-    k_records<<<stride_grid(ccap), kT, 0, s>>>(n, d_tot + 1, 0, ccap, t->child, t->px, t->py, t->pz,
+    launch_pdl(k_group_fin, stride_grid(n), kT, 0, s, n, d_tot + 2, 0, t->gbeg, t->gend, t->px, t->py, t->pz,
+                                              t->sseg, t->gbox, t->gseg);
+    launch_pdl(k_records, stride_grid(ccap), kT, 0, s, n, d_tot + 1, 0, ccap, t->child, t->px, t->py, t->pz,
                                                t->pm32, t->pm64, t->nlev, t->ncbeg, t->nccnt, t->nmom,
-                                               t->ncom, t->crec, status); note_launch();
+                                               t->ncom, t->crec, status);
     cudaEventRecord(e1, s);
     // the counts and the status word, read once the build is complete (its
     // only host synchronisation)

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "og.h"
@@ -204,6 +205,28 @@ void tune_free(og_ctx *c);
 void pm_free(og_ctx *c);   // og_pm.cu: the context's cuFFT plans
 // count of kernels launched by this library in this process
 void note_launch();
+
+// Programmatic dependent launch: the kernel may be scheduled while the one
+// before it in the stream finishes; it calls pdl_wait() first, which returns
+// once that kernel (and so everything before it) has completed and its writes
+// are visible.  Kernels launched this way are otherwise ordered as usual.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    note_launch();
+}
 og_status cuda_fail(cudaError_t e, const char *what);
 // stream-ordered device allocation; fails without asking the device while
 // og_debug_fail_allocations has injected failures left (og_capi.cu)

@@ -253,6 +253,7 @@ __device__ __forceinline__ void mass_bit_span(double m, int &lo, int &hi) {
 // grid-stride pass, one pair of atomics per block
 __global__ void __launch_bounds__(kMomThreads) k_mass_span(int64_t n, const double *__restrict__ pm64,
                                                            int *mbits) {
+    pdl_wait();
     __shared__ int wlo[kMomThreads / 32], whi[kMomThreads / 32];
     int lo = 0x7fffffff, hi = (int)0x80000000;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
@@ -308,6 +309,7 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_tiles(int64_t n, const doub
                                                            const uint32_t *__restrict__ pz,
                                                            const int *__restrict__ mbits,
                                                            Mom192 *tile_sum, uint32_t *status) {
+    pdl_wait();
     if (!span_ok(mbits, status)) return;
     const int b = mbits[0];
     const int64_t q0 = (int64_t)blockIdx.x * kMomTile + (int64_t)threadIdx.x * kMomItems;
@@ -323,6 +325,7 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_tiles(int64_t n, const doub
 __global__ void __launch_bounds__(kScanBlock) k_mom_scan_l1(int64_t ntiles, const int *__restrict__ mbits,
                                                             Mom192 *tile_sum, Mom192 *block_sum,
                                                             uint32_t *status) {
+    pdl_wait();
     if (!span_ok(mbits, status)) return;
     const int64_t k = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     Mom192 v, excl, total;
@@ -338,6 +341,7 @@ __global__ void __launch_bounds__(kScanBlock) k_mom_scan_l1(int64_t ntiles, cons
 __global__ void __launch_bounds__(kScanTop) k_mom_scan_l2(int64_t nblocks, const int *__restrict__ mbits,
                                                           Mom192 *block_sum, Mom192 *total_out,
                                                           uint32_t *status) {
+    pdl_wait();
     if (!span_ok(mbits, status)) return;
     const int64_t per = (nblocks + kScanTop - 1) / kScanTop;
     const int64_t k0 = (int64_t)threadIdx.x * per;
@@ -367,6 +371,7 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_prefix(int64_t n, const dou
                                                             const Mom192 *__restrict__ tile_off,
                                                             const Mom192 *__restrict__ block_off,
                                                             Mom192 *P, uint32_t *status) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char stage_all[];
     if (!span_ok(mbits, status)) return;
     const int b = mbits[0];
@@ -508,6 +513,7 @@ __global__ void __launch_bounds__(kMomThreads) k_node_moments(
     const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
     const Mom192 *__restrict__ P, const int *__restrict__ mbits, NodeMom *nmom, uint32_t *ncom,
     uint32_t *status) {
+    pdl_wait();
     if (!span_ok(mbits, status)) return;
     int64_t m = nsplit ? B + (int64_t)*nsplit : m_host;
     if (m > mcap) m = mcap;                    // the host reports the overflow
@@ -552,7 +558,7 @@ void mass_span(og_tree *t, cudaStream_t s) {
     cudaMemsetAsync(t->mbits + 1, 0x80, sizeof(int), s);
     const int64_t nb = (t->n + kMomThreads - 1) / kMomThreads;
     const unsigned grid = (unsigned)(nb < 1 ? 1 : nb > 1024 ? 1024 : nb);
-    k_mass_span<<<grid, kMomThreads, 0, s>>>(t->n, t->pm64, t->mbits); note_launch();
+    launch_pdl(k_mass_span, grid, kMomThreads, 0, s, t->n, t->pm64, t->mbits);
 }
 
 size_t moments_scratch_bytes(int64_t n) {
@@ -574,21 +580,21 @@ void node_moments(og_tree *t, const uint32_t *d_nsplit, int64_t mcap, void *scra
     q += up((size_t)ntiles * sizeof(Mom192));
     Mom192 *blocks = reinterpret_cast<Mom192 *>(q);
     uint32_t *status = t->ctx->d_status;
-    k_mom_tiles<<<(unsigned)ntiles, kMomThreads, 0, s>>>(n, t->pm64, t->px, t->py, t->pz, t->mbits,
-                                                         tiles, status); note_launch();
-    k_mom_scan_l1<<<(unsigned)nblocks, kScanBlock, 0, s>>>(ntiles, t->mbits, tiles, blocks, status); note_launch();
-    k_mom_scan_l2<<<1, kScanTop, 0, s>>>(nblocks, t->mbits, blocks, &P[n], status); note_launch();
+    launch_pdl(k_mom_tiles, (unsigned)ntiles, kMomThreads, 0, s, n, t->pm64, t->px, t->py, t->pz, t->mbits,
+                                                         tiles, status);
+    launch_pdl(k_mom_scan_l1, (unsigned)nblocks, kScanBlock, 0, s, ntiles, t->mbits, tiles, blocks, status);
+    launch_pdl(k_mom_scan_l2, 1, kScanTop, 0, s, nblocks, t->mbits, blocks, &P[n], status);
     // the stage is above the default 48 KB of shared memory (set per call: the
     // attribute belongs to the current device)
     cudaFuncSetAttribute(k_mom_prefix, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (kMomThreads / 32) * kWarpStage);
-    k_mom_prefix<<<(unsigned)ntiles, kMomThreads, (kMomThreads / 32) * kWarpStage, s>>>(
-        n, t->pm64, t->px, t->py, t->pz, t->mbits, tiles, blocks, P, status); note_launch();
+    launch_pdl(k_mom_prefix, (unsigned)ntiles, kMomThreads, (kMomThreads / 32) * kWarpStage, s, 
+        n, t->pm64, t->px, t->py, t->pz, t->mbits, tiles, blocks, P, status);
     const int64_t mb = (mcap + kMomThreads - 1) / kMomThreads;
     const unsigned grid = (unsigned)(mb < 4096 ? (mb > 0 ? mb : 1) : 4096);
-    k_node_moments<<<grid, kMomThreads, 0, s>>>(d_nsplit, t->nseg, t->nnodes, mcap, t->nbeg, t->nend,
+    launch_pdl(k_node_moments, grid, kMomThreads, 0, s, d_nsplit, t->nseg, t->nnodes, mcap, t->nbeg, t->nend,
                                                 t->nlev, t->px, t->py, t->pz, P, t->mbits, t->nmom,
-                                                t->ncom, status); note_launch();
+                                                t->ncom, status);
 }
 
 }  // namespace og

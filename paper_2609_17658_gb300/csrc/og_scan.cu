@@ -59,6 +59,7 @@ __device__ uint32_t block_exclusive(uint32_t v, uint32_t *s_warp, uint32_t *tota
 template <class Op>
 __global__ void __launch_bounds__(kScanThreads) k_tile_reduce(const uint32_t *__restrict__ in,
                                                                int64_t n, uint32_t *tile_tot) {
+    pdl_wait();
     __shared__ uint32_t s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     uint32_t acc = Op::id();
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_downsweep(const uint32_t 
                                                                   uint32_t *out, int64_t n,
                                                                   const uint32_t *tile_tot,
                                                                   uint32_t *d_total) {
+    pdl_wait();
     __shared__ uint32_t s_items[kScanTile];
     __shared__ uint32_t s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -126,10 +128,10 @@ void scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, 
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     uint32_t *tile = static_cast<uint32_t *>(scratch);
     if (ntiles > 1) {
-        k_tile_reduce<Op><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tile); note_launch();
+        launch_pdl(k_tile_reduce<Op>, (unsigned)ntiles, kScanThreads, 0, s, in, n, tile);
     }
-    k_tile_downsweep<Op, kExclusive><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tile,
-                                                                             d_total); note_launch();
+    launch_pdl(k_tile_downsweep<Op, kExclusive>, (unsigned)ntiles, kScanThreads, 0, s, in, out, n, tile,
+                                                                             d_total);
 }
 
 }  // namespace

@@ -55,6 +55,7 @@ __device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t *warp_t
 __global__ void __launch_bounds__(kThreads) k_upsweep(const uint64_t *__restrict__ keys, int64_t n,
                                                       int shift, uint32_t *counts,
                                                       int64_t ntiles, const uint32_t *hist8) {
+    pdl_wait();
     __shared__ uint32_t hist[kWarps][kRadix];
     const int warp = threadIdx.x >> 5;
     if (trivial_pass(hist8, shift, n)) return;
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const uint64_t *__restrict
 // histogram of all eight digit positions over all keys (to skip trivial passes)
 __global__ void __launch_bounds__(kThreads) k_all_digits(const uint64_t *__restrict__ keys,
                                                          int64_t n, uint32_t *hist8) {
+    pdl_wait();
     __shared__ uint32_t h[8][kRadix];
     for (int i = threadIdx.x; i < 8 * kRadix; i += kThreads) (&h[0][0])[i] = 0;
     __syncthreads();
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const uint64_t *__restri
                                                         int shift, const uint32_t *offsets,
                                                         int64_t ntiles, const uint32_t *hist8,
                                                         int fused) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DownSmem &S = *reinterpret_cast<DownSmem *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -240,7 +243,7 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     cudaMemsetAsync(hist8, 0, 8 * kRadix * sizeof(uint32_t), s);
     int grid = (int)((n + kThreads * 16 - 1) / (kThreads * 16));
     if (grid > 1184) grid = 1184;
-    k_all_digits<<<grid, kThreads, 0, s>>>(keys, n, hist8); note_launch();
+    launch_pdl(k_all_digits, grid, kThreads, 0, s, keys, n, hist8);
     const int fused = ntiles <= kFusedTiles ? 1 : 0;
 
     static bool attr_set = false;
@@ -254,11 +257,11 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     int npasses = (bits + 7) / 8;
     for (int pass = 0; pass < npasses; ++pass) {
         int shift = 8 * pass;
-        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles, hist8); note_launch();
+        launch_pdl(k_upsweep, (unsigned)ntiles, kThreads, 0, s, kin, n, shift, counts, ntiles, hist8);
         if (!fused) scan_exclusive_u32(counts, counts, (int64_t)kRadix * ntiles, nullptr, scan_scratch, s);
-        k_downsweep<<<(unsigned)ntiles, kThreads, sizeof(DownSmem), s>>>(kin, vin, kout, vout, n,
+        launch_pdl(k_downsweep, (unsigned)ntiles, kThreads, sizeof(DownSmem), s, kin, vin, kout, vout, n,
                                                                          shift, counts, ntiles, hist8,
-                                                                         fused); note_launch();
+                                                                         fused);
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
     }
@@ -282,11 +285,11 @@ void radix_sort_pairs_every_pass(uint64_t *keys, uint32_t *vals, uint64_t *keys_
     const int npasses = (bits + 7) / 8;
     for (int pass = 0; pass < npasses; ++pass) {
         const int shift = 8 * pass;
-        k_upsweep<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, n, shift, counts, ntiles, nullptr); note_launch();
+        launch_pdl(k_upsweep, (unsigned)ntiles, kThreads, 0, s, kin, n, shift, counts, ntiles, nullptr);
         scan_exclusive_u32(counts, counts, (int64_t)kRadix * ntiles, nullptr, scan_scratch, s);
-        k_downsweep<<<(unsigned)ntiles, kThreads, sizeof(DownSmem), s>>>(kin, vin, kout, vout, n,
+        launch_pdl(k_downsweep, (unsigned)ntiles, kThreads, sizeof(DownSmem), s, kin, vin, kout, vout, n,
                                                                          shift, counts, ntiles, nullptr,
-                                                                         0); note_launch();
+                                                                         0);
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
     }
