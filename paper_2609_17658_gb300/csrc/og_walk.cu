@@ -535,9 +535,8 @@ __global__ void __maxnreg__(kPot ? 128 : 96) k_walk(WalkArgs a) {
         }
         // lane -> (target, replica): P lanes per replica, R = 32 / P replicas
         const int P = gsize > 16u ? 32 : gsize > 8u ? 16 : gsize > 4u ? 8 : gsize > 2u ? 4 : gsize > 1u ? 2 : 1;
-        const int lp = __ffs(P) - 1;  // P is a power of two
-        const int R = 32 >> lp;
-        const int tl = lane & (P - 1), rep = lane >> lp;
+        const int R = 32 / P;
+        const int tl = lane & (P - 1), rep = lane / P;
         const uint32_t i = gb + tl;
         const bool active = (uint32_t)tl < gsize;
         const uint32_t xi = active ? T.px[i] : 0u;

@@ -44,6 +44,7 @@ def _compare_refit(gt, ot):
     inv = np.empty(m, dtype=np.int64)
     inv[gmap] = np.arange(m)
     assert np.array_equal(gt.export(og.OG_F_MASS)[inv].view(np.uint64), ot.get(oracle.F_MASS).view(np.uint64))
+    assert np.array_equal(gt.export(og.OG_F_MSUM)[inv].view(np.uint64), ot.get(oracle.F_MSUM).view(np.uint64))
     assert np.array_equal(gt.export(og.OG_F_COM)[inv], ot.get(oracle.F_COM))
     ext = gt.export(og.OG_F_EXTENT)
     assert np.array_equal(ext[0][inv], ot.get(oracle.F_EXT_S))
@@ -104,3 +105,21 @@ def test_refit_rejects_wrong_input(ctx):
     bad[3, 2] = np.inf
     with pytest.raises(og.OGError):
         gt.refit(bad)
+
+
+def test_refit_exact_moments_with_spread_masses(ctx):
+    """The refit's moments are the same exact sums as the build's: masses spread
+    over 2^-20..2^20 and some zero, positions drifted across cells and the
+    periodic boundary; node masses, sums and centres of mass bitwise the oracle's."""
+    r = np.random.default_rng(41)
+    pos, _, prm = gi.config("clustered-2m", n=30000)
+    mass = np.ldexp(1.0 + r.random(len(pos)), r.integers(-20, 21, len(pos)))
+    mass[r.random(len(pos)) < 0.1] = 0.0
+    prm = dict(prm, opening=gi.OPEN_BH)
+    gt = og.Tree(ctx, pos, mass, prm)
+    ot = oracle.Tree(pos, mass, prm)
+    for k, scale in enumerate((3e-4, 3e-3)):
+        pos = _drift(pos, 50 + k, scale)
+        gt.refit(pos)
+        ot.refit(pos)
+        _compare_refit(gt, ot)
