@@ -10,11 +10,13 @@
 //
 //   a1/a2  k_quantize_keys   f64 positions -> u32 fixed point -> 63-bit Morton key
 //   a3     radix sort (og_sort.cu), k_permute gathers sorted SoA positions/masses
-//   a4     k_split_levels   level of every adjacent-key split (shared 3-bit digits)
-//          k_split_nodes    the node a split belongs to: its key range (galloping
-//                           search on key prefixes) and whether it is the node's
-//                           first split; first splits are numbered by a scan
-//          k_split_node_id  node id of every split
+//   a4     k_split_tiles    level of every adjacent-key split (shared 3-bit digits)
+//          k_split_carry    and, per level threshold, the nearest lower split
+//          k_split_ranges   across tiles; the node a split belongs to: its key
+//                           range (nearest lower splits on both sides) and whether
+//                           it is the node's first split; first splits are
+//                           numbered by a scan
+//          k_node_init      nodes of first splits, node id of every split
 //          k_link           parent of every node, owner node of every particle,
 //                           octant-occupancy bits of every node
 //          k_place          child array in key order, grouped by parent
@@ -185,70 +187,204 @@ __global__ void k_permute(int64_t n, const uint32_t *__restrict__ perm,
     pm32[i] = __double2float_rn(m);
 }
 
-__global__ void k_split_levels(const uint64_t *__restrict__ skey, const uint32_t *__restrict__ sseg,
-                               int64_t n, uint8_t *lv) {
-    pdl_wait();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    lv[i] = (sseg[i] != sseg[i + 1]) ? kSep : (uint8_t)lcp_levels(skey[i], skey[i + 1]);
+// The node of a split of level L is the key range around it whose adjacent
+// splits all have levels >= L (the lcp of two sorted keys is the smallest
+// split level between them); so its ends are the nearest splits of a level
+// below L on either side (a box boundary counts as below every level).  The
+// levels take 23 values, so "nearest split below t" is answered for every
+// threshold t at once: a ballot per threshold inside a warp, a fold over the
+// warps of a tile, and a scan over the tiles.
+constexpr int kSplitTile = 1024;       // splits per block
+constexpr int kNT = kLevels + 2;       // thresholds t = 0 .. kLevels + 1: level < t
+constexpr int kNone = 0x7fffffff;      // no split below t on the right
+
+// a split's level as an ordered value: a box boundary below every level
+__device__ __forceinline__ int split_rank(uint8_t v) { return v == kSep ? -1 : (int)v; }
+
+// per warp and threshold t: the lanes whose split lies below t, and the last
+// and first such split index (-1 / kNone when there is none)
+__device__ __forceinline__ void warp_below(int v, int64_t base, int lane, unsigned &mine_m, int &mine_l,
+                                           int &mine_f) {
+#pragma unroll
+    for (int t = 0; t < kNT; ++t) {
+        const unsigned m = __ballot_sync(0xffffffffu, v < t);
+        if (lane == t) {
+            mine_m = m;
+            mine_l = m ? (int)(base + 31 - __clz(m)) : -1;
+            mine_f = m ? (int)(base + __ffs(m) - 1) : kNone;
+        }
+    }
 }
 
-// Node of split i: the maximal key range around i whose keys share lv[i]
-// leading digits.  It is the node's first split iff no split of the same
-// level lies between the range start and i.
-__global__ void k_split_nodes(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ lv,
-                              const uint32_t *__restrict__ sseg, const uint32_t *__restrict__ seg_off,
-                              int64_t n, uint32_t *sb, uint32_t *se, uint32_t *first) {
+// levels of all splits; per tile and threshold, its last and first split below t
+__global__ void __launch_bounds__(kSplitTile) k_split_tiles(const uint64_t *__restrict__ skey,
+                                                            const uint32_t *__restrict__ sseg, int64_t nsplit,
+                                                            uint8_t *lv, int *tlast, int *tfirst) {
     pdl_wait();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    if (lv[i] == kSep) {
-        sb[i] = se[i] = 0;
-        first[i] = 0;
+    __shared__ int wl[32][kNT], wf[32][kNT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kSplitTile + threadIdx.x;
+    int v = kNT;  // past the last split: below no threshold
+    if (i < nsplit) {
+        const uint8_t l = (sseg[i] != sseg[i + 1]) ? kSep : (uint8_t)lcp_levels(skey[i], skey[i + 1]);
+        lv[i] = l;
+        v = split_rank(l);
+    }
+    unsigned m = 0u;
+    int ml = -1, mf = kNone;
+    warp_below(v, (int64_t)blockIdx.x * kSplitTile + warp * 32, lane, m, ml, mf);
+    if (lane < kNT) {
+        wl[warp][lane] = ml;
+        wf[warp][lane] = mf;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNT) {
+        const int t = threadIdx.x;
+        int r = -1;
+        for (int w = 0; w < 32; ++w) r = max(r, wl[w][t]);
+        tlast[blockIdx.x * kNT + t] = r;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + kNT) {
+        const int t = threadIdx.x - 32;
+        int r = kNone;
+        for (int w = 0; w < 32; ++w) r = min(r, wf[w][t]);
+        tfirst[blockIdx.x * kNT + t] = r;
+    }
+}
+
+// per tile and threshold t: the last split below t in the tiles before it and
+// the first one in the tiles after it (one block per threshold)
+__global__ void __launch_bounds__(kSplitTile) k_split_carry(int64_t ntiles, const int *__restrict__ tlast,
+                                                            const int *__restrict__ tfirst, int *clast,
+                                                            int *cfirst) {
+    pdl_wait();
+    __shared__ int ws[32];
+    const int t = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // left to right: exclusive running maximum of tlast
+    int run = -1;
+    for (int64_t c0 = 0; c0 < ntiles; c0 += kSplitTile) {
+        const int64_t k = c0 + threadIdx.x;
+        const int x = k < ntiles ? tlast[k * kNT + t] : -1;
+        int inc = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc = max(inc, o);
+        }
+        if (lane == 31) ws[warp] = inc;
+        __syncthreads();
+        int before = run;
+        for (int w = 0; w < warp; ++w) before = max(before, ws[w]);
+        const int ex = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane > 0) before = max(before, ex);
+        if (k < ntiles) clast[k * kNT + t] = before;
+        for (int w = 0; w < 32; ++w) run = max(run, ws[w]);
+        __syncthreads();
+    }
+    // right to left: exclusive running minimum of tfirst
+    run = kNone;
+    for (int64_t c0 = 0; c0 < ntiles; c0 += kSplitTile) {
+        const int64_t k = ntiles - 1 - (c0 + threadIdx.x);  // thread 0 takes the last tile
+        const int x = k >= 0 ? tfirst[k * kNT + t] : kNone;
+        int inc = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc = min(inc, o);
+        }
+        if (lane == 31) ws[warp] = inc;
+        __syncthreads();
+        int after = run;
+        for (int w = 0; w < warp; ++w) after = min(after, ws[w]);
+        const int ex = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane > 0) after = min(after, ex);
+        if (k >= 0) cfirst[k * kNT + t] = after;
+        for (int w = 0; w < 32; ++w) run = min(run, ws[w]);
+        __syncthreads();
+    }
+}
+
+// Node of every split: its key range [sb, se) (written for first splits), and
+// whether it is its node's first split: no split of the same level between the
+// range start and it.  A later split of the node keeps the nearest split to
+// its left of a level <= L (prevle), which is the node's previous split, or
+// at level kLevels the node's first split.
+__global__ void __launch_bounds__(kSplitTile) k_split_ranges(const uint8_t *__restrict__ lv, int64_t nsplit,
+                                                             const int *__restrict__ clast,
+                                                             const int *__restrict__ cfirst, uint32_t *sb,
+                                                             uint32_t *se, uint32_t *first, uint32_t *prevle) {
+    pdl_wait();
+    __shared__ unsigned wm[32][kNT];
+    __shared__ int wl[32][kNT], wf[32][kNT];
+    __shared__ int pl[32][kNT], pf[32][kNT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kSplitTile + threadIdx.x;
+    const int v = i < nsplit ? split_rank(lv[i]) : kNT;
+    const int64_t base = (int64_t)blockIdx.x * kSplitTile + warp * 32;
+    unsigned m = 0u;
+    int ml = -1, mf = kNone;
+    warp_below(v, base, lane, m, ml, mf);
+    if (lane < kNT) {
+        wm[warp][lane] = m;
+        wl[warp][lane] = ml;
+        wf[warp][lane] = mf;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNT) {
+        const int t = threadIdx.x;
+        int r = clast[blockIdx.x * kNT + t];
+        for (int w = 0; w < 32; ++w) {
+            pl[w][t] = r;
+            r = max(r, wl[w][t]);
+        }
+    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + kNT) {
+        const int t = threadIdx.x - 32;
+        int r = cfirst[blockIdx.x * kNT + t];
+        for (int w = 31; w >= 0; --w) {
+            pf[w][t] = r;
+            r = min(r, wf[w][t]);
+        }
+    }
+    __syncthreads();
+    if (i >= nsplit) return;
+    if (v < 0) {  // a boundary between two boxes
+        first[i] = 0u;
         return;
     }
-    const int L = lv[i];
-    const uint64_t ki = skey[i];
-    const uint32_t sg = sseg[i];
-    const int64_t lo_bound = seg_off[sg], hi_bound = seg_off[sg + 1];  // this box's particles
-    // smallest b <= i with lcp(skey[b], ki) >= L: gallop left, then bisect
-    int64_t ok = i, step = 1, bad = lo_bound - 1;
-    while (true) {
-        int64_t j = i - step;
-        if (j < lo_bound) { bad = lo_bound - 1; break; }
-        if (lcp_levels(skey[j], ki) >= L) { ok = j; step <<= 1; }
-        else { bad = j; break; }
+    const int L = v;
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned above = lane == 31 ? 0u : (0xfffffffeu << lane);
+    const unsigned mL = wm[warp][L], mL1 = wm[warp][L + 1];
+    // nearest split of a level < L to the left (or -1) and to the right (or the end)
+    const int left = (mL & below) ? (int)(base + 31 - __clz(mL & below)) : pl[warp][L];
+    int right = (mL & above) ? (int)(base + __ffs(mL & above) - 1) : pf[warp][L];
+    if (right > (int)nsplit) right = (int)nsplit;
+    // nearest split of a level <= L to the left
+    const int le = (mL1 & below) ? (int)(base + 31 - __clz(mL1 & below)) : pl[warp][L + 1];
+    const bool isfirst = L >= 1 && le == left;
+    first[i] = isfirst ? 1u : 0u;
+    if (isfirst) {
+        sb[i] = (uint32_t)(left + 1);
+        se[i] = (uint32_t)(right + 1);
+    } else {
+        // a node of level < kLevels has at most 7 splits of its level; one of
+        // level kLevels (a run of equal keys) any number, and its first split
+        // is the range start
+        prevle[i] = (uint32_t)(L == kLevels ? left + 1 : le);
     }
-    while (ok - bad > 1) {
-        int64_t mid = bad + (ok - bad) / 2;
-        if (lcp_levels(skey[mid], ki) >= L) ok = mid; else bad = mid;
-    }
-    const int64_t b = ok;
-    // largest e-1 >= i+1 with lcp(ki, skey[e-1]) >= L
-    ok = i + 1;
-    step = 1;
-    int64_t badr = hi_bound;
-    while (true) {
-        int64_t j = i + 1 + step;
-        if (j >= hi_bound) { badr = hi_bound; break; }
-        if (lcp_levels(ki, skey[j]) >= L) { ok = j; step <<= 1; }
-        else { badr = j; break; }
-    }
-    while (badr - ok > 1) {
-        int64_t mid = ok + (badr - ok) / 2;
-        if (lcp_levels(ki, skey[mid]) >= L) ok = mid; else badr = mid;
-    }
-    sb[i] = (uint32_t)b;
-    se[i] = (uint32_t)(ok + 1);
-    first[i] = (L >= 1 && (b == i || lcp_levels(skey[b], ki) > L)) ? 1u : 0u;
 }
 
+// Roots, the nodes of first splits (level, key range, cell origin), and the
+// node id of every split: its box's root at level 0, else the node of the
+// first split reached along prevle (at most 7 steps).
 __global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ seg_off,
                             const uint32_t *__restrict__ first, const uint32_t *__restrict__ nid,
                             const uint8_t *__restrict__ lv, const uint32_t *__restrict__ sb,
-                            const uint32_t *__restrict__ se, const uint32_t *__restrict__ px,
+                            const uint32_t *__restrict__ se, const uint32_t *__restrict__ prevle,
+                            const uint32_t *__restrict__ sseg, const uint32_t *__restrict__ px,
                             const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
-                            uint8_t *nlev, uint32_t *nbeg, uint32_t *nend, uint32_t *norg) {
+                            uint8_t *nlev, uint32_t *nbeg, uint32_t *nend, uint32_t *norg, uint32_t *sid,
+                            uint32_t *status) {
     pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < B) {  // the root of box i covers the whole box
@@ -257,40 +393,35 @@ __global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ s
         nend[i] = seg_off[i + 1];
         norg[3 * i + 0] = norg[3 * i + 1] = norg[3 * i + 2] = 0u;
     }
-    if (i >= n - 1 || !first[i]) return;
-    const uint32_t id = (uint32_t)B + nid[i];
-    const int L = lv[i];
-    nlev[id] = (uint8_t)L;
-    nbeg[id] = sb[i];
-    nend[id] = se[i];
-    // the cell: the top L bits of every coordinate of its particles
-    const uint32_t mask = ~(uint32_t)((1ull << (32 - L)) - 1ull);
-    const uint32_t q = sb[i];
-    norg[3 * id + 0] = px[q] & mask;
-    norg[3 * id + 1] = py[q] & mask;
-    norg[3 * id + 2] = pz[q] & mask;
-}
-
-__global__ void k_split_node_id(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ lv,
-                                const uint32_t *__restrict__ sb, const uint32_t *__restrict__ first,
-                                const uint32_t *__restrict__ nid, const uint32_t *__restrict__ sseg,
-                                int64_t n, int64_t B, uint32_t *sid) {
-    pdl_wait();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     const int L = lv[i];
     if (L == kSep) { sid[i] = 0xffffffffu; return; }
     if (L == 0) { sid[i] = sseg[i]; return; }  // the root of this box
-    if (first[i]) { sid[i] = (uint32_t)B + nid[i]; return; }
-    // first split f in [b, i]: smallest j with lcp(skey[b], skey[j+1]) == L
-    const int64_t b = sb[i];
-    const uint64_t kb = skey[b];
-    int64_t lo = b, hi = i;  // answer in [lo, hi]; hi satisfies the predicate
-    while (lo < hi) {
-        int64_t mid = lo + (hi - lo) / 2;
-        if (lcp_levels(kb, skey[mid + 1]) <= L) hi = mid; else lo = mid + 1;
+    if (first[i]) {
+        const uint32_t id = (uint32_t)B + nid[i];
+        sid[i] = id;
+        nlev[id] = (uint8_t)L;
+        nbeg[id] = sb[i];
+        nend[id] = se[i];
+        // the cell: the top L bits of every coordinate of its particles
+        const uint32_t mask = ~(uint32_t)((1ull << (32 - L)) - 1ull);
+        const uint32_t q = sb[i];
+        norg[3 * id + 0] = px[q] & mask;
+        norg[3 * id + 1] = py[q] & mask;
+        norg[3 * id + 2] = pz[q] & mask;
+        return;
     }
-    sid[i] = (uint32_t)B + nid[lo];
+    uint32_t j = prevle[i];
+    for (int guard = 0;; ++guard) {
+        if (guard > 7 || (int64_t)j >= n - 1) {
+            atomicOr(status, ST_INTERNAL);
+            sid[i] = sseg[i];
+            return;
+        }
+        if (first[j]) break;
+        j = prevle[j];
+    }
+    sid[i] = (uint32_t)B + nid[j];
 }
 
 __device__ __forceinline__ int split_at(const uint8_t *lv, int64_t j, int64_t n) {
@@ -1037,6 +1168,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         add(4, n); add(4, n); add(4, n);                        // qx qy qz
         add(8, n); add(4, n); add(8, n); add(4, n); add(8, n); add(4, n);  // keys, idx, alt, key copy, pseg
         add(1, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // lv sb se first nid sid
+        add(4, 4 * kNT * ((n + kSplitTile - 1) / kSplitTile));  // split tile summaries
         add(4, n + B);                  // nnc
         add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs gid unit
         sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + B + 8) +
@@ -1057,7 +1189,11 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     uint8_t *lv = W.take<uint8_t>(n);
     uint32_t *sbeg = W.take<uint32_t>(n), *send = W.take<uint32_t>(n);
     uint32_t *first = W.take<uint32_t>(n), *nid = W.take<uint32_t>(n), *sid = W.take<uint32_t>(n);
+    int *tsum = W.take<int>(4 * kNT * ((n + kSplitTile - 1) / kSplitTile));
     uint32_t *occ = t->nocc, *nnc = W.take<uint32_t>(n + B);
+    // a split's previous split in its node: needed only until k_node_init,
+    // before nnc is first cleared
+    uint32_t *prevle = nnc;
     uint32_t *fp = W.take<uint32_t>(n), *rs = W.take<uint32_t>(n), *gs = W.take<uint32_t>(n);
     uint32_t *gid = W.take<uint32_t>(n);
     uint32_t *unit = W.take<uint32_t>(n);
@@ -1114,18 +1250,21 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     int64_t nsplit = n - 1;
     cudaMemsetAsync(d_tot, 0, 4 * sizeof(uint32_t), s);
     if (nsplit > 0) {
-        launch_pdl(k_split_levels, nblk(nsplit), kT, 0, s, t->skey, t->sseg, n, lv);
-        launch_pdl(k_split_nodes, nblk(nsplit), kT, 0, s, t->skey, lv, t->sseg, t->seg_off, n, sbeg, send,
-                                                  first);
+        const int64_t ntiles = (nsplit + kSplitTile - 1) / kSplitTile;
+        int *tlast = tsum, *tfirst = tsum + ntiles * kNT;
+        int *clast = tsum + 2 * ntiles * kNT, *cfirst = tsum + 3 * ntiles * kNT;
+        launch_pdl(k_split_tiles, dim3((unsigned)ntiles), kSplitTile, 0, s, t->skey, t->sseg, nsplit, lv, tlast,
+                   tfirst);
+        launch_pdl(k_split_carry, dim3(kNT), kSplitTile, 0, s, ntiles, (const int *)tlast, (const int *)tfirst,
+                   clast, cfirst);
+        launch_pdl(k_split_ranges, dim3((unsigned)ntiles), kSplitTile, 0, s, (const uint8_t *)lv, nsplit,
+                   (const int *)clast, (const int *)cfirst, sbeg, send, first, prevle);
         scan_exclusive_u32(first, nid, nsplit, d_tot, scan_scratch, s);
     }
     const uint32_t *nsp = d_tot;
     launch_pdl(k_node_init, nblk(nsplit > B ? nsplit : B), kT, 0, s, n, B, t->seg_off, first, nid, lv, sbeg,
-                                                            send, t->px, t->py, t->pz, t->nlev,
-                                                            t->nbeg, t->nend, t->norg);
-    if (nsplit > 0) {
-        launch_pdl(k_split_node_id, nblk(nsplit), kT, 0, s, t->skey, lv, sbeg, first, nid, t->sseg, n, B, sid);
-    }
+                                                            send, prevle, t->sseg, t->px, t->py, t->pz,
+                                                            t->nlev, t->nbeg, t->nend, t->norg, sid, status);
     cudaMemsetAsync(occ, 0, mcap * sizeof(uint32_t), s);
     cudaMemsetAsync(nnc, 0, mcap * sizeof(uint32_t), s);
     // child counts beyond the last node stay 0, so the scan over mcap entries

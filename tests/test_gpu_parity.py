@@ -62,6 +62,16 @@ def _case(name):
         pos += np.repeat(np.arange(8) * 1e-3, 4)[:, None]
         prm = gi.default_params(eps=1e-3, r_s=0.0)   # no cutoff: half-box pairs interact
         return pos, np.full(32, 1 / 32), prm
+    if name == "equal-runs":
+        # runs of 1500 equal positions that straddle the 1024-split tiles of
+        # the node-range kernels, beside runs at nearby and distant cells
+        r = np.random.default_rng(9)
+        pos = r.random((6000, 3))
+        pos[700:2200] = [0.25, 0.5, 0.75]
+        pos[2200:3700] = [0.25, 0.5, 0.75 + 2.0 ** -32]
+        pos[3700:3720] = [0.9, 0.1, 0.4]
+        pos[5000:5999] = [0.25, 0.5, 0.75]
+        return pos, np.full(6000, 1 / 6000), base
     if name == "lattice":
         pos, mass = gi.lattice(16)
         return pos, mass, gi.default_params(eps=1e-3, r_s=0.05)
@@ -69,7 +79,7 @@ def _case(name):
 
 
 BUILD_CASES = ["uniform-32k", "halo-20k", "n=1", "n=2", "n=7", "n=8", "n=9", "n=33", "identical",
-               "cell-faces", "box-edges", "half-box", "lattice"]
+               "cell-faces", "box-edges", "half-box", "lattice", "equal-runs"]
 
 
 @pytest.mark.parametrize("name", BUILD_CASES)
