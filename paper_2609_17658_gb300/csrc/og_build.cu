@@ -1218,7 +1218,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
                                            qz, keys, B > 1 ? key0 : nullptr, idx, status);
     // a3: by key, then (several boxes) stably by box
     bool in_alt = false;
-    radix_sort_pairs(keys, idx, keys_alt, idx_alt, n, 63, sort_scratch, s, &in_alt);
+    radix_sort_pairs(keys, idx, keys_alt, idx_alt, n, 63, sort_scratch, s, &in_alt, status);
     if (B > 1) {
         uint32_t *perm1 = in_alt ? idx_alt : idx;
         uint64_t *segkey = in_alt ? keys : keys_alt;      // the free key buffer
@@ -1228,7 +1228,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         int bits = 1;
         while ((1ll << bits) < B) ++bits;
         bool alt2 = false;
-        radix_sort_pairs(segkey, perm1, segkey_alt, perm1_alt, n, bits, sort_scratch, s, &alt2);
+        radix_sort_pairs(segkey, perm1, segkey_alt, perm1_alt, n, bits, sort_scratch, s, &alt2, status);
         const uint32_t *perm_src = alt2 ? perm1_alt : perm1;
         cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         launch_pdl(k_gather_keys, nblk(n), kT, 0, s, n, t->perm, key0, pseg, t->skey, t->sseg);

@@ -250,7 +250,8 @@ void scan_inclusive_max_u32(const uint32_t *in, uint32_t *out, int64_t n, void *
 // radix sort of (key, value) pairs, stable, keys of `bits` significant bits
 size_t radix_sort_scratch_bytes(int64_t n);
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                      int64_t n, int bits, void *scratch, cudaStream_t s, bool *result_in_alt);
+                      int64_t n, int bits, void *scratch, cudaStream_t s, bool *result_in_alt,
+                      uint32_t *status);
 
 // the same sort with every digit pass run (no histogram read-back, no host
 // synchronisation); with an even pass count the result is back in keys/vals

@@ -1030,7 +1030,7 @@ og_status walk_pass(og_tree *t, int opening, bool first_pass, const float *a_old
         void *scr = v1 + ng + 64;
         k_cost_keys<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(ng, t->gcost, k0, v0); note_launch();
         bool alt = false;
-        radix_sort_pairs(k0, v0, k1, v1, ng, 8, scr, s, &alt);
+        radix_sort_pairs(k0, v0, k1, v1, ng, 8, scr, s, &alt, t->ctx->d_status);
         cudaMemcpyAsync(t->gorder, alt ? v1 : v0, ng * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         a.tree0.gorder = t->gorder;
     }
@@ -1140,7 +1140,7 @@ og_status walk_multi(og_ctx *c, og_tree *const *trees, int64_t ntrees, int openi
     cudaMemcpyAsync(doff, hoff.data(), (ntrees + 1) * 8, cudaMemcpyHostToDevice, s);
     k_item_keys<<<(unsigned)((nitems + 255) / 256), 256, 0, s>>>(nitems, ntrees, doff, dv, k0, v0); note_launch();
     bool alt = false;
-    radix_sort_pairs(k0, v0, k1, v1, nitems, 8, scr, s, &alt);
+    radix_sort_pairs(k0, v0, k1, v1, nitems, 8, scr, s, &alt, c->d_status);
     WalkArgs a{};
     fill_common(a, c, nullptr);
     a.trees = dv;
