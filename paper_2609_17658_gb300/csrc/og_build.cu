@@ -10,6 +10,7 @@
 //
 //   a1/a2  k_quantize_keys   f64 positions -> u32 fixed point -> 63-bit Morton key
 //   a3     radix sort (og_sort.cu), k_permute gathers sorted SoA positions/masses
+//                           and the masses' set-bit span
 //   a4     k_split_tiles    level of every adjacent-key split (shared 3-bit digits)
 //          k_split_carry    and, per level threshold, the nearest lower split
 //          k_split_ranges   across tiles; the node a split belongs to: its key
@@ -127,13 +128,22 @@ __global__ void k_fill_seg(int64_t n, int64_t B, const uint32_t *__restrict__ se
     pseg[i] = (uint32_t)lo;
 }
 
+// In a build (d_tot set) it also clears what later kernels accumulate into:
+// the device totals, the masses' set-bit span (empty: lowest 0x7f7f7f7f
+// above highest 0x80808080), and with one box its sorted box indices (all 0).
 __global__ void k_quantize_keys(const double *__restrict__ pos, int64_t n, const uint32_t *__restrict__ pseg,
                                 const SegGeom *__restrict__ geom, uint32_t *qx, uint32_t *qy,
                                 uint32_t *qz, uint64_t *key, uint64_t *key_copy, uint32_t *idx,
-                                uint32_t *status) {
+                                uint32_t *sseg_zero, uint32_t *d_tot, int *mbits, uint32_t *status) {
     pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && d_tot) {
+        d_tot[0] = d_tot[1] = d_tot[2] = d_tot[3] = 0u;
+        mbits[0] = 0x7f7f7f7f;
+        mbits[1] = (int)0x80808080u;
+    }
     if (i >= n) return;
+    if (sseg_zero) sseg_zero[i] = 0u;
     const SegGeom g = geom[pseg ? pseg[i] : 0];
     const double box = g.box, inv_box = g.inv_box;
     const bool pow2 = g.pow2 != 0;
@@ -169,22 +179,46 @@ __global__ void k_gather_keys(int64_t n, const uint32_t *__restrict__ perm,
     sseg[i] = pseg[j];
 }
 
-__global__ void k_permute(int64_t n, const uint32_t *__restrict__ perm,
-                          const uint32_t *__restrict__ qx, const uint32_t *__restrict__ qy,
-                          const uint32_t *__restrict__ qz, const double *__restrict__ mass,
-                          uint32_t *px, uint32_t *py, uint32_t *pz, float *pm32, double *pm64,
-                          uint32_t *status) {
+// Positions and masses in key order; the masses are checked here, and their
+// set-bit span (the units of the exact moments) is gathered: a block's lowest
+// and highest exponents, merged by atomics only where they widen the span.
+__global__ void __launch_bounds__(kT) k_permute(int64_t n, const uint32_t *__restrict__ perm,
+                                                const uint32_t *__restrict__ qx, const uint32_t *__restrict__ qy,
+                                                const uint32_t *__restrict__ qz, const double *__restrict__ mass,
+                                                uint32_t *px, uint32_t *py, uint32_t *pz, float *pm32,
+                                                double *pm64, int *mbits, uint32_t *status) {
     pdl_wait();
+    __shared__ int wlo[kT / 32], whi[kT / 32];
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t j = perm[i];
-    px[i] = qx[j];
-    py[i] = qy[j];
-    pz[i] = qz[j];
-    double m = mass[j];
-    if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
-    pm64[i] = m;
-    pm32[i] = __double2float_rn(m);
+    int lo = 0x7fffffff, hi = (int)0x80000000;
+    if (i < n) {
+        uint32_t j = perm[i];
+        px[i] = qx[j];
+        py[i] = qy[j];
+        pz[i] = qz[j];
+        double m = mass[j];
+        if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
+        pm64[i] = m;
+        pm32[i] = __double2float_rn(m);
+        mass_bit_span(m, lo, hi);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31u) == 0u) {
+        wlo[threadIdx.x >> 5] = lo;
+        whi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kT / 32; ++w) {
+            lo = min(lo, wlo[w]);
+            hi = max(hi, whi[w]);
+        }
+        if (lo <= hi) {
+            if (lo < __ldcg(&mbits[0])) atomicMin(&mbits[0], lo);
+            if (hi > __ldcg(&mbits[1])) atomicMax(&mbits[1], hi);
+        }
+    }
 }
 
 // The node of a split of level L is the key range around it whose adjacent
@@ -374,8 +408,8 @@ __global__ void __launch_bounds__(kSplitTile) k_split_ranges(const uint8_t *__re
     }
 }
 
-// Roots, the nodes of first splits (level, key range, cell origin), and the
-// node id of every split: its box's root at level 0, else the node of the
+// Roots, the nodes of first splits (level, key range, cell origin), cleared
+// per-node accumulators, and the node id of every split: its box's root at level 0, else the node of the
 // first split reached along prevle (at most 7 steps).
 __global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ seg_off,
                             const uint32_t *__restrict__ first, const uint32_t *__restrict__ nid,
@@ -384,9 +418,14 @@ __global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ s
                             const uint32_t *__restrict__ sseg, const uint32_t *__restrict__ px,
                             const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
                             uint8_t *nlev, uint32_t *nbeg, uint32_t *nend, uint32_t *norg, uint32_t *sid,
-                            uint32_t *status) {
+                            int64_t mcap, uint32_t *occ, uint32_t *nnc, uint32_t *nccnt, uint32_t *status) {
     pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < mcap) {  // per-node accumulators of the kernels that follow
+        occ[i] = 0u;
+        nnc[i] = 0u;
+        nccnt[i] = 0u;
+    }
     if (i < B) {  // the root of box i covers the whole box
         nlev[i] = 0;
         nbeg[i] = seg_off[i];
@@ -1063,7 +1102,8 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
         launch_pdl(k_fill_seg, nblk(n), kT, 0, s, n, B, t->seg_off, pseg);
     }
     launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx,
-                                           qy, qz, keys, nullptr, idx, t->ctx->d_status);
+                                           qy, qz, keys, nullptr, idx, nullptr, nullptr, nullptr,
+                                           t->ctx->d_status);
     launch_pdl(k_repos, nblk(n), kT, 0, s, n, t->perm, qx, qy, qz, t->px, t->py, t->pz);
     node_moments(t, nullptr, t->nnodes, mom_scratch, s);
     extents_bottom_up(t, t->next_s, t->next_l);
@@ -1191,10 +1231,10 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     uint32_t *first = W.take<uint32_t>(n), *nid = W.take<uint32_t>(n), *sid = W.take<uint32_t>(n);
     int *tsum = W.take<int>(4 * kNT * ((n + kSplitTile - 1) / kSplitTile));
     uint32_t *occ = t->nocc, *nnc = W.take<uint32_t>(n + B);
-    // a split's previous split in its node: needed only until k_node_init,
-    // before nnc is first cleared
-    uint32_t *prevle = nnc;
     uint32_t *fp = W.take<uint32_t>(n), *rs = W.take<uint32_t>(n), *gs = W.take<uint32_t>(n);
+    // a split's previous split in its node: needed only until k_node_init,
+    // long before the groups' first use of fp
+    uint32_t *prevle = fp;
     uint32_t *gid = W.take<uint32_t>(n);
     uint32_t *unit = W.take<uint32_t>(n);
     void *sort_scratch = W.take<char>((int64_t)radix_sort_scratch_bytes(n));
@@ -1214,8 +1254,14 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     }
     // the masses are checked where they are first read (k_permute), so that a
     // host copy of them can still be in flight here
+    // one box: the keys and the permutation are sorted in place in the tree
+    if (B == 1) {
+        keys = t->skey;
+        idx = t->perm;
+    }
     launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx, qy,
-                                           qz, keys, B > 1 ? key0 : nullptr, idx, status);
+                                           qz, keys, B > 1 ? key0 : nullptr, idx, B > 1 ? nullptr : t->sseg,
+                                           d_tot, t->mbits, status);
     // a3: by key, then (several boxes) stably by box
     bool in_alt = false;
     radix_sort_pairs(keys, idx, keys_alt, idx_alt, n, 63, sort_scratch, s, &in_alt, status);
@@ -1232,23 +1278,20 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         const uint32_t *perm_src = alt2 ? perm1_alt : perm1;
         cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         launch_pdl(k_gather_keys, nblk(n), kT, 0, s, n, t->perm, key0, pseg, t->skey, t->sseg);
-    } else {
-        const uint64_t *skey_src = in_alt ? keys_alt : keys;
-        const uint32_t *perm_src = in_alt ? idx_alt : idx;
-        cudaMemcpyAsync(t->skey, skey_src, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(t->perm, perm_src, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
-        cudaMemsetAsync(t->sseg, 0, n * sizeof(uint32_t), s);
+    } else if (in_alt) {
+        // an odd number of passes left the result in the other buffers
+        cudaMemcpyAsync(t->skey, keys_alt, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(t->perm, idx_alt, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
     }
     if (t->mass_ready) cudaStreamWaitEvent(s, t->mass_ready, 0);
     launch_pdl(k_permute, nblk(n), kT, 0, s, n, t->perm, qx, qy, qz, d_mass, t->px, t->py, t->pz, t->pm32,
-                                     t->pm64, status);
+                                     t->pm64, t->mbits, status);
     // a4: nodes from splits.  The node count stays on the device (d_tot[0]
     // counts the first splits, m = B + that): the kernels up to the groups
     // read it there and are sized for the most nodes a tree can have, so the
     // host does not wait for it.
     uint32_t h_tot[4] = {0, 0, 0, 0};
     int64_t nsplit = n - 1;
-    cudaMemsetAsync(d_tot, 0, 4 * sizeof(uint32_t), s);
     if (nsplit > 0) {
         const int64_t ntiles = (nsplit + kSplitTile - 1) / kSplitTile;
         int *tlast = tsum, *tfirst = tsum + ntiles * kNT;
@@ -1262,14 +1305,12 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         scan_exclusive_u32(first, nid, nsplit, d_tot, scan_scratch, s);
     }
     const uint32_t *nsp = d_tot;
-    launch_pdl(k_node_init, nblk(nsplit > B ? nsplit : B), kT, 0, s, n, B, t->seg_off, first, nid, lv, sbeg,
-                                                            send, prevle, t->sseg, t->px, t->py, t->pz,
-                                                            t->nlev, t->nbeg, t->nend, t->norg, sid, status);
-    cudaMemsetAsync(occ, 0, mcap * sizeof(uint32_t), s);
-    cudaMemsetAsync(nnc, 0, mcap * sizeof(uint32_t), s);
-    // child counts beyond the last node stay 0, so the scan over mcap entries
-    // gives the node's child offsets and, as its total, the child entries
-    cudaMemsetAsync(t->nccnt, 0, mcap * sizeof(uint32_t), s);
+    // (mcap = n + B covers the splits and the roots too.)  Child counts beyond
+    // the last node stay 0, so the scan over mcap entries gives the nodes'
+    // child offsets and, as its total, the child entries.
+    launch_pdl(k_node_init, nblk(mcap), kT, 0, s, n, B, t->seg_off, first, nid, lv, sbeg, send, prevle,
+               t->sseg, t->px, t->py, t->pz, t->nlev, t->nbeg, t->nend, t->norg, sid, mcap, occ, nnc, t->nccnt,
+               status);
     launch_pdl(k_link, nblk(n + mcap), kT, 0, s, n, nsp, B, t->skey, lv, sid, t->sseg, t->nlev, t->nbeg,
                                          t->nend, t->npar, t->owner, occ, nnc, status);
     launch_pdl(k_ccnt, nblk(mcap), kT, 0, s, nsp, B, t->nlev, t->nbeg, t->nend, occ, t->nccnt);
@@ -1278,9 +1319,8 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
                                           t->npar, t->owner, t->child, t->npos, status);
     launch_pdl(k_threading, nblk(ccap), kT, 0, s, n, nsp, B, t->child, t->ncbeg, t->nccnt, t->npar,
                                           t->npos, t->owner, t->nnext, t->nsib, t->pnext, status);
-    // a5: exact moments and centres of mass of every node (the masses' set-bit
-    // span first: it fixes the integer units)
-    mass_span(t, s);
+    // a5: exact moments and centres of mass of every node (in units fixed by
+    // the masses' set-bit span, which k_permute gathered)
     node_moments(t, nsp, mcap, mom_scratch, s);
     // a6: groups (one group size for the whole forest)
     const int G = t->prm.group_max;

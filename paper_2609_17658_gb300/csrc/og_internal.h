@@ -263,9 +263,25 @@ void radix_sort_pairs_every_pass(uint64_t *keys, uint32_t *vals, uint64_t *keys_
 // then every node's mass, sums and centre of mass.  The node count is
 // B + *d_nsplit (device) or, with d_nsplit null, t->nnodes; at most mcap.
 size_t moments_scratch_bytes(int64_t n);
-// t->mbits: the lowest and highest set-bit exponents over the sorted masses
-void mass_span(og_tree *t, cudaStream_t s);
+// t->mbits holds the lowest and highest set-bit exponents over the masses
+// (gathered by the build's k_permute with mass_bit_span)
 void node_moments(og_tree *t, const uint32_t *d_nsplit, int64_t mcap, void *scratch, cudaStream_t s);
+
+// lowest and highest set-bit exponents of a mass: m = s 2^e (s < 2^53) has
+// bits from 2^lo to below 2^hi; zero, negative and non-finite masses have none
+__device__ __forceinline__ void mass_bit_span(double m, int &lo, int &hi) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    const unsigned E = (unsigned)(bits >> 52) & 0x7ffu;
+    unsigned long long s = bits & ((1ull << 52) - 1ull);
+    if ((bits >> 63) || E == 0x7ffu || (E == 0u && s == 0ull)) return;
+    int ex = -1074;
+    if (E) {
+        s |= 1ull << 52;
+        ex = (int)E - 1075;
+    }
+    lo = min(lo, ex + __ffsll((long long)s) - 1);
+    hi = max(hi, ex + 64 - __clzll((long long)s));
+}
 
 // build stages (og_build.cu)
 og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass);

@@ -15,7 +15,8 @@
 // not depend on the tree's shape or on the launch, and there is no pass per
 // tree level.
 //
-//   k_mass_span      the lowest and highest set bit over all masses (atomics)
+//   (the lowest and highest set bit over all masses come from the build's
+//   k_permute, which reads the masses first)
 //   k_mom_tiles      per tile of 512 sorted particles: the sums of the tile
 //   k_mom_scan_l1/2  exclusive prefix over the tiles, in two levels (blocks of
 //                    256 tiles, then the block totals)
@@ -231,51 +232,6 @@ __device__ __forceinline__ bool span_ok(const int *mbits, uint32_t *status) {
         return false;
     }
     return true;
-}
-
-// lowest and highest set-bit exponents of a mass: m = s 2^e (s < 2^53) has
-// bits from 2^lo to below 2^hi; zero, negative and non-finite masses have none
-__device__ __forceinline__ void mass_bit_span(double m, int &lo, int &hi) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
-    const unsigned E = (unsigned)(bits >> 52) & 0x7ffu;
-    unsigned long long s = bits & ((1ull << 52) - 1ull);
-    if ((bits >> 63) || E == 0x7ffu || (E == 0u && s == 0ull)) return;
-    int ex = -1074;
-    if (E) {
-        s |= 1ull << 52;
-        ex = (int)E - 1075;
-    }
-    lo = min(lo, ex + __ffsll((long long)s) - 1);
-    hi = max(hi, ex + 64 - __clzll((long long)s));
-}
-
-// mbits[0] = lowest, mbits[1] = highest set-bit exponent over all masses; a
-// grid-stride pass, one pair of atomics per block
-__global__ void __launch_bounds__(kMomThreads) k_mass_span(int64_t n, const double *__restrict__ pm64,
-                                                           int *mbits) {
-    pdl_wait();
-    __shared__ int wlo[kMomThreads / 32], whi[kMomThreads / 32];
-    int lo = 0x7fffffff, hi = (int)0x80000000;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (int64_t)gridDim.x * blockDim.x)
-        mass_bit_span(pm64[q], lo, hi);
-    lo = __reduce_min_sync(0xffffffffu, lo);
-    hi = __reduce_max_sync(0xffffffffu, hi);
-    if ((threadIdx.x & 31u) == 0u) {
-        wlo[threadIdx.x >> 5] = lo;
-        whi[threadIdx.x >> 5] = hi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < kMomThreads / 32; ++w) {
-            lo = min(lo, wlo[w]);
-            hi = max(hi, whi[w]);
-        }
-        if (lo <= hi) {
-            atomicMin(&mbits[0], lo);
-            atomicMax(&mbits[1], hi);
-        }
-    }
 }
 
 // this thread's kMomItems consecutive particles q0, q0 + 1 (vector loads);
@@ -551,15 +507,6 @@ __global__ void __launch_bounds__(kMomThreads) k_node_moments(
 inline int64_t mom_tiles(int64_t n) { return (n + kMomTile - 1) / kMomTile; }
 
 }  // namespace
-
-void mass_span(og_tree *t, cudaStream_t s) {
-    // empty span: lowest 0x7f7f7f7f, highest 0x80808080 (bytewise fills)
-    cudaMemsetAsync(t->mbits, 0x7f, sizeof(int), s);
-    cudaMemsetAsync(t->mbits + 1, 0x80, sizeof(int), s);
-    const int64_t nb = (t->n + kMomThreads - 1) / kMomThreads;
-    const unsigned grid = (unsigned)(nb < 1 ? 1 : nb > 1024 ? 1024 : nb);
-    launch_pdl(k_mass_span, grid, kMomThreads, 0, s, t->n, t->pm64, t->mbits);
-}
 
 size_t moments_scratch_bytes(int64_t n) {
     const auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
