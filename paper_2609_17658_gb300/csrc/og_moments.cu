@@ -186,6 +186,55 @@ __device__ __forceinline__ void store_mom(Mom192 *p, const Mom192 &r) {
     v[5] = make_ulonglong2(r.q[3].w1, r.q[3].w2);
 }
 
+// The per-particle prefixes P are stored modulo 2^128 (64-byte records: the
+// two low words of each sum) when the mass span W is at most kMassSpanShort:
+// a node's sums are then below 2^(W + 26 + 32) <= 2^128 (at most 2^26
+// particles, coordinates below 2^32), so the differences of the truncated
+// prefixes are still the exact sums.  Wider spans keep the 96-byte records.
+constexpr int kMassSpanShort = 70;
+
+__device__ __forceinline__ bool short_prefix(const int *mbits) {
+    // an empty span (lowest above highest) counts as short
+    return (long long)mbits[1] - (long long)mbits[0] <= kMassSpanShort;
+}
+
+__device__ __forceinline__ void store_prefix(unsigned char *P, int64_t i, const Mom192 &r, bool shrt) {
+    if (shrt) {
+        ulonglong2 *v = reinterpret_cast<ulonglong2 *>(P + (size_t)i * 64);
+        v[0] = make_ulonglong2(r.q[0].w0, r.q[0].w1);
+        v[1] = make_ulonglong2(r.q[1].w0, r.q[1].w1);
+        v[2] = make_ulonglong2(r.q[2].w0, r.q[2].w1);
+        v[3] = make_ulonglong2(r.q[3].w0, r.q[3].w1);
+    } else {
+        store_mom(reinterpret_cast<Mom192 *>(P + (size_t)i * 96), r);
+    }
+}
+
+// P[q1] - P[q0], the exact sums of the particles q0 .. q1 - 1
+__device__ __forceinline__ Mom192 prefix_diff(const unsigned char *P, int64_t q0, int64_t q1, bool shrt) {
+    Mom192 D;
+    if (shrt) {
+        const ulonglong2 *a = reinterpret_cast<const ulonglong2 *>(P + (size_t)q1 * 64);
+        const ulonglong2 *c = reinterpret_cast<const ulonglong2 *>(P + (size_t)q0 * 64);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const ulonglong2 x = a[k], y = c[k];
+            unsigned long long lo, hi;
+            asm("sub.cc.u64 %0, %2, %4;\n\t"
+                "subc.u64 %1, %3, %5;"
+                : "=l"(lo), "=l"(hi)
+                : "l"(x.x), "l"(x.y), "l"(y.x), "l"(y.y));
+            D.q[k] = {lo, hi, 0ull};
+        }
+    } else {
+        D = load_mom(reinterpret_cast<const Mom192 *>(P + (size_t)q1 * 96));
+        const Mom192 Pb = load_mom(reinterpret_cast<const Mom192 *>(P + (size_t)q0 * 96));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sub192(D.q[k], Pb.q[k]);
+    }
+    return D;
+}
+
 // Inclusive scan of one value per thread over the block; returns the thread's
 // exclusive prefix and the block total.
 template <int kThreads>
@@ -293,9 +342,9 @@ __global__ void __launch_bounds__(kScanBlock) k_mom_scan_l1(int64_t ntiles, cons
 }
 
 // second level: exclusive prefixes of the block totals (in place, several
-// per thread when there are more than kScanTop), the grand total to *total_out
+// per thread when there are more than kScanTop), the grand total to P[n]
 __global__ void __launch_bounds__(kScanTop) k_mom_scan_l2(int64_t nblocks, const int *__restrict__ mbits,
-                                                          Mom192 *block_sum, Mom192 *total_out,
+                                                          Mom192 *block_sum, unsigned char *P, int64_t n,
                                                           uint32_t *status) {
     pdl_wait();
     if (!span_ok(mbits, status)) return;
@@ -311,7 +360,7 @@ __global__ void __launch_bounds__(kScanTop) k_mom_scan_l2(int64_t nblocks, const
         store_mom(&block_sum[k], excl);
         mom_add(excl, v);
     }
-    if (threadIdx.x == 0) store_mom(total_out, total);
+    if (threadIdx.x == 0) store_prefix(P, n, total, short_prefix(mbits));
 }
 
 // Per particle the exclusive prefix: the tile's offset (both scan levels)
@@ -326,7 +375,7 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_prefix(int64_t n, const dou
                                                             const int *__restrict__ mbits,
                                                             const Mom192 *__restrict__ tile_off,
                                                             const Mom192 *__restrict__ block_off,
-                                                            Mom192 *P, uint32_t *status) {
+                                                            unsigned char *P, uint32_t *status) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char stage_all[];
     if (!span_ok(mbits, status)) return;
@@ -343,21 +392,40 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_prefix(int64_t n, const dou
     mom_add(run, load_mom(&block_off[blockIdx.x / kScanBlock]));
     mom_add(run, excl);
     unsigned char *stage = stage_all + warp * kWarpStage;
-    store_mom(reinterpret_cast<Mom192 *>(stage + lane * kLaneStage), run);
-    mom_add(run, v0);
-    store_mom(reinterpret_cast<Mom192 *>(stage + lane * kLaneStage + 96), run);
-    __syncwarp();
-    // the warp's records: 64 x 96 bytes = 384 chunks of 16 bytes, contiguous in P
     const int64_t wq0 = tile0 + (int64_t)warp * 64;
-    unsigned char *dst = reinterpret_cast<unsigned char *>(P + wq0);
+    if (short_prefix(mbits)) {
+        // 64 records of 64 bytes: 256 chunks of 16 bytes, contiguous in P
+        store_prefix(stage + lane * kLaneStage, 0, run, true);
+        mom_add(run, v0);
+        store_prefix(stage + lane * kLaneStage, 1, run, true);
+        __syncwarp();
+        unsigned char *dst = P + (size_t)wq0 * 64;
 #pragma unroll 4
-    for (int k = 0; k < 12; ++k) {
-        const int c = k * 32 + lane;
-        const int r = c / 6, part = c - 6 * r;
-        if (wq0 + r < n) {
-            const uint4 u = *reinterpret_cast<const uint4 *>(stage + (r >> 1) * kLaneStage + (r & 1) * 96 +
-                                                            part * 16);
-            *reinterpret_cast<uint4 *>(dst + (size_t)c * 16) = u;
+        for (int k = 0; k < 8; ++k) {
+            const int c = k * 32 + lane;
+            const int r = c >> 2, part = c & 3;
+            if (wq0 + r < n) {
+                const uint4 u = *reinterpret_cast<const uint4 *>(stage + (r >> 1) * kLaneStage + (r & 1) * 64 +
+                                                                part * 16);
+                *reinterpret_cast<uint4 *>(dst + (size_t)c * 16) = u;
+            }
+        }
+    } else {
+        // 64 records of 96 bytes: 384 chunks of 16 bytes
+        store_mom(reinterpret_cast<Mom192 *>(stage + lane * kLaneStage), run);
+        mom_add(run, v0);
+        store_mom(reinterpret_cast<Mom192 *>(stage + lane * kLaneStage + 96), run);
+        __syncwarp();
+        unsigned char *dst = P + (size_t)wq0 * 96;
+#pragma unroll 4
+        for (int k = 0; k < 12; ++k) {
+            const int c = k * 32 + lane;
+            const int r = c / 6, part = c - 6 * r;
+            if (wq0 + r < n) {
+                const uint4 u = *reinterpret_cast<const uint4 *>(stage + (r >> 1) * kLaneStage + (r & 1) * 96 +
+                                                                part * 16);
+                *reinterpret_cast<uint4 *>(dst + (size_t)c * 16) = u;
+            }
         }
     }
 }
@@ -467,20 +535,18 @@ __global__ void __launch_bounds__(kMomThreads) k_node_moments(
     const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ nend,
     const uint8_t *__restrict__ nlev, const uint32_t *__restrict__ px,
     const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
-    const Mom192 *__restrict__ P, const int *__restrict__ mbits, NodeMom *nmom, uint32_t *ncom,
+    const unsigned char *__restrict__ P, const int *__restrict__ mbits, NodeMom *nmom, uint32_t *ncom,
     uint32_t *status) {
     pdl_wait();
     if (!span_ok(mbits, status)) return;
     int64_t m = nsplit ? B + (int64_t)*nsplit : m_host;
     if (m > mcap) m = mcap;                    // the host reports the overflow
     const int b = mbits[0];
+    const bool shrt = short_prefix(mbits);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
          j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t q0 = nbeg[j], q1 = nend[j];
-        Mom192 D = load_mom(&P[q1]);
-        const Mom192 Pb = load_mom(&P[q0]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sub192(D.q[k], Pb.q[k]);
+        const Mom192 D = prefix_diff(P, q0, q1, shrt);
         nmom[j] = NodeMom{to_double(D.q[0], b), to_double(D.q[1], b), to_double(D.q[2], b),
                           to_double(D.q[3], b)};
         uint32_t c[3];
@@ -521,7 +587,7 @@ void node_moments(og_tree *t, const uint32_t *d_nsplit, int64_t mcap, void *scra
     const int64_t nblocks = (ntiles + kScanBlock - 1) / kScanBlock;
     const auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     char *q = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(scratch) + 255) & ~(uintptr_t)255);
-    Mom192 *P = reinterpret_cast<Mom192 *>(q);
+    unsigned char *P = reinterpret_cast<unsigned char *>(q);   // 64- or 96-byte records
     q += up((size_t)(n + 1) * sizeof(Mom192));
     Mom192 *tiles = reinterpret_cast<Mom192 *>(q);
     q += up((size_t)ntiles * sizeof(Mom192));
@@ -530,7 +596,7 @@ void node_moments(og_tree *t, const uint32_t *d_nsplit, int64_t mcap, void *scra
     launch_pdl(k_mom_tiles, (unsigned)ntiles, kMomThreads, 0, s, n, t->pm64, t->px, t->py, t->pz, t->mbits,
                                                          tiles, status);
     launch_pdl(k_mom_scan_l1, (unsigned)nblocks, kScanBlock, 0, s, ntiles, t->mbits, tiles, blocks, status);
-    launch_pdl(k_mom_scan_l2, 1, kScanTop, 0, s, nblocks, t->mbits, blocks, &P[n], status);
+    launch_pdl(k_mom_scan_l2, 1, kScanTop, 0, s, nblocks, t->mbits, blocks, P, n, status);
     // the stage is above the default 48 KB of shared memory (set per call: the
     // attribute belongs to the current device)
     cudaFuncSetAttribute(k_mom_prefix, cudaFuncAttributeMaxDynamicSharedMemorySize,
