@@ -132,8 +132,8 @@ __global__ void k_fill_seg(int64_t n, int64_t B, const uint32_t *__restrict__ se
 // the device totals, the masses' set-bit span (empty: lowest 0x7f7f7f7f
 // above highest 0x80808080), and with one box its sorted box indices (all 0).
 __global__ void k_quantize_keys(const double *__restrict__ pos, int64_t n, const uint32_t *__restrict__ pseg,
-                                const SegGeom *__restrict__ geom, uint32_t *qx, uint32_t *qy,
-                                uint32_t *qz, uint64_t *key, uint64_t *key_copy, uint32_t *idx,
+                                const SegGeom *__restrict__ geom, uint4 *q4, uint64_t *key,
+                                uint64_t *key_copy, uint32_t *idx,
                                 uint32_t *sseg_zero, uint32_t *d_tot, int *mbits, uint32_t *status) {
     pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,9 +150,7 @@ __global__ void k_quantize_keys(const double *__restrict__ pos, int64_t n, const
     uint32_t x = quantize(pos[3 * i + 0], box, inv_box, pow2, g.shift, status);
     uint32_t y = quantize(pos[3 * i + 1], box, inv_box, pow2, g.shift, status);
     uint32_t z = quantize(pos[3 * i + 2], box, inv_box, pow2, g.shift, status);
-    qx[i] = x;
-    qy[i] = y;
-    qz[i] = z;
+    q4[i] = make_uint4(x, y, z, 0u);   // one 16-byte record: the permute gathers it whole
     const uint64_t k = (spread21(x >> 11) << 2) | (spread21(y >> 11) << 1) | spread21(z >> 11);
     key[i] = k;
     if (key_copy) key_copy[i] = k;
@@ -183,8 +181,7 @@ __global__ void k_gather_keys(int64_t n, const uint32_t *__restrict__ perm,
 // set-bit span (the units of the exact moments) is gathered: a block's lowest
 // and highest exponents, merged by atomics only where they widen the span.
 __global__ void __launch_bounds__(kT) k_permute(int64_t n, const uint32_t *__restrict__ perm,
-                                                const uint32_t *__restrict__ qx, const uint32_t *__restrict__ qy,
-                                                const uint32_t *__restrict__ qz, const double *__restrict__ mass,
+                                                const uint4 *__restrict__ q4, const double *__restrict__ mass,
                                                 uint32_t *px, uint32_t *py, uint32_t *pz, float *pm32,
                                                 double *pm64, int *mbits, uint32_t *status) {
     pdl_wait();
@@ -193,9 +190,10 @@ __global__ void __launch_bounds__(kT) k_permute(int64_t n, const uint32_t *__res
     int lo = 0x7fffffff, hi = (int)0x80000000;
     if (i < n) {
         uint32_t j = perm[i];
-        px[i] = qx[j];
-        py[i] = qy[j];
-        pz[i] = qz[j];
+        const uint4 q = q4[j];
+        px[i] = q.x;
+        py[i] = q.y;
+        pz[i] = q.z;
         double m = mass[j];
         if (!isfinite(m) || m < 0.0) atomicOr(status, ST_BAD_INPUT);
         pm64[i] = m;
@@ -235,19 +233,30 @@ constexpr int kNone = 0x7fffffff;      // no split below t on the right
 // a split's level as an ordered value: a box boundary below every level
 __device__ __forceinline__ int split_rank(uint8_t v) { return v == kSep ? -1 : (int)v; }
 
-// per warp and threshold t: the lanes whose split lies below t, and the last
-// and first such split index (-1 / kNone when there is none)
-__device__ __forceinline__ void warp_below(int v, int64_t base, int lane, unsigned &mine_m, int &mine_l,
-                                           int &mine_f) {
+// The lanes of a warp whose split lies below threshold t, for a t of each
+// lane's own choosing: the values u = rank + 1 (0 .. kNT + 1, five bits) go
+// out as five bit-plane ballots, and each lane compares them with its own
+// threshold bit by bit, from the top (u < t + 1 iff the split's level < t).
+struct WarpLevels {
+    unsigned b[5];
+};
+__device__ __forceinline__ WarpLevels warp_levels(int v) {
+    const unsigned u = (unsigned)(v + 1);
+    WarpLevels w;
 #pragma unroll
-    for (int t = 0; t < kNT; ++t) {
-        const unsigned m = __ballot_sync(0xffffffffu, v < t);
-        if (lane == t) {
-            mine_m = m;
-            mine_l = m ? (int)(base + 31 - __clz(m)) : -1;
-            mine_f = m ? (int)(base + __ffs(m) - 1) : kNone;
-        }
+    for (int k = 0; k < 5; ++k) w.b[k] = __ballot_sync(0xffffffffu, (u >> k) & 1u);
+    return w;
+}
+__device__ __forceinline__ unsigned lanes_below(const WarpLevels &w, int t) {
+    const unsigned c = (unsigned)(t + 1);   // t <= kNT - 1, so c < 32
+    unsigned less = 0u, eq = 0xffffffffu;
+#pragma unroll
+    for (int k = 4; k >= 0; --k) {
+        const bool cb = (c >> k) & 1u;
+        less |= cb ? (eq & ~w.b[k]) : 0u;
+        eq &= cb ? w.b[k] : ~w.b[k];
     }
+    return less;
 }
 
 // levels of all splits; per tile and threshold, its last and first split below t
@@ -264,24 +273,23 @@ __global__ void __launch_bounds__(kSplitTile) k_split_tiles(const uint64_t *__re
         lv[i] = l;
         v = split_rank(l);
     }
-    unsigned m = 0u;
-    int ml = -1, mf = kNone;
-    warp_below(v, (int64_t)blockIdx.x * kSplitTile + warp * 32, lane, m, ml, mf);
+    // lane t < kNT: this warp's last and first split below threshold t
+    const int64_t base = (int64_t)blockIdx.x * kSplitTile + warp * 32;
+    const unsigned m = lanes_below(warp_levels(v), lane < kNT ? lane : 0);
     if (lane < kNT) {
-        wl[warp][lane] = ml;
-        wf[warp][lane] = mf;
+        wl[warp][lane] = m ? (int)(base + 31 - __clz(m)) : -1;
+        wf[warp][lane] = m ? (int)(base + __ffs(m) - 1) : kNone;
     }
     __syncthreads();
-    if (threadIdx.x < kNT) {
-        const int t = threadIdx.x;
-        int r = -1;
-        for (int w = 0; w < 32; ++w) r = max(r, wl[w][t]);
-        tlast[blockIdx.x * kNT + t] = r;
-    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + kNT) {
-        const int t = threadIdx.x - 32;
-        int r = kNone;
-        for (int w = 0; w < 32; ++w) r = min(r, wf[w][t]);
-        tfirst[blockIdx.x * kNT + t] = r;
+    // warp t folds threshold t over the 32 warps of the tile
+    if (warp < kNT) {
+        int l = wl[lane][warp], f = wf[lane][warp];
+        l = __reduce_max_sync(0xffffffffu, l);
+        f = __reduce_min_sync(0xffffffffu, f);
+        if (lane == 0) {
+            tlast[blockIdx.x * kNT + warp] = l;
+            tfirst[blockIdx.x * kNT + warp] = f;
+        }
     }
 }
 
@@ -348,36 +356,43 @@ __global__ void __launch_bounds__(kSplitTile) k_split_ranges(const uint8_t *__re
                                                              const int *__restrict__ cfirst, uint32_t *sb,
                                                              uint32_t *se, uint32_t *first, uint32_t *prevle) {
     pdl_wait();
-    __shared__ unsigned wm[32][kNT];
     __shared__ int wl[32][kNT], wf[32][kNT];
     __shared__ int pl[32][kNT], pf[32][kNT];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kSplitTile + threadIdx.x;
     const int v = i < nsplit ? split_rank(lv[i]) : kNT;
     const int64_t base = (int64_t)blockIdx.x * kSplitTile + warp * 32;
-    unsigned m = 0u;
-    int ml = -1, mf = kNone;
-    warp_below(v, base, lane, m, ml, mf);
-    if (lane < kNT) {
-        wm[warp][lane] = m;
-        wl[warp][lane] = ml;
-        wf[warp][lane] = mf;
+    const WarpLevels W = warp_levels(v);
+    {
+        const unsigned m = lanes_below(W, lane < kNT ? lane : 0);
+        if (lane < kNT) {
+            wl[warp][lane] = m ? (int)(base + 31 - __clz(m)) : -1;
+            wf[warp][lane] = m ? (int)(base + __ffs(m) - 1) : kNone;
+        }
     }
     __syncthreads();
-    if (threadIdx.x < kNT) {
-        const int t = threadIdx.x;
-        int r = clast[blockIdx.x * kNT + t];
-        for (int w = 0; w < 32; ++w) {
-            pl[w][t] = r;
-            r = max(r, wl[w][t]);
+    // warp t: for threshold t, the nearest split below t in the warps (and
+    // tiles) before each warp and after it
+    if (warp < kNT) {
+        const int t = warp;
+        int l = wl[lane][t];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, l, d);
+            if (lane >= d) l = max(l, o);
         }
-    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + kNT) {
-        const int t = threadIdx.x - 32;
-        int r = cfirst[blockIdx.x * kNT + t];
-        for (int w = 31; w >= 0; --w) {
-            pf[w][t] = r;
-            r = min(r, wf[w][t]);
+        int lex = __shfl_up_sync(0xffffffffu, l, 1);
+        const int cl = clast[blockIdx.x * kNT + t];
+        pl[lane][t] = lane == 0 ? cl : max(cl, lex);
+        int f = wf[lane][t];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_down_sync(0xffffffffu, f, d);
+            if (lane + d < 32) f = min(f, o);
         }
+        int fex = __shfl_down_sync(0xffffffffu, f, 1);
+        const int cf = cfirst[blockIdx.x * kNT + t];
+        pf[lane][t] = lane == 31 ? cf : min(cf, fex);
     }
     __syncthreads();
     if (i >= nsplit) return;
@@ -388,7 +403,7 @@ __global__ void __launch_bounds__(kSplitTile) k_split_ranges(const uint8_t *__re
     const int L = v;
     const unsigned below = (1u << lane) - 1u;
     const unsigned above = lane == 31 ? 0u : (0xfffffffeu << lane);
-    const unsigned mL = wm[warp][L], mL1 = wm[warp][L + 1];
+    const unsigned mL = lanes_below(W, L), mL1 = lanes_below(W, L + 1);
     // nearest split of a level < L to the left (or -1) and to the right (or the end)
     const int left = (mL & below) ? (int)(base + 31 - __clz(mL & below)) : pl[warp][L];
     int right = (mL & above) ? (int)(base + __ffs(mL & above) - 1) : pf[warp][L];
@@ -404,7 +419,17 @@ __global__ void __launch_bounds__(kSplitTile) k_split_ranges(const uint8_t *__re
         // a node of level < kLevels has at most 7 splits of its level; one of
         // level kLevels (a run of equal keys) any number, and its first split
         // is the range start
-        prevle[i] = (uint32_t)(L == kLevels ? left + 1 : le);
+        // when the range starts in this warp, its first split is the lowest
+        // split of a level <= L after the range start, found from the mask
+        uint32_t f = (uint32_t)le;
+        if (L == kLevels) {
+            f = (uint32_t)(left + 1);
+        } else if (left + 1 >= base) {
+            const int sh = left - (int)base;   // -1 .. 30: the lanes after left
+            const unsigned after = sh < 0 ? 0xffffffffu : ~((2u << sh) - 1u);
+            f = (uint32_t)(base + __ffs(mL1 & after) - 1);
+        }
+        prevle[i] = f;
     }
 }
 
@@ -881,16 +906,15 @@ __global__ void k_cell_ext(int64_t m, const uint8_t *__restrict__ nlev, const ui
 }
 
 // refit: drifted fixed-point positions into sorted order (masses unchanged)
-__global__ void k_repos(int64_t n, const uint32_t *__restrict__ perm, const uint32_t *__restrict__ qx,
-                        const uint32_t *__restrict__ qy, const uint32_t *__restrict__ qz,
+__global__ void k_repos(int64_t n, const uint32_t *__restrict__ perm, const uint4 *__restrict__ q4,
                         uint32_t *px, uint32_t *py, uint32_t *pz) {
     pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t j = perm[i];
-    px[i] = qx[j];
-    py[i] = qy[j];
-    pz[i] = qz[j];
+    const uint4 q = q4[perm[i]];
+    px[i] = q.x;
+    py[i] = q.y;
+    pz[i] = q.z;
 }
 
 // the walk's child records; the child count is *d_nchild (the build) or
@@ -1079,11 +1103,11 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
         if (st) return st;
     }
     const size_t mom_bytes = moments_scratch_bytes(n);
-    size_t sb = (size_t)n * (3 * 4 + 8 + 4 + 4) + 4096 + mom_bytes + 4 * (kLevels + 3) * sizeof(uint32_t) + 256;
+    size_t sb = (size_t)n * (16 + 8 + 4 + 4) + 4096 + mom_bytes + 4 * (kLevels + 3) * sizeof(uint32_t) + 256;
     void *scratch = nullptr;
     if ((err = dev_malloc_async(&scratch, sb, s)) != cudaSuccess) return cuda_fail(err, "cudaMallocAsync (refit)");
     Bump W(scratch, sb);
-    uint32_t *qx = W.take<uint32_t>(n), *qy = W.take<uint32_t>(n), *qz = W.take<uint32_t>(n);
+    uint4 *q4 = W.take<uint4>(n);
     uint64_t *keys = W.take<uint64_t>(n);
     uint32_t *idx = W.take<uint32_t>(n);
     uint32_t *pseg = W.take<uint32_t>(n);
@@ -1101,10 +1125,10 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
     if (B > 1) {
         launch_pdl(k_fill_seg, nblk(n), kT, 0, s, n, B, t->seg_off, pseg);
     }
-    launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx,
-                                           qy, qz, keys, nullptr, idx, nullptr, nullptr, nullptr,
+    launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, q4,
+                                           keys, nullptr, idx, nullptr, nullptr, nullptr,
                                            t->ctx->d_status);
-    launch_pdl(k_repos, nblk(n), kT, 0, s, n, t->perm, qx, qy, qz, t->px, t->py, t->pz);
+    launch_pdl(k_repos, nblk(n), kT, 0, s, n, t->perm, (const uint4 *)q4, t->px, t->py, t->pz);
     node_moments(t, nullptr, t->nnodes, mom_scratch, s);
     extents_bottom_up(t, t->next_s, t->next_l);
     launch_pdl(k_group_fin, stride_grid(t->ngroups), kT, 0, s, n, nullptr, t->ngroups, t->gbeg, t->gend, t->px,
@@ -1205,7 +1229,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     size_t sb_bytes = 0;
     {
         auto add = [&](size_t sz, int64_t cnt) { sb_bytes += ((size_t)(cnt > 0 ? cnt : 1) * sz + 255) & ~(size_t)255; };
-        add(4, n); add(4, n); add(4, n);                        // qx qy qz
+        add(16, n);                                             // q4
         add(8, n); add(4, n); add(8, n); add(4, n); add(8, n); add(4, n);  // keys, idx, alt, key copy, pseg
         add(1, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // lv sb se first nid sid
         add(4, 4 * kNT * ((n + kSplitTile - 1) / kSplitTile));  // split tile summaries
@@ -1219,7 +1243,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         return err == cudaErrorMemoryAllocation ? (set_error("device allocation of %zu bytes failed", sb_bytes), OG_ERR_OOM)
                                                 : cuda_fail(err, "cudaMallocAsync");
     Bump W(scratch, sb_bytes);
-    uint32_t *qx = W.take<uint32_t>(n), *qy = W.take<uint32_t>(n), *qz = W.take<uint32_t>(n);
+    uint4 *q4 = W.take<uint4>(n);
     uint64_t *keys = W.take<uint64_t>(n);
     uint32_t *idx = W.take<uint32_t>(n);
     uint64_t *keys_alt = W.take<uint64_t>(n);
@@ -1259,8 +1283,8 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         keys = t->skey;
         idx = t->perm;
     }
-    launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, qx, qy,
-                                           qz, keys, B > 1 ? key0 : nullptr, idx, B > 1 ? nullptr : t->sseg,
+    launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, q4,
+                                           keys, B > 1 ? key0 : nullptr, idx, B > 1 ? nullptr : t->sseg,
                                            d_tot, t->mbits, status);
     // a3: by key, then (several boxes) stably by box
     bool in_alt = false;
@@ -1284,7 +1308,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         cudaMemcpyAsync(t->perm, idx_alt, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
     }
     if (t->mass_ready) cudaStreamWaitEvent(s, t->mass_ready, 0);
-    launch_pdl(k_permute, nblk(n), kT, 0, s, n, t->perm, qx, qy, qz, d_mass, t->px, t->py, t->pz, t->pm32,
+    launch_pdl(k_permute, nblk(n), kT, 0, s, n, t->perm, (const uint4 *)q4, d_mass, t->px, t->py, t->pz, t->pm32,
                                      t->pm64, t->mbits, status);
     // a4: nodes from splits.  The node count stays on the device (d_tot[0]
     // counts the first splits, m = B + that): the kernels up to the groups

@@ -318,11 +318,31 @@ __global__ void __launch_bounds__(kMomThreads) k_mom_tiles(int64_t n, const doub
     if (!span_ok(mbits, status)) return;
     const int b = mbits[0];
     const int64_t q0 = (int64_t)blockIdx.x * kMomTile + (int64_t)threadIdx.x * kMomItems;
-    Mom192 v0, v1, excl, total;
+    __shared__ Mom192 wsum[kMomThreads / 32];
+    Mom192 v0, v1;
     load_pair(n, q0, pm64, px, py, pz, b, v0, v1);
     mom_add(v0, v1);
-    block_scan<kMomThreads>(v0, excl, total);
-    if (threadIdx.x == 0) store_mom(&tile_sum[blockIdx.x], total);
+    // the tile's total: a butterfly over the warp (sums modulo 2^192 do not
+    // depend on the order), then the warps' totals
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        Mom192 o;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            o.q[k].w0 = __shfl_xor_sync(0xffffffffu, v0.q[k].w0, d);
+            o.q[k].w1 = __shfl_xor_sync(0xffffffffu, v0.q[k].w1, d);
+            o.q[k].w2 = __shfl_xor_sync(0xffffffffu, v0.q[k].w2, d);
+        }
+        mom_add(v0, o);
+    }
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Mom192 t = wsum[0];
+#pragma unroll
+        for (int w = 1; w < kMomThreads / 32; ++w) mom_add(t, wsum[w]);
+        store_mom(&tile_sum[blockIdx.x], t);
+    }
 }
 
 // first level: each block turns its kScanBlock tile sums into exclusive
