@@ -177,19 +177,21 @@ __global__ void k_gather_keys(int64_t n, const uint32_t *__restrict__ perm,
     sseg[i] = pseg[j];
 }
 
-// Positions and masses in key order; the masses are checked here, and their
+// Positions and masses in key order, and the inverse permutation (the force
+// call gathers its caller-order outputs through it); the masses are checked here, and their
 // set-bit span (the units of the exact moments) is gathered: a block's lowest
 // and highest exponents, merged by atomics only where they widen the span.
 __global__ void __launch_bounds__(kT) k_permute(int64_t n, const uint32_t *__restrict__ perm,
                                                 const uint4 *__restrict__ q4, const double *__restrict__ mass,
                                                 uint32_t *px, uint32_t *py, uint32_t *pz, float *pm32,
-                                                double *pm64, int *mbits, uint32_t *status) {
+                                                double *pm64, uint32_t *inv, int *mbits, uint32_t *status) {
     pdl_wait();
     __shared__ int wlo[kT / 32], whi[kT / 32];
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int lo = 0x7fffffff, hi = (int)0x80000000;
     if (i < n) {
         uint32_t j = perm[i];
+        inv[j] = (uint32_t)i;
         const uint4 q = q4[j];
         px[i] = q.x;
         py[i] = q.y;
@@ -986,6 +988,7 @@ static size_t tree_bytes(int64_t n, int64_t B) {
     size_t b = 0;
     auto add = [&](size_t sz, int64_t cnt) { b += ((size_t)(cnt > 0 ? cnt : 1) * sz + 255) & ~(size_t)255; };
     add(8, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n); add(8, n); add(4, n);  // particles
+    add(4, n);                                                                      // inv
     add(1, m); add(4, m); add(4, m); add(4, m); add(4, m); add(4, m);               // nlev..npos
     add(4, m); add(4, m); add(4, m); add(32, m); add(4, 3 * m);                     // npar.. ncom
     add(4, n); add(4, n);                                                           // pnext, owner
@@ -1168,6 +1171,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     const int64_t mcap = n + B, ccap = n + mcap;
     t->skey = A.take<uint64_t>(n);
     t->perm = A.take<uint32_t>(n);
+    t->inv = A.take<uint32_t>(n);
     t->px = A.take<uint32_t>(n);
     t->py = A.take<uint32_t>(n);
     t->pz = A.take<uint32_t>(n);
@@ -1309,7 +1313,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     }
     if (t->mass_ready) cudaStreamWaitEvent(s, t->mass_ready, 0);
     launch_pdl(k_permute, nblk(n), kT, 0, s, n, t->perm, (const uint4 *)q4, d_mass, t->px, t->py, t->pz, t->pm32,
-                                     t->pm64, t->mbits, status);
+                                     t->pm64, t->inv, t->mbits, status);
     // a4: nodes from splits.  The node count stays on the device (d_tot[0]
     // counts the first splits, m = B + that): the kernels up to the groups
     // read it there and are sized for the most nodes a tree can have, so the

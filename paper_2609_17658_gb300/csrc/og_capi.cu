@@ -74,13 +74,16 @@ __global__ void k_gather_aold(int64_t n, const uint32_t *__restrict__ perm,
     out[2 * n + i] = a_old[3ull * j + 2];
 }
 
-__global__ void k_unpermute(int64_t n, const uint32_t *__restrict__ perm,
+// Outputs in caller order, gathered: caller index j reads sorted position
+// inv[j] (the sorted arrays were just written by the walk and sit in L2), and
+// the stores of consecutive j are contiguous.
+__global__ void k_unpermute(int64_t n, const uint32_t *__restrict__ inv,
                             const float *__restrict__ acc_sorted,
                             const uint32_t *__restrict__ npp_s, const uint32_t *__restrict__ npn_s,
                             float *acc, uint32_t *npp, uint32_t *npn) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t j = perm[i];
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t i = inv[j];
     if (acc) {
         acc[3ull * j + 0] = acc_sorted[i];
         acc[3ull * j + 1] = acc_sorted[n + i];
@@ -91,13 +94,13 @@ __global__ void k_unpermute(int64_t n, const uint32_t *__restrict__ perm,
 }
 
 // FP64 output: the walk's unscaled FP32 sums times G (2^32 / L)^2 in FP64
-__global__ void k_unpermute_f64(int64_t n, const uint32_t *__restrict__ perm,
+__global__ void k_unpermute_f64(int64_t n, const uint32_t *__restrict__ inv,
                                 const float *__restrict__ acc_sorted,
                                 const uint32_t *__restrict__ npp_s, const uint32_t *__restrict__ npn_s,
                                 double scale, double *acc, uint32_t *npp, uint32_t *npn) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t j = perm[i];
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t i = inv[j];
     acc[3ull * j + 0] = (double)acc_sorted[i] * scale;
     acc[3ull * j + 1] = (double)acc_sorted[n + i] * scale;
     acc[3ull * j + 2] = (double)acc_sorted[2 * n + i] * scale;
@@ -105,11 +108,11 @@ __global__ void k_unpermute_f64(int64_t n, const uint32_t *__restrict__ perm,
     if (npn) npn[j] = npn_s[i];
 }
 
-__global__ void k_unpermute_pot(int64_t n, const uint32_t *__restrict__ perm,
+__global__ void k_unpermute_pot(int64_t n, const uint32_t *__restrict__ inv,
                                 const float *__restrict__ pot_sorted, float *pot) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    pot[perm[i]] = pot_sorted[i];
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    pot[j] = pot_sorted[inv[j]];
 }
 
 // 1 for a group holding at least one active particle (active: caller order)
@@ -132,16 +135,15 @@ __global__ void k_group_compact(int64_t ng, const uint32_t *__restrict__ flag,
 }
 
 // k_unpermute for the active particles only
-__global__ void k_unpermute_active(int64_t n, const uint32_t *__restrict__ perm,
+__global__ void k_unpermute_active(int64_t n, const uint32_t *__restrict__ inv,
                                    const uint8_t *__restrict__ active,
                                    const float *__restrict__ acc_sorted,
                                    const uint32_t *__restrict__ npp_s,
                                    const uint32_t *__restrict__ npn_s, float *acc, uint32_t *npp,
                                    uint32_t *npn) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t j = perm[i];
-    if (!active[j]) return;
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || !active[j]) return;
+    const uint32_t i = inv[j];
     acc[3ull * j + 0] = acc_sorted[i];
     acc[3ull * j + 1] = acc_sorted[n + i];
     acc[3ull * j + 2] = acc_sorted[2 * n + i];
@@ -553,20 +555,20 @@ og_status og_tree_force(og_tree *t, const float *a_old, float *acc, uint32_t *n_
         // host outputs: the counts first, their copy on the side stream beside
         // the accelerations' reordering (the copies share the link, the
         // reordering does not)
-        k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+        k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->inv, t->a_sorted, t->npp_sorted, t->npn_sorted,
                                            nullptr, d_npp, d_npn); note_launch();
         cudaEventRecord(c->ev_to_side, s);
         cudaStreamWaitEvent(c->copy_stream, c->ev_to_side, 0);
         if (n_pp) cudaMemcpyAsync(n_pp, d_npp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->copy_stream);
         if (n_pn) cudaMemcpyAsync(n_pn, d_npn, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->copy_stream);
         cudaEventRecord(c->ev_from_side, c->copy_stream);
-        k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+        k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->inv, t->a_sorted, t->npp_sorted, t->npn_sorted,
                                            d_acc, nullptr, nullptr); note_launch();
         cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
         cudaStreamWaitEvent(s, c->ev_from_side, 0);
         cudaFreeAsync(out_tmp, s);
     } else {
-        k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+        k_unpermute<<<nblk(n), kT, 0, s>>>(n, t->inv, t->a_sorted, t->npp_sorted, t->npn_sorted,
                                            d_acc, d_npp, d_npn); note_launch();
         if (!dev) {
             cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
@@ -631,7 +633,7 @@ og_status og_tree_force_f64(og_tree *t, const float *a_old, double *acc, uint32_
         d_npp = n_pp ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) : nullptr;
         d_npn = n_pn ? reinterpret_cast<uint32_t *>(d_acc + 3 * n) + n : nullptr;
     }
-    k_unpermute_f64<<<nblk(n), kT, 0, s>>>(n, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+    k_unpermute_f64<<<nblk(n), kT, 0, s>>>(n, t->inv, t->a_sorted, t->npp_sorted, t->npn_sorted,
                                            scale, d_acc, d_npp, d_npn); note_launch();
     if (!dev) {
         cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -668,7 +670,7 @@ og_status og_tree_force_pot(og_tree *t, const float *a_old, float *acc, float *p
     og_status st = og_tree_force(t, a_old, acc, n_pp, n_pn);
     t->pot_next = nullptr;
     if (st == OG_OK) {
-        k_unpermute_pot<<<nblk(n), kT, 0, s>>>(n, t->perm, pot_sorted, d_pot); note_launch();
+        k_unpermute_pot<<<nblk(n), kT, 0, s>>>(n, t->inv, pot_sorted, d_pot); note_launch();
         if (!dev) cudaMemcpyAsync(pot, d_pot, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "potential");
     }
@@ -748,7 +750,7 @@ og_status og_tree_force_active(og_tree *t, const uint8_t *active, const float *a
             if (n_pp) cudaMemcpyAsync(d_npp, n_pp, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
             if (n_pn) cudaMemcpyAsync(d_npn, n_pn, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
         }
-        k_unpermute_active<<<nblk(n), kT, 0, s>>>(n, t->perm, d_active, t->a_sorted, t->npp_sorted,
+        k_unpermute_active<<<nblk(n), kT, 0, s>>>(n, t->inv, d_active, t->a_sorted, t->npp_sorted,
                                                   t->npn_sorted, d_acc, d_npp, d_npn); note_launch();
         if (!dev) {
             cudaMemcpyAsync(acc, d_acc, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
@@ -848,7 +850,7 @@ og_status og_batch_force(og_ctx *c, int64_t nbox, const og_box *boxes, og_batch_
     float *o_acc = static_cast<float *>(out);
     uint32_t *o_pp = reinterpret_cast<uint32_t *>(o_acc + 3 * total);
     uint32_t *o_pn = o_pp + total;
-    k_unpermute<<<nblk(total), kT, 0, s>>>(total, t->perm, t->a_sorted, t->npp_sorted, t->npn_sorted,
+    k_unpermute<<<nblk(total), kT, 0, s>>>(total, t->inv, t->a_sorted, t->npp_sorted, t->npn_sorted,
                                            o_acc, o_pp, o_pn); note_launch();
     for (int64_t b = 0; b < nbox; ++b) {
         const int64_t o = t->h_seg_off[b], nb = boxes[b].n;

@@ -102,7 +102,8 @@ struct og_tree {
     uint32_t *gseg = nullptr;         // box of each group
     // sorted particles
     uint64_t *skey = nullptr;
-    uint32_t *perm = nullptr;
+    uint32_t *perm = nullptr;         // sorted position -> caller index
+    uint32_t *inv = nullptr;          // caller index -> sorted position
     uint32_t *px = nullptr, *py = nullptr, *pz = nullptr;
     float *pm32 = nullptr;
     double *pm64 = nullptr;
