@@ -130,13 +130,17 @@ __global__ void k_fill_seg(int64_t n, int64_t B, const uint32_t *__restrict__ se
 
 // In a build (d_tot set) it also clears what later kernels accumulate into:
 // the device totals, the masses' set-bit span (empty: lowest 0x7f7f7f7f
-// above highest 0x80808080), and with one box its sorted box indices (all 0).
+// above highest 0x80808080), the scans' look words and tile counters, and with
+// one box its sorted box indices (all 0).
 __global__ void k_quantize_keys(const double *__restrict__ pos, int64_t n, const uint32_t *__restrict__ pseg,
                                 const SegGeom *__restrict__ geom, uint4 *q4, uint64_t *key,
                                 uint64_t *key_copy, uint32_t *idx,
-                                uint32_t *sseg_zero, uint32_t *d_tot, int *mbits, uint32_t *status) {
+                                uint32_t *sseg_zero, uint32_t *d_tot, int *mbits,
+                                unsigned long long *scan_look, int64_t nlook, uint32_t *status) {
     pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the look words and tile counters of the build's one-kernel scans
+    for (int64_t k = i; k < nlook; k += (int64_t)gridDim.x * blockDim.x) scan_look[k] = 0ull;
     if (i == 0 && d_tot) {
         d_tot[0] = d_tot[1] = d_tot[2] = d_tot[3] = 0u;
         mbits[0] = 0x7f7f7f7f;
@@ -1129,7 +1133,7 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
         launch_pdl(k_fill_seg, nblk(n), kT, 0, s, n, B, t->seg_off, pseg);
     }
     launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, q4,
-                                           keys, nullptr, idx, nullptr, nullptr, nullptr,
+                                           keys, nullptr, idx, nullptr, nullptr, nullptr, nullptr, (int64_t)0,
                                            t->ctx->d_status);
     launch_pdl(k_repos, nblk(n), kT, 0, s, n, t->perm, (const uint4 *)q4, t->px, t->py, t->pz);
     node_moments(t, nullptr, t->nnodes, mom_scratch, s);
@@ -1237,6 +1241,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         add(8, n); add(4, n); add(8, n); add(4, n); add(8, n); add(4, n);  // keys, idx, alt, key copy, pseg
         add(1, n); add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // lv sb se first nid sid
         add(4, 4 * kNT * ((n + kSplitTile - 1) / kSplitTile));  // split tile summaries
+        add(8, (int64_t)scan_look_words(n + B) + 2);            // scans' look words, counters
         add(4, n + B);                  // nnc
         add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs gid unit
         sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + B + 8) +
@@ -1258,6 +1263,12 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     uint32_t *sbeg = W.take<uint32_t>(n), *send = W.take<uint32_t>(n);
     uint32_t *first = W.take<uint32_t>(n), *nid = W.take<uint32_t>(n), *sid = W.take<uint32_t>(n);
     int *tsum = W.take<int>(4 * kNT * ((n + kSplitTile - 1) / kSplitTile));
+    // the four one-kernel scans of the build share these look words (tags 1-4);
+    // their tile counters are the last two words (four 32-bit counters)
+    const int64_t nlook_w = (int64_t)scan_look_words(n + B);
+    unsigned long long *scan_look = W.take<unsigned long long>(nlook_w + 2);
+    const int64_t nlook = nlook_w + 2;
+    uint32_t *scan_ctr = reinterpret_cast<uint32_t *>(scan_look + nlook_w);
     uint32_t *occ = t->nocc, *nnc = W.take<uint32_t>(n + B);
     uint32_t *fp = W.take<uint32_t>(n), *rs = W.take<uint32_t>(n), *gs = W.take<uint32_t>(n);
     // a split's previous split in its node: needed only until k_node_init,
@@ -1289,7 +1300,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     }
     launch_pdl(k_quantize_keys, nblk(n), kT, 0, s, d_pos, n, B > 1 ? pseg : nullptr, t->geom, q4,
                                            keys, B > 1 ? key0 : nullptr, idx, B > 1 ? nullptr : t->sseg,
-                                           d_tot, t->mbits, status);
+                                           d_tot, t->mbits, scan_look, nlook, status);
     // a3: by key, then (several boxes) stably by box
     bool in_alt = false;
     radix_sort_pairs(keys, idx, keys_alt, idx_alt, n, 63, sort_scratch, s, &in_alt, status);
@@ -1330,7 +1341,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
                    clast, cfirst);
         launch_pdl(k_split_ranges, dim3((unsigned)ntiles), kSplitTile, 0, s, (const uint8_t *)lv, nsplit,
                    (const int *)clast, (const int *)cfirst, sbeg, send, first, prevle);
-        scan_exclusive_u32(first, nid, nsplit, d_tot, scan_scratch, s);
+        scan_exclusive_u32_look(first, nid, nsplit, d_tot, scan_look, scan_ctr + 0, 1, status, scan_scratch, s);
     }
     const uint32_t *nsp = d_tot;
     // (mcap = n + B covers the splits and the roots too.)  Child counts beyond
@@ -1342,7 +1353,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     launch_pdl(k_link, nblk(n + mcap), kT, 0, s, n, nsp, B, t->skey, lv, sid, t->sseg, t->nlev, t->nbeg,
                                          t->nend, t->npar, t->owner, occ, nnc, status);
     launch_pdl(k_ccnt, nblk(mcap), kT, 0, s, nsp, B, t->nlev, t->nbeg, t->nend, occ, t->nccnt);
-    scan_exclusive_u32(t->nccnt, t->ncbeg, mcap, d_tot + 1, scan_scratch, s);
+    scan_exclusive_u32_look(t->nccnt, t->ncbeg, mcap, d_tot + 1, scan_look, scan_ctr + 1, 2, status, scan_scratch, s);
     launch_pdl(k_place, nblk(n + mcap), kT, 0, s, n, nsp, B, t->skey, t->nlev, t->nbeg, t->ncbeg, occ,
                                           t->npar, t->owner, t->child, t->npos, status);
     launch_pdl(k_threading, nblk(ccap), kT, 0, s, n, nsp, B, t->child, t->ncbeg, t->nccnt, t->npar,
@@ -1354,9 +1365,9 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     const int G = t->prm.group_max;
     launch_pdl(k_frontier, nblk(n), kT, 0, s, n, B, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit);
     launch_pdl(k_runmark, nblk(n), kT, 0, s, n, fp, rs);
-    scan_inclusive_max_u32(rs, rs, n, scan_scratch, s);
+    scan_inclusive_max_u32_look(rs, rs, n, scan_look, scan_ctr + 2, 3, status, scan_scratch, s);
     launch_pdl(k_groupmark, nblk(n), kT, 0, s, n, G, rs, fp, unit, t->nbeg, t->nend, gs);
-    scan_exclusive_u32(gs, gid, n, d_tot + 2, scan_scratch, s);
+    scan_exclusive_u32_look(gs, gid, n, d_tot + 2, scan_look, scan_ctr + 3, 4, status, scan_scratch, s);
     launch_pdl(k_group_init, nblk(n), kT, 0, s, n, gs, gid, t->gbeg);
     // group count (d_tot[2]) and child count (d_tot[1]) from the device
     launch_pdl(k_group_fin, stride_grid(n), kT, 0, s, n, d_tot + 2, 0, t->gbeg, t->gend, t->px, t->py, t->pz,

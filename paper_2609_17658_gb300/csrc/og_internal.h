@@ -247,6 +247,19 @@ void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *
                         void *scratch, cudaStream_t s);
 void scan_inclusive_max_u32(const uint32_t *in, uint32_t *out, int64_t n, void *scratch,
                             cudaStream_t s);
+// The same scans as one kernel with a decoupled look-back (up to 64 tiles of
+// 4096 elements; longer scans take the two-kernel form, with scratch of
+// scan_scratch_bytes(n)).  look holds scan_look_words(n) words, cleared before
+// their first use; tag (1 .. 2^30 - 1) must differ between uses of the same
+// words; ctr is a word that is 0 before the call.  A look-back that waits too
+// long sets ST_INTERNAL in *status.
+size_t scan_look_words(int64_t n);
+void scan_exclusive_u32_look(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total,
+                             unsigned long long *look, uint32_t *ctr, uint32_t tag, uint32_t *status,
+                             void *scratch, cudaStream_t s);
+void scan_inclusive_max_u32_look(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *look,
+                                 uint32_t *ctr, uint32_t tag, uint32_t *status, void *scratch,
+                                 cudaStream_t s);
 
 // radix sort of (key, value) pairs, stable, keys of `bits` significant bits
 size_t radix_sort_scratch_bytes(int64_t n);

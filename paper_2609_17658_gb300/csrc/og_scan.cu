@@ -118,6 +118,119 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_downsweep(const uint32_t 
     }
 }
 
+// The same scan in one kernel: tiles numbered in the order their blocks
+// start publish their totals, and warp 0 of each tile gathers the totals of
+// the tiles before it, 32 at a time, until it meets an inclusive one
+// (decoupled look-back).  A look word: flag (2 bits: 1 own total, 2
+// inclusive), the use's tag (bits 32..61), the value (low 32 bits); a word
+// of another tag reads as not yet published, so one clearing serves
+// successive uses with distinct tags.  Every wait is bounded.
+constexpr unsigned long long kScanOwn = 1ull << 62, kScanInc = 2ull << 62;
+constexpr int kScanSpinLimit = 1 << 22;
+// above this many tiles the look-back's waits cost more than the second
+// launch they save: the two-kernel scan runs instead
+constexpr int64_t kScanLookMaxTiles = 64;
+
+__device__ __forceinline__ void st_word(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <class Op>
+__device__ __forceinline__ uint32_t warp_fold(uint32_t v);
+template <>
+__device__ __forceinline__ uint32_t warp_fold<OpSum>(uint32_t v) { return __reduce_add_sync(0xffffffffu, v); }
+template <>
+__device__ __forceinline__ uint32_t warp_fold<OpMax>(uint32_t v) { return __reduce_max_sync(0xffffffffu, v); }
+
+template <class Op, bool kExclusive>
+__global__ void __launch_bounds__(kScanThreads) k_scan_look(const uint32_t *in, uint32_t *out, int64_t n,
+                                                            unsigned long long *look, uint32_t *ctr,
+                                                            unsigned long long tag, uint32_t *d_total,
+                                                            uint32_t *status) {
+    pdl_wait();
+    __shared__ uint32_t s_items[kScanTile];
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_tile, s_pre;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        s_items[k * kScanThreads + threadIdx.x] = i < n ? in[i] : Op::id();
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t acc = Op::id();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = s_items[threadIdx.x * kScanItems + k];
+        acc = Op::op(acc, v[k]);
+    }
+    uint32_t tot;
+    uint32_t r = block_exclusive<Op>(acc, s_warp, &tot);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned long long tg = tag << 32;
+        const unsigned long long tmask = 0x3fffffffull << 32;
+        uint32_t pre = Op::id();
+        if (tile == 0) {
+            if (lane == 0) st_word(&look[0], kScanInc | tg | tot);
+        } else {
+            if (lane == 0) st_word(&look[tile], kScanOwn | tg | tot);
+            int64_t j = tile - 1;
+            int spins = 0;
+            while (true) {
+                const int64_t q = j - lane;
+                // before the first tile: an inclusive identity
+                const unsigned long long w = q >= 0 ? ld_word(&look[q]) : (kScanInc | tg | Op::id());
+                const bool ready = (w & tmask) == tg && (w >> 62) != 0ull;
+                const unsigned notready = __ballot_sync(0xffffffffu, !ready);
+                const unsigned inc = __ballot_sync(0xffffffffu, ready && (w >> 62) == 2ull);
+                const int L = inc ? __ffs(inc) - 1 : 32;        // nearest inclusive word
+                const unsigned need = L == 32 ? 0xffffffffu : ((2u << L) - 1u);
+                if (notready & need) {
+                    if (++spins > kScanSpinLimit) {  // a tile that never publishes: give up
+                        if (lane == 0) atomicOr(status, ST_INTERNAL);
+                        break;
+                    }
+                    if (spins > 32) __nanosleep(32);
+                    continue;
+                }
+                pre = Op::op(pre, warp_fold<Op>(lane <= L ? (uint32_t)w : Op::id()));
+                if (L < 32) break;
+                j -= 32;
+            }
+            if (lane == 0) st_word(&look[tile], kScanInc | tg | Op::op(pre, tot));
+        }
+        if (lane == 0) s_pre = pre;
+    }
+    __syncthreads();
+    const uint32_t tile_pre = s_pre;
+    r = Op::op(tile_pre, r);
+    if (d_total && threadIdx.x == 0 && base + kScanTile >= n) *d_total = Op::op(tile_pre, tot);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (kExclusive) {
+            s_items[threadIdx.x * kScanItems + k] = r;
+            r = Op::op(r, v[k]);
+        } else {
+            r = Op::op(r, v[k]);
+            s_items[threadIdx.x * kScanItems + k] = r;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = s_items[k * kScanThreads + threadIdx.x];
+    }
+}
+
 template <class Op, bool kExclusive>
 void scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, void *scratch,
                cudaStream_t s) {
@@ -135,6 +248,37 @@ void scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, 
 }
 
 }  // namespace
+
+size_t scan_look_words(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile); }
+
+void scan_exclusive_u32_look(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total,
+                             unsigned long long *look, uint32_t *ctr, uint32_t tag, uint32_t *status,
+                             void *scratch, cudaStream_t s) {
+    if (n <= 0) {
+        if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s);
+        return;
+    }
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles > kScanLookMaxTiles) {
+        scan_impl<OpSum, true>(in, out, n, d_total, scratch, s);
+        return;
+    }
+    launch_pdl(k_scan_look<OpSum, true>, (unsigned)ntiles, kScanThreads, 0, s, in, out, n, look, ctr,
+               (unsigned long long)tag, d_total, status);
+}
+
+void scan_inclusive_max_u32_look(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *look,
+                                 uint32_t *ctr, uint32_t tag, uint32_t *status, void *scratch,
+                                 cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles > kScanLookMaxTiles) {
+        scan_impl<OpMax, false>(in, out, n, nullptr, scratch, s);
+        return;
+    }
+    launch_pdl(k_scan_look<OpMax, false>, (unsigned)ntiles, kScanThreads, 0, s, in, out, n, look, ctr,
+               (unsigned long long)tag, (uint32_t *)nullptr, status);
+}
 
 size_t scan_scratch_bytes(int64_t n) {
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;

@@ -369,6 +369,10 @@ size_t radix_sort_scratch_bytes(int64_t n) {
     // one-kernel passes: histograms, tile counters, one look word per tile and digit
     size_t one = 8 * kRadix * sizeof(uint32_t) + 256 + (size_t)kRadix * ntiles * sizeof(unsigned long long) +
                  1024;
+    // large sorts: histograms, counters, the count scans' look words, counts, scan scratch
+    size_t large = 8 * kRadix * sizeof(uint32_t) + 256 + scan_look_words((int64_t)kRadix * ntiles) * 8 + 256 +
+                   counts + scan_scratch_bytes((int64_t)kRadix * ntiles) + 1024;
+    if (large > one) one = large;
     return every > one ? every : one;
 }
 
@@ -382,8 +386,12 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     uint32_t *hist8 = reinterpret_cast<uint32_t *>(p);
     uint32_t *tile_ctr = hist8 + 8 * kRadix;
     unsigned long long *look = reinterpret_cast<unsigned long long *>(p + 8 * kRadix * sizeof(uint32_t) + 256);
+    // large sorts: the look words of the tile counts' one-kernel scans (one
+    // tag per pass), then the counts
+    const size_t scan_words = scan_look_words((int64_t)kRadix * ntiles);
     const size_t clear = 8 * kRadix * sizeof(uint32_t) + 256 +
-                         (ntiles > kOneSweepMaxTiles ? 0 : (size_t)kRadix * ntiles * sizeof(unsigned long long));
+                         (ntiles > kOneSweepMaxTiles ? scan_words : (size_t)kRadix * ntiles) *
+                             sizeof(unsigned long long);
 
     // the digit histograms of all passes (they give every pass its digit
     // bases and show which passes are trivial); counters and look words cleared
@@ -406,13 +414,15 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     if (ntiles > kOneSweepMaxTiles) {
         // many tiles: the look-back's waits cost more than the count and scan
         // launches they save
-        uint32_t *counts = reinterpret_cast<uint32_t *>(look);
-        void *scan_scratch = counts + (size_t)kRadix * ntiles;
+        uint32_t *counts = reinterpret_cast<uint32_t *>(
+            (reinterpret_cast<uintptr_t>(look + scan_words) + 255) & ~(uintptr_t)255);
+        void *scan_scratch = counts + (size_t)kRadix * ntiles;   // the two-kernel form's tile totals
         for (int pass = 0; pass < npasses; ++pass) {
             const int shift = 8 * pass;
             launch_pdl(k_upsweep, (unsigned)ntiles, kThreads, 0, s, (const uint64_t *)kin, n, shift, counts,
                        ntiles, (const uint32_t *)hist8);
-            scan_exclusive_u32(counts, counts, (int64_t)kRadix * ntiles, nullptr, scan_scratch, s);
+            scan_exclusive_u32_look(counts, counts, (int64_t)kRadix * ntiles, nullptr, look, tile_ctr + 8 + pass,
+                                    (uint32_t)(pass + 1), status, scan_scratch, s);
             launch_pdl(k_downsweep, (unsigned)ntiles, kThreads, sizeof(DownSmem), s, (const uint64_t *)kin,
                        (const uint32_t *)vin, kout, vout, n, shift, (const uint32_t *)counts, ntiles,
                        (const uint32_t *)hist8);
