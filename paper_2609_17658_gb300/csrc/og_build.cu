@@ -788,29 +788,44 @@ __global__ void __launch_bounds__(kRunThreads) k_extents_run(
 // frontier node of p: the deepest node with more than G particles containing
 // p (or its box's root); unit: the child of the frontier node that contains p
 // (its first particle), or p itself when p hangs directly from it
-__global__ void k_frontier(int64_t n, int64_t B, int G, const uint32_t *__restrict__ owner,
-                           const int32_t *__restrict__ npar, const uint32_t *__restrict__ nbeg,
-                           const uint32_t *__restrict__ nend, uint32_t *fp, uint32_t *unit) {
-    pdl_wait();
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+// the frontier node of particle p (its nearest ancestor above G particles, or
+// its box's root) and its unit (the start of the largest ancestor of at most G
+// particles below it, or p itself)
+__device__ __forceinline__ uint32_t frontier_of(int64_t p, int64_t B, int G, const uint32_t *__restrict__ owner,
+                                                const int32_t *__restrict__ npar,
+                                                const uint32_t *__restrict__ nbeg,
+                                                const uint32_t *__restrict__ nend, int64_t &prev) {
     uint32_t node = owner[p];
-    int64_t prev = -1;
+    prev = -1;
     for (int guard = 0; node >= (uint64_t)B && nend[node] - nbeg[node] <= (uint32_t)G &&
                         guard <= kLevels + 2;
          ++guard) {
         prev = node;
         node = (uint32_t)npar[node];
     }
-    fp[p] = node;
-    unit[p] = prev < 0 ? (uint32_t)p : nbeg[prev];
+    return node;
 }
 
-__global__ void k_runmark(int64_t n, const uint32_t *__restrict__ fp, uint32_t *rs) {
+// frontier node and unit of every particle, and the run marks: p where the
+// frontier node changes (else 0), for the maximum scan that gives each
+// particle the start of its run
+__global__ void k_frontier(int64_t n, int64_t B, int G, const uint32_t *__restrict__ owner,
+                           const int32_t *__restrict__ npar, const uint32_t *__restrict__ nbeg,
+                           const uint32_t *__restrict__ nend, uint32_t *fp, uint32_t *unit, uint32_t *rs) {
     pdl_wait();
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t pc = p < n ? p : n - 1;          // every lane takes part in the shuffle
+    int64_t prev;
+    const uint32_t f = frontier_of(pc, B, G, owner, npar, nbeg, nend, prev);
+    uint32_t fl = __shfl_up_sync(0xffffffffu, f, 1);
+    if ((threadIdx.x & 31) == 0 && pc > 0) {
+        int64_t unused;
+        fl = frontier_of(pc - 1, B, G, owner, npar, nbeg, nend, unused);
+    }
     if (p >= n) return;
-    rs[p] = (p == 0 || fp[p] != fp[p - 1]) ? (uint32_t)p : 0u;
+    fp[p] = f;
+    unit[p] = prev < 0 ? (uint32_t)p : nbeg[prev];
+    rs[p] = (p == 0 || f != fl) ? (uint32_t)p : 0u;
 }
 
 // group starts: inside a frontier node of at most 8G particles, runs of
@@ -827,14 +842,6 @@ __global__ void k_groupmark(int64_t n, int G, const uint32_t *__restrict__ runst
     const bool merge = (uint64_t)(nend[f] - nbeg[f]) <= 8ull * (uint64_t)G;
     if (merge) gs[p] = ((p - runstart[p]) % G == 0) ? 1u : 0u;
     else gs[p] = (unit[p] == (uint32_t)p) ? 1u : 0u;
-}
-
-__global__ void k_group_init(int64_t n, const uint32_t *__restrict__ gs,
-                             const uint32_t *__restrict__ gid, uint32_t *gbeg) {
-    pdl_wait();
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n || !gs[p]) return;
-    gbeg[gid[p]] = (uint32_t)p;
 }
 
 __device__ __forceinline__ void group_box(int64_t n, int64_t ng, int64_t g,
@@ -1243,7 +1250,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
         add(4, 4 * kNT * ((n + kSplitTile - 1) / kSplitTile));  // split tile summaries
         add(8, (int64_t)scan_look_words(n + B) + 2);            // scans' look words, counters
         add(4, n + B);                  // nnc
-        add(4, n); add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs gid unit
+        add(4, n); add(4, n); add(4, n); add(4, n);  // fp rs gs unit
         sb_bytes += radix_sort_scratch_bytes(n) + scan_scratch_bytes(2 * n + B + 8) +
                     moments_scratch_bytes(n) + 4096;
     }
@@ -1274,7 +1281,6 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     // a split's previous split in its node: needed only until k_node_init,
     // long before the groups' first use of fp
     uint32_t *prevle = fp;
-    uint32_t *gid = W.take<uint32_t>(n);
     uint32_t *unit = W.take<uint32_t>(n);
     void *sort_scratch = W.take<char>((int64_t)radix_sort_scratch_bytes(n));
     void *scan_scratch = W.take<char>((int64_t)scan_scratch_bytes(2 * n + B + 8));
@@ -1363,12 +1369,11 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     node_moments(t, nsp, mcap, mom_scratch, s);
     // a6: groups (one group size for the whole forest)
     const int G = t->prm.group_max;
-    launch_pdl(k_frontier, nblk(n), kT, 0, s, n, B, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit);
-    launch_pdl(k_runmark, nblk(n), kT, 0, s, n, fp, rs);
+    launch_pdl(k_frontier, nblk(n), kT, 0, s, n, B, G, t->owner, t->npar, t->nbeg, t->nend, fp, unit, rs);
     scan_inclusive_max_u32_look(rs, rs, n, scan_look, scan_ctr + 2, 3, status, scan_scratch, s);
     launch_pdl(k_groupmark, nblk(n), kT, 0, s, n, G, rs, fp, unit, t->nbeg, t->nend, gs);
-    scan_exclusive_u32_look(gs, gid, n, d_tot + 2, scan_look, scan_ctr + 3, 4, status, scan_scratch, s);
-    launch_pdl(k_group_init, nblk(n), kT, 0, s, n, gs, gid, t->gbeg);
+    // group starts, compacted into gbeg; their count to d_tot[2]
+    scan_compact_u32_look(gs, t->gbeg, n, d_tot + 2, scan_look, scan_ctr + 3, 4, status, scan_scratch, s);
     // group count (d_tot[2]) and child count (d_tot[1]) from the device
     launch_pdl(k_group_fin, stride_grid(n), kT, 0, s, n, d_tot + 2, 0, t->gbeg, t->gend, t->px, t->py, t->pz,
                                               t->sseg, t->gbox, t->gseg);

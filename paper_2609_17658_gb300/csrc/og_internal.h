@@ -257,6 +257,11 @@ size_t scan_look_words(int64_t n);
 void scan_exclusive_u32_look(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total,
                              unsigned long long *look, uint32_t *ctr, uint32_t tag, uint32_t *status,
                              void *scratch, cudaStream_t s);
+// compaction: idx[k] = the k-th index i with flags[i] != 0 (flags 0 or 1), the
+// count to *d_total
+void scan_compact_u32_look(const uint32_t *flags, uint32_t *idx, int64_t n, uint32_t *d_total,
+                           unsigned long long *look, uint32_t *ctr, uint32_t tag, uint32_t *status, void *scratch,
+                           cudaStream_t s);
 void scan_inclusive_max_u32_look(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *look,
                                  uint32_t *ctr, uint32_t tag, uint32_t *status, void *scratch,
                                  cudaStream_t s);

@@ -76,7 +76,7 @@ template <class Op, bool kExclusive>
 __global__ void __launch_bounds__(kScanThreads) k_tile_downsweep(const uint32_t *__restrict__ in,
                                                                   uint32_t *out, int64_t n,
                                                                   const uint32_t *tile_tot,
-                                                                  uint32_t *d_total) {
+                                                                  uint32_t *d_total, uint32_t *compact) {
     pdl_wait();
     __shared__ uint32_t s_items[kScanTile];
     __shared__ uint32_t s_warp[32];
@@ -101,6 +101,15 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_downsweep(const uint32_t 
     uint32_t tot;
     uint32_t r = Op::op(tile_pre, block_exclusive<Op>(acc, s_warp, &tot));
     if (d_total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) *d_total = Op::op(tile_pre, tot);
+    if (compact) {
+        // compaction: flagged item i goes to slot (exclusive prefix of i)
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (v[k]) compact[r] = (uint32_t)(base + (int64_t)threadIdx.x * kScanItems + k);
+            r = Op::op(r, v[k]);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         if (kExclusive) {
@@ -151,7 +160,7 @@ template <class Op, bool kExclusive>
 __global__ void __launch_bounds__(kScanThreads) k_scan_look(const uint32_t *in, uint32_t *out, int64_t n,
                                                             unsigned long long *look, uint32_t *ctr,
                                                             unsigned long long tag, uint32_t *d_total,
-                                                            uint32_t *status) {
+                                                            uint32_t *compact, uint32_t *status) {
     pdl_wait();
     __shared__ uint32_t s_items[kScanTile];
     __shared__ uint32_t s_warp[32];
@@ -214,6 +223,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_look(const uint32_t *in, 
     const uint32_t tile_pre = s_pre;
     r = Op::op(tile_pre, r);
     if (d_total && threadIdx.x == 0 && base + kScanTile >= n) *d_total = Op::op(tile_pre, tot);
+    if (compact) {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (v[k]) compact[r] = (uint32_t)(base + (int64_t)threadIdx.x * kScanItems + k);
+            r = Op::op(r, v[k]);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         if (kExclusive) {
@@ -233,7 +250,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_look(const uint32_t *in, 
 
 template <class Op, bool kExclusive>
 void scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, void *scratch,
-               cudaStream_t s) {
+               cudaStream_t s, uint32_t *compact = nullptr) {
     if (n <= 0) {
         if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s);
         return;
@@ -244,7 +261,7 @@ void scan_impl(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, 
         launch_pdl(k_tile_reduce<Op>, (unsigned)ntiles, kScanThreads, 0, s, in, n, tile);
     }
     launch_pdl(k_tile_downsweep<Op, kExclusive>, (unsigned)ntiles, kScanThreads, 0, s, in, out, n, tile,
-                                                                             d_total);
+                                                                             d_total, compact);
 }
 
 }  // namespace
@@ -264,7 +281,23 @@ void scan_exclusive_u32_look(const uint32_t *in, uint32_t *out, int64_t n, uint3
         return;
     }
     launch_pdl(k_scan_look<OpSum, true>, (unsigned)ntiles, kScanThreads, 0, s, in, out, n, look, ctr,
-               (unsigned long long)tag, d_total, status);
+               (unsigned long long)tag, d_total, (uint32_t *)nullptr, status);
+}
+
+void scan_compact_u32_look(const uint32_t *flags, uint32_t *idx, int64_t n, uint32_t *d_total,
+                           unsigned long long *look, uint32_t *ctr, uint32_t tag, uint32_t *status, void *scratch,
+                           cudaStream_t s) {
+    if (n <= 0) {
+        if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s);
+        return;
+    }
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles > kScanLookMaxTiles) {
+        scan_impl<OpSum, true>(flags, nullptr, n, d_total, scratch, s, idx);
+        return;
+    }
+    launch_pdl(k_scan_look<OpSum, true>, (unsigned)ntiles, kScanThreads, 0, s, flags, (uint32_t *)nullptr, n, look,
+               ctr, (unsigned long long)tag, d_total, idx, status);
 }
 
 void scan_inclusive_max_u32_look(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *look,
@@ -277,7 +310,7 @@ void scan_inclusive_max_u32_look(const uint32_t *in, uint32_t *out, int64_t n, u
         return;
     }
     launch_pdl(k_scan_look<OpMax, false>, (unsigned)ntiles, kScanThreads, 0, s, in, out, n, look, ctr,
-               (unsigned long long)tag, (uint32_t *)nullptr, status);
+               (unsigned long long)tag, (uint32_t *)nullptr, (uint32_t *)nullptr, status);
 }
 
 size_t scan_scratch_bytes(int64_t n) {
