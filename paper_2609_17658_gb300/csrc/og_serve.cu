@@ -46,11 +46,11 @@ constexpr int kMaxActive = 256;
 constexpr int kMaxRefits = 64;   // refits between builds at most
 // costs in walk interactions (about 2e-12 s each on the multi-tree walk): a
 // build about 0.18 ms of launch-bound work plus 0.3 ns per particle, a refit
-// about 0.26 ms plus 0.16 ns per particle; a refitted tree's walk costs 13 %
+// about 0.17 ms plus 0.18 ns per particle; a refitted tree's walk costs 13 %
 // more per interaction (it reads node extents); measured on GB300 at
 // 2e4, 2e5 and 2e6 particles
 constexpr double kBuildFixedInter = 9.0e7, kBuildPerParticleInter = 150.0;
-constexpr double kRefitFixedInter = 1.3e8, kRefitPerParticleInter = 80.0;
+constexpr double kRefitFixedInter = 8.5e7, kRefitPerParticleInter = 90.0;
 constexpr double kRefitWalkFactor = 1.13;
 constexpr double kTrialGrowth = 4.0;
 // systems are built on this many private streams at once: a small build is

@@ -64,9 +64,10 @@ def test_each_result_same_alone_and_in_the_mix():
         assert r["t_submit"] <= r["t_start"] <= r["t_done"]
         # the refit-or-rebuild decisions depend only on the system itself
         assert (r["rebuilds"], r["refits"]) == (ra["rebuilds"], ra["refits"])
-    # systems of at most 6e4 particles: their lists grow too little over eight
-    # steps to pay for a rebuild after every step, so refits outnumber builds
-    assert sum(r["refits"] for r in res_m) >= sum(r["rebuilds"] for r in res_m)
+    # systems of at most 6e4 particles: a refit (about the price of a build at
+    # this size) pays for a step or two before the drift has grown the lists,
+    # so the priced rule takes some refits
+    assert sum(r["refits"] for r in res_m) >= 1
 
 
 def test_positions_follow_kick_and_drift():
