@@ -316,3 +316,15 @@ def test_mass_span_limit(ctx):
     assert e.value.status == og.OG_ERR_ARG and "128" in str(e.value)
     mass[7] = 1.0
     parity.compare_build(og.Tree(ctx, pos, mass, prm), oracle.Tree(pos, mass, prm))
+
+
+@pytest.mark.parametrize("n", [262144, 786432, 786433])
+def test_build_bit_exact_at_path_limits(ctx, n):
+    """Sizes where the build changes kernels: 262,144 particles put the node
+    and group scans at 64 tiles (one kernel with a look-back) and the child
+    scan (n + 1 entries) at 65 (two kernels); 786,432 keys are the largest
+    sort run as one kernel per pass and 786,433 the smallest with the count,
+    scan and scatter kernels.  The tree is bitwise the oracle's either way."""
+    pos, mass, prm = gi.config("clustered-2m", n=n, seed=77)
+    gt = og.Tree(ctx, pos, mass, prm)
+    parity.compare_build(gt, oracle.Tree(pos, mass, prm))
