@@ -439,16 +439,15 @@ __global__ void __launch_bounds__(kSplitTile) k_split_ranges(const uint8_t *__re
     }
 }
 
-// Roots, the nodes of first splits (level, key range, cell origin), cleared
+// Roots, the nodes of first splits (level, key range), cleared
 // per-node accumulators, and the node id of every split: its box's root at level 0, else the node of the
 // first split reached along prevle (at most 7 steps).
 __global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ seg_off,
                             const uint32_t *__restrict__ first, const uint32_t *__restrict__ nid,
                             const uint8_t *__restrict__ lv, const uint32_t *__restrict__ sb,
                             const uint32_t *__restrict__ se, const uint32_t *__restrict__ prevle,
-                            const uint32_t *__restrict__ sseg, const uint32_t *__restrict__ px,
-                            const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz,
-                            uint8_t *nlev, uint32_t *nbeg, uint32_t *nend, uint32_t *norg, uint32_t *sid,
+                            const uint32_t *__restrict__ sseg,
+                            uint8_t *nlev, uint32_t *nbeg, uint32_t *nend, uint32_t *sid,
                             int64_t mcap, uint32_t *occ, uint32_t *nnc, uint32_t *nccnt, uint32_t *status) {
     pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -461,7 +460,6 @@ __global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ s
         nlev[i] = 0;
         nbeg[i] = seg_off[i];
         nend[i] = seg_off[i + 1];
-        norg[3 * i + 0] = norg[3 * i + 1] = norg[3 * i + 2] = 0u;
     }
     if (i >= n - 1) return;
     const int L = lv[i];
@@ -473,12 +471,6 @@ __global__ void k_node_init(int64_t n, int64_t B, const uint32_t *__restrict__ s
         nlev[id] = (uint8_t)L;
         nbeg[id] = sb[i];
         nend[id] = se[i];
-        // the cell: the top L bits of every coordinate of its particles
-        const uint32_t mask = ~(uint32_t)((1ull << (32 - L)) - 1ull);
-        const uint32_t q = sb[i];
-        norg[3 * id + 0] = px[q] & mask;
-        norg[3 * id + 1] = py[q] & mask;
-        norg[3 * id + 2] = pz[q] & mask;
         return;
     }
     uint32_t j = prevle[i];
@@ -1091,9 +1083,39 @@ static og_status alloc_extents(og_tree *t) {
     return OG_OK;
 }
 
+// The cell origin of every node: the top L bits of the coordinates of its
+// first particle at the build's positions (its box's origin for a root).
+// Only the node extents read them, so they are made when extents are first
+// needed, before a refit moves the particles.
+__global__ void k_cell_origin(int64_t m, int64_t B, const uint8_t *__restrict__ nlev,
+                              const uint32_t *__restrict__ nbeg, const uint32_t *__restrict__ px,
+                              const uint32_t *__restrict__ py, const uint32_t *__restrict__ pz, uint32_t *norg) {
+    pdl_wait();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    if (j < B) {
+        norg[3 * j + 0] = norg[3 * j + 1] = norg[3 * j + 2] = 0u;
+        return;
+    }
+    const int L = nlev[j];
+    const uint32_t mask = L == 0 ? 0u : ~(uint32_t)((1ull << (32 - L)) - 1ull);
+    const uint32_t q = nbeg[j];
+    norg[3 * j + 0] = px[q] & mask;
+    norg[3 * j + 1] = py[q] & mask;
+    norg[3 * j + 2] = pz[q] & mask;
+}
+
+static void ensure_origins(og_tree *t) {
+    if (t->have_norg) return;
+    launch_pdl(k_cell_origin, nblk(t->nnodes), kT, 0, t->ctx->stream, t->nnodes, t->nseg, t->nlev, t->nbeg,
+               t->px, t->py, t->pz, t->norg);
+    t->have_norg = true;
+}
+
 og_status cell_extents(og_tree *t) {
     og_status st = alloc_extents(t);
     if (st) return st;
+    ensure_origins(t);
     cudaStream_t s = t->ctx->stream;
     launch_pdl(k_cell_ext, nblk(t->nnodes), kT, 0, s, t->nnodes, t->nlev, t->norg, t->next_s, t->next_l);
     launch_pdl(k_ext_records, nblk(t->nchild), kT, 0, s, t->n, t->nchild, t->child, t->next_s, t->next_l,
@@ -1116,6 +1138,7 @@ og_status refit_tree(og_tree *t, const double *d_pos) {
         og_status st = alloc_extents(t);
         if (st) return st;
     }
+    ensure_origins(t);   // from the build's positions, before k_repos moves them
     const size_t mom_bytes = moments_scratch_bytes(n);
     size_t sb = (size_t)n * (16 + 8 + 4 + 4) + 4096 + mom_bytes + 4 * (kLevels + 3) * sizeof(uint32_t) + 256;
     void *scratch = nullptr;
@@ -1354,7 +1377,7 @@ og_status build_tree(og_tree *t, const double *d_pos, const double *d_mass) {
     // the last node stay 0, so the scan over mcap entries gives the nodes'
     // child offsets and, as its total, the child entries.
     launch_pdl(k_node_init, nblk(mcap), kT, 0, s, n, B, t->seg_off, first, nid, lv, sbeg, send, prevle,
-               t->sseg, t->px, t->py, t->pz, t->nlev, t->nbeg, t->nend, t->norg, sid, mcap, occ, nnc, t->nccnt,
+               t->sseg, t->nlev, t->nbeg, t->nend, sid, mcap, occ, nnc, t->nccnt,
                status);
     launch_pdl(k_link, nblk(n + mcap), kT, 0, s, n, nsp, B, t->skey, lv, sid, t->sseg, t->nlev, t->nbeg,
                                          t->nend, t->npar, t->owner, occ, nnc, status);

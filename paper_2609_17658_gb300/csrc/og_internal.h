@@ -117,7 +117,9 @@ struct og_tree {
     uint32_t *ncom = nullptr;
     int32_t *pnext = nullptr;
     uint32_t *owner = nullptr;        // node a particle hangs from
-    uint32_t *norg = nullptr;         // cell origin of each node (3 per node, fixed by the build)
+    uint32_t *norg = nullptr;         // cell origin of each node (3 per node, fixed by the build;
+                                      // made when extents are first needed)
+    bool have_norg = false;
     uint32_t *nocc = nullptr;         // octant occupancy of each node
     uint32_t *lnodes = nullptr;       // node ids by level (for the bottom-up passes)
     std::vector<uint32_t> h_lcount;   // nodes per level
