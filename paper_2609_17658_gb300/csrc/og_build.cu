@@ -274,8 +274,19 @@ __global__ void __launch_bounds__(kSplitTile) k_split_tiles(const uint64_t *__re
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kSplitTile + threadIdx.x;
     int v = kNT;  // past the last split: below no threshold
+    // key i and box i of every lane (i <= nsplit = n - 1 is a particle); the
+    // next particle's from the lane above, the warp's last lane loads its own
+    const int64_t ic = i <= nsplit ? i : nsplit;
+    const uint64_t k0 = skey[ic];
+    const uint32_t s0 = sseg[ic];
+    uint64_t k1 = __shfl_down_sync(0xffffffffu, k0, 1);
+    uint32_t s1 = __shfl_down_sync(0xffffffffu, s0, 1);
+    if (lane == 31 && i < nsplit) {
+        k1 = skey[i + 1];
+        s1 = sseg[i + 1];
+    }
     if (i < nsplit) {
-        const uint8_t l = (sseg[i] != sseg[i + 1]) ? kSep : (uint8_t)lcp_levels(skey[i], skey[i + 1]);
+        const uint8_t l = (s0 != s1) ? kSep : (uint8_t)lcp_levels(k0, k1);
         lv[i] = l;
         v = split_rank(l);
     }
@@ -367,6 +378,13 @@ __global__ void __launch_bounds__(kSplitTile) k_split_ranges(const uint8_t *__re
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kSplitTile + threadIdx.x;
     const int v = i < nsplit ? split_rank(lv[i]) : kNT;
+    // warp t's carries for threshold t, loaded first so that their latency
+    // passes while the warp works on its ballots
+    int cl = -1, cf = kNone;
+    if (warp < kNT) {
+        cl = clast[blockIdx.x * kNT + warp];
+        cf = cfirst[blockIdx.x * kNT + warp];
+    }
     const int64_t base = (int64_t)blockIdx.x * kSplitTile + warp * 32;
     const WarpLevels W = warp_levels(v);
     {
@@ -388,7 +406,6 @@ __global__ void __launch_bounds__(kSplitTile) k_split_ranges(const uint8_t *__re
             if (lane >= d) l = max(l, o);
         }
         int lex = __shfl_up_sync(0xffffffffu, l, 1);
-        const int cl = clast[blockIdx.x * kNT + t];
         pl[lane][t] = lane == 0 ? cl : max(cl, lex);
         int f = wf[lane][t];
 #pragma unroll
@@ -397,7 +414,6 @@ __global__ void __launch_bounds__(kSplitTile) k_split_ranges(const uint8_t *__re
             if (lane + d < 32) f = min(f, o);
         }
         int fex = __shfl_down_sync(0xffffffffu, f, 1);
-        const int cf = cfirst[blockIdx.x * kNT + t];
         pf[lane][t] = lane == 31 ? cf : min(cf, fex);
     }
     __syncthreads();
