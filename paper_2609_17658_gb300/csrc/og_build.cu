@@ -28,8 +28,11 @@
 //                           refit's extents only, made on the first refit)
 //          k_extents_level  a refit's node extents, one launch per large level
 //          k_extents_run    a run of small levels in one block (a barrier per level)
-//   a6     k_frontier .. k_group_fin   walk groups and their integer boxes
+//   a6     k_frontier       frontier node, unit and run start mark of every particle
+//          k_groupmark      group starts (then compacted into gbeg by a scan)
+//          k_group_fin      group ends, boxes and box index
 //          k_records        32-byte child records read by the walk
+//          k_cell_origin    node cell origins, made when extents are first needed
 //
 // Every decision is integer or exact, so the result is identical to the
 // oracle's recursive construction.

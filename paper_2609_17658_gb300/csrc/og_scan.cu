@@ -1,9 +1,11 @@
 // og_scan.cu -- device-wide prefix scans (tile reduce, then a downsweep in which
-// every tile adds up the totals of the tiles before it).
+// every tile adds up the totals of the tiles before it; short scans in one
+// kernel with a decoupled look-back).
 //
 // Tiles of 4096 elements: 512 threads x 8 consecutive items, staged through
-// shared memory so that global loads and stores stay coalesced.  Used for
-// compaction offsets (node ids, child offsets, group ids, run starts).
+// shared memory so that global loads and stores stay coalesced.  Used for the
+// node ids of the first splits, the child offsets, the run starts (a maximum
+// scan), the group starts (a compaction) and the sort's tile counts.
 #include "og_internal.h"
 
 namespace og {
