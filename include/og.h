@@ -50,9 +50,9 @@ typedef enum {
     OG_ERR_ARG = -1,         /* invalid argument (NaN position, N out of range, ...) */
     OG_ERR_OOM = -2,         /* device or host allocation failed */
     OG_ERR_CUDA = -3,        /* a CUDA runtime call failed */
-    OG_ERR_TIMEOUT = -4,     /* reserved for a bounded device-side wait that ran out; no
-                                kernel of this library waits on another block, so no
-                                call returns it */
+    OG_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out: a tile of a one-kernel
+                                sort pass or scan waited too long for the count of an
+                                earlier tile (the context stays usable) */
     OG_ERR_BUDGET = -5,      /* the request does not fit the HBM budget */
     OG_ERR_OVERFLOW = -6,    /* a fixed-capacity device buffer overflowed */
     OG_ERR_STATE = -7,       /* call not valid in the handle's state */
@@ -520,6 +520,17 @@ og_status og_device_code_version(int32_t *version);
  * OG_ERR_ARG if skip or count < 0.  Nothing reaches the GPU: the failure is
  * made on the host, before the allocation is asked for. */
 og_status og_debug_fail_allocations(int32_t skip, int32_t count);
+
+/* Test of the bounded device-side waits (the paper has no counterpart).  The
+ * build's short scans and small sorts run as one kernel in which a tile waits
+ * for the counts that earlier tiles publish, up to a poll limit.  This runs
+ * that scan over n zeros (2 to 64 tiles of 4096 elements, 4097 <= n <=
+ * 262144) with the first tile never taken, so the second tile's wait runs
+ * out; the kernel then gives up, finishes, and the call returns
+ * OG_ERR_TIMEOUT, after which the context is usable as before.  It allocates
+ * and frees its own scratch.  OG_ERR_ARG for a NULL context or n out of
+ * range. */
+og_status og_debug_scan_wait_timeout(og_ctx *c, int64_t n);
 
 #ifdef __cplusplus
 }

@@ -204,6 +204,11 @@ og_status status_from(og_ctx *c, uint32_t st) {
         set_error("debug list buffer overflow");
         return OG_ERR_OVERFLOW;
     }
+    if (st & ST_TIMEOUT) {
+        set_error("a device-side wait on another block ran out (the look-back of a one-kernel sort "
+                  "pass or scan)");
+        return OG_ERR_TIMEOUT;
+    }
     set_error("internal consistency check failed (status 0x%x)", st);
     return OG_ERR_STATE;
 }
@@ -241,6 +246,18 @@ extern "C" {
 const char *og_last_error(void) { return g_err; }
 
 int64_t og_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+og_status og_debug_scan_wait_timeout(og_ctx *c, int64_t n) {
+    if (!c) { set_error("og_debug_scan_wait_timeout: NULL context"); return OG_ERR_ARG; }
+    og_status st = scan_wait_timeout_probe(c, n);
+    if (st != OG_OK) return st;
+    // the status word: the probe's wait must have run out
+    uint32_t *h = pinned_status(c);
+    cudaMemcpyAsync(h, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "og_debug_scan_wait_timeout");
+    return status_from(c, *h);
+}
 
 og_status og_debug_fail_allocations(int32_t skip, int32_t count) {
     if (skip < 0 || count < 0) {

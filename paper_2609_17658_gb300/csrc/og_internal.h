@@ -30,6 +30,7 @@ enum : uint32_t {
     ST_LIST_OVF = 1u << 2,    // debug list buffer overflow
     ST_INTERNAL = 1u << 3,    // an internal consistency check failed
     ST_MASS_RANGE = 1u << 4,  // masses span too many binary orders for exact moments
+    ST_TIMEOUT = 1u << 5,     // a bounded wait on another block of the grid ran out
 };
 
 // 32-byte record of one child slot, read by the walk (particle or node)
@@ -256,6 +257,9 @@ void scan_inclusive_max_u32(const uint32_t *in, uint32_t *out, int64_t n, void *
 // words; ctr is a word that is 0 before the call.  A look-back that waits too
 // long sets ST_INTERNAL in *status.
 size_t scan_look_words(int64_t n);
+// test hook: a one-kernel scan whose first tile never publishes (see
+// og_debug_scan_wait_timeout); returns the status word's bits
+og_status scan_wait_timeout_probe(og_ctx *c, int64_t n);
 void scan_exclusive_u32_look(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total,
                              unsigned long long *look, uint32_t *ctr, uint32_t tag, uint32_t *status,
                              void *scratch, cudaStream_t s);

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_downsweep(const uint32_t 
 // of another tag reads as not yet published, so one clearing serves
 // successive uses with distinct tags.  Every wait is bounded.
 constexpr unsigned long long kScanOwn = 1ull << 62, kScanInc = 2ull << 62;
-constexpr int kScanSpinLimit = 1 << 22;
+constexpr int kScanSpinLimit = 1 << 20;
 // above this many tiles the look-back's waits cost more than the second
 // launch they save: the two-kernel scan runs instead
 constexpr int64_t kScanLookMaxTiles = 64;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_look(const uint32_t *in, 
                 const unsigned need = L == 32 ? 0xffffffffu : ((2u << L) - 1u);
                 if (notready & need) {
                     if (++spins > kScanSpinLimit) {  // a tile that never publishes: give up
-                        if (lane == 0) atomicOr(status, ST_INTERNAL);
+                        if (lane == 0) atomicOr(status, ST_TIMEOUT);
                         break;
                     }
                     if (spins > 32) __nanosleep(32);
@@ -313,6 +313,36 @@ void scan_inclusive_max_u32_look(const uint32_t *in, uint32_t *out, int64_t n, u
     }
     launch_pdl(k_scan_look<OpMax, false>, (unsigned)ntiles, kScanThreads, 0, s, in, out, n, look, ctr,
                (unsigned long long)tag, (uint32_t *)nullptr, (uint32_t *)nullptr, status);
+}
+
+og_status scan_wait_timeout_probe(og_ctx *c, int64_t n) {
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles < 2 || ntiles > kScanLookMaxTiles) {
+        set_error("og_debug_scan_wait_timeout: n must span 2 to %lld tiles of %d", (long long)kScanLookMaxTiles,
+                  kScanTile);
+        return OG_ERR_ARG;
+    }
+    cudaStream_t s = c->stream;
+    const size_t bytes = (size_t)n * 2 * sizeof(uint32_t) + (size_t)ntiles * 8 + 512;
+    void *buf = nullptr;
+    cudaError_t e = dev_malloc_async(&buf, bytes, s);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? OG_ERR_OOM : cuda_fail(e, "cudaMallocAsync (probe)");
+    unsigned long long *look = static_cast<unsigned long long *>(buf);   // ntiles words, all 0
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(look + ntiles);
+    uint32_t *in = ctr + 32;
+    uint32_t *out = in + n;
+    cudaMemsetAsync(buf, 0, bytes, s);
+    // the tile counter starts at 1 and the grid has one block fewer than
+    // tiles: tile 0 is never taken, so its look word never carries tag 1 and
+    // tile 1 waits until its poll limit runs out
+    const uint32_t one = 1u;
+    cudaMemcpyAsync(ctr, &one, sizeof(one), cudaMemcpyHostToDevice, s);
+    launch_pdl(k_scan_look<OpSum, true>, (unsigned)(ntiles - 1), kScanThreads, 0, s, (const uint32_t *)in, out, n,
+               look, ctr, (unsigned long long)1, (uint32_t *)nullptr, (uint32_t *)nullptr, c->d_status);
+    cudaFreeAsync(buf, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "scan probe");
+    return OG_OK;
 }
 
 size_t scan_scratch_bytes(int64_t n) {

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_downsweep(const uint64_t *__res
 // (6 bits, pass + 1, so that words of the previous pass read as not ready),
 // count (low 32 bits).
 constexpr unsigned long long kLookOwn = 1ull << 62, kLookInc = 2ull << 62;
-constexpr int kLookSpinLimit = 1 << 22;
+constexpr int kLookSpinLimit = 1 << 20;
 
 __device__ __forceinline__ void st_look(unsigned long long *p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint64_t *__rest
             const unsigned long long w = ld_look(&look[j * kRadix + t]);
             if ((w & tag_mask) != tag || (w >> 62) == 0ull) {
                 if (++spins > kLookSpinLimit) {  // a tile that never publishes: give up
-                    atomicOr(status, ST_INTERNAL);
+                    atomicOr(status, ST_TIMEOUT);
                     break;
                 }
                 if (spins > 32) __nanosleep(64);

@@ -119,6 +119,8 @@ def lib():
         L.og_device_code_version.restype = C.c_int
         L.og_debug_fail_allocations.argtypes = [C.c_int32, C.c_int32]
         L.og_debug_fail_allocations.restype = C.c_int
+        L.og_debug_scan_wait_timeout.argtypes = [P, i64]
+        L.og_debug_scan_wait_timeout.restype = C.c_int
         L.og_serve_cancel.argtypes = [P, C.c_uint64]
         L.og_serve_cancel.restype = C.c_int
         L.og_sort_keys_noalloc.argtypes = [P, P, P, i64, P]
@@ -177,6 +179,13 @@ def og_debug_fail_allocations(count: int, skip: int = 0) -> None:
     the ``count`` after them fail (tests of error handling; see
     include/og.h).  count = 0 clears it."""
     _check(lib().og_debug_fail_allocations(int(skip), int(count)))
+
+
+def og_debug_scan_wait_timeout(ctx, n: int) -> None:
+    """Run the one-kernel scan with its first tile never taken, so that a
+    bounded wait runs out (tests of error handling; see include/og.h); raises
+    OGError with OG_ERR_TIMEOUT."""
+    _check(lib().og_debug_scan_wait_timeout(ctx, int(n)))
 
 
 def og_serve_cancel(ctx, ticket: int) -> None:

@@ -152,3 +152,23 @@ def test_cancel_queued_and_running_requests():
         with pytest.raises(og.OGError) as e:
             og.og_serve_cancel(ctx.h, 10 ** 9)
         assert e.value.status == og.OG_ERR_ARG
+
+
+def test_bounded_device_wait_runs_out_and_the_context_stays_usable():
+    """A tile of the one-kernel scan waits for the count of an earlier tile up
+    to a poll limit.  With the first tile never taken that wait runs out: the
+    kernel gives up and finishes, the call returns OG_ERR_TIMEOUT (about half a
+    second of polling), and the same context then builds and walks bitwise as
+    before.  Nothing faults or hangs: the wait is bounded by construction."""
+    pos, mass, prm = _system()
+    with og.Context(0) as ctx:
+        ref, rpp, rpn = og.Tree(ctx, pos, mass, prm).force()
+        with pytest.raises(og.OGError) as e:
+            og.og_debug_scan_wait_timeout(ctx.h, 40000)
+        assert e.value.status == og.OG_ERR_TIMEOUT
+        acc, npp, npn = og.Tree(ctx, pos, mass, prm).force()
+        assert np.array_equal(acc, ref) and np.array_equal(npp, rpp) and np.array_equal(npn, rpn)
+        for n in (4096, 64 * 4096 + 1):            # one tile; more tiles than one kernel takes
+            with pytest.raises(og.OGError) as e:
+                og.og_debug_scan_wait_timeout(ctx.h, n)
+            assert e.value.status == og.OG_ERR_ARG
